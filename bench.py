@@ -1,0 +1,315 @@
+"""Benchmark: ms per 2D low-rank Poisson solve (n = 16384, eps = 1e-6).
+
+One step = one full low-rank solve (forward DST of the factors, cross
+approximation in frequency space, rounding, inverse DST) of the 5-point
+Dirichlet Poisson problem on a 16384 x 16384 interior grid, right-hand side
+f = 1/(1+x+y) + 0.5 sin(3 pi x) exp(-2y) in factored form compressed to eps.
+The headline value is the mixed-precision path; the float64 path is timed in
+the same run.  Inputs are resident on the device; L2 is flushed (a 512 MiB
+write) between timed steps, outside the timed events.
+
+--impl reference times the CPU FP64 oracle on the host cores (the reference
+arm of this benchmark).  With torchrun (N > 1) every rank runs independent
+replicas of the solve (the single solve does not shard); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 16384
+EPS = 1e-6
+METRIC = "ms per 2D low-rank Poisson solve (n=16384, eps=1e-6), mixed vs FP64; % roofline"
+WORKLOAD = "lowrank_poisson2d_5pt_n16384_eps1e-6_smooth_rhs"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_GRID)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_worker(n: int, seconds: float, steps: int):
+    """Time the oracle's low-rank solve; prints one JSON line."""
+    import numpy as np
+    from oracle import poisson_lowrank as O
+    from paper_1306_2150_gb300 import inputs
+    U, V = inputs.smooth_sum(n, EPS)
+    times = []
+    t_end = time.perf_counter() + seconds
+    while len(times) < max(1, steps) or time.perf_counter() < t_end:
+        t0 = time.perf_counter()
+        O.lr_poisson2d(U, V, "5pt", EPS)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end and len(times) >= 1:
+            break
+    print(json.dumps({"ms": 1e3 * statistics.median(times), "solves": len(times),
+                      "total_s": sum(times), "rank_in": U.shape[1]}))
+    _ = np
+
+
+def run_cpu_baseline(n: int, seconds: float, steps: int = 1) -> dict:
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    env.pop("RANK", None)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--n", str(n),
+                          "--cpu-seconds", str(seconds), "--steps", str(steps)],
+                         capture_output=True, text=True, env=env, cwd=ROOT)
+    line = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    if out.returncode != 0 or not line:
+        return {"error": (out.stderr or out.stdout)[-300:]}
+    r = json.loads(line[-1])
+    return {"value": round(r["ms"], 3), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": f"{r['solves']} oracle low-rank solves at n={n} (scipy DST-I + numpy cross "
+                      f"+ numpy QR/SVD), single thread, median"}
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        try:
+            rows = [l.split(",") for l in open(self.path).read().splitlines() if l.strip()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def algorithmic_bytes(n: int, r: int, k: int, R: int, w: int) -> dict:
+    """Bytes each phase must move at minimum (inputs read once, outputs written
+    once; no scratch): forward DST reads U, V (float64) and writes Uh, Vh (w);
+    the cross reads Uh, Vh and writes the k-column skeleton C, R; the inverse
+    DST reads the R kept columns of both factors (w) and writes float64."""
+    return {"forward_dst": 2 * n * r * (8 + w), "cross": 2 * n * (r + k) * w,
+            "inverse_dst": 2 * n * R * (w + 8)}
+
+
+def gpu_arm(args, rank: int, world: int) -> dict | None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1306_2150_gb300 import inputs, lr
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    n = args.n
+    U, V = inputs.smooth_sum(n, EPS)
+    r = U.shape[1]
+    Ud = torch.from_numpy(U).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = lr.Handle(stream)
+    out = (lr.colmajor_empty(n, 64), torch.empty(64, dtype=torch.float64, device="cuda"),
+           lr.colmajor_empty(n, 64))
+    results = {}
+    for prec in ("mixed", "fp64"):
+        for _ in range(args.warmup):
+            lr.lr_poisson2d(h, Ud, Vd, eps=EPS, prec=prec, out=out)
+        res = lr.lr_poisson2d(h, Ud, Vd, eps=EPS, prec=prec, out=out, timing=True)
+        phases = lr.lr_get_phase_times(h)
+        info = res.info
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        ph = []
+        clocks = Clocks(torch.cuda.current_device())
+        with clocks:
+            for i in range(args.steps):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+                lr.lr_poisson2d(h, Ud, Vd, eps=EPS, prec=prec, out=out, async_=True,
+                                timing=True)
+                ev[i][1].record(stream)
+                stream.synchronize()
+                ph.append(lr.lr_get_phase_times(h))
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        per = [a.elapsed_time(b) for a, b in ev]
+        info2, _, _ = lr.lr_get_info(h)
+        # end-to-end through the C ABI from pinned host memory, result back
+        Uh = torch.from_numpy(U).pin_memory()
+        Vh = torch.from_numpy(V).pin_memory()
+        Ub = torch.empty_like(Ud)
+        Vb = torch.empty_like(Vd)
+        host_out = torch.empty((2 * n * 64 + 64,), dtype=torch.float64).pin_memory()
+        e2e = []
+        for i in range(max(3, args.steps // 2)):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Ub.copy_(Uh, non_blocking=True)
+            Vb.copy_(Vh, non_blocking=True)
+            rr = lr.lr_poisson2d(h, Ub, Vb, eps=EPS, prec=prec, out=out)
+            R = rr.info.rank
+            host_out[: n * R].view(R, n).copy_(out[0][:, :R].t(), non_blocking=True)
+            host_out[n * R: 2 * n * R].view(R, n).copy_(out[2][:, :R].t(), non_blocking=True)
+            host_out[2 * n * R: 2 * n * R + R].copy_(out[1][:R], non_blocking=True)
+            b.record(stream)
+            stream.synchronize()
+            e2e.append(a.elapsed_time(b))
+        R = info2.rank
+        results[prec] = {
+            "ms": statistics.median(per), "ms_mean": statistics.mean(per), "per_step": per,
+            "phases": {k: statistics.median([p[k] for p in ph]) for k in ph[0]},
+            "rank": R, "aca_steps": info2.aca_steps, "launches": info2.launches,
+            "cluster_size": info2.cluster_size, "clocks": clocks.summary(),
+            "e2e_ms": statistics.median(e2e),
+            "h2d": 2 * n * r * 8, "d2h": (2 * n * R + R) * 8,
+            "r": r, "first_phases": phases, "status": res.status, "info_rank": info.rank,
+        }
+    h.close()
+    return results
+
+
+def main():
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.n, args.cpu_seconds, args.steps)
+        return
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        # The reference arm is the CPU oracle: rank 0 alone runs it.
+        if rank != 0:
+            return
+        cb = run_cpu_baseline(args.n, max(5.0, args.cpu_seconds), steps=args.steps)
+        line = {"impl": "reference", "metric": METRIC, "value": cb.get("value"), "unit": "ms",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": cb.get("value"), "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": args.n, "eps": EPS, "operator": "5pt",
+                           "rhs": "1/(1+x+y)+0.5 sin(3 pi x) exp(-2y), compressed to eps"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb.get("value"), "unit": "ms", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = gpu_arm(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([res["mixed"]["ms"], res["fp64"]["ms"], res["mixed"]["e2e_ms"]],
+                         device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        res["mixed"]["ms"], res["fp64"]["ms"], res["mixed"]["e2e_ms"] = t.tolist()
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    import json as _j
+    peaks = {}
+    try:
+        peaks = _j.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    mx, f64 = res["mixed"], res["fp64"]
+    n = args.n
+    # dominant kernel of the mixed path: the phase with the largest time
+    ph = mx["phases"]
+    dom = max(("forward_dst", "cross", "inverse_dst"), key=lambda k: ph[k])
+    byts = algorithmic_bytes(n, mx["r"], mx["aca_steps"], mx["rank"], 4)[dom]
+    achieved = byts / (ph[dom] * 1e-3) / 1e9
+    value = mx["ms"] / 1.0  # per rank one solve per step; ms per solve
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mx["ms"], 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "eps": EPS, "operator": "5pt",
+                   "rhs_rank": mx["r"], "solution_rank": mx["rank"], "cross_steps": mx["aca_steps"],
+                   "l2": "flushed (512 MiB write) between timed steps",
+                   "replicas_per_gpu": 1, "parallelism": "replicas" if world > 1 else "single"},
+        "fp64": {"value": round(f64["ms"], 4), "unit": "ms", "rank": f64["rank"],
+                 "cross_steps": f64["aca_steps"],
+                 "phases_ms": {k: round(v, 4) for k, v in f64["phases"].items()}},
+        "mixed_over_fp64_speedup": round(f64["ms"] / mx["ms"], 3),
+        "phases_ms": {k: round(v, 4) for k, v in ph.items()},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2),
+                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 5),
+                     "traffic": None, "peak_source": peak_src},
+        "e2e": {"value": round(mx["e2e_ms"], 4), "unit": "ms", "h2d_bytes_per_step": mx["h2d"],
+                "d2h_bytes_per_step": mx["d2h"]},
+        "gpu_launches": mx["launches"] * args.steps,
+        "clocks": mx["clocks"],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = run_cpu_baseline(n, args.cpu_seconds)
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * lrpoisson.h -- C ABI of the GB300 (sm_103a) low-rank Poisson solver.
+ *
+ * The method is the low-rank Poisson solve of Muravleva & Oseledets,
+ * "Fast low-rank solution of the Poisson equation with application to the
+ * Stokes problem" (arXiv:1306.2150):
+ *
+ *   A X = F,  F = U V^T  (Section 3, Eq. flr:lr), A the discrete Laplacian of
+ *   the unit square with homogeneous Dirichlet conditions (Section 2, 4.1);
+ *   Uh = S U, Vh = S V with S the orthonormal DST-I (Section 4.1, Eq. flr:diag);
+ *   Xh[i,j] = (Uh Vh^T)[i,j] / Lambda[i,j] approximated by a cross
+ *   (Section 4.2, Eq. flr:div); rounding by QR + a small SVD (Section 3);
+ *   X = (S Uo) diag(s) (S Vo)^T.
+ *
+ * Conventions for every entry point:
+ *   - All matrix pointers are DEVICE pointers owned by the caller.  Factor
+ *     matrices are column-major float64 with leading dimension ld >= rows;
+ *     pointers must be 16-byte aligned.
+ *   - Work is enqueued on the handle's stream.  Unless LR_FLAG_ASYNC is set,
+ *     a call returns after that stream has finished the work, so the output
+ *     rank and status are known on return.
+ *   - Errors are returned as lr_status; nothing is thrown across the ABI.
+ *     lr_last_error() gives a one-line description of the last failure.
+ *   - The library owns only workspace inside the handle (device memory grown
+ *     on demand with cudaMalloc, pinned host memory for status), released by
+ *     lr_destroy().
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef LRPOISSON_H
+#define LRPOISSON_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LR_OK = 0,
+  LR_EINVAL = 1,     /* invalid argument (sizes, pointers, alignment, options) */
+  LR_ENOMEM = 2,     /* device or pinned allocation failed */
+  LR_ENOCONV = 3,    /* cross hit its step cap or the rank was cut to capacity;
+                        the best partial result is written */
+  LR_ETIMEOUT = 4,   /* a bounded device wait ran out */
+  LR_ECUDA = 5       /* a CUDA runtime call failed */
+} lr_status;
+
+typedef enum {
+  LR_FP64 = 0,       /* every step in float64 */
+  LR_MIXED = 1       /* float32 transforms and row/column sampling; float64
+                        pivot values, Gram accumulation and QR cores */
+} lr_precision;
+
+typedef enum {
+  /* 5-point Laplacian, m interior points per direction, h = 1/(m+1):
+     Lambda[i,j] = mu_i + mu_j, mu_i = (4/h^2) sin^2(i pi h / 2)
+     (Section 4.2, Eq. flr:div). */
+  LR_OP_5PT = 0,
+  /* semi-staggered Laplacian of Section 2, Delta = B_x B_x^T + B_y B_y^T, on
+     n = m+1 cells (h = 1/n): Lambda[i,j] = (l_i (4-l_j) + (4-l_i) l_j)/(16 h^2),
+     l_i = 4 sin^2(i pi h / 2), the symbol of A1 (x) A2 + A2 (x) A1, A1 = G G^T,
+     A2 = H H^T (Section 4.1). */
+  LR_OP_SEMISTAGGERED = 1
+} lr_operator;
+
+/* Bits of lr_options.flags. */
+#define LR_FLAG_ASYNC 1u   /* do not wait for the stream; read rank/status with
+                              lr_get_info() after synchronising the stream */
+#define LR_FLAG_TIMING 2u  /* record CUDA events between the phases of a solve;
+                              read them with lr_get_phase_times() */
+
+/* Phases of lr_poisson2d timed under LR_FLAG_TIMING. */
+#define LR_PHASE_FORWARD_DST 0  /* DST of the right-hand side factors      */
+#define LR_PHASE_CROSS 1        /* cross approximation (one cluster launch) */
+#define LR_PHASE_ROUNDING 2     /* k x k core and rotation of the skeleton  */
+#define LR_PHASE_INVERSE_DST 3  /* DST of the kept factors                  */
+#define LR_NUM_PHASES 4
+
+typedef struct lr_handle_s* lr_handle;
+
+/* A low-rank matrix X = U diag(s) V^T of size n1 x n2 (Section 3, Def. of the
+ * low-rank format).  U is n1 x rmax, V is n2 x rmax (column-major, leading
+ * dimension ld), s has rmax entries; the first r columns / entries are used.
+ * On input s may be NULL (all ones).  On output U and V have orthonormal
+ * columns and s holds the singular values in descending order. */
+typedef struct {
+  int n1, n2;
+  int r;
+  int rmax;
+  int ld;
+  double* U;
+  double* s;
+  double* V;
+} lr_mat;
+
+typedef struct {
+  lr_precision prec;
+  lr_operator op;
+  double eps;            /* relative Frobenius tolerance of cross and rounding */
+  int rmax;              /* cap on cross steps (<= 64) */
+  double aca_tol_factor; /* cross stop tolerance = aca_tol_factor * eps */
+  int probes;            /* residual probes after the cross stops (0 = none) */
+  unsigned long long seed; /* splitmix64 seed of the probe positions */
+  unsigned int flags;    /* LR_FLAG_* */
+  int cluster_size;      /* CTAs per cross cluster (0 = automatic, 1..16) */
+} lr_options;
+
+/* Result details of the last solve on a handle. */
+typedef struct {
+  int status;            /* lr_status of the last solve */
+  int aca_steps;         /* skeleton columns k built by the cross */
+  int rank;              /* rank R kept by the rounding */
+  int converged;         /* cross stop test passed */
+  int cut;               /* rank cut to the output capacity */
+  int probe_rounds;
+  int zero_rows;         /* rows skipped because their residual was exactly 0 */
+  int cluster_size;      /* CTAs used by the cross */
+  int launches;          /* kernels launched by the solve */
+  double norm_est;       /* cross estimate of ||Xh||_F */
+  double sigma0;         /* largest singular value kept */
+} lr_info;
+
+/* Defaults: LR_MIXED, LR_OP_5PT, eps 1e-6, rmax 64, aca_tol_factor 1,
+ * 16 probes, seed 0, flags 0, cluster_size 0. */
+void lr_options_default(lr_options* opt);
+
+/* Create a handle bound to a CUDA stream (cudaStream_t, NULL = legacy default
+ * stream) on the current device.  Returns LR_ECUDA if no device is usable. */
+lr_status lr_create(lr_handle* h, void* cuda_stream);
+lr_status lr_set_stream(lr_handle h, void* cuda_stream);
+lr_status lr_destroy(lr_handle h);
+const char* lr_last_error(lr_handle h);
+const char* lr_status_string(lr_status s);
+
+/* Orthonormal DST-I of order m applied to ncols columns (Section 4.1,
+ * "DST of the factors", Eq. flr:diag): out[:,c] = S in[:,c],
+ * S[i,k] = sqrt(2/(m+1)) sin(pi i k/(m+1)).  in/out are column-major float64
+ * with leading dimensions ld_in, ld_out >= m; in == out is allowed.
+ * prec selects float64 or float32 arithmetic.  m >= 1, ncols >= 0. */
+lr_status lr_dst1(lr_handle h, int m, int ncols, const double* in, int ld_in,
+                  double* out, int ld_out, lr_precision prec);
+
+/* Low-rank Poisson solve A X = F (Sections 4.1-4.2 with the rounding of
+ * Section 3).  rhs: n1 = n2 = m (1 <= m <= 131072), rank r (1..64), U, V;
+ * rhs->s must be NULL (fold weights into U).
+ * sol: n1 = n2 = m, capacity sol->rmax, U, s, V written; sol->r set on return
+ * (synchronous mode).  The solution satisfies ||X - A^-1 F||_F <= ~2 eps
+ * ||A^-1 F||_F for the default options.  Returns LR_ENOCONV with a partial
+ * result if the cross needed more than opt->rmax steps or the rank exceeded
+ * sol->rmax.  opt NULL means defaults. */
+lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt);
+
+/* Rounding (recompression) of X = U diag(s) V^T in place (Section 3): QR of
+ * both factors, SVD of the r x r core, truncation at relative Frobenius
+ * tolerance eps, at most min(rmax, X->rmax) columns kept.  float64
+ * throughout.  X->s is required: it holds the input weights (set them to 1
+ * for a plain U V^T) and receives the singular values.  X->r (1..64) is
+ * updated; U and V are overwritten with orthonormal columns.  Returns
+ * LR_ENOCONV if more than rmax columns were needed (result cut). */
+lr_status lr_truncate(lr_handle h, lr_mat* X, double eps, int rmax);
+
+/* Details of the last lr_poisson2d on this handle.  pivots_I / pivots_J (host,
+ * may be NULL) receive up to cap cross pivot indices (0-based). */
+lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, int cap);
+
+/* Milliseconds of each phase (LR_PHASE_*) of the last lr_poisson2d run with
+ * LR_FLAG_TIMING, measured with CUDA events on the handle's stream.  Waits for
+ * the last event.  n <= LR_NUM_PHASES entries are written.  LR_EINVAL if the
+ * last solve was not timed. */
+lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRPOISSON_H */

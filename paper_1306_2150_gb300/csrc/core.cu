@@ -1,0 +1,339 @@
+// Rounding of a low-rank matrix (Section 3: "rounding" without a full SVD,
+// O((n+m) r^2 + r^3)): for X = L diag(d) R^T with tall L, R (k columns),
+//   L = Q_L Lc^T, R = Q_R Lr^T     (Lc, Lr lower-triangular Cholesky factors
+//                                   of the Gram matrices L^T L, R^T R)
+//   M = Lc^T diag(d) Lr = W S Z^T   (k x k core, one-sided Jacobi SVD)
+//   keep the largest K singular values with sqrt(sum dropped s^2) <= eps ||s||
+//   X ~= (L Tc) diag(s_K) (R Tr)^T,  Tc = Lc^-T W_K,  Tr = Lr^-T Z_K,
+// so L Tc and R Tr have orthonormal columns.  The Gram matrices of the cross
+// skeleton come for free from the cross (its norm update needs them); for
+// lr_truncate they are formed by a tall-skinny reduction.
+//
+// The k x k work runs in one CTA.  GB300 executes FP64 at a small fraction of
+// its FP32 rate, so the O(k^3 * sweeps) Jacobi iteration may run in FP32
+// (mixed precision) while Cholesky, the core product and the triangular
+// solves stay in FP64.
+#include <cfloat>
+
+#include "lr_internal.h"
+
+namespace lrp {
+
+constexpr int KP = KMAX + 1;  // padded row length of the shared k x k arrays
+
+template <typename JT>
+struct CoreSmem {
+  double Lc[KMAX * KP];
+  double Lr[KMAX * KP];
+  JT Mx[KMAX * KP];   // column q at Mx[q * KP + i]
+  JT Zm[KMAX * KP];
+  double sig[KMAX];
+  double g0c[KMAX], g0r[KMAX];
+  double d[KMAX];
+  int perm[KMAX];
+  int flag;
+  int K;
+};
+
+template <typename JT>
+__device__ __forceinline__ JT warp_sum_t(JT v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, typename JT>
+__global__ void __launch_bounds__(512, 1) core_kernel(CoreArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CoreSmem<JT>& S = *reinterpret_cast<CoreSmem<JT>*>(smem_raw);
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
+  const int k = A.k_dev ? *A.k_dev : A.k_host;
+  if (k <= 0) {
+    if (tid == 0) { A.st->rank = 0; A.st->cut = 0; A.st->sigma0 = 0.0; }
+    return;
+  }
+  // Load Gram matrices (full, symmetric) and weights.
+  for (int idx = tid; idx < k * k; idx += NT) {
+    const int i = idx % k, j = idx / k;
+    S.Lc[i * KP + j] = A.GC[i + (size_t)j * A.ldg];
+    S.Lr[i * KP + j] = A.GR[i + (size_t)j * A.ldg];
+  }
+  for (int i = tid; i < k; i += NT) {
+    S.d[i] = A.d[i];
+    S.g0c[i] = A.GC[i + (size_t)i * A.ldg];
+    S.g0r[i] = A.GR[i + (size_t)i * A.ldg];
+  }
+  __syncthreads();
+  // Cholesky of both Gram matrices (lower, row-major Lx[i*KP+j], i >= j).
+  // A pivot that has lost all but 1e-13 of its original size is lifted to
+  // that floor, so an (almost) dependent column gives a tiny singular value
+  // that the truncation drops, instead of a breakdown.
+  for (int j = 0; j < k; ++j) {
+    if (tid < 2) {
+      double* L = tid == 0 ? S.Lc : S.Lr;
+      const double g0 = tid == 0 ? S.g0c[j] : S.g0r[j];
+      double djj = L[j * KP + j];
+      const double floor_ = 1e-13 * g0 > DBL_MIN ? 1e-13 * g0 : DBL_MIN;
+      if (!(djj > floor_)) djj = floor_;
+      L[j * KP + j] = sqrt(djj);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < 2 * k; i += NT) {
+      if (i < k) S.Lc[i * KP + j] /= S.Lc[j * KP + j];
+      else if (i - k > j) S.Lr[(i - k) * KP + j] /= S.Lr[j * KP + j];
+    }
+    __syncthreads();
+    const int rem = k - j - 1;
+    for (int idx = tid; idx < 2 * rem * rem; idx += NT) {
+      const int side = idx / (rem * rem), w = idx % (rem * rem);
+      const int i = j + 1 + w / rem, jj = j + 1 + w % rem;
+      if (jj > i) continue;
+      double* L = side == 0 ? S.Lc : S.Lr;
+      L[i * KP + jj] -= L[i * KP + j] * L[jj * KP + j];
+    }
+    __syncthreads();
+  }
+  // Zero the strict upper triangles.
+  for (int idx = tid; idx < k * k; idx += NT) {
+    const int i = idx / k, j = idx % k;
+    if (j > i) { S.Lc[i * KP + j] = 0.0; S.Lr[i * KP + j] = 0.0; }
+  }
+  __syncthreads();
+  // Core M = Lc^T diag(d) Lr : M[p][q] = sum_{i >= max(p,q)} Lc[i][p] d_i Lr[i][q].
+  const int ke = k + (k & 1);  // even number of columns for the pairing
+  for (int idx = tid; idx < ke * ke; idx += NT) {
+    const int p = idx % ke, qq = idx / ke;   // row p, column qq
+    double acc = 0.0;
+    if (p < k && qq < k) {
+      const int i0 = p > qq ? p : qq;
+      for (int i = i0; i < k; ++i) acc += S.Lc[i * KP + p] * S.d[i] * S.Lr[i * KP + qq];
+    }
+    S.Mx[qq * KP + p] = (JT)acc;
+    S.Zm[qq * KP + p] = (JT)(p == qq ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  // One-sided (Hestenes) Jacobi with round-robin pair ordering.
+  const JT tol = (sizeof(JT) == 8) ? (JT)(4.0 * DBL_EPSILON) : (JT)(4.0 * FLT_EPSILON);
+  const int npairs = ke / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) S.flag = 0;
+    __syncthreads();
+    for (int round = 0; round < ke - 1; ++round) {
+      for (int pr = warp; pr < npairs; pr += NW) {
+        // positions pr and ke-1-pr of the rotating order: 0 fixed, others shift
+        const int pos0 = pr, pos1 = ke - 1 - pr;
+        const int c0 = pos0 == 0 ? 0 : 1 + (pos0 - 1 + round) % (ke - 1);
+        const int c1 = pos1 == 0 ? 0 : 1 + (pos1 - 1 + round) % (ke - 1);
+        JT* x = S.Mx + c0 * KP;
+        JT* y = S.Mx + c1 * KP;
+        JT al = 0, be = 0, ga = 0;
+        for (int i = lane; i < k; i += 32) {
+          al += x[i] * x[i];
+          be += y[i] * y[i];
+          ga += x[i] * y[i];
+        }
+        al = warp_sum_t(al);
+        be = warp_sum_t(be);
+        ga = warp_sum_t(ga);
+        if (fabs(ga) > tol * sqrt(al) * sqrt(be) && ga != JT(0)) {
+          const JT zeta = (be - al) / (JT(2) * ga);
+          const JT t = (zeta >= JT(0) ? JT(1) : JT(-1)) / (fabs(zeta) + sqrt(JT(1) + zeta * zeta));
+          const JT c = JT(1) / sqrt(JT(1) + t * t);
+          const JT s = c * t;
+          JT* zx = S.Zm + c0 * KP;
+          JT* zy = S.Zm + c1 * KP;
+          for (int i = lane; i < ke; i += 32) {
+            const JT xi = x[i], yi = y[i];
+            x[i] = c * xi - s * yi;
+            y[i] = s * xi + c * yi;
+            const JT zxi = zx[i], zyi = zy[i];
+            zx[i] = c * zxi - s * zyi;
+            zy[i] = s * zxi + c * zyi;
+          }
+          if (lane == 0) S.flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (S.flag == 0) break;
+    __syncthreads();
+  }
+  // Singular values (column norms) and their descending order.
+  for (int qq = warp; qq < k; qq += NW) {
+    double acc = 0.0;
+    for (int i = lane; i < k; i += 32) acc += (double)S.Mx[qq * KP + i] * (double)S.Mx[qq * KP + i];
+    acc = warp_sum_t(acc);
+    if (lane == 0) S.sig[qq] = sqrt(acc);
+  }
+  __syncthreads();
+  for (int qq = tid; qq < k; qq += NT) {
+    int rank = 0;
+    for (int p = 0; p < k; ++p)
+      if (S.sig[p] > S.sig[qq] || (S.sig[p] == S.sig[qq] && p < qq)) ++rank;
+    S.perm[rank] = qq;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double total = 0.0;
+    for (int p = 0; p < k; ++p) total += S.sig[p] * S.sig[p];
+    int K;
+    if (S.sig[S.perm[0]] == 0.0) {
+      K = 0;
+    } else {
+      const double lim = A.eps * sqrt(total);
+      double tail2 = 0.0;
+      K = k;
+      for (int p = k - 1; p >= 1; --p) {
+        const double sp = S.sig[S.perm[p]];
+        const double t2 = tail2 + sp * sp;
+        if (sqrt(t2) > lim) break;
+        tail2 = t2;
+        K = p;
+      }
+    }
+    const int cut = K > A.rmax_out;
+    if (cut) K = A.rmax_out;
+    S.K = K;
+    A.st->rank = K;
+    A.st->cut = cut;
+    A.st->sigma0 = S.sig[S.perm[0]];
+  }
+  __syncthreads();
+  const int K = S.K;
+  for (int p = tid; p < K; p += NT) A.s_out[p] = S.sig[S.perm[p]];
+  // Tc = Lc^-T W_K (W column p = M column perm[p] / sig), Tr = Lr^-T Z_K.
+  for (int job = tid; job < 2 * K; job += NT) {
+    const int side = job / K, p = job % K;
+    const int src = S.perm[p];
+    const double* L = side == 0 ? S.Lc : S.Lr;
+    T* out = side == 0 ? A.Tc : A.Tr;
+    const double inv = side == 0 ? (S.sig[src] > 0.0 ? 1.0 / S.sig[src] : 0.0) : 1.0;
+    const JT* col = side == 0 ? S.Mx + src * KP : S.Zm + src * KP;
+    // back substitution with L^T (upper triangular): x_i = (w_i - sum_{j>i} L[j][i] x_j) / L[i][i]
+    double xs[KMAX];
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = (double)col[i] * inv;
+      for (int j = i + 1; j < k; ++j) acc -= L[j * KP + i] * xs[j];
+      xs[i] = acc / L[i * KP + i];
+    }
+    for (int i = 0; i < k; ++i) out[i + (size_t)p * KMAX] = (T)xs[i];
+  }
+}
+
+template <typename T>
+cudaError_t launch_core(const CoreArgs<T>& a, bool jacobi_fp32, cudaStream_t st) {
+  if (jacobi_fp32) {
+    auto kern = core_kernel<T, float>;
+    const size_t sm = sizeof(CoreSmem<float>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<1, 512, sm, st>>>(a);
+  } else {
+    auto kern = core_kernel<T, double>;
+    const size_t sm = sizeof(CoreSmem<double>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<1, 512, sm, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_core<double>(const CoreArgs<double>&, bool, cudaStream_t);
+template cudaError_t launch_core<float>(const CoreArgs<float>&, bool, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Gram matrix G = X^T X of a tall float64 matrix: per-block partial sums in a
+// fixed order, then a deterministic sum over blocks.
+// ---------------------------------------------------------------------------
+constexpr int kGramRows = 64;
+
+__global__ void __launch_bounds__(256) gram_partial_kernel(const double* __restrict__ X, int rows, int ld,
+                                                           int k, double* __restrict__ partial) {
+  __shared__ double tile[kGramRows * KMAX];
+  const int r0 = blockIdx.x * kGramRows;
+  const int nr = min(kGramRows, rows - r0);
+  for (int idx = threadIdx.x; idx < kGramRows * k; idx += blockDim.x) {
+    const int i = idx % kGramRows, l = idx / kGramRows;
+    tile[l * kGramRows + i] = i < nr ? X[(size_t)l * ld + r0 + i] : 0.0;
+  }
+  __syncthreads();
+  double* out = partial + (size_t)blockIdx.x * KMAX * KMAX;
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int p = idx % k, q = idx / k;
+    if (p > q) continue;
+    double acc = 0.0;
+    for (int i = 0; i < nr; ++i) acc += tile[p * kGramRows + i] * tile[q * kGramRows + i];
+    out[p + q * KMAX] = acc;
+  }
+}
+
+__global__ void gram_sum_kernel(const double* __restrict__ partial, int nblk, int k, double* __restrict__ G,
+                                int ldg) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < k * k; idx += gridDim.x * blockDim.x) {
+    const int p = idx % k, q = idx / k;
+    if (p > q) continue;
+    double acc = 0.0;
+    for (int b = 0; b < nblk; ++b) acc += partial[(size_t)b * KMAX * KMAX + p + q * KMAX];
+    G[p + (size_t)q * ldg] = acc;
+    G[q + (size_t)p * ldg] = acc;
+  }
+}
+
+cudaError_t launch_gram(const double* X, int rows, int ld, int k, double* G, int ldg, double* partial,
+                        int num_sms, cudaStream_t st) {
+  (void)num_sms;
+  const int nblk = (rows + kGramRows - 1) / kGramRows;
+  gram_partial_kernel<<<nblk, 256, 0, st>>>(X, rows, ld, k, partial);
+  gram_sum_kernel<<<(k * k + 255) / 256, 256, 0, st>>>(partial, nblk, k, G, ldg);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rotation out[:, q] = sum_{l<k} in[:, l] Tm[l, q], q < rank (device values).
+// ---------------------------------------------------------------------------
+template <typename TI, typename TO, typename TM>
+__global__ void __launch_bounds__(256) rotate_kernel(const TI* __restrict__ in, int ld_in, int rows,
+                                                     const int* k_dev, int k_host, const TM* __restrict__ Tm,
+                                                     const int* rank_dev, TO* __restrict__ out, int ld_out) {
+  __shared__ TM tm[KMAX * KMAX];
+  const int k = k_dev ? *k_dev : k_host;
+  const int R = *rank_dev;
+  for (int idx = threadIdx.x; idx < k * R; idx += blockDim.x) {
+    const int l = idx % k, qq = idx / k;
+    tm[l + qq * KMAX] = Tm[l + (size_t)qq * KMAX];
+  }
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  for (int q0 = 0; q0 < R; q0 += 8) {
+    TM acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = TM(0);
+    for (int l = 0; l < k; ++l) {
+      const TM x = (TM)in[row + (size_t)l * ld_in];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] += x * tm[l + (q0 + c) * KMAX];
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (q0 + c < R) out[row + (size_t)(q0 + c) * ld_out] = (TO)acc[c];
+  }
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_rotate(const TI* in, int ld_in, int rows, const int* k_dev, int k_host, const void* Tm,
+                          bool tm_f32, const int* rank_dev, TO* out, int ld_out, cudaStream_t st) {
+  const int grid = (rows + 255) / 256;
+  if (tm_f32)
+    rotate_kernel<TI, TO, float><<<grid, 256, 0, st>>>(in, ld_in, rows, k_dev, k_host,
+                                                       static_cast<const float*>(Tm), rank_dev, out, ld_out);
+  else
+    rotate_kernel<TI, TO, double><<<grid, 256, 0, st>>>(in, ld_in, rows, k_dev, k_host,
+                                                        static_cast<const double*>(Tm), rank_dev, out, ld_out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rotate<double, double>(const double*, int, int, const int*, int, const void*, bool,
+                                                   const int*, double*, int, cudaStream_t);
+template cudaError_t launch_rotate<float, float>(const float*, int, int, const int*, int, const void*, bool,
+                                                 const int*, float*, int, cudaStream_t);
+
+}  // namespace lrp

@@ -1,0 +1,525 @@
+// DST-I of factor columns (Section 4.1: "DST of the factors U and V", the
+// transform that diagonalises the Laplacian, Eq. flr:diag), on the GPU.
+//
+// The orthonormal DST-I of order m, y_k = sqrt(2/N) sum_j x_j sin(pi j k / N)
+// (N = m + 1), is evaluated by Bluestein's chirp identity
+//   j k = (j^2 + k^2 - (k - j)^2) / 2,  w_t = exp(i pi t^2 / (2N)),
+//   y_k = sqrt(2/N) Im( w_k  sum_j (x_j w_j) conj(w_{k-j}) ),
+// a linear convolution computed as a circular one of power-of-two length
+// M >= 2m - 1 by FFT.  2N is not smooth for the grid sizes of interest
+// (2 * 16385 = 2*5*29*113), so no mixed-radix FFT of length 2N is used.
+//
+// Kernels (complex working precision T = float or double):
+//   small path (M <= 4096): one CTA holds whole sequences in shared memory:
+//       chirp multiply, FFT, spectrum multiply, inverse FFT, chirp, store.
+//   four-step path (M = M1 * M2): sequence index t = t1 + M1 t2,
+//       frequency index k = k2 + M2 k1, scratch stored as [k2][t1]:
+//     col_fwd : per t1, length-M2 FFT over t2, twiddle exp(-2 pi i t1 k2/M)
+//     row_mid : per k2, length-M1 FFT over t1 -> k1, times the kernel
+//               spectrum (stored in the same [k2][k1] order), inverse FFT,
+//               twiddle exp(+2 pi i t1 k2/M)
+//     col_inv : per t1, inverse length-M2 FFT over k2 -> t2, chirp, store.
+//   The frequency-domain product is taken in the permuted order the forward
+//   passes leave, so no transposition pass is needed.
+// Shared-memory FFTs are in-place Stockham radix-4 (one radix-2 pass when
+// log2 L is odd): every thread keeps its 16 elements in registers between the
+// read and the write phase of a pass.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "lr_internal.h"
+
+namespace lrp {
+
+constexpr int EPT = 16;  // elements per thread in every FFT tile
+
+// ---------------------------------------------------------------------------
+// Shared-memory Stockham passes.  Element e of sequence f is buf[f*fs + e*es].
+// FMAJOR: consecutive threads take consecutive sequences (column tiles, fs=1);
+// otherwise consecutive threads take consecutive elements of one sequence.
+// tw[q] = exp(-2 pi i q / M) with M = 2^logM >= L.
+// ---------------------------------------------------------------------------
+template <typename T, int LOGR, bool FMAJOR>
+__device__ __forceinline__ void stockham_pass(cpx<T>* buf, int logL, int lognf, int es, int fs,
+                                              int logNs, const cpx<T>* __restrict__ tw, int logM,
+                                              bool inverse) {
+  constexpr int R = 1 << LOGR;
+  constexpr int NB = EPT / R;  // butterflies per thread
+  const int NT = blockDim.x;
+  const int logLR = logL - LOGR;
+  const int maskLR = (1 << logLR) - 1;
+  const int maskNs = (1 << logNs) - 1;
+  const int twshift = logM - LOGR - logNs;
+  cpx<T> v[EPT];
+#pragma unroll
+  for (int s = 0; s < NB; ++s) {
+    const int g = threadIdx.x + s * NT;
+    int f, j;
+    if (FMAJOR) { f = g & ((1 << lognf) - 1); j = g >> lognf; }
+    else { f = g >> logLR; j = g & maskLR; }
+    const int k = j & maskNs;
+    cpx<T> x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = buf[f * fs + (j + (r << logLR)) * es];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      cpx<T> w = tw[(r * k) << twshift];
+      if (inverse) w.im = -w.im;
+      x[r] = cmul(x[r], w);
+    }
+    if (R == 2) {
+      v[s * R + 0] = cadd(x[0], x[1]);
+      v[s * R + 1] = csub(x[0], x[1]);
+    } else {
+      const cpx<T> s0 = cadd(x[0], x[2]), s1 = csub(x[0], x[2]);
+      const cpx<T> s2 = cadd(x[1], x[3]), s3 = csub(x[1], x[3]);
+      // forward: X1 = s1 - i s3, X3 = s1 + i s3; inverse swaps them
+      const cpx<T> mis3 = {s3.im, -s3.re};  // -i * s3
+      v[s * R + 0] = cadd(s0, s2);
+      v[s * R + 2] = csub(s0, s2);
+      v[s * R + 1] = inverse ? csub(s1, mis3) : cadd(s1, mis3);
+      v[s * R + 3] = inverse ? cadd(s1, mis3) : csub(s1, mis3);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < NB; ++s) {
+    const int g = threadIdx.x + s * NT;
+    int f, j;
+    if (FMAJOR) { f = g & ((1 << lognf) - 1); j = g >> lognf; }
+    else { f = g >> logLR; j = g & maskLR; }
+    const int k = j & maskNs;
+    const int base = ((j >> logNs) << (logNs + LOGR)) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[f * fs + (base + (r << logNs)) * es] = v[s * R + r];
+  }
+  __syncthreads();
+}
+
+// Full length-2^logL FFT of 2^lognf sequences; blockDim.x * EPT must equal
+// the number of elements 2^(logL + lognf).  Unnormalised.
+template <typename T, bool FMAJOR>
+__device__ void smem_fft(cpx<T>* buf, int logL, int lognf, int es, int fs,
+                         const cpx<T>* __restrict__ tw, int logM, bool inverse) {
+  int logNs = 0;
+  if (logL & 1) {
+    stockham_pass<T, 1, FMAJOR>(buf, logL, lognf, es, fs, logNs, tw, logM, inverse);
+    logNs += 1;
+  }
+  while (logNs < logL) {
+    stockham_pass<T, 2, FMAJOR>(buf, logL, lognf, es, fs, logNs, tw, logM, inverse);
+    logNs += 2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column addressing.
+// ---------------------------------------------------------------------------
+struct ColArgs {
+  const void* in[2];
+  void* out[2];
+  int ld_in[2];
+  int ld_out[2];
+  int ncol[2];
+  const int* dyn_count;
+};
+
+__device__ __forceinline__ bool col_live(const ColArgs& c, int col, int& seg, int& cc) {
+  seg = col < c.ncol[0] ? 0 : 1;
+  cc = seg ? col - c.ncol[0] : col;
+  if (seg == 1 && cc >= c.ncol[1]) return false;
+  if (c.dyn_count && cc >= *c.dyn_count) return false;
+  return true;
+}
+
+template <typename T, bool IN64>
+__device__ __forceinline__ T load_in(const ColArgs& c, int seg, int cc, int t) {
+  if (IN64) return (T)(static_cast<const double*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t]);
+  return static_cast<const T*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t];
+}
+template <typename T, bool OUT64>
+__device__ __forceinline__ void store_out(const ColArgs& c, int seg, int cc, int t, T v) {
+  if (OUT64) static_cast<double*>(c.out[seg])[(size_t)cc * c.ld_out[seg] + t] = (double)v;
+  else static_cast<T*>(c.out[seg])[(size_t)cc * c.ld_out[seg] + t] = v;
+}
+
+struct GeomArgs {
+  int m, logM, logM1, logM2;
+  int ncols;        // total column slots (ncol0 + ncol1)
+};
+
+// ---------------------------------------------------------------------------
+// Small path: 2^lognf sequences of length M per CTA.
+// ---------------------------------------------------------------------------
+template <typename T, bool IN64, bool OUT64>
+__global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
+    ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
+    const cpx<T>* __restrict__ bhat, int lognf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int M = 1 << g.logM;
+  const int nf = 1 << lognf;
+  const int items = (g.ncols + nf - 1) >> lognf;
+  const int nelem = nf << g.logM;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x) {
+      const int row = idx >> g.logM, t = idx & (M - 1);
+      const int col = (item << lognf) + row;
+      int seg, cc;
+      cpx<T> v = {T(0), T(0)};
+      if (col < g.ncols && t < g.m && col_live(c, col, seg, cc)) {
+        const T x = load_in<T, IN64>(c, seg, cc, t);
+        const cpx<T> w = chirp[t];
+        v = {x * w.re, x * w.im};
+      }
+      buf[idx] = v;
+    }
+    __syncthreads();
+    smem_fft<T, false>(buf, g.logM, lognf, 1, M, tw, g.logM, false);
+    for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x)
+      buf[idx] = cmul(buf[idx], bhat[idx & (M - 1)]);
+    __syncthreads();
+    smem_fft<T, false>(buf, g.logM, lognf, 1, M, tw, g.logM, true);
+    for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x) {
+      const int row = idx >> g.logM, t = idx & (M - 1);
+      const int col = (item << lognf) + row;
+      int seg, cc;
+      if (col < g.ncols && t < g.m && col_live(c, col, seg, cc)) {
+        const cpx<T> w = chirp[t], z = buf[idx];
+        store_out<T, OUT64>(c, seg, cc, t, w.re * z.im + w.im * z.re);  // Im(w z)
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Four-step path, column passes.  A tile holds TX = 4096 / M2 consecutive t1
+// values and all M2 values of t2 (or k2): tile[t2 * TX + dt1].
+// ---------------------------------------------------------------------------
+template <typename T, bool IN64>
+__global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
+    ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
+    cpx<T>* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int M1 = 1 << g.logM1;
+  const int logTX = 12 - g.logM2, TX = 1 << logTX;
+  const int blocks_per_col = M1 >> logTX;
+  const int items = g.ncols * blocks_per_col;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = item / blocks_per_col;
+    const int t1_0 = (item - col * blocks_per_col) << logTX;
+    int seg, cc;
+    if (!col_live(c, col, seg, cc)) continue;  // uniform across the CTA
+    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+      const int t2 = idx >> logTX, dt = idx & (TX - 1);
+      const int t = t1_0 + dt + (t2 << g.logM1);
+      cpx<T> v = {T(0), T(0)};
+      if (t < g.m) {
+        const T x = load_in<T, IN64>(c, seg, cc, t);
+        const cpx<T> w = chirp[t];
+        v = {x * w.re, x * w.im};
+      }
+      buf[idx] = v;
+    }
+    __syncthreads();
+    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, tw, g.logM, false);
+    cpx<T>* wc = work + ((size_t)col << g.logM);
+    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+      const int k2 = idx >> logTX, dt = idx & (TX - 1);
+      const int t1 = t1_0 + dt;
+      wc[(k2 << g.logM1) + t1] = cmul(buf[idx], tw[t1 * k2]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, bool OUT64>
+__global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
+    ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
+    const cpx<T>* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int M1 = 1 << g.logM1;
+  const int logTX = 12 - g.logM2, TX = 1 << logTX;
+  const int blocks_per_col = M1 >> logTX;
+  const int items = g.ncols * blocks_per_col;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = item / blocks_per_col;
+    const int t1_0 = (item - col * blocks_per_col) << logTX;
+    int seg, cc;
+    if (!col_live(c, col, seg, cc)) continue;
+    const cpx<T>* wc = work + ((size_t)col << g.logM);
+    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+      const int k2 = idx >> logTX, dt = idx & (TX - 1);
+      buf[idx] = wc[(k2 << g.logM1) + t1_0 + dt];
+    }
+    __syncthreads();
+    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, tw, g.logM, true);
+    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+      const int t2 = idx >> logTX, dt = idx & (TX - 1);
+      const int t = t1_0 + dt + (t2 << g.logM1);
+      if (t < g.m) {
+        const cpx<T> w = chirp[t], z = buf[idx];
+        store_out<T, OUT64>(c, seg, cc, t, w.re * z.im + w.im * z.re);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Row pass: RY = 4096 / M1 rows k2 per tile, each of M1 contiguous elements.
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
+    ColArgs c, GeomArgs g, const cpx<T>* __restrict__ tw, const cpx<T>* __restrict__ bhat,
+    cpx<T>* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int M1 = 1 << g.logM1, M2 = 1 << g.logM2;
+  const int logRY = 12 - g.logM1;
+  const int blocks_per_col = M2 >> logRY;
+  const int items = g.ncols * blocks_per_col;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = item / blocks_per_col;
+    const int k2_0 = (item - col * blocks_per_col) << logRY;
+    int seg, cc;
+    if (!col_live(c, col, seg, cc)) continue;
+    cpx<T>* wc = work + ((size_t)col << g.logM) + ((size_t)k2_0 << g.logM1);
+    const cpx<T>* bh = bhat + ((size_t)k2_0 << g.logM1);
+    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) buf[idx] = wc[idx];
+    __syncthreads();
+    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, tw, g.logM, false);
+    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) buf[idx] = cmul(buf[idx], bh[idx]);
+    __syncthreads();
+    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, tw, g.logM, true);
+    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+      const int k2 = k2_0 + (idx >> g.logM1), t1 = idx & (M1 - 1);
+      wc[idx] = cmulc(buf[idx], tw[t1 * k2]);  // times exp(+2 pi i t1 k2 / M)
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launcher.
+// ---------------------------------------------------------------------------
+template <typename T>
+static const TablesT& tables_of(const Plan& p);
+template <> const TablesT& tables_of<double>(const Plan& p) { return p.t64; }
+template <> const TablesT& tables_of<float>(const Plan& p) { return p.t32; }
+
+template <typename T, bool IN64, bool OUT64>
+static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs& g, void* work,
+                                int num_sms, cudaStream_t st) {
+  const TablesT& tb = tables_of<T>(p);
+  const cpx<T>* chirp = static_cast<const cpx<T>*>(tb.chirp);
+  const cpx<T>* tw = static_cast<const cpx<T>*>(tb.tw);
+  const cpx<T>* bhat = static_cast<const cpx<T>*>(tb.bhat);
+  const int M = 1 << g.logM;
+  if (M <= kSmallM) {
+    // 2^lognf sequences per CTA so that every CTA has 4096 elements when
+    // possible, but never more sequences than columns.
+    // 2^lognf sequences per CTA: at least 512 elements (a warp of threads),
+    // more only while there are still two CTAs per SM and the tile fits.
+    int lognf = 0;
+    while ((M << lognf) < 512) ++lognf;
+    while ((M << (lognf + 1)) <= kTileElems && (g.ncols >> (lognf + 1)) >= 2 * num_sms) ++lognf;
+    const int nelem = M << lognf;
+    const int threads = nelem / EPT;
+    const size_t smem = (size_t)nelem * sizeof(cpx<T>);
+    const int items = (g.ncols + (1 << lognf) - 1) >> lognf;
+    const int grid = items < 8 * num_sms ? items : 8 * num_sms;
+    auto kern = dst_small_kernel<T, IN64, OUT64>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, threads, smem, st>>>(c, g, chirp, tw, bhat, lognf);
+    return cudaGetLastError();
+  }
+  const size_t smem = (size_t)kTileElems * sizeof(cpx<T>);
+  const int items_col = g.ncols * ((1 << g.logM1) >> (12 - g.logM2));
+  const int items_row = g.ncols * ((1 << g.logM2) >> (12 - g.logM1));
+  const int cap = 8 * num_sms;
+  cpx<T>* wk = static_cast<cpx<T>*>(work);
+  auto k1 = dst_col_fwd_kernel<T, IN64>;
+  auto k2 = dst_row_mid_kernel<T>;
+  auto k3 = dst_col_inv_kernel<T, OUT64>;
+  cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k1<<<items_col < cap ? items_col : cap, kFftThreads, smem, st>>>(c, g, chirp, tw, wk);
+  k2<<<items_row < cap ? items_row : cap, kFftThreads, smem, st>>>(c, g, tw, bhat, wk);
+  k3<<<items_col < cap ? items_col : cap, kFftThreads, smem, st>>>(c, g, chirp, tw, wk);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dst(const Plan& p, const ColumnSet& cs, IoType in_t, IoType out_t, void* work,
+                       int num_sms, cudaStream_t st) {
+  ColArgs c;
+  for (int s = 0; s < 2; ++s) {
+    c.in[s] = cs.in[s];
+    c.out[s] = cs.out[s];
+    c.ld_in[s] = cs.ld_in[s];
+    c.ld_out[s] = cs.ld_out[s];
+    c.ncol[s] = cs.ncol[s];
+  }
+  c.dyn_count = cs.dyn_count;
+  GeomArgs g{p.m, p.logM, p.logM1, p.logM2, cs.ncol[0] + cs.ncol[1]};
+  if (g.ncols == 0) return cudaSuccess;
+  const bool i64 = in_t == IoType::F64, o64 = out_t == IoType::F64;
+  if (i64 && o64) return launch_dst_t<T, true, true>(p, c, g, work, num_sms, st);
+  if (i64 && !o64) return launch_dst_t<T, true, false>(p, c, g, work, num_sms, st);
+  if (!i64 && o64) return launch_dst_t<T, false, true>(p, c, g, work, num_sms, st);
+  return launch_dst_t<T, false, false>(p, c, g, work, num_sms, st);
+}
+
+template cudaError_t launch_dst<double>(const Plan&, const ColumnSet&, IoType, IoType, void*, int, cudaStream_t);
+template cudaError_t launch_dst<float>(const Plan&, const ColumnSet&, IoType, IoType, void*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Plan tables (built once per order m on the host in float64, uploaded).
+// ---------------------------------------------------------------------------
+
+// exp(2 pi i q / L) for 0 <= q < L, L a multiple of 4.  q is reduced to the
+// first quadrant in integers and the angle kept below pi/4, so the float64
+// result is within about one ulp.
+static std::complex<double> cis2pi(long long q, long long L) {
+  const long long quarter = L / 4;
+  q %= L;
+  if (q < 0) q += L;
+  const int p = (int)(q / quarter);
+  const long long r = q - p * quarter;
+  double c, s;
+  if (2 * r <= quarter) {
+    const double th = 2.0 * M_PI * (double)r / (double)L;
+    c = std::cos(th);
+    s = std::sin(th);
+  } else {
+    const double th = 2.0 * M_PI * (double)(quarter - r) / (double)L;
+    c = std::sin(th);
+    s = std::cos(th);
+  }
+  switch (p) {
+    case 0: return {c, s};
+    case 1: return {-s, c};
+    case 2: return {-c, -s};
+    default: return {s, -c};
+  }
+}
+
+// In-place iterative radix-2 FFT of length 2^logn (forward, exp(-2 pi i/n)).
+static void host_fft(std::vector<std::complex<double>>& a, int logn) {
+  const size_t n = (size_t)1 << logn;
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    const size_t step = n / len;
+    for (size_t i = 0; i < n; i += len)
+      for (size_t j = 0; j < len / 2; ++j) {
+        const std::complex<double> w = std::conj(cis2pi((long long)(j * step), (long long)n));
+        const std::complex<double> u = a[i + j], v = a[i + j + len / 2] * w;
+        a[i + j] = u + v;
+        a[i + j + len / 2] = u - v;
+      }
+  }
+}
+
+Plan::~Plan() {
+  for (void* q : allocations) cudaFree(q);
+}
+
+template <typename T>
+static std::string upload(Plan& p, const std::vector<std::complex<double>>& v, void** dst) {
+  std::vector<cpx<T>> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = {(T)v[i].real(), (T)v[i].imag()};
+  void* d = nullptr;
+  if (cudaMalloc(&d, h.size() * sizeof(cpx<T>)) != cudaSuccess) return "cudaMalloc of plan table failed";
+  p.allocations.push_back(d);
+  if (cudaMemcpy(d, h.data(), h.size() * sizeof(cpx<T>), cudaMemcpyHostToDevice) != cudaSuccess)
+    return "upload of plan table failed";
+  *dst = d;
+  return "";
+}
+
+template <typename T>
+static std::string upload_real(Plan& p, const std::vector<double>& v, T** dst) {
+  std::vector<T> h(v.begin(), v.end());
+  void* d = nullptr;
+  if (cudaMalloc(&d, h.size() * sizeof(T)) != cudaSuccess) return "cudaMalloc of symbol failed";
+  p.allocations.push_back(d);
+  if (cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return "upload of symbol failed";
+  *dst = static_cast<T*>(d);
+  return "";
+}
+
+std::string build_plan(int m, Plan& p) {
+  p.m = m;
+  const long long N = (long long)m + 1;
+  int logM = ilog2(2LL * m - 1);
+  if (logM < 6) logM = 6;
+  p.logM = logM;
+  p.logM1 = (logM + 1) / 2;
+  p.logM2 = logM / 2;
+  const size_t M = (size_t)1 << logM;
+  // chirp w_{t+1} = exp(2 pi i (t+1)^2 / (4N))
+  std::vector<std::complex<double>> chirp(m), tw(M), b(M, {0.0, 0.0});
+  for (int t = 0; t < m; ++t) {
+    const long long u = t + 1;
+    chirp[t] = cis2pi((u * u) % (4 * N), 4 * N);
+  }
+  for (size_t q = 0; q < M; ++q) tw[q] = std::conj(cis2pi((long long)q, (long long)M));
+  // kernel conj(w_d) at d mod M for |d| <= m-1 (w_0 = 1, w_{-d} = w_d)
+  b[0] = {1.0, 0.0};
+  for (int d = 1; d < m; ++d) {
+    const std::complex<double> wd = std::conj(chirp[d - 1]);
+    b[d] = wd;
+    b[M - d] = wd;
+  }
+  host_fft(b, logM);
+  const double scale = std::sqrt(2.0 / (double)N) / (double)M;
+  for (auto& z : b) z *= scale;
+  std::vector<std::complex<double>> bh(M);
+  if (M <= (size_t)kSmallM) {
+    bh = b;
+  } else {
+    const size_t M1 = (size_t)1 << p.logM1, M2 = (size_t)1 << p.logM2;
+    for (size_t k2 = 0; k2 < M2; ++k2)
+      for (size_t k1 = 0; k1 < M1; ++k1) bh[k2 * M1 + k1] = b[k2 + M2 * k1];
+  }
+  std::string e;
+  if (!(e = upload<double>(p, chirp, &p.t64.chirp)).empty()) return e;
+  if (!(e = upload<double>(p, tw, &p.t64.tw)).empty()) return e;
+  if (!(e = upload<double>(p, bh, &p.t64.bhat)).empty()) return e;
+  if (!(e = upload<float>(p, chirp, &p.t32.chirp)).empty()) return e;
+  if (!(e = upload<float>(p, tw, &p.t32.tw)).empty()) return e;
+  if (!(e = upload<float>(p, bh, &p.t32.bhat)).empty()) return e;
+  // Symbol: lambda_i = 4 sin^2(i pi/(2N)), 4 - lambda_i = 4 cos^2(i pi/(2N)).
+  std::vector<double> a5(m), b5(m, 1.0), as(m), bs(m);
+  const double N2 = (double)N * (double)N;
+  for (int i = 0; i < m; ++i) {
+    const std::complex<double> z = cis2pi(i + 1, 4 * N);  // angle (i+1) pi / (2N)
+    const double lam = 4.0 * z.imag() * z.imag();
+    const double lamc = 4.0 * z.real() * z.real();
+    a5[i] = lam * N2;             // mu_i = lambda_i / h^2
+    as[i] = lam * N2 / 16.0;      // lambda_i / (16 h^2)
+    bs[i] = lamc;
+  }
+  if (!(e = upload_real<double>(p, a5, &p.sym_a64[0])).empty()) return e;
+  if (!(e = upload_real<double>(p, b5, &p.sym_b64[0])).empty()) return e;
+  if (!(e = upload_real<double>(p, as, &p.sym_a64[1])).empty()) return e;
+  if (!(e = upload_real<double>(p, bs, &p.sym_b64[1])).empty()) return e;
+  if (!(e = upload_real<float>(p, a5, &p.sym_a32[0])).empty()) return e;
+  if (!(e = upload_real<float>(p, b5, &p.sym_b32[0])).empty()) return e;
+  if (!(e = upload_real<float>(p, as, &p.sym_a32[1])).empty()) return e;
+  if (!(e = upload_real<float>(p, bs, &p.sym_b32[1])).empty()) return e;
+  return "";
+}
+
+}  // namespace lrp

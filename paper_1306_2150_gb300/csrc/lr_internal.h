@@ -1,0 +1,132 @@
+// Internal interfaces between the translation units of liblrpoisson.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "lr_common.cuh"
+
+namespace lrp {
+
+// ---------------------------------------------------------------------------
+// Sine-transform plan: tables for the Bluestein evaluation of the DST-I of
+// order m (Section 4.1) with a power-of-two FFT of length M >= 2m - 1.
+//   chirp[t]  = exp(i pi (t+1)^2 / (2N)), N = m + 1, t < m
+//   tw[q]     = exp(-2 pi i q / M), q < M
+//   bhat      = FFT_M of the chirp kernel conj(w_|d|), |d| < m, scaled by
+//               sqrt(2/N)/M; natural order if M <= kSmallM, else stored as
+//               [k2][k1] for the four-step split M = M1 * M2.
+// Symbol tables: Lambda[i,j] = a_i b_j + b_i a_j (both operator kinds).
+// ---------------------------------------------------------------------------
+constexpr int kSmallM = 4096;      // one CTA holds a whole length-M sequence
+constexpr int kTileElems = 4096;   // complex elements per CTA tile
+constexpr int kFftThreads = 256;   // 16 elements per thread
+
+struct TablesT {
+  void* chirp = nullptr;  // cpx<T>[m]
+  void* tw = nullptr;     // cpx<T>[M]
+  void* bhat = nullptr;   // cpx<T>[M]
+  void* a = nullptr;      // T[m] per operator kind (index by op)
+  void* b = nullptr;
+};
+
+struct Plan {
+  int m = 0;
+  int logM = 0, logM1 = 0, logM2 = 0;
+  TablesT t64, t32;                       // float64 and float32 copies
+  double* sym_a64[2] = {nullptr, nullptr};  // per operator kind
+  double* sym_b64[2] = {nullptr, nullptr};
+  float* sym_a32[2] = {nullptr, nullptr};
+  float* sym_b32[2] = {nullptr, nullptr};
+  std::vector<void*> allocations;
+  ~Plan();
+};
+
+std::string build_plan(int m, Plan& p);   // returns "" on success
+
+// A set of columns to transform: segment 0 has ncol0 columns, segment 1
+// ncol1 columns.  If dyn_count is non-null the number of live columns of each
+// segment is *dyn_count (read on the device) and ncol0/ncol1 are capacities.
+struct ColumnSet {
+  const void* in[2] = {nullptr, nullptr};
+  void* out[2] = {nullptr, nullptr};
+  int ld_in[2] = {0, 0};
+  int ld_out[2] = {0, 0};
+  int ncol[2] = {0, 0};
+  const int* dyn_count = nullptr;
+};
+
+enum class IoType { F64, WORK };   // caller float64 buffers or working precision
+
+// Launch the DST-I of every column of cs (forward and inverse are the same
+// orthonormal, symmetric S).  work: complex scratch of M * (ncol0 + ncol1)
+// elements of the working precision.  Returns a CUDA error code.
+template <typename T>
+cudaError_t launch_dst(const Plan& p, const ColumnSet& cs, IoType in_t, IoType out_t,
+                       void* work, int num_sms, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Cross approximation in frequency space (Section 4.2).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CrossArgs {
+  int m, r, kcap, ld;
+  const T* Uh;
+  const T* Vh;
+  T* C;            // m x kcap, column l: residual column / delta_l
+  T* R;            // m x kcap, column l: residual row / delta_l
+  const T* a;      // symbol
+  const T* b;
+  double* d;       // kcap pivot values
+  int* I;
+  int* J;
+  double* GC;      // kcap x kcap Gram matrices (column-major, ld kcap)
+  double* GR;
+  SolveState* st;
+  double tol;
+  int probes;
+  unsigned long long seed;
+  int max_probe_rounds;
+  int max_zero_rows;
+};
+
+template <typename T>
+cudaError_t launch_cross(const CrossArgs<T>& a, int cluster_size, cudaStream_t st, int* used_cluster);
+
+// ---------------------------------------------------------------------------
+// Rounding core (Section 3): Cholesky of the Gram matrices, SVD of the k x k
+// core, truncation, coefficient matrices Tc, Tr (k x R, ld KMAX).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CoreArgs {
+  const double* GC;
+  const double* GR;
+  int ldg;          // leading dimension of GC/GR
+  const double* d;  // weights (k)
+  const int* k_dev; // k on the device (nullptr: use k_host)
+  int k_host;
+  double eps;
+  int rmax_out;
+  T* Tc;            // KMAX x KMAX
+  T* Tr;
+  double* s_out;    // R singular values
+  SolveState* st;
+};
+template <typename T>
+cudaError_t launch_core(const CoreArgs<T>& a, bool jacobi_fp32, cudaStream_t st);
+
+// Gram matrices of two tall factors (float64): G = X^T X.
+cudaError_t launch_gram(const double* X, int rows, int ld, int k, double* G, int ldg,
+                        double* partial, int num_sms, cudaStream_t st);
+
+// Rotation: out[:, q] = sum_l in[:, l] * Tm[l, q] for q < rank (rank on the device).
+template <typename TI, typename TO>
+cudaError_t launch_rotate(const TI* in, int ld_in, int rows, const int* k_dev, int k_host,
+                          const void* Tm, bool tm_f32, const int* rank_dev, TO* out, int ld_out,
+                          cudaStream_t st);
+
+}  // namespace lrp

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of liblrpoisson.so (C ABI in include/lrpoisson.h).
+
+Argument marshalling only: every numerical step runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the stream.  Factor matrices are
+float64 CUDA tensors of shape (rows, cols) stored column-major
+(``t.stride(0) == 1``), which is the layout the C ABI expects.
+
+There is no CPU fallback: if the compiled library is missing, ``load()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblrpoisson.so")
+
+LR_OK, LR_EINVAL, LR_ENOMEM, LR_ENOCONV, LR_ETIMEOUT, LR_ECUDA = range(6)
+LR_FP64, LR_MIXED = 0, 1
+LR_OP_5PT, LR_OP_SEMISTAGGERED = 0, 1
+LR_FLAG_ASYNC = 1
+LR_FLAG_TIMING = 2
+PHASES = ("forward_dst", "cross", "rounding", "inverse_dst")
+
+PRECISIONS = {"fp64": LR_FP64, "mixed": LR_MIXED}
+OPERATORS = {"5pt": LR_OP_5PT, "semi": LR_OP_SEMISTAGGERED}
+
+# Every function the header declares (checked against the header by the tests).
+EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
+           "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
+           "lr_truncate", "lr_get_info", "lr_get_phase_times")
+
+
+class LrMat(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("r", ctypes.c_int),
+                ("rmax", ctypes.c_int), ("ld", ctypes.c_int),
+                ("U", ctypes.c_void_p), ("s", ctypes.c_void_p), ("V", ctypes.c_void_p)]
+
+
+class LrOptions(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("op", ctypes.c_int), ("eps", ctypes.c_double),
+                ("rmax", ctypes.c_int), ("aca_tol_factor", ctypes.c_double),
+                ("probes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("flags", ctypes.c_uint), ("cluster_size", ctypes.c_int)]
+
+
+class LrInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("aca_steps", ctypes.c_int), ("rank", ctypes.c_int),
+                ("converged", ctypes.c_int), ("cut", ctypes.c_int),
+                ("probe_rounds", ctypes.c_int), ("zero_rows", ctypes.c_int),
+                ("cluster_size", ctypes.c_int), ("launches", ctypes.c_int),
+                ("norm_est", ctypes.c_double),
+                ("sigma0", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load the compiled library (once).  Raises RuntimeError if it is absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} not found: build it with `python -m paper_1306_2150_gb300.build` "
+                           "(there is no CPU fallback)")
+    try:  # torch first: it loads the CUDA runtime the library links against
+        import torch  # noqa: F401
+    except Exception:
+        pass
+    lib = ctypes.CDLL(p)
+    c_int, c_void_p, c_double = ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+    lib.lr_options_default.argtypes = [ctypes.POINTER(LrOptions)]
+    lib.lr_options_default.restype = None
+    lib.lr_create.argtypes = [ctypes.POINTER(c_void_p), c_void_p]
+    lib.lr_create.restype = c_int
+    lib.lr_set_stream.argtypes = [c_void_p, c_void_p]
+    lib.lr_set_stream.restype = c_int
+    lib.lr_destroy.argtypes = [c_void_p]
+    lib.lr_destroy.restype = c_int
+    lib.lr_last_error.argtypes = [c_void_p]
+    lib.lr_last_error.restype = ctypes.c_char_p
+    lib.lr_status_string.argtypes = [c_int]
+    lib.lr_status_string.restype = ctypes.c_char_p
+    lib.lr_dst1.argtypes = [c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_int]
+    lib.lr_dst1.restype = c_int
+    lib.lr_poisson2d.argtypes = [c_void_p, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
+                                 ctypes.POINTER(LrOptions)]
+    lib.lr_poisson2d.restype = c_int
+    lib.lr_truncate.argtypes = [c_void_p, ctypes.POINTER(LrMat), c_double, c_int]
+    lib.lr_truncate.restype = c_int
+    lib.lr_get_info.argtypes = [c_void_p, ctypes.POINTER(LrInfo), ctypes.POINTER(c_int),
+                                ctypes.POINTER(c_int), c_int]
+    lib.lr_get_info.restype = c_int
+    lib.lr_get_phase_times.argtypes = [c_void_p, ctypes.POINTER(c_double), c_int]
+    lib.lr_get_phase_times.restype = c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class LrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def status_string(s: int) -> str:
+    return load().lr_status_string(int(s)).decode()
+
+
+def lr_options_default() -> LrOptions:
+    o = LrOptions()
+    load().lr_options_default(ctypes.byref(o))
+    return o
+
+
+class Handle:
+    """lr_create / lr_destroy around a CUDA stream (torch's current stream by
+    default)."""
+
+    def __init__(self, stream=None):
+        import torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        ptr = ctypes.c_void_p()
+        st = lib.lr_create(ctypes.byref(ptr), ctypes.c_void_p(stream.cuda_stream))
+        if st != LR_OK:
+            raise LrError(st, "lr_create failed")
+        self.ptr = ptr
+
+    def last_error(self) -> str:
+        return load().lr_last_error(self.ptr).decode()
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().lr_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def colmajor_empty(rows: int, cols: int, device="cuda"):
+    """float64 tensor of shape (rows, cols), column-major, 16-byte aligned
+    columns (leading dimension rounded up to an even count)."""
+    import torch
+    ld = rows + (rows & 1)
+    return torch.empty((max(cols, 1), ld), dtype=torch.float64, device=device).t()[:rows, :cols]
+
+
+def as_colmajor(t):
+    import torch
+    if t.dtype != torch.float64:
+        t = t.to(torch.float64)
+    if t.dim() == 1:
+        t = t[:, None]
+    if t.stride(0) == 1 and t.stride(1) >= t.shape[0] and t.stride(1) % 2 == 0 \
+            and t.data_ptr() % 16 == 0:
+        return t
+    out = colmajor_empty(t.shape[0], t.shape[1], t.device)
+    out.copy_(t)
+    return out
+
+
+def _ld(t) -> int:
+    return int(t.stride(1)) if t.shape[1] > 1 else max(int(t.stride(1)), t.shape[0])
+
+
+@dataclass
+class SolveResult:
+    U: object
+    s: object
+    V: object
+    info: LrInfo
+    status: int
+    pivots_I: list
+    pivots_J: list
+
+
+def _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size) -> LrOptions:
+    o = lr_options_default()
+    o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    o.op = OPERATORS[op] if isinstance(op, str) else int(op)
+    o.eps = float(eps)
+    o.rmax = int(rmax)
+    o.aca_tol_factor = float(aca_tol_factor)
+    o.probes = int(probes)
+    o.seed = int(seed)
+    o.flags = int(flags)
+    o.cluster_size = int(cluster_size)
+    return o
+
+
+def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rmax: int = 64,
+                 rmax_out: int = 64, aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
+                 cluster_size: int = 0, async_: bool = False, out=None, check: bool = True,
+                 timing: bool = False):
+    """Low-rank solve of A X = U V^T.  Returns SolveResult with the solution
+    factors (views of rank R) unless ``async_`` (then read lr_get_info after
+    synchronising the stream).  ``out`` = (Uo, s, Vo) preallocated outputs."""
+    U = as_colmajor(U)
+    V = as_colmajor(V)
+    m, r = U.shape
+    if V.shape != (m, r):
+        raise ValueError("U and V must have the same shape")
+    if U.stride(1) != V.stride(1):
+        V2 = colmajor_empty(m, r, V.device)
+        V2.copy_(V)
+        V = V2
+        if U.stride(1) != V.stride(1):
+            U2 = colmajor_empty(m, r, U.device)
+            U2.copy_(U)
+            U = U2
+    if out is None:
+        import torch
+        Uo = colmajor_empty(m, rmax_out, U.device)
+        Vo = colmajor_empty(m, rmax_out, U.device)
+        s = torch.empty(rmax_out, dtype=torch.float64, device=U.device)
+    else:
+        Uo, s, Vo = out
+    rhs = LrMat(m, m, r, r, _ld(U), U.data_ptr(), None, V.data_ptr())
+    sol = LrMat(m, m, 0, Uo.shape[1], _ld(Uo), Uo.data_ptr(), s.data_ptr(), Vo.data_ptr())
+    if _ld(Vo) != _ld(Uo):
+        raise ValueError("output factors need the same leading dimension")
+    flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_TIMING if timing else 0)
+    o = _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size)
+    st = load().lr_poisson2d(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o))
+    if async_:
+        if st != LR_OK:
+            raise LrError(st, h.last_error())
+        return None
+    if check and st not in (LR_OK, LR_ENOCONV):
+        raise LrError(st, h.last_error())
+    info, pi, pj = lr_get_info(h)
+    R = sol.r
+    return SolveResult(Uo[:, :R], s[:R], Vo[:, :R], info, st, pi, pj)
+
+
+def lr_get_info(h: Handle, cap: int = 64):
+    info = LrInfo()
+    pi = (ctypes.c_int * cap)()
+    pj = (ctypes.c_int * cap)()
+    st = load().lr_get_info(h.ptr, ctypes.byref(info), pi, pj, cap)
+    if st != LR_OK:
+        raise LrError(st, "lr_get_info failed")
+    k = min(info.aca_steps, cap)
+    return info, list(pi[:k]), list(pj[:k])
+
+
+def lr_dst1(h: Handle, X, prec="fp64", out=None):
+    """Orthonormal DST-I of every column of X (float64 CUDA, column-major)."""
+    X = as_colmajor(X)
+    m, n = X.shape
+    Y = colmajor_empty(m, n, X.device) if out is None else out
+    p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    st = load().lr_dst1(h.ptr, m, n, X.data_ptr(), _ld(X), Y.data_ptr(), _ld(Y), p)
+    if st != LR_OK:
+        raise LrError(st, h.last_error())
+    return Y
+
+
+def lr_truncate(h: Handle, U, s, V, eps: float, rmax: int = 64):
+    """Rounding of U diag(s) V^T (s None: ones).  Returns (U, s, V, status)
+    with the kept rank."""
+    import torch
+    U = as_colmajor(U)
+    V = as_colmajor(V)
+    n1, r = U.shape
+    n2 = V.shape[0]
+    ld = max(_ld(U), _ld(V))
+    ld += ld & 1
+    Uw = torch.empty((r, ld), dtype=torch.float64, device=U.device).t()
+    Vw = torch.empty((r, ld), dtype=torch.float64, device=U.device).t()
+    Uw[:n1].copy_(U)
+    Vw[:n2].copy_(V)
+    sw = torch.ones(r, dtype=torch.float64, device=U.device) if s is None else \
+        s.to(torch.float64).clone().contiguous()
+    X = LrMat(n1, n2, r, r, ld, Uw.data_ptr(), sw.data_ptr(), Vw.data_ptr())
+    st = load().lr_truncate(h.ptr, ctypes.byref(X), float(eps), int(rmax))
+    if st not in (LR_OK, LR_ENOCONV):
+        raise LrError(st, h.last_error())
+    R = X.r
+    return Uw[:n1, :R], sw[:R], Vw[:n2, :R], st
+
+
+def lr_get_phase_times(h: Handle) -> dict:
+    """Per-phase milliseconds of the last solve run with ``timing=True``."""
+    ms = (ctypes.c_double * len(PHASES))()
+    st = load().lr_get_phase_times(h.ptr, ms, len(PHASES))
+    if st != LR_OK:
+        raise LrError(st, h.last_error())
+    return dict(zip(PHASES, list(ms)))
