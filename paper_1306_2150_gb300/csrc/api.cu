@@ -136,8 +136,8 @@ lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options&
     *Vh = cv.template take<T>(sizeof(T) * ldw * r);
     *C = cv.template take<T>(sizeof(T) * ldw * kcap);
     *R = cv.template take<T>(sizeof(T) * ldw * kcap);
-    *Uo = cv.template take<T>(sizeof(T) * ldw * kcap);
-    *Vo = cv.template take<T>(sizeof(T) * ldw * kcap);
+    *Uo = cv.template take<T>(16);
+    *Vo = cv.template take<T>(16);
     *work = cv.template take<char>(four_step ? sizeof(cpx<T>) * M * cols_fft : 16);
     *GC = cv.template take<double>(sizeof(double) * kcap * kcap);
     *GR = cv.template take<double>(sizeof(double) * kcap * kcap);
@@ -200,21 +200,23 @@ lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options&
   co.eps = o.eps; co.rmax_out = ncap_out;
   co.Tc = Tc; co.Tr = Tr; co.s_out = sol->s; co.st = st;
   LR_CUDA(h, launch_core<T>(co, f32, stm), "rounding core");
-  LR_CUDA(h, (launch_rotate<T, T>(C, ldw, m, &st->k, 0, Tc, f32, &st->rank, Uo, ldw, stm)), "rotation U");
-  LR_CUDA(h, (launch_rotate<T, T>(R, ldw, m, &st->k, 0, Tr, f32, &st->rank, Vo, ldw, stm)), "rotation V");
 
   LR_MARK(3);
-  // T6: inverse DST of the kept columns into the caller's float64 factors.
+  // T6: inverse DST of the kept columns into the caller's float64 factors;
+  // the rotation of the skeleton by Tc, Tr (the last step of the rounding) is
+  // applied as the transform loads its input.
   ColumnSet iv;
-  iv.in[0] = Uo; iv.in[1] = Vo;
+  iv.in[0] = C; iv.in[1] = R;
+  iv.tm[0] = Tc; iv.tm[1] = Tr;
+  iv.k_dev = &st->k;
   iv.ld_in[0] = ldw; iv.ld_in[1] = ldw;
   iv.out[0] = sol->U; iv.out[1] = sol->V;
   iv.ld_out[0] = sol->ld; iv.ld_out[1] = sol->ld;
   iv.ncol[0] = ncap_out; iv.ncol[1] = ncap_out;
   iv.dyn_count = &st->rank;
-  LR_CUDA(h, launch_dst<T>(*plan, iv, IoType::WORK, IoType::F64, work, h->num_sms, stm), "inverse DST");
+  LR_CUDA(h, launch_dst<T>(*plan, iv, IoType::ROT, IoType::F64, work, h->num_sms, stm), "inverse DST");
   LR_MARK(4);
-  h->info.launches = 2 * (four_step ? 3 : 1) + 4;
+  h->info.launches = 2 * (four_step ? 3 : 1) + 2;
 
   LR_CUDA(h, cudaMemcpyAsync(h->h_state, st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm), "state copy");
   LR_CUDA(h, cudaMemcpyAsync(h->h_piv, I, sizeof(int) * kcap, cudaMemcpyDeviceToHost, stm), "pivot copy");
@@ -348,7 +350,7 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
   if (!rhs->U || !rhs->V || !sol->U || !sol->V || !sol->s) return fail(h, LR_EINVAL, "null factor pointer");
   if (!aligned16(rhs->U) || !aligned16(rhs->V) || !aligned16(sol->U) || !aligned16(sol->V) || !aligned16(sol->s))
     return fail(h, LR_EINVAL, "factor pointers must be 16-byte aligned");
-  if ((long long)m * 8 > (long long)16 * 8192) return fail(h, LR_EINVAL, "m too large (max 131072)");
+  if (m > 131072) return fail(h, LR_EINVAL, "m too large (max 131072)");
   Plan* plan = nullptr;
   s = get_plan(h, m, &plan);
   if (s != LR_OK) return s;

@@ -29,6 +29,7 @@ struct CoreSmem {
   JT Zm[KMAX * KP];
   double sig[KMAX];
   double g0c[KMAX], g0r[KMAX];
+  double invc[KMAX], invr[KMAX];  // reciprocal Cholesky pivots
   double d[KMAX];
   int perm[KMAX];
   int flag;
@@ -42,8 +43,15 @@ __device__ __forceinline__ JT warp_sum_t(JT v) {
   return v;
 }
 
+template <typename JT> __device__ __forceinline__ JT rsqrt_t(JT x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
+template <typename JT> __device__ __forceinline__ JT fdiv_t(JT a, JT b);
+template <> __device__ __forceinline__ float fdiv_t<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fdiv_t<double>(double a, double b) { return a / b; }
+
 template <typename T, typename JT>
-__global__ void __launch_bounds__(512, 1) core_kernel(CoreArgs<T> A) {
+__global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CoreSmem<JT>& S = *reinterpret_cast<CoreSmem<JT>*>(smem_raw);
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
@@ -75,12 +83,14 @@ __global__ void __launch_bounds__(512, 1) core_kernel(CoreArgs<T> A) {
       double djj = L[j * KP + j];
       const double floor_ = 1e-13 * g0 > DBL_MIN ? 1e-13 * g0 : DBL_MIN;
       if (!(djj > floor_)) djj = floor_;
-      L[j * KP + j] = sqrt(djj);
+      const double ljj = sqrt(djj);
+      L[j * KP + j] = ljj;
+      (tid == 0 ? S.invc : S.invr)[j] = 1.0 / ljj;
     }
     __syncthreads();
     for (int i = j + 1 + tid; i < 2 * k; i += NT) {
-      if (i < k) S.Lc[i * KP + j] /= S.Lc[j * KP + j];
-      else if (i - k > j) S.Lr[(i - k) * KP + j] /= S.Lr[j * KP + j];
+      if (i < k) S.Lc[i * KP + j] *= S.invc[j];
+      else if (i - k > j) S.Lr[(i - k) * KP + j] *= S.invr[j];
     }
     __syncthreads();
     const int rem = k - j - 1;
@@ -113,42 +123,60 @@ __global__ void __launch_bounds__(512, 1) core_kernel(CoreArgs<T> A) {
   }
   __syncthreads();
   // One-sided (Hestenes) Jacobi with round-robin pair ordering.
-  const JT tol = (sizeof(JT) == 8) ? (JT)(4.0 * DBL_EPSILON) : (JT)(4.0 * FLT_EPSILON);
+  // Stop when every pair is orthogonal to 2k ulps: the rounding error of the
+  // computed inner product itself is about k ulps, so a tighter test would
+  // rotate rounding noise forever.  Whatever the sweep count, the discarded
+  // columns' norms are exactly the error of the truncated product, because
+  // every rotation is orthogonal.
+  const JT tol = (JT)((k < 4 ? 8 : 2 * k) * ((sizeof(JT) == 8) ? DBL_EPSILON : (double)FLT_EPSILON));
+  // Round-robin (circle) pair schedule: in round t, position p meets
+  // position ke-1-p; position 0 holds column 0, the others rotate.
   const int npairs = ke / 2;
+  __shared__ unsigned char pair_c0[KMAX][KMAX / 2], pair_c1[KMAX][KMAX / 2];
+  for (int idx = tid; idx < (ke - 1) * npairs; idx += NT) {
+    const int round = idx / npairs, pr = idx % npairs;
+    const int pos1 = ke - 1 - pr;
+    pair_c0[round][pr] = (unsigned char)(pr == 0 ? 0 : 1 + (pr - 1 + round) % (ke - 1));
+    pair_c1[round][pr] = (unsigned char)(1 + (pos1 - 1 + round) % (ke - 1));
+  }
+  __syncthreads();
+  // One warp per pair: lanes hold rows (k <= 64: two per lane) of both
+  // columns in registers for the inner products and the update.
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (tid == 0) S.flag = 0;
     __syncthreads();
     for (int round = 0; round < ke - 1; ++round) {
       for (int pr = warp; pr < npairs; pr += NW) {
-        // positions pr and ke-1-pr of the rotating order: 0 fixed, others shift
-        const int pos0 = pr, pos1 = ke - 1 - pr;
-        const int c0 = pos0 == 0 ? 0 : 1 + (pos0 - 1 + round) % (ke - 1);
-        const int c1 = pos1 == 0 ? 0 : 1 + (pos1 - 1 + round) % (ke - 1);
+        const int c0 = pair_c0[round][pr], c1 = pair_c1[round][pr];
         JT* x = S.Mx + c0 * KP;
         JT* y = S.Mx + c1 * KP;
-        JT al = 0, be = 0, ga = 0;
-        for (int i = lane; i < k; i += 32) {
-          al += x[i] * x[i];
-          be += y[i] * y[i];
-          ga += x[i] * y[i];
-        }
+        const int i0 = lane, i1 = lane + 32;
+        const JT x0 = i0 < ke ? x[i0] : JT(0), y0 = i0 < ke ? y[i0] : JT(0);
+        const JT x1 = i1 < ke ? x[i1] : JT(0), y1 = i1 < ke ? y[i1] : JT(0);
+        JT al = x0 * x0 + x1 * x1, be = y0 * y0 + y1 * y1, ga = x0 * y0 + x1 * y1;
         al = warp_sum_t(al);
         be = warp_sum_t(be);
         ga = warp_sum_t(ga);
-        if (fabs(ga) > tol * sqrt(al) * sqrt(be) && ga != JT(0)) {
-          const JT zeta = (be - al) / (JT(2) * ga);
-          const JT t = (zeta >= JT(0) ? JT(1) : JT(-1)) / (fabs(zeta) + sqrt(JT(1) + zeta * zeta));
-          const JT c = JT(1) / sqrt(JT(1) + t * t);
+        if (ga != JT(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const JT zeta = fdiv_t<JT>(be - al, JT(2) * ga);
+          const JT t = fdiv_t<JT>(zeta >= JT(0) ? JT(1) : JT(-1), fabs(zeta) + sqrt(JT(1) + zeta * zeta));
+          const JT c = rsqrt_t<JT>(JT(1) + t * t);
           const JT s = c * t;
           JT* zx = S.Zm + c0 * KP;
           JT* zy = S.Zm + c1 * KP;
-          for (int i = lane; i < ke; i += 32) {
-            const JT xi = x[i], yi = y[i];
-            x[i] = c * xi - s * yi;
-            y[i] = s * xi + c * yi;
-            const JT zxi = zx[i], zyi = zy[i];
-            zx[i] = c * zxi - s * zyi;
-            zy[i] = s * zxi + c * zyi;
+          if (i0 < ke) {
+            x[i0] = c * x0 - s * y0;
+            y[i0] = s * x0 + c * y0;
+            const JT a = zx[i0], b = zy[i0];
+            zx[i0] = c * a - s * b;
+            zy[i0] = s * a + c * b;
+          }
+          if (i1 < ke) {
+            x[i1] = c * x1 - s * y1;
+            y[i1] = s * x1 + c * y1;
+            const JT a = zx[i1], b = zy[i1];
+            zx[i1] = c * a - s * b;
+            zy[i1] = s * a + c * b;
           }
           if (lane == 0) S.flag = 1;
         }
@@ -206,6 +234,7 @@ __global__ void __launch_bounds__(512, 1) core_kernel(CoreArgs<T> A) {
     const int side = job / K, p = job % K;
     const int src = S.perm[p];
     const double* L = side == 0 ? S.Lc : S.Lr;
+    const double* inv_diag = side == 0 ? S.invc : S.invr;
     T* out = side == 0 ? A.Tc : A.Tr;
     const double inv = side == 0 ? (S.sig[src] > 0.0 ? 1.0 / S.sig[src] : 0.0) : 1.0;
     const JT* col = side == 0 ? S.Mx + src * KP : S.Zm + src * KP;
@@ -214,7 +243,7 @@ __global__ void __launch_bounds__(512, 1) core_kernel(CoreArgs<T> A) {
     for (int i = k - 1; i >= 0; --i) {
       double acc = (double)col[i] * inv;
       for (int j = i + 1; j < k; ++j) acc -= L[j * KP + i] * xs[j];
-      xs[i] = acc / L[i * KP + i];
+      xs[i] = acc * inv_diag[i];
     }
     for (int i = 0; i < k; ++i) out[i + (size_t)p * KMAX] = (T)xs[i];
   }
@@ -227,13 +256,13 @@ cudaError_t launch_core(const CoreArgs<T>& a, bool jacobi_fp32, cudaStream_t st)
     const size_t sm = sizeof(CoreSmem<float>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<1, 512, sm, st>>>(a);
+    kern<<<1, 256, sm, st>>>(a);
   } else {
     auto kern = core_kernel<T, double>;
     const size_t sm = sizeof(CoreSmem<double>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    kern<<<1, 512, sm, st>>>(a);
+    kern<<<1, 256, sm, st>>>(a);
   }
   return cudaGetLastError();
 }

@@ -11,18 +11,22 @@
 //   ||S_k||^2 += 2 sum_{l<k} d_l d (C_l.c)(R_l.r) + d^2 |c|^2 |r|^2
 //   stop after two consecutive steps with |d| |c| |r| <= tol ||S_k||, then a
 //   splitmix64-drawn probe of residual entries (restart at a bad probe's row).
-// The Gram entries C_l.c and R_l.r are kept (FP64) for the rounding.
+// The Gram entries C_l.c and R_l.r are kept for the rounding.
 //
 // One persistent launch per solve: a thread-block cluster of CS CTAs
-// (CS <= 16) splits the index range 0..m-1 into CS contiguous slices; each
-// thread owns up to RPT indices of its CTA's slice for both the row and the
-// column side.  A half-step is: broadcast row/coefficient vectors, evaluate the
-// owned residual entries, reduce (argmax, sum of squares, k dot products) with
-// warp shuffles and shared memory, publish the CTA partial in shared memory,
-// one cluster barrier, then every CTA reads all partials through distributed
-// shared memory in rank order, so every CTA takes the same decision with the
-// same arithmetic.  Partials are double-buffered by half-step parity, which
-// makes one barrier per half-step enough.
+// (CS <= 16) splits the index range 0..m-1 into CS contiguous slices of S
+// indices; each thread owns up to RPT indices of its CTA's slice for both the
+// row and the column side.  The CTA keeps its slices of Uh, Vh, of the symbol
+// and of the first KS skeleton columns in shared memory (column-major, so a
+// warp reads 32 consecutive words), so a half-step touches global memory only
+// for skeleton columns beyond KS.  Pivot rows are read from the owning CTA's
+// shared memory through distributed shared memory.  A half-step is:
+// broadcast, evaluate the owned residual entries, reduce (argmax, sum of
+// squares, k dot products) with warp shuffles, publish the CTA partial, one
+// cluster barrier, then every CTA reduces all partials (one lane per CTA) in
+// the same order, so every CTA takes the same decision with the same
+// arithmetic.  Partials are double-buffered by half-step parity, which makes
+// one barrier per half-step enough.
 #include <cooperative_groups.h>
 
 #include <climits>
@@ -33,10 +37,13 @@ namespace cg = cooperative_groups;
 
 namespace lrp {
 
+// Reductions accumulate in the working precision T: the float path never
+// issues FP64 arithmetic per thread (GB300 runs FP64 at a small fraction of
+// the FP32 rate); sums are widened to FP64 only where they are stored.
 template <typename T>
 struct Partial {
-  double sumsq;
-  double dots[KMAX];
+  T sumsq;
+  T dots[KMAX];
   T absmax;
   T val;
   int idx;
@@ -62,128 +69,344 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& a, int& i, T& v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T oa = __shfl_xor_sync(0xffffffffu, a, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+    if (better(oa, oi, a, i)) { a = oa; i = oi; v = ov; }
+  }
+}
+
+template <typename T>
 struct Shared {
-  double wdots[32][KMAX];
-  double wsum[32];
-  double d[KMAX];        // pivot values (identical copy in every CTA)
-  double dots[KMAX];     // cluster-reduced dot products of the last half-step
-  double gc[KMAX];       // C_l . c of the current step
-  double gr[KMAX];       // R_l . r of the current step
-  double sumsq, val;
+  T wdots[KMAX][32];       // per-warp dot partials, [l][warp]
+  T wsum[32];
+  T wabs[32], wval[32];
+  int widx[32];
+  T d[KMAX];               // pivot values (identical copy in every CTA)
+  T dots[KMAX];            // cluster-reduced dot products of the last half-step
+  T gr[KMAX];              // R_l . r of the current step
+  T vec[KMAX];             // broadcast row of Uh or Vh
+  T coef[KMAX];            // broadcast coefficients
+  T piv_a, piv_b;          // symbol at the pivot index
+  double probe[32];
+  int probe_row[32];
+  T sumsq, val;
+  T norm2;                 // ||S_k||_F^2 of the skeleton
+  T rsq;                   // |rho|^2 of the current step
+  T delta;                 // pivot value of the current step
   int idx;
   int flag;
+  int small;               // consecutive small terms
 };
 
-// Reduce over the CTA and then the cluster: argmax |v| among candidates
-// (lowest index on ties), sum of v^2 and dots[l] = sum v * X[:, l], l < k.
-// Results land in sh.idx (-1 if no candidate), sh.val, sh.sumsq, sh.dots.
+// Dynamic shared-memory layout (identical in every CTA of the cluster).
+// Every cached column has SP = blockDim.x * RPT entries (the CTA's S indices
+// plus neutral padding), and thread t owns entries RPT*t .. RPT*t + RPT - 1,
+// so a thread reads its rows of a column with one vector load.
+template <typename T>
+struct Cache {
+  T* U;  // SP * r (if cache_uv)
+  T* V;
+  T* a;  // SP
+  T* b;
+  T* C;  // SP * KS
+  T* R;
+  unsigned char* used_r;  // SP
+  unsigned char* used_c;
+};
+
+template <typename T>
+__device__ __forceinline__ Cache<T> carve(unsigned char* base, int SP, int r, int KS, bool cache_uv) {
+  Cache<T> c;
+  T* p = reinterpret_cast<T*>(base);
+  c.U = p; p += cache_uv ? (size_t)SP * r : 0;
+  c.V = p; p += cache_uv ? (size_t)SP * r : 0;
+  c.a = p; p += SP;
+  c.b = p; p += SP;
+  c.C = p; p += (size_t)SP * KS;
+  c.R = p; p += (size_t)SP * KS;
+  c.used_r = reinterpret_cast<unsigned char*>(p);
+  c.used_c = c.used_r + SP;
+  return c;
+}
+
+// RPT consecutive entries starting at p (p aligned to RPT * sizeof(T), at
+// most 16 bytes per access).
 template <typename T, int RPT>
-__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, const T (&v)[RPT],
+__device__ __forceinline__ void ld_rows(const T* p, T (&x)[RPT]) {
+  constexpr int B = RPT * (int)sizeof(T);
+  if constexpr (B >= 16) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i) {
+      const float4 q = reinterpret_cast<const float4*>(p)[i];
+      const T* t = reinterpret_cast<const T*>(&q);
+#pragma unroll
+      for (int j = 0; j < 16 / (int)sizeof(T); ++j) x[i * (16 / (int)sizeof(T)) + j] = t[j];
+    }
+  } else if constexpr (B == 8) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    const T* t = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) x[j] = t[j];
+  } else {
+    x[0] = p[0];
+  }
+}
+
+// Own-row entries of column l of a skeleton factor: shared cache for l < KS,
+// global memory otherwise.
+template <typename T, int RPT>
+__device__ __forceinline__ void own_col(const T* Xs, const T* Xg, int SP, int ld, int KS, int l,
+                                        const int (&e)[RPT], const bool (&ok)[RPT], T (&x)[RPT]) {
+  if (l < KS) {
+    ld_rows<T, RPT>(Xs + (size_t)l * SP + RPT * threadIdx.x, x);
+  } else {
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) x[s] = ok[s] ? __ldcg(&Xg[e[s] + (size_t)l * ld]) : T(0);
+  }
+}
+
+template <typename T> __device__ __forceinline__ T ratio(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float ratio<float>(float a, float b) { return __fdividef(a, b); }
+
+// Sum over the warp of a[i], i < W, for every i at once (recursive halving:
+// at each stage a lane keeps one half of its vector and receives the
+// partner's copy of that half).  Afterwards every lane L holds the sum for
+// index L mod W.  W - 1 + log2(32/W) shuffles instead of 5 W; the addition
+// pattern is fixed, so every CTA gets the same bits.
+template <typename T, int W>
+__device__ __forceinline__ T warp_transpose_sum(T (&a)[W], int lane) {
+#pragma unroll
+  for (int h = W / 2; h >= 1; h >>= 1) {
+    const bool up = (lane & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? a[i] : a[i + h];
+      const T keep = up ? a[i + h] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  T x = a[0];
+#pragma unroll
+  for (int o = W; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Warp partials of dots[l] = sum over own rows of X[row, l] v[row] for
+// l in [l0, l0 + W) with l < k.
+template <typename T, int RPT, int W>
+__device__ __forceinline__ void warp_dots(const T (&v)[RPT], const bool (&ok)[RPT], const int (&e)[RPT],
+                                          const T* Xs, const T* Xg, int SP, int ld, int KS, int l0, int k,
+                                          Shared<T>& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T a[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    a[i] = T(0);
+    const int l = l0 + i;
+    if (l < k) {
+      T x[RPT];
+      own_col<T, RPT>(Xs, Xg, SP, ld, KS, l, e, ok, x);
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) a[i] += x[s] * v[s];
+    }
+  }
+  const T x = warp_transpose_sum<T, W>(a, lane);
+  if (lane < W && l0 + lane < k) sh.wdots[l0 + lane][warp] = x;
+}
+
+// Reduce over the CTA and then the cluster: argmax |v| among candidates
+// (lowest index on ties), sum of v^2 and dots[l] = sum v * X[own row, l], l < k.
+// Results land in sh.idx (-1 if no candidate), sh.val, sh.sumsq, sh.dots.
+// v must be 0 for rows that are not owned (ok false).
+template <typename T, int RPT>
+__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, int SP, const T (&v)[RPT],
                                                const bool (&ok)[RPT], const bool (&cand)[RPT],
-                                               const int (&e)[RPT], const T* __restrict__ X, int ld,
-                                               int k, Partial<T>* xb, int& par, Shared& sh,
-                                               T* wabs, T* wval, int* widx) {
+                                               const int (&e)[RPT], const T* Xs, const T* Xg, int ld,
+                                               int KS, int k, Partial<T>* xb, int& par, Shared<T>& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
   T babs = T(-1), bval = T(0), ssq = T(0);
   int bidx = INT_MAX;
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    if (!ok[s]) continue;
     ssq += v[s] * v[s];
     if (cand[s]) {
       const T av = fabs(v[s]);
       if (better(av, e[s], babs, bidx)) { babs = av; bidx = e[s]; bval = v[s]; }
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const T oa = __shfl_xor_sync(0xffffffffu, babs, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-    const T ov = __shfl_xor_sync(0xffffffffu, bval, o);
-    if (better(oa, oi, babs, bidx)) { babs = oa; bidx = oi; bval = ov; }
-  }
+  warp_argmax(babs, bidx, bval);
   ssq = warp_sum(ssq);
-  for (int l = 0; l < k; ++l) {
-    T acc = T(0);
-#pragma unroll
-    for (int s = 0; s < RPT; ++s)
-      if (ok[s]) acc += X[e[s] + (size_t)l * ld] * v[s];
-    acc = warp_sum(acc);
-    if (lane == 0) sh.wdots[warp][l] = (double)acc;
-  }
-  if (lane == 0) { wabs[warp] = babs; widx[warp] = bidx; wval[warp] = bval; sh.wsum[warp] = (double)ssq; }
+  // 16-wide chunks: 16 shuffles per chunk, and a 16-entry register buffer
+  // keeps the register pressure low when a thread owns several rows.
+  if (k > 0 && k <= 8) warp_dots<T, RPT, 8>(v, ok, e, Xs, Xg, SP, ld, KS, 0, k, sh);
+  else
+    for (int l0 = 0; l0 < k; l0 += 16) warp_dots<T, RPT, 16>(v, ok, e, Xs, Xg, SP, ld, KS, l0, k, sh);
+  if (lane == 0) { sh.wabs[warp] = babs; sh.widx[warp] = bidx; sh.wval[warp] = bval; sh.wsum[warp] = ssq; }
   __syncthreads();
   Partial<T>& P = xb[par];
-  if (tid == 0) {
-    T ba = T(-1), bv = T(0);
-    int bi = INT_MAX;
-    double ss = 0.0;
-    for (int w = 0; w < NW; ++w) {
-      if (better(wabs[w], widx[w], ba, bi)) { ba = wabs[w]; bi = widx[w]; bv = wval[w]; }
-      ss += sh.wsum[w];
-    }
-    P.absmax = ba; P.idx = bi; P.val = bv; P.sumsq = ss;
+  if (warp == 0) {
+    T a = lane < NW ? sh.wabs[lane] : T(-1);
+    int i = lane < NW ? sh.widx[lane] : INT_MAX;
+    T vv = lane < NW ? sh.wval[lane] : T(0);
+    T ss = lane < NW ? sh.wsum[lane] : T(0);
+    warp_argmax(a, i, vv);
+    ss = warp_sum(ss);
+    if (lane == 0) { P.absmax = a; P.idx = i; P.val = vv; P.sumsq = ss; }
   }
-  for (int l = tid; l < k; l += blockDim.x) {
-    double acc = 0.0;
-    for (int w = 0; w < NW; ++w) acc += sh.wdots[w][l];
-    P.dots[l] = acc;
+  // CTA sums of the dots: one l per half-warp of 16 lanes, lane w reads warp
+  // w's partial (at most 16 warps).
+  for (int base = warp * 32; base < k * 16; base += (int)blockDim.x) {
+    const int t = base + lane, l = t >> 4, w = t & 15;
+    T x = (t < k * 16 && w < NW) ? sh.wdots[l][w] : T(0);
+    x += __shfl_xor_sync(0xffffffffu, x, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    if (w == 0 && t < k * 16) P.dots[l] = x;
   }
   cl.sync();
-  if (tid == 0) {
-    T ba = T(-1), bv = T(0);
-    int bi = INT_MAX;
-    double ss = 0.0;
-    for (int rk = 0; rk < CS; ++rk) {
-      const Partial<T>* Q = cl.map_shared_rank(&xb[par], rk);
-      const T qa = Q->absmax;
-      const int qi = Q->idx;
-      if (better(qa, qi, ba, bi)) { ba = qa; bi = qi; bv = Q->val; }
-      ss += Q->sumsq;
+  if (warp == 0) {
+    T a = T(-1), vv = T(0), ss = T(0);
+    int i = INT_MAX;
+    if (lane < CS) {
+      const Partial<T>* Q = cl.map_shared_rank(&xb[par], lane);
+      a = Q->absmax; i = Q->idx; vv = Q->val; ss = Q->sumsq;
     }
-    sh.idx = (bi == INT_MAX || ba < T(0)) ? -1 : bi;
-    sh.val = (double)bv;
-    sh.sumsq = ss;
+    warp_argmax(a, i, vv);
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      sh.idx = (i == INT_MAX || a < T(0)) ? -1 : i;
+      sh.val = vv;
+      sh.sumsq = ss;
+    }
   }
-  for (int l = tid; l < k; l += blockDim.x) {
-    double acc = 0.0;
-    for (int rk = 0; rk < CS; ++rk) acc += cl.map_shared_rank(&xb[par], rk)->dots[l];
-    sh.dots[l] = acc;
+  // Cluster sums of the dots: one l per half-warp, lane q reads CTA q.
+  for (int base = warp * 32; base < k * 16; base += (int)blockDim.x) {
+    const int t = base + lane, l = t >> 4, qq = t & 15;
+    T x = (t < k * 16 && qq < CS) ? cl.map_shared_rank(&xb[par], qq)->dots[l] : T(0);
+    x += __shfl_xor_sync(0xffffffffu, x, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    if (qq == 0 && t < k * 16) sh.dots[l] = x;
   }
   __syncthreads();
   par ^= 1;
 }
 
+// Load the broadcast vectors of a half-step at pivot index p: vec = F[p, :r]
+// (F = Uh or Vh), coef[l] = X[p, l] (X = C or R, l < k) times the pivot
+// weights, and the symbol at p.  Values cached in the owner CTA's shared
+// memory are read through distributed shared memory.
+template <typename T>
+__device__ __forceinline__ void load_broadcast(cg::cluster_group& cl, int S, int SP, int p, int r, int k,
+                                               int KS, bool cache_uv, const Cache<T>& cc, const T* Fs,
+                                               const T* __restrict__ Fg, const T* Xs, const T* Xg, int ld,
+                                               Shared<T>& sh) {
+  const int owner = p / S, loc = p - owner * S;
+  const int tid = threadIdx.x;
+  if (tid < r) {
+    sh.vec[tid] = cache_uv ? *cl.map_shared_rank(Fs + (size_t)tid * SP + loc, owner) : Fg[p + (size_t)tid * ld];
+  } else if (tid >= KMAX && tid < KMAX + k) {
+    const int l = tid - KMAX;
+    const T x = l < KS ? *cl.map_shared_rank(Xs + (size_t)l * SP + loc, owner) : __ldcg(&Xg[p + (size_t)l * ld]);
+    sh.coef[l] = x * sh.d[l];
+  } else if (tid == 2 * KMAX) {
+    sh.piv_a = *cl.map_shared_rank(cc.a + loc, owner);
+    sh.piv_b = *cl.map_shared_rank(cc.b + loc, owner);
+  }
+  __syncthreads();
+}
+
+// Residual entries of the owned indices for a half-step at a pivot with
+// broadcast vectors in sh: out[s] = (sum_al vec[al] F[own, al]) /
+// (pa * b_own + pb * a_own) - sum_l coef[l] X[own, l].
 template <typename T, int RPT>
-__global__ void __launch_bounds__(1024, 1) cross_kernel(CrossArgs<T> A) {
+__device__ __forceinline__ void eval_entries(const Shared<T>& sh, const Cache<T>& cc, const T* Fs,
+                                             const T* __restrict__ Fg, const T* Xs, const T* Xg, int SP,
+                                             int ld, int r, int k, int KS, bool cache_uv, const int (&e)[RPT],
+                                             const bool (&ok)[RPT], T (&out)[RPT]) {
+  const int base = RPT * threadIdx.x;
+  T num[RPT];
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) num[s] = T(0);
+  for (int al = 0; al < r; ++al) {
+    T f[RPT];
+    if (cache_uv) {
+      ld_rows<T, RPT>(Fs + (size_t)al * SP + base, f);
+    } else {
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) f[s] = ok[s] ? Fg[e[s] + (size_t)al * ld] : T(0);
+    }
+    const T w = sh.vec[al];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) num[s] += w * f[s];
+  }
+  T av[RPT], bv[RPT];
+  ld_rows<T, RPT>(cc.a + base, av);
+  ld_rows<T, RPT>(cc.b + base, bv);
+  const T pa = sh.piv_a, pb = sh.piv_b;
+#pragma unroll
+  for (int s = 0; s < RPT; ++s) out[s] = ratio<T>(num[s], pa * bv[s] + pb * av[s]);
+  for (int l = 0; l < k; ++l) {
+    T x[RPT];
+    own_col<T, RPT>(Xs, Xg, SP, ld, KS, l, e, ok, x);
+    const T c = sh.coef[l];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) out[s] -= c * x[s];
+  }
+#pragma unroll
+  for (int s = 0; s < RPT; ++s)
+    if (!ok[s]) out[s] = T(0);
+}
+
+template <typename T, int RPT>
+__global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, int cache_uv_i) {
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank();
   const int CS = (int)cl.num_blocks();
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int m = A.m, r = A.r, ld = A.ld;
   const int S = (m + CS - 1) / CS;
+  const int SP = NT * RPT;  // >= S
   const int row0 = min(m, q * S), row1 = min(m, row0 + S);
+  const bool cache_uv = cache_uv_i != 0;
+  const T tol2 = (T)(A.tol * A.tol);
 
   __shared__ Partial<T> xb[2];
-  __shared__ Shared sh;
-  __shared__ T wabs[32], wval[32];
-  __shared__ int widx[32];
-  __shared__ T s_vec[KMAX];
-  __shared__ T s_coef[KMAX];
-  __shared__ double s_probe[32];
-  __shared__ int s_probe_row[32];
-  extern __shared__ unsigned char used[];  // [0, S): rows, [S, 2S): columns
-  unsigned char* used_r = used;
-  unsigned char* used_c = used + S;
+  __shared__ Shared<T> sh;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const Cache<T> cc = carve<T>(dyn, SP, r, KS, cache_uv);
 
-  for (int i = tid; i < 2 * S; i += NT) used[i] = 0;
+  // Fill the caches (neutral values past the end of the index range).
+  for (int i = tid; i < SP; i += NT) {
+    const int e = row0 + i;
+    const bool in = e < row1;
+    cc.a[i] = in ? A.a[e] : T(1);
+    cc.b[i] = in ? A.b[e] : T(1);
+    cc.used_r[i] = 0;
+    cc.used_c[i] = 0;
+    if (cache_uv)
+      for (int al = 0; al < r; ++al) {
+        cc.U[(size_t)al * SP + i] = in ? A.Uh[e + (size_t)al * ld] : T(0);
+        cc.V[(size_t)al * SP + i] = in ? A.Vh[e + (size_t)al * ld] : T(0);
+      }
+  }
+  for (int i = tid; i < SP * KS; i += NT) { cc.C[i] = T(0); cc.R[i] = T(0); }
+  if (tid == 0) { sh.norm2 = T(0); sh.small = 0; }
+  __syncthreads();
 
   int e[RPT];
   bool ok[RPT], cand[RPT];
   T v[RPT], score[RPT];
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    e[s] = row0 + tid + s * NT;
+    e[s] = row0 + RPT * tid + s;
     ok[s] = e[s] < row1;
   }
   const T a0 = A.a[0], b0 = A.b[0];
@@ -192,123 +415,104 @@ __global__ void __launch_bounds__(1024, 1) cross_kernel(CrossArgs<T> A) {
   for (int s = 0; s < RPT; ++s) {
     score[s] = T(0);
     if (ok[s]) {
+      const int loc = RPT * tid + s;
       T acc = T(0);
       for (int al = 0; al < r; ++al) {
-        const T u = A.Uh[e[s] + (size_t)al * ld];
+        const T u = cache_uv ? cc.U[(size_t)al * SP + loc] : A.Uh[e[s] + (size_t)al * ld];
         acc += u * u;
       }
-      const T lam0 = A.a[e[s]] * b0 + A.b[e[s]] * a0;
+      const T lam0 = cc.a[loc] * b0 + cc.b[loc] * a0;
       score[s] = acc / (lam0 * lam0);
     }
     cand[s] = ok[s];
   }
-  __syncthreads();
   int par = 0;
-  cluster_reduce<T, RPT>(cl, CS, score, ok, cand, e, A.C, ld, 0, xb, par, sh, wabs, wval, widx);
+  cluster_reduce<T, RPT>(cl, CS, SP, score, ok, cand, e, cc.C, A.C, ld, KS, 0, xb, par, sh);
   int istar = sh.idx;
 
-  double norm2 = 0.0;
-  int k = 0, small = 0, probe_rounds = 0, zero_rows = 0;
+  int k = 0, probe_rounds = 0, zero_rows = 0;
   int converged = 0;
   while (k < A.kcap && istar >= 0) {
     // ---------------- row half-step at istar
-    for (int al = tid; al < r; al += NT) s_vec[al] = A.Uh[istar + (size_t)al * ld];
-    for (int l = tid; l < k; l += NT) s_coef[l] = (T)((double)__ldcg(&A.C[istar + (size_t)l * ld]) * sh.d[l]);
-    __syncthreads();
-    {
-      const T ai = A.a[istar], bi = A.b[istar];
+    load_broadcast<T>(cl, S, SP, istar, r, k, KS, cache_uv, cc, cc.U, A.Uh, cc.C, A.C, ld, sh);
+    eval_entries<T, RPT>(sh, cc, cc.V, A.Vh, cc.R, A.R, SP, ld, r, k, KS, cache_uv, e, ok, v);
 #pragma unroll
-      for (int s = 0; s < RPT; ++s) {
-        v[s] = T(0);
-        if (!ok[s]) continue;
-        const int j = e[s];
-        T num = T(0);
-        for (int al = 0; al < r; ++al) num += s_vec[al] * A.Vh[j + (size_t)al * ld];
-        T x = num / (ai * A.b[j] + bi * A.a[j]);
-        for (int l = 0; l < k; ++l) x -= s_coef[l] * A.R[j + (size_t)l * ld];
-        v[s] = x;
-        cand[s] = used_c[j - row0] == 0;
-      }
-    }
-    if (istar >= row0 && istar < row1 && tid == 0) used_r[istar - row0] = 1;
-    cluster_reduce<T, RPT>(cl, CS, v, ok, cand, e, A.R, ld, k, xb, par, sh, wabs, wval, widx);
+    for (int s = 0; s < RPT; ++s) cand[s] = ok[s] && cc.used_c[RPT * tid + s] == 0;
+    if (istar >= row0 && istar < row1 && tid == 0) cc.used_r[istar - row0] = 1;
+    cluster_reduce<T, RPT>(cl, CS, SP, v, ok, cand, e, cc.R, A.R, ld, KS, k, xb, par, sh);
     const int jstar = sh.idx;
-    const double delta = jstar >= 0 ? sh.val : 0.0;
-    if (delta == 0.0) {
+    if (tid == 0) {
+      const T dv = jstar >= 0 ? sh.val : T(0);
+      sh.flag = dv == T(0);
+      sh.delta = dv;
+      sh.rsq = sh.sumsq;
+      if (jstar >= row0 && jstar < row1) cc.used_c[jstar - row0] = 1;
+    }
+    __syncthreads();
+    if (sh.flag) {
       // The row is already represented exactly: move to the best-scored
       // unused row (rows are marked used above).
       ++zero_rows;
 #pragma unroll
-      for (int s = 0; s < RPT; ++s) cand[s] = ok[s] && used_r[e[s] - row0] == 0;
-      __syncthreads();
-      cluster_reduce<T, RPT>(cl, CS, score, ok, cand, e, A.C, ld, 0, xb, par, sh, wabs, wval, widx);
+      for (int s = 0; s < RPT; ++s) cand[s] = ok[s] && cc.used_r[RPT * tid + s] == 0;
+      cluster_reduce<T, RPT>(cl, CS, SP, score, ok, cand, e, cc.C, A.C, ld, KS, 0, xb, par, sh);
       if (zero_rows > A.max_zero_rows || sh.idx < 0) { converged = 1; break; }
       istar = sh.idx;
       continue;
     }
-    const double rsq = sh.sumsq;
-    for (int l = tid; l < k; l += NT) sh.gr[l] = sh.dots[l] / delta;
-    if (jstar >= row0 && jstar < row1 && tid == 0) used_c[jstar - row0] = 1;
     // ---------------- column half-step at jstar
-    const T tdelta = (T)delta;
+    const T tdelta = sh.delta;
+    for (int l = tid; l < k; l += NT) sh.gr[l] = sh.dots[l] / tdelta;
 #pragma unroll
-    for (int s = 0; s < RPT; ++s)
-      if (ok[s]) A.R[e[s] + (size_t)k * ld] = v[s] / tdelta;
-    for (int al = tid; al < r; al += NT) s_vec[al] = A.Vh[jstar + (size_t)al * ld];
-    for (int l = tid; l < k; l += NT) s_coef[l] = (T)(sh.d[l] * (double)__ldcg(&A.R[jstar + (size_t)l * ld]));
-    __syncthreads();
-    {
-      const T aj = A.a[jstar], bj = A.b[jstar];
-#pragma unroll
-      for (int s = 0; s < RPT; ++s) {
-        v[s] = T(0);
-        if (!ok[s]) continue;
-        const int i = e[s];
-        T num = T(0);
-        for (int al = 0; al < r; ++al) num += A.Uh[i + (size_t)al * ld] * s_vec[al];
-        T x = num / (A.a[i] * bj + A.b[i] * aj);
-        for (int l = 0; l < k; ++l) x -= A.C[i + (size_t)l * ld] * s_coef[l];
-        x = x / tdelta;
-        v[s] = x;
-        A.C[i + (size_t)k * ld] = x;
-        cand[s] = used_r[i - row0] == 0;
-      }
+    for (int s = 0; s < RPT; ++s) {
+      if (!ok[s]) continue;
+      const T rv = v[s] / tdelta;
+      if (k < KS) cc.R[(size_t)k * SP + RPT * tid + s] = rv;
+      A.R[e[s] + (size_t)k * ld] = rv;
     }
-    cluster_reduce<T, RPT>(cl, CS, v, ok, cand, e, A.C, ld, k, xb, par, sh, wabs, wval, widx);
+    // (column k of R is read by other CTAs only after later cluster barriers)
+    load_broadcast<T>(cl, S, SP, jstar, r, k, KS, cache_uv, cc, cc.V, A.Vh, cc.R, A.R, ld, sh);
+    eval_entries<T, RPT>(sh, cc, cc.U, A.Uh, cc.C, A.C, SP, ld, r, k, KS, cache_uv, e, ok, v);
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      v[s] = v[s] / tdelta;
+      cand[s] = ok[s] && cc.used_r[RPT * tid + s] == 0;
+      if (!ok[s]) continue;
+      if (k < KS) cc.C[(size_t)k * SP + RPT * tid + s] = v[s];
+      A.C[e[s] + (size_t)k * ld] = v[s];
+    }
+    cluster_reduce<T, RPT>(cl, CS, SP, v, ok, cand, e, cc.C, A.C, ld, KS, k, xb, par, sh);
     const int inext = sh.idx;
-    const double csq = sh.sumsq;
-    // ---------------- bookkeeping (identical in every CTA)
-    const double rr = rsq / (delta * delta);
-    double cross_sum = 0.0;
+    // ---------------- bookkeeping (thread 0 of every CTA, same arithmetic)
     if (tid == 0) {
-      for (int l = 0; l < k; ++l) cross_sum += sh.d[l] * sh.dots[l] * sh.gr[l];
+      const T delta = sh.delta;
+      const T csq = sh.sumsq;
+      const T rr = sh.rsq / (delta * delta);
+      T cs = T(0);
+      for (int l = 0; l < k; ++l) cs += sh.d[l] * sh.dots[l] * sh.gr[l];
+      sh.norm2 += T(2) * delta * cs + delta * delta * csq * rr;
       sh.d[k] = delta;
-    }
-    if (q == 0) {
-      for (int l = tid; l < k; l += NT) {
-        A.GC[l + (size_t)k * A.kcap] = sh.dots[l];
-        A.GC[k + (size_t)l * A.kcap] = sh.dots[l];
-        A.GR[l + (size_t)k * A.kcap] = sh.gr[l];
-        A.GR[k + (size_t)l * A.kcap] = sh.gr[l];
-      }
-      if (tid == 0) {
-        A.GC[k + (size_t)k * A.kcap] = csq;
-        A.GR[k + (size_t)k * A.kcap] = rr;
-        A.d[k] = delta;
+      const T term2 = delta * delta * csq * rr;       // |d|^2 |c|^2 |r|^2
+      sh.small = (term2 <= tol2 * sh.norm2) ? sh.small + 1 : 0;
+      if (q == 0) {
+        A.GC[k + (size_t)k * A.kcap] = (double)csq;
+        A.GR[k + (size_t)k * A.kcap] = (double)rr;
+        A.d[k] = (double)delta;
         A.I[k] = istar;
         A.J[k] = jstar;
       }
     }
-    if (tid == 0) {
-      norm2 += 2.0 * delta * cross_sum + delta * delta * csq * rr;
-      sh.val = norm2;
-    }
+    if (q == 0)
+      for (int l = tid; l < k; l += NT) {
+        const double gc = (double)sh.dots[l], gr = (double)sh.gr[l];
+        A.GC[l + (size_t)k * A.kcap] = gc;
+        A.GC[k + (size_t)l * A.kcap] = gc;
+        A.GR[l + (size_t)k * A.kcap] = gr;
+        A.GR[k + (size_t)l * A.kcap] = gr;
+      }
     __syncthreads();
-    norm2 = sh.val;
     ++k;
-    const double term = fabs(delta) * sqrt(csq * rr);
-    small = (term <= A.tol * sqrt(fmax(norm2, 0.0))) ? small + 1 : 0;
-    if (small >= 2) {
+    if (sh.small >= 2) {
       if (probe_rounds >= A.max_probe_rounds || A.probes <= 0) { converged = 1; break; }
       // Residual probes at splitmix64-drawn entries; one warp per probe, the
       // same arithmetic in every CTA.
@@ -323,37 +527,37 @@ __global__ void __launch_bounds__(1024, 1) cross_kernel(CrossArgs<T> A) {
         for (int al = lane; al < r; al += 32)
           num += (double)A.Uh[pi + (size_t)al * ld] * (double)A.Vh[pj + (size_t)al * ld];
         for (int l = lane; l < k; l += 32)
-          sk += (double)__ldcg(&A.C[pi + (size_t)l * ld]) * sh.d[l] *
+          sk += (double)__ldcg(&A.C[pi + (size_t)l * ld]) * (double)sh.d[l] *
                 (double)__ldcg(&A.R[pj + (size_t)l * ld]);
         num = warp_sum(num);
         sk = warp_sum(sk);
         const double den = (double)A.a[pi] * (double)A.b[pj] + (double)A.b[pi] * (double)A.a[pj];
-        if (lane == 0) { s_probe[warp] = fabs(num / den - sk); s_probe_row[warp] = pi; }
+        if (lane == 0) { sh.probe[warp] = fabs(num / den - sk); sh.probe_row[warp] = pi; }
       }
       __syncthreads();
       if (tid == 0) {
         double worst = -1.0;
         int wrow = -1;
         for (int p = 0; p < P; ++p)
-          if (s_probe[p] > worst) { worst = s_probe[p]; wrow = s_probe_row[p]; }
-        sh.flag = worst <= A.tol * sqrt(fmax(norm2, 0.0)) ? -1 : wrow;
+          if (sh.probe[p] > worst) { worst = sh.probe[p]; wrow = sh.probe_row[p]; }
+        const double n2 = (double)sh.norm2;
+        sh.flag = worst <= A.tol * sqrt(n2 > 0.0 ? n2 : 0.0) ? -1 : wrow;
+        if (sh.flag >= 0) sh.small = 0;
       }
       __syncthreads();
       ++probe_rounds;
       const int bad_row = sh.flag;
       if (bad_row < 0) { converged = 1; break; }
-      small = 0;
-      // Restart at the bad probe's row if unused, else at the best unused score.
-      bool row_used = false;
-      if (bad_row >= row0 && bad_row < row1) row_used = used_r[bad_row - row0] != 0;
-      // every CTA needs the owner's answer: publish through the score reduction
-#pragma unroll
-      for (int s = 0; s < RPT; ++s) cand[s] = ok[s] && used_r[e[s] - row0] == 0;
+      // Restart at the bad probe's row if unused, else at the best unused
+      // score; the owner's answer reaches every CTA through the reduction.
       T bump[RPT];
 #pragma unroll
-      for (int s = 0; s < RPT; ++s) bump[s] = (ok[s] && e[s] == bad_row && !row_used) ? T(INFINITY) : score[s];
-      __syncthreads();
-      cluster_reduce<T, RPT>(cl, CS, bump, ok, cand, e, A.C, ld, 0, xb, par, sh, wabs, wval, widx);
+      for (int s = 0; s < RPT; ++s) {
+        const bool unused = ok[s] && cc.used_r[RPT * tid + s] == 0;
+        cand[s] = unused;
+        bump[s] = (unused && e[s] == bad_row) ? T(INFINITY) : score[s];
+      }
+      cluster_reduce<T, RPT>(cl, CS, SP, bump, ok, cand, e, cc.C, A.C, ld, KS, 0, xb, par, sh);
       istar = sh.idx;
       if (istar < 0) { converged = 1; break; }
       continue;
@@ -368,16 +572,34 @@ __global__ void __launch_bounds__(1024, 1) cross_kernel(CrossArgs<T> A) {
     A.st->converged = converged;
     A.st->probe_rounds = probe_rounds;
     A.st->zero_rows = zero_rows;
-    A.st->norm2 = norm2;
+    A.st->norm2 = (double)sh.norm2;
   }
-  (void)lane;
 }
 
 template <typename T, int RPT>
-static cudaError_t launch_cross_rpt(const CrossArgs<T>& a, int cs, int nt, size_t dsmem, cudaStream_t st) {
+static cudaError_t launch_cross_rpt(const CrossArgs<T>& a, int cs, int nt, cudaStream_t st) {
   auto kern = cross_kernel<T, RPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  // Shared-memory budget: symbol slices and flags always, Uh/Vh slices if
+  // they fit in half of what is left, then as many skeleton columns as fit.
+  const long long SP = (long long)nt * RPT;
+  const long long w = (long long)sizeof(T);
+  const long long budget = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
+  const long long fixed = 2LL * SP * w + 2LL * SP + 64;
+  const long long uv = 2LL * SP * a.r * w;
+  const bool cache_uv = uv <= (budget - fixed) / 2;
+  const long long left = budget - fixed - (cache_uv ? uv : 0);
+  long long KS = left / (2LL * SP * w);
+  if (KS > a.kcap) KS = a.kcap;
+  if (KS < 0) KS = 0;
+  const size_t dsmem = (size_t)(fixed + (cache_uv ? uv : 0) + 2LL * SP * KS * w);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -396,33 +618,48 @@ static cudaError_t launch_cross_rpt(const CrossArgs<T>& a, int cs, int nt, size_
   e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
   if (e != cudaSuccess) return e;
   if (nclusters < 1) return cudaErrorInvalidConfiguration;
-  return cudaLaunchKernelEx(&cfg, kern, a);
+  return cudaLaunchKernelEx(&cfg, kern, a, (int)KS, cache_uv ? 1 : 0);
+}
+
+// Rows per thread RPT (a power of two) and threads per CTA for S indices:
+// about four rows per thread, 160 to 512 threads (the broadcast uses threads
+// up to 2*KMAX); more rows per thread only when S exceeds 512 * 4.
+static void cross_shape(int S, int* nt, int* rpt) {
+  int r = 1;
+  while (r < 4 && r * 160 < S) r *= 2;
+  while (r < 16 && r * 512 < S) r *= 2;
+  int t = (S + r - 1) / r;
+  t = (t + 31) / 32 * 32;
+  if (t < 160) t = 160;
+  *nt = t;
+  *rpt = r;
 }
 
 template <typename T>
 cudaError_t launch_cross(const CrossArgs<T>& a, int cluster_size, cudaStream_t st, int* used_cluster) {
+  // Largest index range a CTA may own: 512 threads x 16 rows.
+  const int cs_min = (a.m + 512 * 16 - 1) / (512 * 16);
   int cs = cluster_size;
   if (cs <= 0) {
     cs = (a.m + 1023) / 1024;
     if (cs > 16) cs = 16;
-    if (cs < 1) cs = 1;
   }
+  if (cs < cs_min) cs = cs_min;
+  if (cs < 1) cs = 1;
+  if (cs > 16) return cudaErrorInvalidValue;
   cudaError_t e = cudaErrorInvalidConfiguration;
-  for (; cs >= 1; cs = (cs > 8 ? 8 : cs - 1)) {
+  for (; cs >= cs_min && cs >= 1; cs = (cs > 8 ? 8 : cs - 1)) {
     const int S = (a.m + cs - 1) / cs;
-    int nt = ((S + 31) / 32) * 32;
-    if (nt > 1024) nt = 1024;
-    if (nt < 64) nt = 64;
-    const int rpt = (S + nt - 1) / nt;
-    const size_t dsmem = (size_t)((2 * S + 15) / 16) * 16;
-    if (rpt <= 1) e = launch_cross_rpt<T, 1>(a, cs, nt, dsmem, st);
-    else if (rpt <= 2) e = launch_cross_rpt<T, 2>(a, cs, nt, dsmem, st);
-    else if (rpt <= 4) e = launch_cross_rpt<T, 4>(a, cs, nt, dsmem, st);
-    else if (rpt <= 8) e = launch_cross_rpt<T, 8>(a, cs, nt, dsmem, st);
-    else e = cudaErrorInvalidValue;  // m too large for this cluster size
+    int nt, rpt;
+    cross_shape(S, &nt, &rpt);
+    if (rpt == 1) e = launch_cross_rpt<T, 1>(a, cs, nt, st);
+    else if (rpt == 2) e = launch_cross_rpt<T, 2>(a, cs, nt, st);
+    else if (rpt == 4) e = launch_cross_rpt<T, 4>(a, cs, nt, st);
+    else if (rpt == 8) e = launch_cross_rpt<T, 8>(a, cs, nt, st);
+    else e = launch_cross_rpt<T, 16>(a, cs, nt, st);
     if (e == cudaSuccess) { if (used_cluster) *used_cluster = cs; return e; }
-    if (e != cudaErrorInvalidConfiguration && e != cudaErrorInvalidValue &&
-        e != cudaErrorInvalidClusterSize && e != cudaErrorLaunchOutOfResources)
+    if (e != cudaErrorInvalidConfiguration && e != cudaErrorInvalidClusterSize &&
+        e != cudaErrorLaunchOutOfResources)
       return e;
     cudaGetLastError();  // clear the launch-configuration error and retry smaller
   }

@@ -124,7 +124,11 @@ struct ColArgs {
   int ld_out[2];
   int ncol[2];
   const int* dyn_count;
+  const void* tm[2];
+  const int* k_dev;
 };
+
+enum : int { IN_F64 = 0, IN_WORK = 1, IN_ROT = 2 };
 
 __device__ __forceinline__ bool col_live(const ColArgs& c, int col, int& seg, int& cc) {
   seg = col < c.ncol[0] ? 0 : 1;
@@ -134,10 +138,19 @@ __device__ __forceinline__ bool col_live(const ColArgs& c, int col, int& seg, in
   return true;
 }
 
-template <typename T, bool IN64>
+// Element t of input column cc of segment seg.  IN_ROT: the column is the
+// rotation sum_{l<k} X[t, l] Tm[l, cc] of a working-precision skeleton X.
+template <typename T, int INM>
 __device__ __forceinline__ T load_in(const ColArgs& c, int seg, int cc, int t) {
-  if (IN64) return (T)(static_cast<const double*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t]);
-  return static_cast<const T*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t];
+  if (INM == IN_F64) return (T)(static_cast<const double*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t]);
+  if (INM == IN_WORK) return static_cast<const T*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t];
+  const T* X = static_cast<const T*>(c.in[seg]);
+  const T* tm = static_cast<const T*>(c.tm[seg]) + (size_t)cc * KMAX;
+  const int k = *c.k_dev;
+  const int ld = c.ld_in[seg];
+  T acc = T(0);
+  for (int l = 0; l < k; ++l) acc += X[(size_t)l * ld + t] * __ldg(&tm[l]);
+  return acc;
 }
 template <typename T, bool OUT64>
 __device__ __forceinline__ void store_out(const ColArgs& c, int seg, int cc, int t, T v) {
@@ -148,12 +161,20 @@ __device__ __forceinline__ void store_out(const ColArgs& c, int seg, int cc, int
 struct GeomArgs {
   int m, logM, logM1, logM2;
   int ncols;        // total column slots (ncol0 + ncol1)
+  int logTile;      // complex elements per four-step tile (2^logTile)
 };
+
+// Twiddles of a length-2^logL FFT, exp(-2 pi i j / L), copied into shared
+// memory from the length-M table (tw[j * M / L]).
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cpx<T>* twS, const cpx<T>* __restrict__ tw, int logL, int logM) {
+  for (int j = threadIdx.x; j < (1 << logL); j += blockDim.x) twS[j] = tw[(size_t)j << (logM - logL)];
+}
 
 // ---------------------------------------------------------------------------
 // Small path: 2^lognf sequences of length M per CTA.
 // ---------------------------------------------------------------------------
-template <typename T, bool IN64, bool OUT64>
+template <typename T, int INM, bool OUT64>
 __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     const cpx<T>* __restrict__ bhat, int lognf) {
@@ -163,6 +184,8 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
   const int nf = 1 << lognf;
   const int items = (g.ncols + nf - 1) >> lognf;
   const int nelem = nf << g.logM;
+  cpx<T>* twS = buf + nelem;
+  load_twiddles(twS, tw, g.logM, g.logM);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x) {
       const int row = idx >> g.logM, t = idx & (M - 1);
@@ -170,18 +193,18 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
       int seg, cc;
       cpx<T> v = {T(0), T(0)};
       if (col < g.ncols && t < g.m && col_live(c, col, seg, cc)) {
-        const T x = load_in<T, IN64>(c, seg, cc, t);
+        const T x = load_in<T, INM>(c, seg, cc, t);
         const cpx<T> w = chirp[t];
         v = {x * w.re, x * w.im};
       }
       buf[idx] = v;
     }
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM, lognf, 1, M, tw, g.logM, false);
+    smem_fft<T, false>(buf, g.logM, lognf, 1, M, twS, g.logM, false);
     for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x)
       buf[idx] = cmul(buf[idx], bhat[idx & (M - 1)]);
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM, lognf, 1, M, tw, g.logM, true);
+    smem_fft<T, false>(buf, g.logM, lognf, 1, M, twS, g.logM, true);
     for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x) {
       const int row = idx >> g.logM, t = idx & (M - 1);
       const int col = (item << lognf) + row;
@@ -199,36 +222,39 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
 // Four-step path, column passes.  A tile holds TX = 4096 / M2 consecutive t1
 // values and all M2 values of t2 (or k2): tile[t2 * TX + dt1].
 // ---------------------------------------------------------------------------
-template <typename T, bool IN64>
+template <typename T, int INM>
 __global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     cpx<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   const int M1 = 1 << g.logM1;
-  const int logTX = 12 - g.logM2, TX = 1 << logTX;
+  const int tile = 1 << g.logTile;
+  const int logTX = g.logTile - g.logM2, TX = 1 << logTX;
   const int blocks_per_col = M1 >> logTX;
   const int items = g.ncols * blocks_per_col;
+  cpx<T>* twS = buf + tile;
+  load_twiddles(twS, tw, g.logM2, g.logM);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int t1_0 = (item - col * blocks_per_col) << logTX;
     int seg, cc;
     if (!col_live(c, col, seg, cc)) continue;  // uniform across the CTA
-    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
       const int t2 = idx >> logTX, dt = idx & (TX - 1);
       const int t = t1_0 + dt + (t2 << g.logM1);
       cpx<T> v = {T(0), T(0)};
       if (t < g.m) {
-        const T x = load_in<T, IN64>(c, seg, cc, t);
+        const T x = load_in<T, INM>(c, seg, cc, t);
         const cpx<T> w = chirp[t];
         v = {x * w.re, x * w.im};
       }
       buf[idx] = v;
     }
     __syncthreads();
-    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, tw, g.logM, false);
+    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, twS, g.logM2, false);
     cpx<T>* wc = work + ((size_t)col << g.logM);
-    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
       const int k2 = idx >> logTX, dt = idx & (TX - 1);
       const int t1 = t1_0 + dt;
       wc[(k2 << g.logM1) + t1] = cmul(buf[idx], tw[t1 * k2]);
@@ -244,22 +270,25 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   const int M1 = 1 << g.logM1;
-  const int logTX = 12 - g.logM2, TX = 1 << logTX;
+  const int tile = 1 << g.logTile;
+  const int logTX = g.logTile - g.logM2, TX = 1 << logTX;
   const int blocks_per_col = M1 >> logTX;
   const int items = g.ncols * blocks_per_col;
+  cpx<T>* twS = buf + tile;
+  load_twiddles(twS, tw, g.logM2, g.logM);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int t1_0 = (item - col * blocks_per_col) << logTX;
     int seg, cc;
     if (!col_live(c, col, seg, cc)) continue;
     const cpx<T>* wc = work + ((size_t)col << g.logM);
-    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
       const int k2 = idx >> logTX, dt = idx & (TX - 1);
       buf[idx] = wc[(k2 << g.logM1) + t1_0 + dt];
     }
     __syncthreads();
-    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, tw, g.logM, true);
-    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, twS, g.logM2, true);
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
       const int t2 = idx >> logTX, dt = idx & (TX - 1);
       const int t = t1_0 + dt + (t2 << g.logM1);
       if (t < g.m) {
@@ -279,9 +308,12 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   const int M1 = 1 << g.logM1, M2 = 1 << g.logM2;
-  const int logRY = 12 - g.logM1;
+  const int tile = 1 << g.logTile;
+  const int logRY = g.logTile - g.logM1;
   const int blocks_per_col = M2 >> logRY;
   const int items = g.ncols * blocks_per_col;
+  cpx<T>* twS = buf + tile;
+  load_twiddles(twS, tw, g.logM1, g.logM);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int k2_0 = (item - col * blocks_per_col) << logRY;
@@ -289,13 +321,13 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
     if (!col_live(c, col, seg, cc)) continue;
     cpx<T>* wc = work + ((size_t)col << g.logM) + ((size_t)k2_0 << g.logM1);
     const cpx<T>* bh = bhat + ((size_t)k2_0 << g.logM1);
-    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) buf[idx] = wc[idx];
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) buf[idx] = wc[idx];
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, tw, g.logM, false);
-    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) buf[idx] = cmul(buf[idx], bh[idx]);
+    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, twS, g.logM1, false);
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) buf[idx] = cmul(buf[idx], bh[idx]);
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, tw, g.logM, true);
-    for (int idx = threadIdx.x; idx < kTileElems; idx += blockDim.x) {
+    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, twS, g.logM1, true);
+    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
       const int k2 = k2_0 + (idx >> g.logM1), t1 = idx & (M1 - 1);
       wc[idx] = cmulc(buf[idx], tw[t1 * k2]);  // times exp(+2 pi i t1 k2 / M)
     }
@@ -311,7 +343,7 @@ static const TablesT& tables_of(const Plan& p);
 template <> const TablesT& tables_of<double>(const Plan& p) { return p.t64; }
 template <> const TablesT& tables_of<float>(const Plan& p) { return p.t32; }
 
-template <typename T, bool IN64, bool OUT64>
+template <typename T, int INM, bool OUT64>
 static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs& g, void* work,
                                 int num_sms, cudaStream_t st) {
   const TablesT& tb = tables_of<T>(p);
@@ -329,28 +361,36 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
     while ((M << (lognf + 1)) <= kTileElems && (g.ncols >> (lognf + 1)) >= 2 * num_sms) ++lognf;
     const int nelem = M << lognf;
     const int threads = nelem / EPT;
-    const size_t smem = (size_t)nelem * sizeof(cpx<T>);
+    const size_t smem = (size_t)(nelem + M) * sizeof(cpx<T>);
     const int items = (g.ncols + (1 << lognf) - 1) >> lognf;
     const int grid = items < 8 * num_sms ? items : 8 * num_sms;
-    auto kern = dst_small_kernel<T, IN64, OUT64>;
+    auto kern = dst_small_kernel<T, INM, OUT64>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, threads, smem, st>>>(c, g, chirp, tw, bhat, lognf);
     return cudaGetLastError();
   }
-  const size_t smem = (size_t)kTileElems * sizeof(cpx<T>);
-  const int items_col = g.ncols * ((1 << g.logM1) >> (12 - g.logM2));
-  const int items_row = g.ncols * ((1 << g.logM2) >> (12 - g.logM1));
+  // Tile of 4096 elements, halved (down to 1024, and not below either
+  // sub-length) while that still leaves fewer than two tiles per SM.
+  GeomArgs g2 = g;
+  g2.logTile = 12;
+  const int logMin = g.logM1 > 10 ? g.logM1 : 10;
+  while (g2.logTile > logMin && (g.ncols << (g.logM - g2.logTile)) < 2 * num_sms) --g2.logTile;
+  const int tile = 1 << g2.logTile;
+  const int threads = tile / EPT;
+  const size_t smem = (size_t)(tile + (1 << g.logM1)) * sizeof(cpx<T>);
+  const int items_col = g.ncols * ((1 << g.logM1) >> (g2.logTile - g.logM2));
+  const int items_row = g.ncols * ((1 << g.logM2) >> (g2.logTile - g.logM1));
   const int cap = 8 * num_sms;
   cpx<T>* wk = static_cast<cpx<T>*>(work);
-  auto k1 = dst_col_fwd_kernel<T, IN64>;
+  auto k1 = dst_col_fwd_kernel<T, INM>;
   auto k2 = dst_row_mid_kernel<T>;
   auto k3 = dst_col_inv_kernel<T, OUT64>;
   cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k1<<<items_col < cap ? items_col : cap, kFftThreads, smem, st>>>(c, g, chirp, tw, wk);
-  k2<<<items_row < cap ? items_row : cap, kFftThreads, smem, st>>>(c, g, tw, bhat, wk);
-  k3<<<items_col < cap ? items_col : cap, kFftThreads, smem, st>>>(c, g, chirp, tw, wk);
+  k1<<<items_col < cap ? items_col : cap, threads, smem, st>>>(c, g2, chirp, tw, wk);
+  k2<<<items_row < cap ? items_row : cap, threads, smem, st>>>(c, g2, tw, bhat, wk);
+  k3<<<items_col < cap ? items_col : cap, threads, smem, st>>>(c, g2, chirp, tw, wk);
   return cudaGetLastError();
 }
 
@@ -366,13 +406,21 @@ cudaError_t launch_dst(const Plan& p, const ColumnSet& cs, IoType in_t, IoType o
     c.ncol[s] = cs.ncol[s];
   }
   c.dyn_count = cs.dyn_count;
-  GeomArgs g{p.m, p.logM, p.logM1, p.logM2, cs.ncol[0] + cs.ncol[1]};
+  c.tm[0] = cs.tm[0];
+  c.tm[1] = cs.tm[1];
+  c.k_dev = cs.k_dev;
+  GeomArgs g{p.m, p.logM, p.logM1, p.logM2, cs.ncol[0] + cs.ncol[1], 12};
   if (g.ncols == 0) return cudaSuccess;
-  const bool i64 = in_t == IoType::F64, o64 = out_t == IoType::F64;
-  if (i64 && o64) return launch_dst_t<T, true, true>(p, c, g, work, num_sms, st);
-  if (i64 && !o64) return launch_dst_t<T, true, false>(p, c, g, work, num_sms, st);
-  if (!i64 && o64) return launch_dst_t<T, false, true>(p, c, g, work, num_sms, st);
-  return launch_dst_t<T, false, false>(p, c, g, work, num_sms, st);
+  const bool o64 = out_t == IoType::F64;
+  if (in_t == IoType::F64)
+    return o64 ? launch_dst_t<T, IN_F64, true>(p, c, g, work, num_sms, st)
+               : launch_dst_t<T, IN_F64, false>(p, c, g, work, num_sms, st);
+  if (in_t == IoType::ROT) {
+    if (!o64) return cudaErrorInvalidValue;
+    return launch_dst_t<T, IN_ROT, true>(p, c, g, work, num_sms, st);
+  }
+  return o64 ? launch_dst_t<T, IN_WORK, true>(p, c, g, work, num_sms, st)
+             : launch_dst_t<T, IN_WORK, false>(p, c, g, work, num_sms, st);
 }
 
 template cudaError_t launch_dst<double>(const Plan&, const ColumnSet&, IoType, IoType, void*, int, cudaStream_t);

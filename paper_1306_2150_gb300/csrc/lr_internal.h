@@ -58,9 +58,15 @@ struct ColumnSet {
   int ld_out[2] = {0, 0};
   int ncol[2] = {0, 0};
   const int* dyn_count = nullptr;
+  // IoType::ROT input: column q of segment s is sum_{l<k} in[s][:, l] tm[s][l + q*KMAX]
+  // (working precision, k read from *k_dev on the device).
+  const void* tm[2] = {nullptr, nullptr};
+  const int* k_dev = nullptr;
 };
 
-enum class IoType { F64, WORK };   // caller float64 buffers or working precision
+// Input/output kinds: caller float64 buffers, working-precision buffers, or
+// (input only) working-precision columns rotated on the fly.
+enum class IoType { F64, WORK, ROT };
 
 // Launch the DST-I of every column of cs (forward and inverse are the same
 // orthonormal, symmetric S).  work: complex scratch of M * (ncol0 + ncol1)
