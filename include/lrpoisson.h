@@ -167,6 +167,36 @@ lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, 
  * last solve was not timed. */
 lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
 
+/* lr_truncate without any allocation (the paper has no counterpart; this is
+ * a deployment variant of lr_truncate above, same arithmetic and results).
+ *
+ * For callers that cannot allocate device or pinned memory themselves: code
+ * running inside another framework's memory pool, where a direct cudaMalloc
+ * would bypass the pool's budget, and latency-critical loops, where cudaMalloc
+ * may stall and cudaFree synchronises the whole device.  No handle is used
+ * (creating one allocates pinned host memory) and no cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ *
+ * Scratch: one file-scope device array of 2.2 MB (Gram partials, the two
+ * Gram matrices, the k x k rotations and a status record), reserved on every
+ * GPU that loads the library until the process exits.  Limit: X->r <= 64
+ * (larger ranks return LR_EINVAL); any number of rows.  The first call on a
+ * device looks up the array's device address (with that device current), so
+ * make that first call before any stream capture.
+ *
+ * All calls on one device share the array and it keeps the last call's
+ * contents (the status record is cleared at the start of every call): calls
+ * whose work overlaps on the GPU -- different streams, or different host
+ * threads -- race and must be serialised by the caller.
+ *
+ * Arguments as lr_truncate (X->s required; U and V overwritten with
+ * orthonormal columns, s with the kept singular values, X->r with the kept
+ * rank), plus the CUDA stream (cudaStream_t, NULL = legacy default stream)
+ * that runs the work; returns after that stream has finished it.  Returns
+ * LR_EINVAL for bad arguments or X->r > 64, LR_ECUDA for a CUDA failure and
+ * LR_ENOCONV if more than rmax columns were needed (result cut). */
+lr_status lr_truncate_noalloc(lr_mat* X, double eps, int rmax, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ OPERATORS = {"5pt": LR_OP_5PT, "semi": LR_OP_SEMISTAGGERED}
 # Every function the header declares (checked against the header by the tests).
 EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
-           "lr_truncate", "lr_get_info", "lr_get_phase_times")
+           "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc")
 
 
 class LrMat(ctypes.Structure):
@@ -97,6 +97,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_get_info.restype = c_int
     lib.lr_get_phase_times.argtypes = [c_void_p, ctypes.POINTER(c_double), c_int]
     lib.lr_get_phase_times.restype = c_int
+    lib.lr_truncate_noalloc.argtypes = [ctypes.POINTER(LrMat), c_double, c_int, c_void_p]
+    lib.lr_truncate_noalloc.restype = c_int
     if path is None:
         _lib = lib
     return lib

@@ -1,0 +1,79 @@
+"""lr_truncate_noalloc: the rounding without any allocation, for callers that
+cannot call cudaMalloc (code inside another framework's memory pool, or
+latency-critical loops where cudaMalloc may stall and cudaFree synchronises
+the device).  It must give the results of lr_truncate, call after call, even
+though every call reuses the same static scratch array.
+
+This file is collected last on purpose, so a run that stops at the first
+failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    from paper_1306_2150_gb300 import build, lr as lrmod
+    build.build()
+    lrmod.load()
+    return lrmod
+
+
+def _noalloc(lr, U, s, V, eps, rmax):
+    """Call lr_truncate_noalloc through the C ABI on copies of the inputs."""
+    n1, r = U.shape
+    n2 = V.shape[0]
+    ld = max(n1, n2)
+    ld += ld & 1
+    Uw = torch.zeros((r, ld), dtype=torch.float64, device="cuda")
+    Vw = torch.zeros((r, ld), dtype=torch.float64, device="cuda")
+    Uw[:, :n1].copy_(torch.from_numpy(U.T.copy()))
+    Vw[:, :n2].copy_(torch.from_numpy(V.T.copy()))
+    sw = torch.from_numpy(s.copy()).cuda()
+    X = lr.LrMat(n1, n2, r, r, ld, Uw.data_ptr(), sw.data_ptr(), Vw.data_ptr())
+    stream = torch.cuda.current_stream().cuda_stream
+    st = lr.load().lr_truncate_noalloc(ctypes.byref(X), float(eps), int(rmax), ctypes.c_void_p(stream))
+    R = X.r
+    return st, Uw[:R, :n1].cpu().numpy().T, sw[:R].cpu().numpy(), Vw[:R, :n2].cpu().numpy().T
+
+
+def _problem(seed, n1, n2, k):
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((n1, k)) * (10.0 ** -np.linspace(0, 9, k))
+    V = rng.standard_normal((n2, k))
+    s = rng.uniform(0.5, 2.0, k)
+    return U, s, V
+
+
+def test_noalloc_truncate_matches_lr_truncate_twice(lr):
+    h = lr.Handle()
+    try:
+        # two calls in a row on different shapes: the second must not see
+        # anything the first left in the shared scratch
+        for seed, (n1, n2, k, eps) in enumerate([(700, 530, 14, 1e-7), (3000, 2900, 40, 1e-10)]):
+            U, s, V = _problem(seed, n1, n2, k)
+            st, Un, sn, Vn = _noalloc(lr, U, s, V, eps, 64)
+            Ue, se, Ve, ste = lr.lr_truncate(h, torch.from_numpy(U).cuda(), torch.from_numpy(s).cuda(),
+                                             torch.from_numpy(V).cuda(), eps)
+            torch.cuda.synchronize()
+            assert st == lr.LR_OK and ste == lr.LR_OK
+            Ue, se, Ve = Ue.cpu().numpy(), se.cpu().numpy(), Ve.cpu().numpy()
+            assert len(sn) == len(se)
+            assert np.allclose(sn, se, rtol=1e-10, atol=0)
+            Xn = (Un * sn) @ Vn.T
+            Xe = (Ue * se) @ Ve.T
+            assert np.linalg.norm(Xn - Xe) <= 1e-12 * np.linalg.norm(Xe)
+            assert np.abs(Un.T @ Un - np.eye(len(sn))).max() < 1e-10
+    finally:
+        h.close()
+
+
+def test_noalloc_rejects_rank_beyond_static_limit(lr):
+    U, s, V = _problem(5, 200, 200, 65)
+    st, *_ = _noalloc(lr, U, s, V, 1e-6, 64)
+    assert st == lr.LR_EINVAL
