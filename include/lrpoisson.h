@@ -66,6 +66,9 @@ typedef enum {
                               lr_get_info() after synchronising the stream */
 #define LR_FLAG_TIMING 2u  /* record CUDA events between the phases of a solve;
                               read them with lr_get_phase_times() */
+#define LR_FLAG_GRAPH 4u   /* capture the enqueued work once as a CUDA graph
+                              (keyed by every pointer, size and option) and
+                              replay it on later calls with the same key */
 
 /* Phases of lr_poisson2d timed under LR_FLAG_TIMING. */
 #define LR_PHASE_FORWARD_DST 0  /* DST of the right-hand side factors      */
@@ -147,6 +150,18 @@ lr_status lr_dst1(lr_handle h, int m, int ncols, const double* in, int ld_in,
  * result if the cross needed more than opt->rmax steps or the rank exceeded
  * sol->rmax.  opt NULL means defaults. */
 lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt);
+
+/* Batched low-rank Poisson solves: `batch` independent problems (host arrays
+ * rhs[batch], sol[batch] of lr_mat with device pointers, each as for
+ * lr_poisson2d, sizes and ranks may differ) with shared options.  Problems
+ * are enqueued in decreasing order of size over 16 internal streams that fork
+ * from and join back into the handle's stream; with LR_FLAG_GRAPH the whole
+ * batch is one replayed CUDA graph.  per_problem (host, may be NULL) receives
+ * each problem's status; the return value is LR_OK or the first failure.
+ * The paper solves one problem at a time; batching is the data-parallel form
+ * of its Section 4.2 solve for many right-hand sides. */
+lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol,
+                               const lr_options* opt, lr_status* per_problem);
 
 /* Rounding (recompression) of X = U diag(s) V^T in place (Section 3): QR of
  * both factors, SVD of the r x r core, truncation at relative Frobenius

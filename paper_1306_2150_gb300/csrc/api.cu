@@ -4,6 +4,7 @@
 // workspace and enqueues the launches on the handle's stream.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -28,6 +29,17 @@ struct lr_handle_s {
   int last_kcap = 0;
   cudaEvent_t ev[LR_NUM_PHASES + 1] = {};
   bool timed = false;
+  // batched solves: internal streams, fork/join events, pinned status array
+  cudaStream_t bstreams[16] = {};
+  cudaEvent_t bjoin[16] = {};
+  cudaEvent_t bfork = nullptr;
+  SolveState* h_bstate = nullptr;
+  int bstate_cap = 0;
+  // captured CUDA graphs (LR_FLAG_GRAPH), keyed by every pointer and size
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::string, cudaGraphExec_t> graphs;
+  unsigned long long ws_gen = 0;
+  int last_cs = 0;
 };
 
 namespace {
@@ -70,6 +82,7 @@ lr_status ensure_ws(lr_handle h, size_t bytes) {
     h->ws = nullptr;
     h->ws_bytes = 0;
   }
+  ++h->ws_gen;  // captured graphs point into the old workspace
   if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
     cudaGetLastError();
     return fail(h, LR_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " workspace bytes failed");
@@ -92,6 +105,22 @@ struct Carve {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+lr_status check_problem(lr_handle h, const lr_mat* rhs, const lr_mat* sol) {
+  if (!rhs || !sol) return fail(h, LR_EINVAL, "null rhs or sol");
+  const int m = rhs->n1;
+  if (m < 1 || rhs->n2 != m) return fail(h, LR_EINVAL, "rhs must be square (n1 == n2 >= 1)");
+  if (rhs->r < 1 || rhs->r > KMAX) return fail(h, LR_EINVAL, "rhs->r must be in [1, 64]");
+  if (rhs->ld < m || sol->ld < m) return fail(h, LR_EINVAL, "leading dimension smaller than m");
+  if (sol->n1 != m || sol->n2 != m) return fail(h, LR_EINVAL, "sol must be m x m");
+  if (sol->rmax < 1) return fail(h, LR_EINVAL, "sol->rmax must be >= 1");
+  if (rhs->s) return fail(h, LR_EINVAL, "rhs->s must be NULL (fold weights into U)");
+  if (!rhs->U || !rhs->V || !sol->U || !sol->V || !sol->s) return fail(h, LR_EINVAL, "null factor pointer");
+  if (!aligned16(rhs->U) || !aligned16(rhs->V) || !aligned16(sol->U) || !aligned16(sol->V) || !aligned16(sol->s))
+    return fail(h, LR_EINVAL, "factor pointers must be 16-byte aligned");
+  if (m > 131072) return fail(h, LR_EINVAL, "m too large (max 131072)");
+  return LR_OK;
+}
+
 lr_status check_opts(lr_handle h, const lr_options& o) {
   if (o.prec != LR_FP64 && o.prec != LR_MIXED) return fail(h, LR_EINVAL, "unknown precision");
   if (o.op != LR_OP_5PT && o.op != LR_OP_SEMISTAGGERED) return fail(h, LR_EINVAL, "unknown operator");
@@ -104,132 +133,298 @@ lr_status check_opts(lr_handle h, const lr_options& o) {
   return LR_OK;
 }
 
-lr_status mark(lr_handle h, bool on, int i) {
-  if (!on) return LR_OK;
-  if (!h->ev[i]) {
-    if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "event create");
-  }
-  LR_CUDA(h, cudaEventRecord(h->ev[i], h->stream), "event record");
-  return LR_OK;
+// Geometry of one solve and its workspace slice.
+struct SolveGeom {
+  int m = 0, r = 0, kcap = 0, ldw = 0, ncap_out = 0, cols_fft = 0;
+  size_t M = 0;
+  bool four_step = false;
+};
+
+SolveGeom geom_of(int m, int r, int sol_rmax, const lr_options& o, const Plan& p) {
+  SolveGeom g;
+  g.m = m;
+  g.r = r;
+  g.kcap = o.rmax < m ? o.rmax : m;
+  g.ldw = round_up(m, 32);
+  g.ncap_out = g.kcap < sol_rmax ? g.kcap : sol_rmax;
+  g.M = (size_t)1 << p.logM;
+  g.cols_fft = (2 * r > 2 * g.kcap) ? 2 * r : 2 * g.kcap;
+  g.four_step = g.M > (size_t)kSmallM;
+  return g;
 }
 
-#define LR_MARK(i)                                  \
-  do {                                              \
-    lr_status ms_ = mark(h, timing, (i));           \
-    if (ms_ != LR_OK) return ms_;                   \
-  } while (0)
-
 template <typename T>
-lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options& o, Plan* plan) {
-  const int m = rhs->n1, r = rhs->r;
-  const int kcap = o.rmax < m ? o.rmax : m;
-  const int ldw = round_up(m, 32);
-  const int ncap_out = kcap < sol->rmax ? kcap : sol->rmax;
-  const size_t M = (size_t)1 << plan->logM;
-  const int cols_fft = (2 * r > 2 * kcap) ? 2 * r : 2 * kcap;
-  const bool four_step = M > (size_t)kSmallM;
-
-  Carve c;
-  auto layout = [&](Carve& cv, T** Uh, T** Vh, T** C, T** R, T** Uo, T** Vo, void** work, double** GC,
-                    double** GR, double** d, int** I, int** J, T** Tc, T** Tr, SolveState** st) {
-    *Uh = cv.template take<T>(sizeof(T) * ldw * r);
-    *Vh = cv.template take<T>(sizeof(T) * ldw * r);
-    *C = cv.template take<T>(sizeof(T) * ldw * kcap);
-    *R = cv.template take<T>(sizeof(T) * ldw * kcap);
-    *Uo = cv.template take<T>(16);
-    *Vo = cv.template take<T>(16);
-    *work = cv.template take<char>(four_step ? sizeof(cpx<T>) * M * cols_fft : 16);
-    *GC = cv.template take<double>(sizeof(double) * kcap * kcap);
-    *GR = cv.template take<double>(sizeof(double) * kcap * kcap);
-    *d = cv.template take<double>(sizeof(double) * kcap);
-    *I = cv.template take<int>(sizeof(int) * kcap);
-    *J = cv.template take<int>(sizeof(int) * kcap);
-    *Tc = cv.template take<T>(sizeof(T) * KMAX * KMAX);
-    *Tr = cv.template take<T>(sizeof(T) * KMAX * KMAX);
-    *st = cv.template take<SolveState>(sizeof(SolveState));
-  };
-  T *Uh, *Vh, *C, *R, *Uo, *Vo, *Tc, *Tr;
+struct Slice {
+  T *Uh, *Vh, *C, *R, *Tc, *Tr;
   void* work;
   double *GC, *GR, *d;
   int *I, *J;
-  SolveState* st;
-  layout(c, &Uh, &Vh, &C, &R, &Uo, &Vo, &work, &GC, &GR, &d, &I, &J, &Tc, &Tr, &st);
-  lr_status s = ensure_ws(h, c.off);
-  if (s != LR_OK) return s;
-  Carve c2;
-  c2.base = static_cast<char*>(h->ws);
-  layout(c2, &Uh, &Vh, &C, &R, &Uo, &Vo, &work, &GC, &GR, &d, &I, &J, &Tc, &Tr, &st);
+};
 
-  cudaStream_t stm = h->stream;
+template <typename T>
+Slice<T> carve_slice(Carve& cv, const SolveGeom& g) {
+  Slice<T> w;
+  w.Uh = cv.template take<T>(sizeof(T) * g.ldw * g.r);
+  w.Vh = cv.template take<T>(sizeof(T) * g.ldw * g.r);
+  w.C = cv.template take<T>(sizeof(T) * g.ldw * g.kcap);
+  w.R = cv.template take<T>(sizeof(T) * g.ldw * g.kcap);
+  w.work = cv.template take<char>(g.four_step ? sizeof(cpx<T>) * g.M * g.cols_fft : 16);
+  w.GC = cv.template take<double>(sizeof(double) * g.kcap * g.kcap);
+  w.GR = cv.template take<double>(sizeof(double) * g.kcap * g.kcap);
+  w.d = cv.template take<double>(sizeof(double) * g.kcap);
+  w.I = cv.template take<int>(sizeof(int) * g.kcap);
+  w.J = cv.template take<int>(sizeof(int) * g.kcap);
+  w.Tc = cv.template take<T>(sizeof(T) * KMAX * KMAX);
+  w.Tr = cv.template take<T>(sizeof(T) * KMAX * KMAX);
+  return w;
+}
+
+int launches_of(const SolveGeom& g) { return 2 * (g.four_step ? 3 : 1) + 2; }
+
+// Enqueue T1-T6 of one solve on stream stm.  ev (optional) receives the
+// phase boundaries.
+template <typename T>
+cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options& o, const Plan& plan,
+                          const SolveGeom& g, const Slice<T>& w, SolveState* st, cudaStream_t stm,
+                          cudaEvent_t* ev, int* used_cs) {
   const bool f32 = sizeof(T) == 4;
-  const bool timing = (o.flags & LR_FLAG_TIMING) != 0;
-  h->timed = timing;
-  LR_CUDA(h, cudaMemsetAsync(st, 0, sizeof(SolveState), stm), "state reset");
-  LR_MARK(0);
-
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(st, 0, sizeof(SolveState), stm)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[0], stm)) != cudaSuccess) return e;
   // T1: forward DST of both factors.
   ColumnSet fw;
   fw.in[0] = rhs->U; fw.in[1] = rhs->V;
   fw.ld_in[0] = rhs->ld; fw.ld_in[1] = rhs->ld;
-  fw.out[0] = Uh; fw.out[1] = Vh;
-  fw.ld_out[0] = ldw; fw.ld_out[1] = ldw;
-  fw.ncol[0] = r; fw.ncol[1] = r;
-  LR_CUDA(h, launch_dst<T>(*plan, fw, IoType::F64, IoType::WORK, work, h->num_sms, stm), "forward DST");
-
-  LR_MARK(1);
+  fw.out[0] = w.Uh; fw.out[1] = w.Vh;
+  fw.ld_out[0] = g.ldw; fw.ld_out[1] = g.ldw;
+  fw.ncol[0] = g.r; fw.ncol[1] = g.r;
+  if ((e = launch_dst<T>(plan, fw, IoType::F64, IoType::WORK, w.work, h->num_sms, stm)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], stm)) != cudaSuccess) return e;
   // T2-T4: cross approximation in frequency space.
   CrossArgs<T> ca;
-  ca.m = m; ca.r = r; ca.kcap = kcap; ca.ld = ldw;
-  ca.Uh = Uh; ca.Vh = Vh; ca.C = C; ca.R = R;
-  ca.a = f32 ? reinterpret_cast<const T*>(plan->sym_a32[o.op]) : reinterpret_cast<const T*>(plan->sym_a64[o.op]);
-  ca.b = f32 ? reinterpret_cast<const T*>(plan->sym_b32[o.op]) : reinterpret_cast<const T*>(plan->sym_b64[o.op]);
-  ca.d = d; ca.I = I; ca.J = J; ca.GC = GC; ca.GR = GR; ca.st = st;
+  ca.m = g.m; ca.r = g.r; ca.kcap = g.kcap; ca.ld = g.ldw;
+  ca.Uh = w.Uh; ca.Vh = w.Vh; ca.C = w.C; ca.R = w.R;
+  ca.a = f32 ? reinterpret_cast<const T*>(plan.sym_a32[o.op]) : reinterpret_cast<const T*>(plan.sym_a64[o.op]);
+  ca.b = f32 ? reinterpret_cast<const T*>(plan.sym_b32[o.op]) : reinterpret_cast<const T*>(plan.sym_b64[o.op]);
+  ca.d = w.d; ca.I = w.I; ca.J = w.J; ca.GC = w.GC; ca.GR = w.GR; ca.st = st;
   ca.tol = o.aca_tol_factor * o.eps;
   ca.probes = o.probes;
   ca.seed = o.seed;
   ca.max_probe_rounds = 4;
   ca.max_zero_rows = 16;
-  int used_cs = 0;
-  LR_CUDA(h, launch_cross<T>(ca, o.cluster_size, stm, &used_cs), "cross");
-
-  LR_MARK(2);
+  if ((e = launch_cross<T>(ca, o.cluster_size, stm, used_cs)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], stm)) != cudaSuccess) return e;
   // T5: rounding core.
   CoreArgs<T> co;
-  co.GC = GC; co.GR = GR; co.ldg = kcap; co.d = d;
+  co.GC = w.GC; co.GR = w.GR; co.ldg = g.kcap; co.d = w.d;
   co.k_dev = &st->k; co.k_host = 0;
-  co.eps = o.eps; co.rmax_out = ncap_out;
-  co.Tc = Tc; co.Tr = Tr; co.s_out = sol->s; co.st = st;
-  LR_CUDA(h, launch_core<T>(co, f32, stm), "rounding core");
-
-  LR_MARK(3);
+  co.eps = o.eps; co.rmax_out = g.ncap_out;
+  co.Tc = w.Tc; co.Tr = w.Tr; co.s_out = sol->s; co.st = st;
+  if ((e = launch_core<T>(co, f32, stm)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[3], stm)) != cudaSuccess) return e;
   // T6: inverse DST of the kept columns into the caller's float64 factors;
   // the rotation of the skeleton by Tc, Tr (the last step of the rounding) is
   // applied as the transform loads its input.
   ColumnSet iv;
-  iv.in[0] = C; iv.in[1] = R;
-  iv.tm[0] = Tc; iv.tm[1] = Tr;
+  iv.in[0] = w.C; iv.in[1] = w.R;
+  iv.tm[0] = w.Tc; iv.tm[1] = w.Tr;
   iv.k_dev = &st->k;
-  iv.ld_in[0] = ldw; iv.ld_in[1] = ldw;
+  iv.ld_in[0] = g.ldw; iv.ld_in[1] = g.ldw;
   iv.out[0] = sol->U; iv.out[1] = sol->V;
   iv.ld_out[0] = sol->ld; iv.ld_out[1] = sol->ld;
-  iv.ncol[0] = ncap_out; iv.ncol[1] = ncap_out;
+  iv.ncol[0] = g.ncap_out; iv.ncol[1] = g.ncap_out;
   iv.dyn_count = &st->rank;
-  LR_CUDA(h, launch_dst<T>(*plan, iv, IoType::ROT, IoType::F64, work, h->num_sms, stm), "inverse DST");
-  LR_MARK(4);
-  h->info.launches = 2 * (four_step ? 3 : 1) + 2;
+  if ((e = launch_dst<T>(plan, iv, IoType::ROT, IoType::F64, w.work, h->num_sms, stm)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[4], stm)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
 
-  LR_CUDA(h, cudaMemcpyAsync(h->h_state, st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm), "state copy");
-  LR_CUDA(h, cudaMemcpyAsync(h->h_piv, I, sizeof(int) * kcap, cudaMemcpyDeviceToHost, stm), "pivot copy");
-  LR_CUDA(h, cudaMemcpyAsync(h->h_piv + KMAX, J, sizeof(int) * kcap, cudaMemcpyDeviceToHost, stm), "pivot copy");
-  h->last_kcap = kcap;
-  h->info.cluster_size = used_cs;
+lr_status ensure_events(lr_handle h) {
+  for (auto& e : h->ev)
+    if (!e && cudaEventCreate(&e) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "event create");
+  return LR_OK;
+}
+
+// Run `body` (which enqueues work on the stream it is given) either directly
+// on the handle's stream, or -- with LR_FLAG_GRAPH -- through a CUDA graph
+// captured once per key on an internal stream and replayed on the handle's
+// stream.  Graphs bake in every pointer, so the key holds all of them and
+// the workspace generation.
+template <typename F>
+lr_status run_maybe_graph(lr_handle h, bool graph, const std::string& key, F&& body) {
+  if (!graph) {
+    cudaError_t e = body(h->stream);
+    return e == cudaSuccess ? LR_OK : cuda_fail(h, e, "enqueue");
+  }
+  const std::string k = key + "|ws" + std::to_string(h->ws_gen);
+  auto it = h->graphs.find(k);
+  if (it == h->graphs.end()) {
+    if (!h->cap_stream) LR_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "stream");
+    LR_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = body(h->cap_stream);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      return cuda_fail(h, e != cudaSuccess ? e : e2, "graph capture");
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    if (h->graphs.size() >= 32) {  // bounded cache
+      for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+      h->graphs.clear();
+    }
+    it = h->graphs.emplace(k, ex).first;
+  }
+  LR_CUDA(h, cudaGraphLaunch(it->second, h->stream), "graph launch");
+  return LR_OK;
+}
+
+std::string key_of(const char* tag, const lr_mat* a, int n, const lr_mat* b, const lr_options& o) {
+  std::string k(tag);
+  char buf[256];
+  for (int i = 0; i < n; ++i) {
+    snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%p,%p,%p;%d,%d,%p,%p,%p", a[i].n1, a[i].r, a[i].rmax, a[i].ld,
+             (void*)a[i].U, (void*)a[i].s, (void*)a[i].V, b[i].rmax, b[i].ld, (void*)b[i].U, (void*)b[i].s,
+             (void*)b[i].V);
+    k += buf;
+  }
+  snprintf(buf, sizeof buf, "|o%d,%d,%.17g,%d,%.17g,%d,%llu,%u,%d", (int)o.prec, (int)o.op, o.eps, o.rmax,
+           o.aca_tol_factor, o.probes, o.seed, o.flags & ~(unsigned)(LR_FLAG_ASYNC | LR_FLAG_TIMING),
+           o.cluster_size);
+  k += buf;
+  return k;
+}
+
+template <typename T>
+lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options& o, Plan* plan) {
+  const SolveGeom g = geom_of(rhs->n1, rhs->r, sol->rmax, o, *plan);
+  Carve c;
+  carve_slice<T>(c, g);
+  const size_t st_off = c.off;
+  c.take<SolveState>(sizeof(SolveState));
+  lr_status s = ensure_ws(h, c.off);
+  if (s != LR_OK) return s;
+  Carve c2;
+  c2.base = static_cast<char*>(h->ws);
+  const Slice<T> w = carve_slice<T>(c2, g);
+  SolveState* st = reinterpret_cast<SolveState*>(static_cast<char*>(h->ws) + st_off);
+  const bool timing = (o.flags & LR_FLAG_TIMING) != 0;
+  const bool graph = (o.flags & LR_FLAG_GRAPH) != 0 && !timing;
+  if (timing && (s = ensure_events(h)) != LR_OK) return s;
+  h->timed = timing;
+  int used_cs = 0;
+  s = run_maybe_graph(h, graph, key_of("single", rhs, 1, sol, o), [&](cudaStream_t stm) -> cudaError_t {
+    cudaError_t e = enqueue_solve<T>(h, rhs, sol, o, *plan, g, w, st, stm, timing ? h->ev : nullptr, &used_cs);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(h->h_state, st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(h->h_piv, w.I, sizeof(int) * g.kcap, cudaMemcpyDeviceToHost, stm)) != cudaSuccess)
+      return e;
+    return cudaMemcpyAsync(h->h_piv + KMAX, w.J, sizeof(int) * g.kcap, cudaMemcpyDeviceToHost, stm);
+  });
+  if (s != LR_OK) return s;
+  h->info.launches = launches_of(g);
+  if (used_cs) h->last_cs = used_cs;   // a replayed graph launches nothing from the host
+  h->info.cluster_size = h->last_cs;
+  h->last_kcap = g.kcap;
   if (o.flags & LR_FLAG_ASYNC) return LR_OK;
-  LR_CUDA(h, cudaStreamSynchronize(stm), "solve");
+  LR_CUDA(h, cudaStreamSynchronize(h->stream), "solve");
   const SolveState& hs = *h->h_state;
   sol->r = hs.rank;
   if (!hs.converged) return fail(h, LR_ENOCONV, "cross did not converge within opt->rmax steps");
   if (hs.cut) return fail(h, LR_ENOCONV, "solution rank exceeds sol->rmax; result truncated");
   return LR_OK;
+}
+
+constexpr int kBatchStreams = 16;
+
+lr_status ensure_batch_streams(lr_handle h) {
+  if (h->bstreams[0]) return LR_OK;
+  for (int i = 0; i < kBatchStreams; ++i) {
+    LR_CUDA(h, cudaStreamCreateWithFlags(&h->bstreams[i], cudaStreamNonBlocking), "stream create");
+    LR_CUDA(h, cudaEventCreateWithFlags(&h->bjoin[i], cudaEventDisableTiming), "event create");
+  }
+  LR_CUDA(h, cudaEventCreateWithFlags(&h->bfork, cudaEventDisableTiming), "event create");
+  return LR_OK;
+}
+
+template <typename T>
+lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options& o,
+                          const std::vector<Plan*>& plans, lr_status* per_problem) {
+  std::vector<SolveGeom> geo(batch);
+  std::vector<size_t> off(batch);
+  Carve c;
+  for (int i = 0; i < batch; ++i) {
+    geo[i] = geom_of(rhs[i].n1, rhs[i].r, sol[i].rmax, o, *plans[i]);
+    off[i] = c.off;
+    carve_slice<T>(c, geo[i]);
+  }
+  const size_t st_off = c.off;
+  c.take<SolveState>(sizeof(SolveState) * batch);
+  lr_status s = ensure_ws(h, c.off);
+  if (s != LR_OK) return s;
+  if ((s = ensure_batch_streams(h)) != LR_OK) return s;
+  if (h->bstate_cap < batch) {
+    if (h->h_bstate) cudaFreeHost(h->h_bstate);
+    h->h_bstate = nullptr;
+    h->bstate_cap = 0;
+    if (cudaMallocHost(&h->h_bstate, sizeof(SolveState) * batch) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, LR_ENOMEM, "pinned status buffer");
+    }
+    h->bstate_cap = batch;
+    ++h->ws_gen;  // graphs captured with the old buffer are stale
+  }
+  char* base = static_cast<char*>(h->ws);
+  SolveState* states = reinterpret_cast<SolveState*>(base + st_off);
+  // Longest-processing-time order, dealt round-robin over the streams.
+  std::vector<int> order(batch);
+  for (int i = 0; i < batch; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)geo[a].m * (geo[a].r + 16) > (double)geo[b].m * (geo[b].r + 16);
+  });
+  int launches = 0;
+  for (int i = 0; i < batch; ++i) launches += launches_of(geo[i]);
+  const bool graph = (o.flags & LR_FLAG_GRAPH) != 0;
+  s = run_maybe_graph(h, graph, key_of("batch", rhs, batch, sol, o), [&](cudaStream_t main) -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaEventRecord(h->bfork, main)) != cudaSuccess) return e;
+    for (int j = 0; j < kBatchStreams; ++j)
+      if ((e = cudaStreamWaitEvent(h->bstreams[j], h->bfork, 0)) != cudaSuccess) return e;
+    for (int n = 0; n < batch; ++n) {
+      const int i = order[n];
+      Carve ci;
+      ci.base = base + off[i];
+      const Slice<T> w = carve_slice<T>(ci, geo[i]);
+      int used = 0;
+      if ((e = enqueue_solve<T>(h, &rhs[i], &sol[i], o, *plans[i], geo[i], w, &states[i],
+                                h->bstreams[n % kBatchStreams], nullptr, &used)) != cudaSuccess)
+        return e;
+    }
+    for (int j = 0; j < kBatchStreams; ++j) {
+      if ((e = cudaEventRecord(h->bjoin[j], h->bstreams[j])) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(main, h->bjoin[j], 0)) != cudaSuccess) return e;
+    }
+    return cudaMemcpyAsync(h->h_bstate, states, sizeof(SolveState) * batch, cudaMemcpyDeviceToHost, main);
+  });
+  if (s != LR_OK) return s;
+  h->info.launches = launches;
+  if (o.flags & LR_FLAG_ASYNC) return LR_OK;
+  LR_CUDA(h, cudaStreamSynchronize(h->stream), "batched solve");
+  lr_status worst = LR_OK;
+  for (int i = 0; i < batch; ++i) {
+    const SolveState& hs = h->h_bstate[i];
+    sol[i].r = hs.rank;
+    const lr_status si = (!hs.converged || hs.cut) ? LR_ENOCONV : LR_OK;
+    if (per_problem) per_problem[i] = si;
+    if (si != LR_OK) worst = si;
+  }
+  if (worst != LR_OK) fail(h, worst, "some problems did not converge or were cut (see per_problem)");
+  return worst;
 }
 
 }  // namespace
@@ -299,6 +494,14 @@ lr_status lr_destroy(lr_handle h) {
   cudaStreamSynchronize(h->stream);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int i = 0; i < 16; ++i) {
+    if (h->bstreams[i]) cudaStreamDestroy(h->bstreams[i]);
+    if (h->bjoin[i]) cudaEventDestroy(h->bjoin[i]);
+  }
+  if (h->bfork) cudaEventDestroy(h->bfork);
+  if (h->h_bstate) cudaFreeHost(h->h_bstate);
   h->plans.clear();
   if (h->ws) cudaFree(h->ws);
   if (h->h_state) cudaFreeHost(h->h_state);
@@ -339,23 +542,39 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
   if (opt) o = *opt; else lr_options_default(&o);
   lr_status s = check_opts(h, o);
   if (s != LR_OK) return s;
-  if (!rhs || !sol) return fail(h, LR_EINVAL, "null rhs or sol");
+  if ((s = check_problem(h, rhs, sol)) != LR_OK) return s;
   const int m = rhs->n1;
-  if (m < 1 || rhs->n2 != m) return fail(h, LR_EINVAL, "rhs must be square (n1 == n2 >= 1)");
-  if (rhs->r < 1 || rhs->r > KMAX) return fail(h, LR_EINVAL, "rhs->r must be in [1, 64]");
-  if (rhs->ld < m || sol->ld < m) return fail(h, LR_EINVAL, "leading dimension smaller than m");
-  if (sol->n1 != m || sol->n2 != m) return fail(h, LR_EINVAL, "sol must be m x m");
-  if (sol->rmax < 1) return fail(h, LR_EINVAL, "sol->rmax must be >= 1");
-  if (rhs->s) return fail(h, LR_EINVAL, "rhs->s must be NULL (fold weights into U)");
-  if (!rhs->U || !rhs->V || !sol->U || !sol->V || !sol->s) return fail(h, LR_EINVAL, "null factor pointer");
-  if (!aligned16(rhs->U) || !aligned16(rhs->V) || !aligned16(sol->U) || !aligned16(sol->V) || !aligned16(sol->s))
-    return fail(h, LR_EINVAL, "factor pointers must be 16-byte aligned");
-  if (m > 131072) return fail(h, LR_EINVAL, "m too large (max 131072)");
   Plan* plan = nullptr;
   s = get_plan(h, m, &plan);
   if (s != LR_OK) return s;
   h->info = lr_info{};
   s = o.prec == LR_MIXED ? solve2d<float>(h, rhs, sol, o, plan) : solve2d<double>(h, rhs, sol, o, plan);
+  h->info.status = s;
+  return s;
+}
+
+lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options* opt,
+                               lr_status* per_problem) {
+  if (!h) return LR_EINVAL;
+  lr_options o;
+  if (opt) o = *opt; else lr_options_default(&o);
+  lr_status s = check_opts(h, o);
+  if (s != LR_OK) return s;
+  if (batch < 0 || (batch > 0 && (!rhs || !sol))) return fail(h, LR_EINVAL, "bad batch arguments");
+  if (batch == 0) return LR_OK;
+  if (o.flags & LR_FLAG_TIMING) return fail(h, LR_EINVAL, "LR_FLAG_TIMING is for single solves");
+  std::vector<Plan*> plans(batch);
+  for (int i = 0; i < batch; ++i) {
+    if ((s = check_problem(h, &rhs[i], &sol[i])) != LR_OK) {
+      if (per_problem) per_problem[i] = s;
+      return fail(h, s, "problem " + std::to_string(i) + ": " + h->err);
+    }
+    if ((s = get_plan(h, rhs[i].n1, &plans[i])) != LR_OK) return s;
+  }
+  h->info = lr_info{};
+  h->timed = false;
+  s = o.prec == LR_MIXED ? solve2d_batched<float>(h, batch, rhs, sol, o, plans, per_problem)
+                         : solve2d_batched<double>(h, batch, rhs, sol, o, plans, per_problem);
   h->info.status = s;
   return s;
 }

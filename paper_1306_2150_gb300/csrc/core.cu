@@ -254,14 +254,14 @@ cudaError_t launch_core(const CoreArgs<T>& a, bool jacobi_fp32, cudaStream_t st)
   if (jacobi_fp32) {
     auto kern = core_kernel<T, float>;
     const size_t sm = sizeof(CoreSmem<float>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+    static cudaError_t set = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (set != cudaSuccess) return set;
     kern<<<1, 256, sm, st>>>(a);
   } else {
     auto kern = core_kernel<T, double>;
     const size_t sm = sizeof(CoreSmem<double>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+    static cudaError_t set = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (set != cudaSuccess) return set;
     kern<<<1, 256, sm, st>>>(a);
   }
   return cudaGetLastError();

@@ -15,40 +15,31 @@
 //
 // One persistent launch per solve: a thread-block cluster of CS CTAs
 // (CS <= 16) splits the index range 0..m-1 into CS contiguous slices of S
-// indices; each thread owns up to RPT indices of its CTA's slice for both the
-// row and the column side.  The CTA keeps its slices of Uh, Vh, of the symbol
-// and of the first KS skeleton columns in shared memory (column-major, so a
-// warp reads 32 consecutive words), so a half-step touches global memory only
-// for skeleton columns beyond KS.  Pivot rows are read from the owning CTA's
-// shared memory through distributed shared memory.  A half-step is:
-// broadcast, evaluate the owned residual entries, reduce (argmax, sum of
-// squares, k dot products) with warp shuffles, publish the CTA partial, one
-// cluster barrier, then every CTA reduces all partials (one lane per CTA) in
-// the same order, so every CTA takes the same decision with the same
-// arithmetic.  Partials are double-buffered by half-step parity, which makes
-// one barrier per half-step enough.
+// indices.  The CTA keeps its slices of Uh, Vh, of the symbol and of the first
+// KS skeleton columns in shared memory (column-major; thread t owns entries
+// RPT*t .. RPT*t + RPT - 1, read with one vector load), so a half-step touches
+// global memory only for skeleton columns beyond KS.
+//
+// A half-step: evaluate the owned residual entries; reduce them in the CTA
+// (argmax, sum of squares, k dot products with warp shuffles); every CTA then
+// pushes its partial -- together with the pivot data its own candidate would
+// need next (that index's row of Uh or Vh, of C or R, and its symbol) -- into
+// an inbox in the shared memory of every CTA of the cluster with remote
+// stores; one cluster barrier; every CTA reduces its inbox in rank order (so
+// all take the same decision with the same arithmetic) and reads the winning
+// candidate's pivot data from its own shared memory.  Inboxes are
+// double-buffered by half-step parity, so one barrier per half-step is enough.
 #include <cooperative_groups.h>
 
 #include <climits>
+#include <map>
+#include <tuple>
 
 #include "lr_internal.h"
 
 namespace cg = cooperative_groups;
 
 namespace lrp {
-
-// Reductions accumulate in the working precision T: the float path never
-// issues FP64 arithmetic per thread (GB300 runs FP64 at a small fraction of
-// the FP32 rate); sums are widened to FP64 only where they are stored.
-template <typename T>
-struct Partial {
-  T sumsq;
-  T dots[KMAX];
-  T absmax;
-  T val;
-  int idx;
-  int pad;
-};
 
 __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long state, unsigned long long t) {
   unsigned long long z = state + t * 0x9E3779B97F4A7C15ULL;
@@ -80,17 +71,36 @@ __device__ __forceinline__ void warp_argmax(T& a, int& i, T& v) {
   }
 }
 
+// A CTA's message of one half-step, as 32-bit words (the layout does not
+// depend on the field values, so remote copies are plain word copies).
+template <typename T>
+struct Msg {
+  static constexpr int W = (int)sizeof(T) / 4;   // words per value
+  static constexpr int ABS = 0, VAL = W, SSQ = 2 * W, CA = 3 * W, CB = 4 * W, IDX = 5 * W;
+  static constexpr int HDR = 6 * W;               // header words (IDX padded to a value)
+  static constexpr int VEC = HDR;                 // candidate's row of Uh or Vh (r values)
+  static constexpr int COEF = VEC + KMAX * W;     // candidate's row of C or R (up to KMAX + 1)
+  static constexpr int DOTS = COEF + (KMAX + 1) * W;
+  static constexpr int WORDS = DOTS + KMAX * W;
+};
+
+template <typename T>
+__device__ __forceinline__ T& mval(unsigned* m, int off) { return *reinterpret_cast<T*>(m + off); }
+template <typename T>
+__device__ __forceinline__ T mval(const unsigned* m, int off) { return *reinterpret_cast<const T*>(m + off); }
+
 template <typename T>
 struct Shared {
   T wdots[KMAX][32];       // per-warp dot partials, [l][warp]
   T wsum[32];
   T wabs[32], wval[32];
   int widx[32];
-  T d[KMAX];               // pivot values (identical copy in every CTA)
+  __align__(16) unsigned out[Msg<T>::WORDS];  // this CTA's message before it is pushed
+  T d[KMAX + 1];           // pivot values (identical copy in every CTA)
   T dots[KMAX];            // cluster-reduced dot products of the last half-step
   T gr[KMAX];              // R_l . r of the current step
-  T vec[KMAX];             // broadcast row of Uh or Vh
-  T coef[KMAX];            // broadcast coefficients
+  T vec[KMAX];             // pivot row of Uh or Vh for the next half-step
+  T craw[KMAX + 1];        // pivot row of C or R for the next half-step
   T piv_a, piv_b;          // symbol at the pivot index
   double probe[32];
   int probe_row[32];
@@ -100,29 +110,36 @@ struct Shared {
   T delta;                 // pivot value of the current step
   int idx;
   int flag;
+  int win;                 // rank whose candidate won the last reduction
   int small;               // consecutive small terms
 };
 
 // Dynamic shared-memory layout (identical in every CTA of the cluster).
 // Every cached column has SP = blockDim.x * RPT entries (the CTA's S indices
-// plus neutral padding), and thread t owns entries RPT*t .. RPT*t + RPT - 1,
-// so a thread reads its rows of a column with one vector load.
+// plus neutral padding).
 template <typename T>
 struct Cache {
-  T* U;  // SP * r (if cache_uv)
+  unsigned* inbox;  // [2][16][Msg::WORDS]
+  T* U;             // SP * r (if cache_uv)
   T* V;
-  T* a;  // SP
+  T* a;             // SP
   T* b;
-  T* C;  // SP * KS
+  T* C;             // SP * KS
   T* R;
   unsigned char* used_r;  // SP
   unsigned char* used_c;
 };
 
 template <typename T>
+__host__ __device__ constexpr size_t inbox_bytes() {
+  return (size_t)2 * 16 * Msg<T>::WORDS * 4;
+}
+
+template <typename T>
 __device__ __forceinline__ Cache<T> carve(unsigned char* base, int SP, int r, int KS, bool cache_uv) {
   Cache<T> c;
-  T* p = reinterpret_cast<T*>(base);
+  c.inbox = reinterpret_cast<unsigned*>(base);
+  T* p = reinterpret_cast<T*>(base + inbox_bytes<T>());
   c.U = p; p += cache_uv ? (size_t)SP * r : 0;
   c.V = p; p += cache_uv ? (size_t)SP * r : 0;
   c.a = p; p += SP;
@@ -219,16 +236,32 @@ __device__ __forceinline__ void warp_dots(const T (&v)[RPT], const bool (&ok)[RP
   if (lane < W && l0 + lane < k) sh.wdots[l0 + lane][warp] = x;
 }
 
-// Reduce over the CTA and then the cluster: argmax |v| among candidates
-// (lowest index on ties), sum of v^2 and dots[l] = sum v * X[own row, l], l < k.
-// Results land in sh.idx (-1 if no candidate), sh.val, sh.sumsq, sh.dots.
-// v must be 0 for rows that are not owned (ok false).
+// Where the pivot data for the next half-step comes from: the factor F (Uh
+// or Vh, r columns) and the skeleton factor X (C or R, kn columns).
+template <typename T>
+struct NextSide {
+  const T* Fs;   // shared cache of F (if cached)
+  const T* Fg;   // F in global memory
+  const T* Xs;   // shared cache of X (columns < KS)
+  const T* Xg;   // X in global memory
+  int kn;
+};
+
+// Reduce over the CTA and the cluster (see the file comment): argmax |v|
+// among candidates (lowest index on ties), sum of v^2 and, for l < k,
+// dots[l] = sum v * Xd[own row, l].  Results: sh.idx (-1 if no candidate),
+// sh.val, sh.sumsq, sh.dots, and the winner's pivot data sh.vec, sh.craw,
+// sh.piv_a, sh.piv_b from nx.  v must be 0 for rows that are not owned.
 template <typename T, int RPT>
-__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, int SP, const T (&v)[RPT],
-                                               const bool (&ok)[RPT], const bool (&cand)[RPT],
-                                               const int (&e)[RPT], const T* Xs, const T* Xg, int ld,
-                                               int KS, int k, Partial<T>* xb, int& par, Shared<T>& sh) {
+__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, int SP, int row0, int r,
+                                               int KS, bool cache_uv, int ld, const Cache<T>& cc,
+                                               const T (&v)[RPT], const bool (&ok)[RPT],
+                                               const bool (&cand)[RPT], const int (&e)[RPT], const T* Xds,
+                                               const T* Xdg, int k, const NextSide<T>& nx, int& par,
+                                               Shared<T>& sh) {
+  using M = Msg<T>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
+  const int q = (int)cl.block_rank();
   T babs = T(-1), bval = T(0), ssq = T(0);
   int bidx = INT_MAX;
 #pragma unroll
@@ -243,12 +276,12 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, in
   ssq = warp_sum(ssq);
   // 16-wide chunks: 16 shuffles per chunk, and a 16-entry register buffer
   // keeps the register pressure low when a thread owns several rows.
-  if (k > 0 && k <= 8) warp_dots<T, RPT, 8>(v, ok, e, Xs, Xg, SP, ld, KS, 0, k, sh);
+  if (k > 0 && k <= 8) warp_dots<T, RPT, 8>(v, ok, e, Xds, Xdg, SP, ld, KS, 0, k, sh);
   else
-    for (int l0 = 0; l0 < k; l0 += 16) warp_dots<T, RPT, 16>(v, ok, e, Xs, Xg, SP, ld, KS, l0, k, sh);
+    for (int l0 = 0; l0 < k; l0 += 16) warp_dots<T, RPT, 16>(v, ok, e, Xds, Xdg, SP, ld, KS, l0, k, sh);
   if (lane == 0) { sh.wabs[warp] = babs; sh.widx[warp] = bidx; sh.wval[warp] = bval; sh.wsum[warp] = ssq; }
   __syncthreads();
-  Partial<T>& P = xb[par];
+  // CTA reduction into this CTA's message.
   if (warp == 0) {
     T a = lane < NW ? sh.wabs[lane] : T(-1);
     int i = lane < NW ? sh.widx[lane] : INT_MAX;
@@ -256,10 +289,14 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, in
     T ss = lane < NW ? sh.wsum[lane] : T(0);
     warp_argmax(a, i, vv);
     ss = warp_sum(ss);
-    if (lane == 0) { P.absmax = a; P.idx = i; P.val = vv; P.sumsq = ss; }
+    if (lane == 0) {
+      mval<T>(sh.out, M::ABS) = a;
+      mval<T>(sh.out, M::VAL) = vv;
+      mval<T>(sh.out, M::SSQ) = ss;
+      sh.out[M::IDX] = (unsigned)i;
+    }
   }
-  // CTA sums of the dots: one l per half-warp of 16 lanes, lane w reads warp
-  // w's partial (at most 16 warps).
+  // dots: one l per half-warp of 16 lanes, lane w reads warp w (NW <= 16)
   for (int base = warp * 32; base < k * 16; base += (int)blockDim.x) {
     const int t = base + lane, l = t >> 4, w = t & 15;
     T x = (t < k * 16 && w < NW) ? sh.wdots[l][w] : T(0);
@@ -267,28 +304,75 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, in
     x += __shfl_xor_sync(0xffffffffu, x, 4);
     x += __shfl_xor_sync(0xffffffffu, x, 2);
     x += __shfl_xor_sync(0xffffffffu, x, 1);
-    if (w == 0 && t < k * 16) P.dots[l] = x;
+    if (w == 0 && t < k * 16) mval<T>(sh.out, M::DOTS + l * M::W) = x;
+  }
+  __syncthreads();
+  // The pivot data the CTA's own candidate would need next.
+  {
+    const int ci = (int)sh.out[M::IDX];
+    if (ci != INT_MAX) {
+      const int loc = ci - row0;
+      if (tid < r) {
+        mval<T>(sh.out, M::VEC + tid * M::W) =
+            cache_uv ? nx.Fs[(size_t)tid * SP + loc] : nx.Fg[ci + (size_t)tid * ld];
+      } else if (tid >= KMAX && tid < KMAX + nx.kn) {
+        const int l = tid - KMAX;
+        mval<T>(sh.out, M::COEF + l * M::W) =
+            l < KS ? nx.Xs[(size_t)l * SP + loc] : __ldcg(&nx.Xg[ci + (size_t)l * ld]);
+      } else if (tid == 2 * KMAX + 1) {
+        mval<T>(sh.out, M::CA) = cc.a[loc];
+        mval<T>(sh.out, M::CB) = cc.b[loc];
+      }
+    }
+  }
+  __syncthreads();
+  // Push the live words of the message into slot q of every CTA's inbox.
+  {
+    const int nv = r * M::W, nc = nx.kn * M::W, nd = k * M::W;
+    const int live = M::HDR + nv + nc + nd;
+    unsigned* slot = cc.inbox + ((size_t)par * 16 + q) * M::WORDS;
+    for (int i = tid; i < CS * live; i += (int)blockDim.x) {
+      const int dst = i / live;
+      int w = i - dst * live;
+      int off;
+      if (w < M::HDR) off = w;
+      else if ((w -= M::HDR) < nv) off = M::VEC + w;
+      else if ((w -= nv) < nc) off = M::COEF + w;
+      else off = M::DOTS + (w - nc);
+      *cl.map_shared_rank(slot + off, dst) = sh.out[off];
+    }
   }
   cl.sync();
+  // Reduce the inbox (local shared memory) in rank order.
+  const unsigned* box = cc.inbox + (size_t)par * 16 * M::WORDS;
   if (warp == 0) {
     T a = T(-1), vv = T(0), ss = T(0);
-    int i = INT_MAX;
+    int i = INT_MAX, src = lane;
     if (lane < CS) {
-      const Partial<T>* Q = cl.map_shared_rank(&xb[par], lane);
-      a = Q->absmax; i = Q->idx; vv = Q->val; ss = Q->sumsq;
+      const unsigned* m = box + (size_t)lane * M::WORDS;
+      a = mval<T>(m, M::ABS); vv = mval<T>(m, M::VAL); ss = mval<T>(m, M::SSQ); i = (int)m[M::IDX];
     }
-    warp_argmax(a, i, vv);
+    // argmax carrying the source rank along with the value
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T oa = __shfl_xor_sync(0xffffffffu, a, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+      const T ov = __shfl_xor_sync(0xffffffffu, vv, o);
+      const int os = __shfl_xor_sync(0xffffffffu, src, o);
+      if (better(oa, oi, a, i)) { a = oa; i = oi; vv = ov; src = os; }
+    }
     ss = warp_sum(ss);
     if (lane == 0) {
-      sh.idx = (i == INT_MAX || a < T(0)) ? -1 : i;
+      const bool none = i == INT_MAX || a < T(0);
+      sh.idx = none ? -1 : i;
       sh.val = vv;
       sh.sumsq = ss;
+      sh.win = none ? -1 : src;
     }
   }
-  // Cluster sums of the dots: one l per half-warp, lane q reads CTA q.
   for (int base = warp * 32; base < k * 16; base += (int)blockDim.x) {
     const int t = base + lane, l = t >> 4, qq = t & 15;
-    T x = (t < k * 16 && qq < CS) ? cl.map_shared_rank(&xb[par], qq)->dots[l] : T(0);
+    T x = (t < k * 16 && qq < CS) ? mval<T>(box + (size_t)qq * M::WORDS, M::DOTS + l * M::W) : T(0);
     x += __shfl_xor_sync(0xffffffffu, x, 8);
     x += __shfl_xor_sync(0xffffffffu, x, 4);
     x += __shfl_xor_sync(0xffffffffu, x, 2);
@@ -296,36 +380,21 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, int CS, in
     if (qq == 0 && t < k * 16) sh.dots[l] = x;
   }
   __syncthreads();
+  // The winner's pivot data for the next half-step.
+  const int win = sh.win;
+  if (win >= 0) {
+    const unsigned* m = box + (size_t)win * M::WORDS;
+    if (tid < r) sh.vec[tid] = mval<T>(m, M::VEC + tid * M::W);
+    else if (tid >= KMAX && tid < KMAX + nx.kn) sh.craw[tid - KMAX] = mval<T>(m, M::COEF + (tid - KMAX) * M::W);
+    else if (tid == 2 * KMAX + 1) { sh.piv_a = mval<T>(m, M::CA); sh.piv_b = mval<T>(m, M::CB); }
+  }
+  __syncthreads();
   par ^= 1;
 }
 
-// Load the broadcast vectors of a half-step at pivot index p: vec = F[p, :r]
-// (F = Uh or Vh), coef[l] = X[p, l] (X = C or R, l < k) times the pivot
-// weights, and the symbol at p.  Values cached in the owner CTA's shared
-// memory are read through distributed shared memory.
-template <typename T>
-__device__ __forceinline__ void load_broadcast(cg::cluster_group& cl, int S, int SP, int p, int r, int k,
-                                               int KS, bool cache_uv, const Cache<T>& cc, const T* Fs,
-                                               const T* __restrict__ Fg, const T* Xs, const T* Xg, int ld,
-                                               Shared<T>& sh) {
-  const int owner = p / S, loc = p - owner * S;
-  const int tid = threadIdx.x;
-  if (tid < r) {
-    sh.vec[tid] = cache_uv ? *cl.map_shared_rank(Fs + (size_t)tid * SP + loc, owner) : Fg[p + (size_t)tid * ld];
-  } else if (tid >= KMAX && tid < KMAX + k) {
-    const int l = tid - KMAX;
-    const T x = l < KS ? *cl.map_shared_rank(Xs + (size_t)l * SP + loc, owner) : __ldcg(&Xg[p + (size_t)l * ld]);
-    sh.coef[l] = x * sh.d[l];
-  } else if (tid == 2 * KMAX) {
-    sh.piv_a = *cl.map_shared_rank(cc.a + loc, owner);
-    sh.piv_b = *cl.map_shared_rank(cc.b + loc, owner);
-  }
-  __syncthreads();
-}
-
-// Residual entries of the owned indices for a half-step at a pivot with
-// broadcast vectors in sh: out[s] = (sum_al vec[al] F[own, al]) /
-// (pa * b_own + pb * a_own) - sum_l coef[l] X[own, l].
+// Residual entries of the owned indices for a half-step at the pivot whose
+// data is in sh: out[s] = (sum_al vec[al] F[own, al]) / (pa * b_own + pb * a_own)
+//                         - sum_l craw[l] d[l] X[own, l].
 template <typename T, int RPT>
 __device__ __forceinline__ void eval_entries(const Shared<T>& sh, const Cache<T>& cc, const T* Fs,
                                              const T* __restrict__ Fg, const T* Xs, const T* Xg, int SP,
@@ -356,7 +425,7 @@ __device__ __forceinline__ void eval_entries(const Shared<T>& sh, const Cache<T>
   for (int l = 0; l < k; ++l) {
     T x[RPT];
     own_col<T, RPT>(Xs, Xg, SP, ld, KS, l, e, ok, x);
-    const T c = sh.coef[l];
+    const T c = sh.craw[l] * sh.d[l];
 #pragma unroll
     for (int s = 0; s < RPT; ++s) out[s] -= c * x[s];
   }
@@ -378,7 +447,6 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
   const bool cache_uv = cache_uv_i != 0;
   const T tol2 = (T)(A.tol * A.tol);
 
-  __shared__ Partial<T> xb[2];
   __shared__ Shared<T> sh;
   extern __shared__ __align__(16) unsigned char dyn[];
   const Cache<T> cc = carve<T>(dyn, SP, r, KS, cache_uv);
@@ -400,6 +468,8 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
   for (int i = tid; i < SP * KS; i += NT) { cc.C[i] = T(0); cc.R[i] = T(0); }
   if (tid == 0) { sh.norm2 = T(0); sh.small = 0; }
   __syncthreads();
+  // Every CTA must be running before anyone pushes into its inbox.
+  cl.sync();
 
   int e[RPT];
   bool ok[RPT], cand[RPT];
@@ -409,6 +479,8 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
     e[s] = row0 + RPT * tid + s;
     ok[s] = e[s] < row1;
   }
+  const NextSide<T> to_row{cc.U, A.Uh, cc.C, A.C, 0};   // kn is set per use
+  const NextSide<T> to_col{cc.V, A.Vh, cc.R, A.R, 0};
   const T a0 = A.a[0], b0 = A.b[0];
   // Start score ||Uh[i]||^2 / Lambda[i,0]^2 (an upper-bound proxy of row size).
 #pragma unroll
@@ -427,19 +499,21 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
     cand[s] = ok[s];
   }
   int par = 0;
-  cluster_reduce<T, RPT>(cl, CS, SP, score, ok, cand, e, cc.C, A.C, ld, KS, 0, xb, par, sh);
+  NextSide<T> nx = to_row;
+  cluster_reduce<T, RPT>(cl, CS, SP, row0, r, KS, cache_uv, ld, cc, score, ok, cand, e, cc.C, A.C, 0, nx, par, sh);
   int istar = sh.idx;
 
   int k = 0, probe_rounds = 0, zero_rows = 0;
   int converged = 0;
   while (k < A.kcap && istar >= 0) {
-    // ---------------- row half-step at istar
-    load_broadcast<T>(cl, S, SP, istar, r, k, KS, cache_uv, cc, cc.U, A.Uh, cc.C, A.C, ld, sh);
+    // ---------------- row half-step at istar (pivot data already in sh)
     eval_entries<T, RPT>(sh, cc, cc.V, A.Vh, cc.R, A.R, SP, ld, r, k, KS, cache_uv, e, ok, v);
 #pragma unroll
     for (int s = 0; s < RPT; ++s) cand[s] = ok[s] && cc.used_c[RPT * tid + s] == 0;
     if (istar >= row0 && istar < row1 && tid == 0) cc.used_r[istar - row0] = 1;
-    cluster_reduce<T, RPT>(cl, CS, SP, v, ok, cand, e, cc.R, A.R, ld, KS, k, xb, par, sh);
+    nx = to_col;
+    nx.kn = k;
+    cluster_reduce<T, RPT>(cl, CS, SP, row0, r, KS, cache_uv, ld, cc, v, ok, cand, e, cc.R, A.R, k, nx, par, sh);
     const int jstar = sh.idx;
     if (tid == 0) {
       const T dv = jstar >= 0 ? sh.val : T(0);
@@ -455,7 +529,10 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
       ++zero_rows;
 #pragma unroll
       for (int s = 0; s < RPT; ++s) cand[s] = ok[s] && cc.used_r[RPT * tid + s] == 0;
-      cluster_reduce<T, RPT>(cl, CS, SP, score, ok, cand, e, cc.C, A.C, ld, KS, 0, xb, par, sh);
+      nx = to_row;
+      nx.kn = k;
+      cluster_reduce<T, RPT>(cl, CS, SP, row0, r, KS, cache_uv, ld, cc, score, ok, cand, e, cc.C, A.C, 0, nx, par,
+                             sh);
       if (zero_rows > A.max_zero_rows || sh.idx < 0) { converged = 1; break; }
       istar = sh.idx;
       continue;
@@ -470,8 +547,6 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
       if (k < KS) cc.R[(size_t)k * SP + RPT * tid + s] = rv;
       A.R[e[s] + (size_t)k * ld] = rv;
     }
-    // (column k of R is read by other CTAs only after later cluster barriers)
-    load_broadcast<T>(cl, S, SP, jstar, r, k, KS, cache_uv, cc, cc.V, A.Vh, cc.R, A.R, ld, sh);
     eval_entries<T, RPT>(sh, cc, cc.U, A.Uh, cc.C, A.C, SP, ld, r, k, KS, cache_uv, e, ok, v);
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
@@ -481,7 +556,13 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
       if (k < KS) cc.C[(size_t)k * SP + RPT * tid + s] = v[s];
       A.C[e[s] + (size_t)k * ld] = v[s];
     }
-    cluster_reduce<T, RPT>(cl, CS, SP, v, ok, cand, e, cc.C, A.C, ld, KS, k, xb, par, sh);
+    // The pivot value is appended only now: the column evaluation above
+    // used d[0..k) and the next row step needs d[0..k].
+    __syncthreads();
+    if (tid == 0) sh.d[k] = tdelta;
+    nx = to_row;
+    nx.kn = k + 1;   // the next row step needs the new column k of C
+    cluster_reduce<T, RPT>(cl, CS, SP, row0, r, KS, cache_uv, ld, cc, v, ok, cand, e, cc.C, A.C, k, nx, par, sh);
     const int inext = sh.idx;
     // ---------------- bookkeeping (thread 0 of every CTA, same arithmetic)
     if (tid == 0) {
@@ -491,7 +572,6 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
       T cs = T(0);
       for (int l = 0; l < k; ++l) cs += sh.d[l] * sh.dots[l] * sh.gr[l];
       sh.norm2 += T(2) * delta * cs + delta * delta * csq * rr;
-      sh.d[k] = delta;
       const T term2 = delta * delta * csq * rr;       // |d|^2 |c|^2 |r|^2
       sh.small = (term2 <= tol2 * sh.norm2) ? sh.small + 1 : 0;
       if (q == 0) {
@@ -557,7 +637,10 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
         cand[s] = unused;
         bump[s] = (unused && e[s] == bad_row) ? T(INFINITY) : score[s];
       }
-      cluster_reduce<T, RPT>(cl, CS, SP, bump, ok, cand, e, cc.C, A.C, ld, KS, 0, xb, par, sh);
+      nx = to_row;
+      nx.kn = k;
+      cluster_reduce<T, RPT>(cl, CS, SP, row0, r, KS, cache_uv, ld, cc, bump, ok, cand, e, cc.C, A.C, 0, nx, par,
+                             sh);
       istar = sh.idx;
       if (istar < 0) { converged = 1; break; }
       continue;
@@ -565,7 +648,7 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
     istar = inext;
     if (istar < 0) { converged = 1; break; }
   }
-  // No CTA may exit while another can still read its shared memory.
+  // No CTA may exit while another can still write into its shared memory.
   cl.sync();
   if (q == 0 && tid == 0) {
     A.st->k = k;
@@ -576,23 +659,56 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
   }
 }
 
+// Per-kernel launch facts that do not change during a process: set the
+// attributes and query the static shared memory once, not before every launch.
+struct KernelFacts {
+  bool ready = false;
+  cudaError_t err = cudaSuccess;
+  int optin = 0;
+  size_t static_smem = 0;
+};
+
+template <typename T, int RPT>
+static KernelFacts& cross_facts() {
+  static KernelFacts f;
+  if (!f.ready) {
+    auto kern = cross_kernel<T, RPT>;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&f.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    f.err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (f.err == cudaSuccess) f.err = cudaFuncGetAttributes(&fa, kern);
+    if (f.err == cudaSuccess) {
+      f.static_smem = fa.sharedSizeBytes;
+      f.err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   f.optin - (int)fa.sharedSizeBytes);
+    }
+    f.ready = true;
+  }
+  return f;
+}
+
+// Clusters of a configuration that fit on the device (memoised).
+static std::map<std::tuple<const void*, int, int, size_t>, int>& cluster_fit_cache() {
+  static std::map<std::tuple<const void*, int, int, size_t>, int> c;
+  return c;
+}
+
 template <typename T, int RPT>
 static cudaError_t launch_cross_rpt(const CrossArgs<T>& a, int cs, int nt, cudaStream_t st) {
   auto kern = cross_kernel<T, RPT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) return e;
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, kern);
-  if (e != cudaSuccess) return e;
-  // Shared-memory budget: symbol slices and flags always, Uh/Vh slices if
-  // they fit in half of what is left, then as many skeleton columns as fit.
+  const KernelFacts& f = cross_facts<T, RPT>();
+  if (f.err != cudaSuccess) return f.err;
+  cudaError_t e;
+  // Shared-memory budget: inboxes, symbol slices and flags always, Uh/Vh
+  // slices if they fit in half of what is left, then as many skeleton
+  // columns as fit.
   const long long SP = (long long)nt * RPT;
   const long long w = (long long)sizeof(T);
-  const long long budget = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
-  const long long fixed = 2LL * SP * w + 2LL * SP + 64;
+  const long long budget = (long long)f.optin - (long long)f.static_smem - 1024;
+  const long long fixed = (long long)inbox_bytes<T>() + 2LL * SP * w + 2LL * SP + 64;
+  if (fixed > budget) return cudaErrorInvalidConfiguration;
   const long long uv = 2LL * SP * a.r * w;
   const bool cache_uv = uv <= (budget - fixed) / 2;
   const long long left = budget - fixed - (cache_uv ? uv : 0);
@@ -600,8 +716,6 @@ static cudaError_t launch_cross_rpt(const CrossArgs<T>& a, int cs, int nt, cudaS
   if (KS > a.kcap) KS = a.kcap;
   if (KS < 0) KS = 0;
   const size_t dsmem = (size_t)(fixed + (cache_uv ? uv : 0) + 2LL * SP * KS * w);
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem);
-  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, 1, 1);
   cfg.blockDim = dim3(nt, 1, 1);
@@ -614,16 +728,23 @@ static cudaError_t launch_cross_rpt(const CrossArgs<T>& a, int cs, int nt, cudaS
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const auto key = std::make_tuple((const void*)kern, cs, nt, dsmem);
+  auto it = cluster_fit_cache().find(key);
   int nclusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
-  if (e != cudaSuccess) return e;
+  if (it == cluster_fit_cache().end()) {
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    cluster_fit_cache()[key] = nclusters;
+  } else {
+    nclusters = it->second;
+  }
   if (nclusters < 1) return cudaErrorInvalidConfiguration;
   return cudaLaunchKernelEx(&cfg, kern, a, (int)KS, cache_uv ? 1 : 0);
 }
 
 // Rows per thread RPT (a power of two) and threads per CTA for S indices:
-// about four rows per thread, 160 to 512 threads (the broadcast uses threads
-// up to 2*KMAX); more rows per thread only when S exceeds 512 * 4.
+// about four rows per thread, 160 to 512 threads (threads up to 2*KMAX + 1
+// carry pivot data); more rows per thread only when S exceeds 512 * 4.
 static void cross_shape(int S, int* nt, int* rpt) {
   int r = 1;
   while (r < 4 && r * 160 < S) r *= 2;

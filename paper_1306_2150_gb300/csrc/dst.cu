@@ -187,25 +187,43 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
   cpx<T>* twS = buf + nelem;
   load_twiddles(twS, tw, g.logM, g.logM);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x) {
-      const int row = idx >> g.logM, t = idx & (M - 1);
-      const int col = (item << lognf) + row;
-      int seg, cc;
-      cpx<T> v = {T(0), T(0)};
-      if (col < g.ncols && t < g.m && col_live(c, col, seg, cc)) {
-        const T x = load_in<T, INM>(c, seg, cc, t);
-        const cpx<T> w = chirp[t];
-        v = {x * w.re, x * w.im};
+    // Every loop below covers exactly EPT elements per thread; it is unrolled
+    // so that a thread's global loads are all in flight together.
+    {
+      cpx<T> v[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        const int row = idx >> g.logM, t = idx & (M - 1);
+        const int col = (item << lognf) + row;
+        int seg, cc;
+        v[s] = {T(0), T(0)};
+        if (col < g.ncols && t < g.m && col_live(c, col, seg, cc)) {
+          const T x = load_in<T, INM>(c, seg, cc, t);
+          const cpx<T> w = chirp[t];
+          v[s] = {x * w.re, x * w.im};
+        }
       }
-      buf[idx] = v;
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
     smem_fft<T, false>(buf, g.logM, lognf, 1, M, twS, g.logM, false);
-    for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x)
-      buf[idx] = cmul(buf[idx], bhat[idx & (M - 1)]);
+    {
+      cpx<T> b[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) b[s] = bhat[(threadIdx.x + s * blockDim.x) & (M - 1)];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        buf[idx] = cmul(buf[idx], b[s]);
+      }
+    }
     __syncthreads();
     smem_fft<T, false>(buf, g.logM, lognf, 1, M, twS, g.logM, true);
-    for (int idx = threadIdx.x; idx < nelem; idx += blockDim.x) {
+#pragma unroll
+    for (int s = 0; s < EPT; ++s) {
+      const int idx = threadIdx.x + s * blockDim.x;
       const int row = idx >> g.logM, t = idx & (M - 1);
       const int col = (item << lognf) + row;
       int seg, cc;
@@ -240,24 +258,39 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
     const int t1_0 = (item - col * blocks_per_col) << logTX;
     int seg, cc;
     if (!col_live(c, col, seg, cc)) continue;  // uniform across the CTA
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-      const int t2 = idx >> logTX, dt = idx & (TX - 1);
-      const int t = t1_0 + dt + (t2 << g.logM1);
-      cpx<T> v = {T(0), T(0)};
-      if (t < g.m) {
-        const T x = load_in<T, INM>(c, seg, cc, t);
-        const cpx<T> w = chirp[t];
-        v = {x * w.re, x * w.im};
+    {
+      cpx<T> v[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        const int t2 = idx >> logTX, dt = idx & (TX - 1);
+        const int t = t1_0 + dt + (t2 << g.logM1);
+        v[s] = {T(0), T(0)};
+        if (t < g.m) {
+          const T x = load_in<T, INM>(c, seg, cc, t);
+          const cpx<T> w = chirp[t];
+          v[s] = {x * w.re, x * w.im};
+        }
       }
-      buf[idx] = v;
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
     smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, twS, g.logM2, false);
     cpx<T>* wc = work + ((size_t)col << g.logM);
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-      const int k2 = idx >> logTX, dt = idx & (TX - 1);
-      const int t1 = t1_0 + dt;
-      wc[(k2 << g.logM1) + t1] = cmul(buf[idx], tw[t1 * k2]);
+    {
+      cpx<T> w[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        w[s] = tw[(t1_0 + (idx & (TX - 1))) * (idx >> logTX)];
+      }
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        const int k2 = idx >> logTX, t1 = t1_0 + (idx & (TX - 1));
+        wc[(k2 << g.logM1) + t1] = cmul(buf[idx], w[s]);
+      }
     }
     __syncthreads();
   }
@@ -282,13 +315,21 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
     int seg, cc;
     if (!col_live(c, col, seg, cc)) continue;
     const cpx<T>* wc = work + ((size_t)col << g.logM);
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-      const int k2 = idx >> logTX, dt = idx & (TX - 1);
-      buf[idx] = wc[(k2 << g.logM1) + t1_0 + dt];
+    {
+      cpx<T> v[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        v[s] = wc[((idx >> logTX) << g.logM1) + t1_0 + (idx & (TX - 1))];
+      }
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
     smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, twS, g.logM2, true);
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
+#pragma unroll
+    for (int s = 0; s < EPT; ++s) {
+      const int idx = threadIdx.x + s * blockDim.x;
       const int t2 = idx >> logTX, dt = idx & (TX - 1);
       const int t = t1_0 + dt + (t2 << g.logM1);
       if (t < g.m) {
@@ -321,15 +362,39 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
     if (!col_live(c, col, seg, cc)) continue;
     cpx<T>* wc = work + ((size_t)col << g.logM) + ((size_t)k2_0 << g.logM1);
     const cpx<T>* bh = bhat + ((size_t)k2_0 << g.logM1);
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) buf[idx] = wc[idx];
+    {
+      cpx<T> v[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) v[s] = wc[threadIdx.x + s * blockDim.x];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
+    }
     __syncthreads();
     smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, twS, g.logM1, false);
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) buf[idx] = cmul(buf[idx], bh[idx]);
+    {
+      cpx<T> b[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) b[s] = bh[threadIdx.x + s * blockDim.x];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        buf[idx] = cmul(buf[idx], b[s]);
+      }
+    }
     __syncthreads();
     smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, twS, g.logM1, true);
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-      const int k2 = k2_0 + (idx >> g.logM1), t1 = idx & (M1 - 1);
-      wc[idx] = cmulc(buf[idx], tw[t1 * k2]);  // times exp(+2 pi i t1 k2 / M)
+    {
+      cpx<T> w[EPT];
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        w[s] = tw[(idx & (M1 - 1)) * (k2_0 + (idx >> g.logM1))];
+      }
+#pragma unroll
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        wc[idx] = cmulc(buf[idx], w[s]);  // times exp(+2 pi i t1 k2 / M)
+      }
     }
     __syncthreads();
   }
@@ -365,7 +430,11 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
     const int items = (g.ncols + (1 << lognf) - 1) >> lognf;
     const int grid = items < 8 * num_sms ? items : 8 * num_sms;
     auto kern = dst_small_kernel<T, INM, OUT64>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool attr_set = false;  // once per instantiation: 128 KB covers every tile
+    if (!attr_set) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTileElems * (int)sizeof(cpx<T>));
+      attr_set = true;
+    }
     kern<<<grid, threads, smem, st>>>(c, g, chirp, tw, bhat, lognf);
     return cudaGetLastError();
   }
@@ -385,9 +454,14 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
   auto k1 = dst_col_fwd_kernel<T, INM>;
   auto k2 = dst_row_mid_kernel<T>;
   auto k3 = dst_col_inv_kernel<T, OUT64>;
-  cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static bool attr_set = false;  // once per instantiation: tile + twiddles <= 2 tiles
+  if (!attr_set) {
+    const int mx = 2 * kTileElems * (int)sizeof(cpx<T>);
+    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    attr_set = true;
+  }
   k1<<<items_col < cap ? items_col : cap, threads, smem, st>>>(c, g2, chirp, tw, wk);
   k2<<<items_row < cap ? items_row : cap, threads, smem, st>>>(c, g2, tw, bhat, wk);
   k3<<<items_col < cap ? items_col : cap, threads, smem, st>>>(c, g2, chirp, tw, wk);

@@ -22,6 +22,7 @@ LR_FP64, LR_MIXED = 0, 1
 LR_OP_5PT, LR_OP_SEMISTAGGERED = 0, 1
 LR_FLAG_ASYNC = 1
 LR_FLAG_TIMING = 2
+LR_FLAG_GRAPH = 4
 PHASES = ("forward_dst", "cross", "rounding", "inverse_dst")
 
 PRECISIONS = {"fp64": LR_FP64, "mixed": LR_MIXED}
@@ -30,7 +31,8 @@ OPERATORS = {"5pt": LR_OP_5PT, "semi": LR_OP_SEMISTAGGERED}
 # Every function the header declares (checked against the header by the tests).
 EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
-           "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc")
+           "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
+           "lr_poisson2d_batched")
 
 
 class LrMat(ctypes.Structure):
@@ -99,6 +101,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_get_phase_times.restype = c_int
     lib.lr_truncate_noalloc.argtypes = [ctypes.POINTER(LrMat), c_double, c_int, c_void_p]
     lib.lr_truncate_noalloc.restype = c_int
+    lib.lr_poisson2d_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
+                                         ctypes.POINTER(LrOptions), ctypes.POINTER(c_int)]
+    lib.lr_poisson2d_batched.restype = c_int
     if path is None:
         _lib = lib
     return lib
@@ -211,7 +216,7 @@ def _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_s
 def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rmax: int = 64,
                  rmax_out: int = 64, aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
                  cluster_size: int = 0, async_: bool = False, out=None, check: bool = True,
-                 timing: bool = False):
+                 timing: bool = False, graph: bool = False):
     """Low-rank solve of A X = U V^T.  Returns SolveResult with the solution
     factors (views of rank R) unless ``async_`` (then read lr_get_info after
     synchronising the stream).  ``out`` = (Uo, s, Vo) preallocated outputs."""
@@ -239,7 +244,8 @@ def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rma
     sol = LrMat(m, m, 0, Uo.shape[1], _ld(Uo), Uo.data_ptr(), s.data_ptr(), Vo.data_ptr())
     if _ld(Vo) != _ld(Uo):
         raise ValueError("output factors need the same leading dimension")
-    flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_TIMING if timing else 0)
+    flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_TIMING if timing else 0) | \
+        (LR_FLAG_GRAPH if graph else 0)
     o = _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size)
     st = load().lr_poisson2d(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o))
     if async_:
@@ -307,3 +313,55 @@ def lr_get_phase_times(h: Handle) -> dict:
     if st != LR_OK:
         raise LrError(st, h.last_error())
     return dict(zip(PHASES, list(ms)))
+
+
+class Batch:
+    """Device buffers of a batch of problems for lr_poisson2d_batched: the
+    right-hand sides (column-major float64) and preallocated outputs."""
+
+    def __init__(self, problems, rmax_out: int = 64, device="cuda"):
+        import torch
+        self.rhs, self.out = [], []
+        for U, V in problems:
+            U = as_colmajor(U.to(device) if hasattr(U, "to") else torch.from_numpy(U).to(device))
+            V = as_colmajor(V.to(device) if hasattr(V, "to") else torch.from_numpy(V).to(device))
+            if U.stride(1) != V.stride(1):
+                V2 = colmajor_empty(V.shape[0], V.shape[1], device)
+                V2.copy_(V)
+                V = V2
+            m = U.shape[0]
+            Uo, Vo = colmajor_empty(m, rmax_out, device), colmajor_empty(m, rmax_out, device)
+            s = torch.empty(rmax_out, dtype=torch.float64, device=device)
+            self.rhs.append((U, V))
+            self.out.append((Uo, s, Vo))
+        n = len(problems)
+        self.c_rhs = (LrMat * n)()
+        self.c_sol = (LrMat * n)()
+        for i, ((U, V), (Uo, s, Vo)) in enumerate(zip(self.rhs, self.out)):
+            m, r = U.shape
+            self.c_rhs[i] = LrMat(m, m, r, r, _ld(U), U.data_ptr(), None, V.data_ptr())
+            self.c_sol[i] = LrMat(m, m, 0, Uo.shape[1], _ld(Uo), Uo.data_ptr(), s.data_ptr(), Vo.data_ptr())
+        self.status = (ctypes.c_int * n)()
+
+    def __len__(self):
+        return len(self.rhs)
+
+    def result(self, i):
+        R = self.c_sol[i].r
+        Uo, s, Vo = self.out[i]
+        return Uo[:, :R], s[:R], Vo[:, :R]
+
+
+def lr_poisson2d_batched(h: Handle, batch: Batch, eps: float = 1e-6, prec="mixed", op="5pt",
+                         rmax: int = 64, aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
+                         cluster_size: int = 0, async_: bool = False, graph: bool = False,
+                         check: bool = True) -> int:
+    """Solve every problem of ``batch``; returns the lr_status of the call
+    (per-problem statuses in ``batch.status``, results via ``batch.result``)."""
+    flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_GRAPH if graph else 0)
+    o = _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size)
+    st = load().lr_poisson2d_batched(h.ptr, len(batch), batch.c_rhs, batch.c_sol, ctypes.byref(o),
+                                     batch.status)
+    if check and st not in (LR_OK, LR_ENOCONV):
+        raise LrError(st, h.last_error())
+    return st
