@@ -40,7 +40,11 @@ typedef enum {
   LR_ENOCONV = 3,    /* cross hit its step cap or the rank was cut to capacity;
                         the best partial result is written */
   LR_ETIMEOUT = 4,   /* a bounded device wait ran out */
-  LR_ECUDA = 5       /* a CUDA runtime call failed */
+  LR_ECUDA = 5,      /* a CUDA runtime call failed */
+  LR_ENONFINITE = 6  /* a non-finite value reached the rounding core (in
+                        LR_MIXED: entries of the frequency-space solution
+                        outside the float32 range; rescale the right-hand
+                        side); no factors are written */
 } lr_status;
 
 typedef enum {
@@ -104,6 +108,16 @@ typedef struct {
   unsigned long long seed; /* splitmix64 seed of the probe positions */
   unsigned int flags;    /* LR_FLAG_* */
   int cluster_size;      /* CTAs per cross cluster (0 = automatic, 1..16) */
+  int refine;            /* LR_MIXED only: maximum rounds of iterative
+                            refinement in float64 (0 = automatic: up to 3
+                            rounds when eps < 1e-7, none otherwise; -1 =
+                            none).  A round forms the residual F - A X
+                            exactly in float64 as a low-rank matrix, rounds
+                            it with a shifted Cholesky QR, solves for the
+                            correction D in mixed precision and rounds X + D
+                            at eps.  Rounds stop early once the correction
+                            is below eps / 10 of X.  Refined solves are
+                            synchronous. */
 } lr_options;
 
 /* Result details of the last solve on a handle. */
@@ -119,10 +133,13 @@ typedef struct {
   int launches;          /* kernels launched by the solve */
   double norm_est;       /* cross estimate of ||Xh||_F */
   double sigma0;         /* largest singular value kept */
+  int refine_rounds;     /* refinement rounds taken (LR_MIXED, eps < 1e-7) */
+  int pad;
+  double refine_corr;    /* sigma_0 of the last correction / sigma_0 of X */
 } lr_info;
 
 /* Defaults: LR_MIXED, LR_OP_5PT, eps 1e-6, rmax 64, aca_tol_factor 1,
- * 16 probes, seed 0, flags 0, cluster_size 0. */
+ * 16 probes, seed 0, flags 0, cluster_size 0, refine 0. */
 void lr_options_default(lr_options* opt);
 
 /* Create a handle bound to a CUDA stream (cudaStream_t, NULL = legacy default
@@ -154,7 +171,7 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
 /* Batched low-rank Poisson solves: `batch` independent problems (host arrays
  * rhs[batch], sol[batch] of lr_mat with device pointers, each as for
  * lr_poisson2d, sizes and ranks may differ) with shared options.  Problems
- * are enqueued in decreasing order of size over 16 internal streams that fork
+ * are enqueued in decreasing order of size over 32 internal streams that fork
  * from and join back into the handle's stream; with LR_FLAG_GRAPH the whole
  * batch is one replayed CUDA graph.  per_problem (host, may be NULL) receives
  * each problem's status; the return value is LR_OK or the first failure.

@@ -2,6 +2,7 @@
 // declared in include/lrpoisson.h.  Every numerical step runs in the kernels of
 // dst.cu, cross.cu and core.cu; this file validates arguments, lays out the
 // workspace and enqueues the launches on the handle's stream.
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
@@ -30,8 +31,8 @@ struct lr_handle_s {
   cudaEvent_t ev[LR_NUM_PHASES + 1] = {};
   bool timed = false;
   // batched solves: internal streams, fork/join events, pinned status array
-  cudaStream_t bstreams[16] = {};
-  cudaEvent_t bjoin[16] = {};
+  cudaStream_t bstreams[32] = {};
+  cudaEvent_t bjoin[32] = {};
   cudaEvent_t bfork = nullptr;
   SolveState* h_bstate = nullptr;
   int bstate_cap = 0;
@@ -40,6 +41,9 @@ struct lr_handle_s {
   std::map<std::string, cudaGraphExec_t> graphs;
   unsigned long long ws_gen = 0;
   int last_cs = 0;
+  // float64 buffers of iterative refinement (solution, correction, residual)
+  void* ws2 = nullptr;
+  size_t ws2_bytes = 0;
 };
 
 namespace {
@@ -59,6 +63,9 @@ lr_status cuda_fail(lr_handle h, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                        \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
   } while (0)
+
+const char* const kNonFiniteMsg =
+    "non-finite value in the rounding core (in LR_MIXED: frequency-space entries outside the float32 range)";
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int round_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -130,6 +137,7 @@ lr_status check_opts(lr_handle h, const lr_options& o) {
     return fail(h, LR_EINVAL, "aca_tol_factor must be positive");
   if (o.probes < 0 || o.probes > 32) return fail(h, LR_EINVAL, "probes must be in [0, 32]");
   if (o.cluster_size < 0 || o.cluster_size > 16) return fail(h, LR_EINVAL, "cluster_size must be in [0, 16]");
+  if (o.refine < -1 || o.refine > 8) return fail(h, LR_EINVAL, "refine must be in [-1, 8]");
   return LR_OK;
 }
 
@@ -335,12 +343,239 @@ lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options&
   LR_CUDA(h, cudaStreamSynchronize(h->stream), "solve");
   const SolveState& hs = *h->h_state;
   sol->r = hs.rank;
+  if (hs.status) return fail(h, static_cast<lr_status>(hs.status), kNonFiniteMsg);
   if (!hs.converged) return fail(h, LR_ENOCONV, "cross did not converge within opt->rmax steps");
   if (hs.cut) return fail(h, LR_ENOCONV, "solution rank exceeds sol->rmax; result truncated");
   return LR_OK;
 }
 
-constexpr int kBatchStreams = 16;
+// Mixed-precision solve followed by up to `rounds` rounds of refinement in
+// float64 (residual correction):
+//   X  <- solve(F)                        (mixed, at max(eps, 1e-6))
+//   repeat: Res = F - A X                 (exact, low rank r + 2R, float64)
+//           Res <- QR-round(Res, 1e-8)    (shifted Cholesky QR + core SVD)
+//           D   = s0 solve(Res / s0)      (mixed, at 1e-6, at unit scale)
+//           X   <- round(X + D, eps)      (float64 rounding, Section 3)
+//   until sigma_0(D) <= sigma_0(X) eps / 10.
+// The float32 error of X lives in its factors, so Res stays low rank; each
+// round multiplies the error by about the accuracy of the correction solve.
+struct RefineBufs {
+  double *XU, *XV, *Xs;        // X, with room for X + D (KMAX columns)
+  double *L, *Rt, *Lb, *Rb;    // residual factors and Cholesky QR ping-pong buffers
+  double *FU, *FV;             // rounded residual (partial sums over chunks of X)
+  double *G0, *G1, *T0, *T1, *Ra0, *Ra1, *Tc, *Tr, *rs, *part;
+  int* qout;
+  SolveState* st;
+};
+
+void carve_refine(Carve& c, RefineBufs& b, int ld, int m) {
+  const size_t col = sizeof(double) * (size_t)ld * KMAX;
+  const size_t sq = sizeof(double) * KMAX * KMAX;
+  b.XU = c.take<double>(col);
+  b.XV = c.take<double>(col);
+  b.L = c.take<double>(col);
+  b.Rt = c.take<double>(col);
+  b.Lb = c.take<double>(col);
+  b.Rb = c.take<double>(col);
+  b.FU = c.take<double>(col);
+  b.FV = c.take<double>(col);
+  b.Xs = c.take<double>(sizeof(double) * KMAX);
+  b.rs = c.take<double>(sizeof(double) * KMAX);
+  b.G0 = c.take<double>(sq);
+  b.G1 = c.take<double>(sq);
+  b.T0 = c.take<double>(sq);
+  b.T1 = c.take<double>(sq);
+  b.Ra0 = c.take<double>(sq);
+  b.Ra1 = c.take<double>(sq);
+  b.Tc = c.take<double>(sq);
+  b.Tr = c.take<double>(sq);
+  b.part = c.take<double>(sq * (size_t)((m + 63) / 64));
+  b.qout = c.take<int>(sizeof(int) * 2);
+  b.st = c.take<SolveState>(sizeof(SolveState));
+}
+
+// Rounding of L diag(d) Rt^T (q <= 64 columns, d = null: ones) through QR
+// factors of L and Rt by shifted Cholesky QR and the SVD of the core
+// R_L diag(d) R_R^T (Section 3).  Backward stable, so it keeps a product far
+// smaller than its factors (a residual) and returns factors orthonormal to
+// working accuracy.  Results (rank K, sigma_0 on the host) go to U, V, s
+// (ld ldo); the weights are folded into U if fold is 1 (s) or 2 (s / s_0).
+// Scratch: b.L, b.Rt, b.Lb, b.Rb, the small matrices and b.st.
+lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const double* Rin, int ldin, int m, int q,
+                   const double* d, double eps, int rmax, double* U, double* V, double* s_out, int ldo, int fold,
+                   int* K, double* sigma0) {
+  cudaStream_t stm = h->stream;
+  const int ld = m + (m & 1);
+  const double* Xl = Lin;
+  const double* Xr = Rin;
+  int ldx = ldin;
+  double* Yl = b.Lb;
+  double* Yr = b.Rb;
+  // Shift of the first step (equilibrated Gram matrix, ||G|| <= q).
+  const double shift = 11.0 * ((double)m * q + (double)q * (q + 1)) * (DBL_EPSILON / 2) * q;
+  for (int step = 0; step < 3; ++step) {
+    LR_CUDA(h, launch_gram(Xl, m, ldx, q, b.G0, q, b.part, h->num_sms, stm), "gram");
+    LR_CUDA(h, launch_gram(Xr, m, ldx, q, b.G1, q, b.part, h->num_sms, stm), "gram");
+    CholQrArgs a;
+    a.G[0] = b.G0; a.G[1] = b.G1;
+    a.T[0] = b.T0; a.T[1] = b.T1;
+    a.Racc[0] = b.Ra0; a.Racc[1] = b.Ra1;
+    a.qout = b.qout;
+    a.q = q;
+    a.first = step == 0;
+    a.shift = step == 0 ? shift : 0.0;
+    a.floor_rel = step == 0 ? 0.5 * shift : 1e-15;
+    LR_CUDA(h, launch_cholqr_step(a, stm), "cholesky qr");
+    LR_CUDA(h, (launch_rotate<double, double>(Xl, ldx, m, nullptr, q, b.T0, false, &b.qout[0], Yl, ld, stm)), "qr");
+    LR_CUDA(h, (launch_rotate<double, double>(Xr, ldx, m, nullptr, q, b.T1, false, &b.qout[1], Yr, ld, stm)), "qr");
+    // ping-pong: Lb -> L -> Lb
+    Xl = Yl;
+    Xr = Yr;
+    ldx = ld;
+    Yl = step == 0 ? b.L : b.Lb;
+    Yr = step == 0 ? b.Rt : b.Rb;
+  }
+  LR_CUDA(h, cudaMemsetAsync(b.st, 0, sizeof(SolveState), stm), "state reset");
+  CoreArgs<double> co;
+  co.GC = b.Ra0; co.GR = b.Ra1; co.ldg = KMAX; co.d = d;
+  co.k_dev = nullptr; co.k_host = q;
+  co.eps = eps; co.rmax_out = rmax;
+  co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = s_out; co.st = b.st;
+  co.tri_given = 1;
+  LR_CUDA(h, launch_core<double>(co, false, stm), "qr rounding core");
+  LR_CUDA(h, (launch_rotate<double, double>(Xl, ld, m, nullptr, q, b.Tc, false, &b.st->rank, U, ldo, stm)), "rot");
+  LR_CUDA(h, (launch_rotate<double, double>(Xr, ld, m, nullptr, q, b.Tr, false, &b.st->rank, V, ldo, stm)), "rot");
+  if (fold) LR_CUDA(h, launch_fold_weights(m, q, &b.st->rank, U, ldo, s_out, fold == 2, stm), "fold");
+  LR_CUDA(h, cudaMemcpyAsync(h->h_state, b.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm), "state copy");
+  LR_CUDA(h, cudaStreamSynchronize(stm), "qr rounding");
+  if (h->h_state->status) return fail(h, static_cast<lr_status>(h->h_state->status), kNonFiniteMsg);
+  *K = h->h_state->rank;
+  *sigma0 = h->h_state->sigma0;
+  if (h->h_state->cut) return fail(h, LR_ENOCONV, "rank exceeds rmax; result truncated");
+  return LR_OK;
+}
+constexpr int kQrRoundLaunches = 3 * 7 + 4;
+
+lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options& o, Plan* plan,
+                          int rounds) {
+  const int m = rhs->n1, r = rhs->r;
+  const int ld = m + (m & 1);
+  RefineBufs b;
+  Carve sizing;
+  carve_refine(sizing, b, ld, m);
+  if (sizing.off > h->ws2_bytes) {
+    if (h->ws2) { cudaStreamSynchronize(h->stream); cudaFree(h->ws2); h->ws2 = nullptr; h->ws2_bytes = 0; }
+    if (cudaMalloc(&h->ws2, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "refinement buffers"); }
+    h->ws2_bytes = sizing.off;
+  }
+  Carve cv;
+  cv.base = static_cast<char*>(h->ws2);
+  carve_refine(cv, b, ld, m);
+  cudaStream_t stm = h->stream;
+  lr_options o1 = o;
+  o1.eps = o.eps > 1e-6 ? o.eps : 1e-6;
+  o1.flags = 0;
+  o1.refine = -1;
+  lr_mat X = {m, m, 0, KMAX, ld, b.XU, b.Xs, b.XV};
+  lr_status s = solve2d<float>(h, rhs, &X, o1, plan);
+  if (s != LR_OK && s != LR_ENOCONV) return s;
+  lr_status worst = s;
+  // The first solve's cross statistics and pivots describe the solve.
+  const SolveState first = *h->h_state;
+  int piv[2 * KMAX];
+  std::memcpy(piv, h->h_piv, sizeof piv);
+  const int cs_first = h->info.cluster_size;
+  int launches = h->info.launches;
+  double sigX = first.sigma0, corr = 0.0;
+  int done = 0;
+  for (int it = 0; it < rounds && X.r > 0; ++it) {
+    const int R1 = X.r;
+    if (R1 >= KMAX) { worst = LR_ENOCONV; fail(h, worst, "no room for the correction (R = 64)"); break; }
+    // Res = F - A X accumulated over chunks X_j of X's columns (largest
+    // singular values first, where F and A X cancel):
+    //   Res_j = round(Res_{j-1} - A X_j),  Res_0 = F,
+    // each rounding on at most 64 columns (width of Res_{j-1} + 2 |X_j|).
+    const double* FUp = rhs->U;
+    const double* FVp = rhs->V;
+    int fr = r, fld = rhs->ld, off = 0, Kres = 0;
+    double rs0 = 0.0;
+    bool stuck = false;
+    while (off < R1) {
+      const int c = std::min(R1 - off, (KMAX - fr) / 2);
+      if (c < 1) { stuck = true; break; }
+      const int q = fr + 2 * c;
+      const bool last = off + c == R1;
+      LR_CUDA(h, launch_residual_factors(m, fr, c, FUp, FVp, fld, X.U + (size_t)off * ld, X.s + off,
+                                         X.V + (size_t)off * ld, ld, (int)o.op, b.L, b.Rt, ld, stm), "residual");
+      // Intermediate sums are kept to 1e-12 of their size (F - A X_1 is
+      // already far below F); the last one only to the accuracy the float32
+      // correction solve can use.
+      s = qr_round(h, b, b.L, b.Rt, ld, m, q, nullptr, last ? 1e-8 : 1e-12, KMAX, b.FU, b.FV, b.rs, ld,
+                   last ? 2 : 1, &Kres, &rs0);
+      if (s != LR_OK) return s;
+      launches += 1 + kQrRoundLaunches;
+      FUp = b.FU;
+      FVp = b.FV;
+      fr = Kres;
+      fld = ld;
+      off += c;
+    }
+    if (stuck) { worst = LR_ENOCONV; fail(h, worst, "residual rank too large for refinement (> 64)"); break; }
+    if (Kres == 0) break;  // X solves the float64 system exactly
+    double* Yl = b.FU;
+    double* Yr = b.FV;
+    // Correction D, written after X's R1 columns (room KMAX - R1).
+    lr_mat res = {m, m, Kres, Kres, ld, Yl, nullptr, Yr};
+    lr_mat D = {m, m, 0, KMAX - R1, ld, X.U + (size_t)R1 * ld, X.s + R1, X.V + (size_t)R1 * ld};
+    s = solve2d<float>(h, &res, &D, o1, plan);
+    if (s != LR_OK && s != LR_ENOCONV) return s;  // ENOCONV: D cut to the room left, or cross cap
+    launches += h->info.launches;
+    const int R2 = D.r;
+    const double sd = h->h_state->sigma0 * rs0;
+    LR_CUDA(h, launch_scale_weights(R2, X.s + R1, b.rs, stm), "scale");
+    // X + D = [XU, DU] diag(Xs, Ds) [XV, DV]^T, rounded at eps.  D lies
+    // mostly in X's column space, which a Gram-based rounding would resolve
+    // only to sqrt(eps64); the QR rounding keeps the factors orthonormal.
+    int Rn = 0;
+    double sig_new = 0.0;
+    s = qr_round(h, b, X.U, X.V, ld, m, R1 + R2, X.s, o.eps, KMAX, X.U, X.V, X.s, ld, 0, &Rn, &sig_new);
+    if (s != LR_OK && s != LR_ENOCONV) return s;
+    if (s != LR_OK) worst = s;
+    launches += 1 + kQrRoundLaunches;
+    X.r = Rn;
+    corr = sigX > 0.0 ? sd / sigX : 0.0;
+    sigX = sig_new;
+    ++done;
+    if (corr <= 0.1 * o.eps) break;
+  }
+  // Copy the result into the caller's buffers.
+  int R = X.r;
+  if (R > sol->rmax) { R = sol->rmax; worst = LR_ENOCONV; fail(h, worst, "solution rank exceeds sol->rmax"); }
+  const size_t col = sizeof(double) * (size_t)ld;
+  if (R > 0) {
+    LR_CUDA(h, cudaMemcpy2DAsync(sol->U, sizeof(double) * sol->ld, X.U, col, sizeof(double) * m, R,
+                                 cudaMemcpyDeviceToDevice, stm), "copy U");
+    LR_CUDA(h, cudaMemcpy2DAsync(sol->V, sizeof(double) * sol->ld, X.V, col, sizeof(double) * m, R,
+                                 cudaMemcpyDeviceToDevice, stm), "copy V");
+    LR_CUDA(h, cudaMemcpyAsync(sol->s, X.s, sizeof(double) * R, cudaMemcpyDeviceToDevice, stm), "copy s");
+  }
+  LR_CUDA(h, cudaStreamSynchronize(stm), "refined solve");
+  sol->r = R;
+  SolveState fin = first;
+  fin.rank = R;
+  fin.sigma0 = sigX;
+  fin.cut = worst == LR_ENOCONV && first.converged;
+  *h->h_state = fin;
+  std::memcpy(h->h_piv, piv, sizeof piv);
+  h->info.cluster_size = cs_first;
+  h->last_cs = cs_first;
+  h->info.launches = launches;
+  h->info.refine_rounds = done;
+  h->info.refine_corr = corr;
+  return worst;
+}
+
+constexpr int kBatchStreams = 32;
 
 lr_status ensure_batch_streams(lr_handle h) {
   if (h->bstreams[0]) return LR_OK;
@@ -389,6 +624,16 @@ lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol
   });
   int launches = 0;
   for (int i = 0; i < batch; ++i) launches += launches_of(geo[i]);
+  // Throughput mode: unless the caller fixed it, give each cross about 2048
+  // indices per CTA.  Its per-step cost is mostly a fixed latency, so fewer,
+  // fuller CTAs per problem spend less SM time and let more problems run at
+  // once (a single solve uses about 1024 indices per CTA for latency).
+  std::vector<lr_options> popt(batch, o);
+  if (o.cluster_size == 0)
+    for (int i = 0; i < batch; ++i) {
+      int cs = (geo[i].m + 2047) / 2048;
+      popt[i].cluster_size = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
+    }
   const bool graph = (o.flags & LR_FLAG_GRAPH) != 0;
   s = run_maybe_graph(h, graph, key_of("batch", rhs, batch, sol, o), [&](cudaStream_t main) -> cudaError_t {
     cudaError_t e;
@@ -401,7 +646,7 @@ lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol
       ci.base = base + off[i];
       const Slice<T> w = carve_slice<T>(ci, geo[i]);
       int used = 0;
-      if ((e = enqueue_solve<T>(h, &rhs[i], &sol[i], o, *plans[i], geo[i], w, &states[i],
+      if ((e = enqueue_solve<T>(h, &rhs[i], &sol[i], popt[i], *plans[i], geo[i], w, &states[i],
                                 h->bstreams[n % kBatchStreams], nullptr, &used)) != cudaSuccess)
         return e;
     }
@@ -419,9 +664,10 @@ lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol
   for (int i = 0; i < batch; ++i) {
     const SolveState& hs = h->h_bstate[i];
     sol[i].r = hs.rank;
-    const lr_status si = (!hs.converged || hs.cut) ? LR_ENOCONV : LR_OK;
+    const lr_status si = hs.status ? static_cast<lr_status>(hs.status)
+                                   : ((!hs.converged || hs.cut) ? LR_ENOCONV : LR_OK);
     if (per_problem) per_problem[i] = si;
-    if (si != LR_OK) worst = si;
+    if (si != LR_OK && worst != LR_ENONFINITE) worst = si;
   }
   if (worst != LR_OK) fail(h, worst, "some problems did not converge or were cut (see per_problem)");
   return worst;
@@ -443,6 +689,7 @@ void lr_options_default(lr_options* o) {
   o->seed = 0;
   o->flags = 0;
   o->cluster_size = 0;
+  o->refine = 0;
 }
 
 const char* lr_status_string(lr_status s) {
@@ -453,6 +700,7 @@ const char* lr_status_string(lr_status s) {
     case LR_ENOCONV: return "LR_ENOCONV";
     case LR_ETIMEOUT: return "LR_ETIMEOUT";
     case LR_ECUDA: return "LR_ECUDA";
+    case LR_ENONFINITE: return "LR_ENONFINITE";
   }
   return "unknown";
 }
@@ -496,7 +744,7 @@ lr_status lr_destroy(lr_handle h) {
     if (e) cudaEventDestroy(e);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < 32; ++i) {
     if (h->bstreams[i]) cudaStreamDestroy(h->bstreams[i]);
     if (h->bjoin[i]) cudaEventDestroy(h->bjoin[i]);
   }
@@ -504,6 +752,7 @@ lr_status lr_destroy(lr_handle h) {
   if (h->h_bstate) cudaFreeHost(h->h_bstate);
   h->plans.clear();
   if (h->ws) cudaFree(h->ws);
+  if (h->ws2) cudaFree(h->ws2);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_piv) cudaFreeHost(h->h_piv);
   delete h;
@@ -548,7 +797,12 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
   s = get_plan(h, m, &plan);
   if (s != LR_OK) return s;
   h->info = lr_info{};
-  s = o.prec == LR_MIXED ? solve2d<float>(h, rhs, sol, o, plan) : solve2d<double>(h, rhs, sol, o, plan);
+  int rounds = o.refine;
+  if (rounds == 0) rounds = o.eps < 1e-7 ? 3 : 0;
+  if (o.prec == LR_MIXED && rounds > 0)
+    s = solve2d_refined(h, rhs, sol, o, plan, rounds);
+  else
+    s = o.prec == LR_MIXED ? solve2d<float>(h, rhs, sol, o, plan) : solve2d<double>(h, rhs, sol, o, plan);
   h->info.status = s;
   return s;
 }
@@ -677,6 +931,7 @@ lr_status lr_truncate(lr_handle h, lr_mat* X, double eps, int rmax) {
     LR_CUDA(h, cudaStreamSynchronize(stm), "lr_truncate copy");
   }
   X->r = R;
+  if (h->h_state->status) return fail(h, static_cast<lr_status>(h->h_state->status), kNonFiniteMsg);
   if (h->h_state->cut) return fail(h, LR_ENOCONV, "rank exceeds rmax; result truncated");
   return LR_OK;
 }

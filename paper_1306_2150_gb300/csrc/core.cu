@@ -60,6 +60,17 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     if (tid == 0) { A.st->rank = 0; A.st->cut = 0; A.st->sigma0 = 0.0; }
     return;
   }
+  if (A.tri_given) {
+    // GC, GR hold upper-triangular QR factors R_L, R_R of factors with
+    // orthonormal Q: take Lc = R_L^T, Lr = R_R^T and skip the Cholesky step.
+    for (int idx = tid; idx < k * k; idx += NT) {
+      const int i = idx / k, j = idx % k;
+      S.Lc[i * KP + j] = j <= i ? A.GC[j + (size_t)i * A.ldg] : 0.0;
+      S.Lr[i * KP + j] = j <= i ? A.GR[j + (size_t)i * A.ldg] : 0.0;
+    }
+    for (int i = tid; i < k; i += NT) S.d[i] = A.d ? A.d[i] : 1.0;
+    __syncthreads();
+  } else {
   // Load Gram matrices (full, symmetric) and weights.
   for (int idx = tid; idx < k * k; idx += NT) {
     const int i = idx % k, j = idx / k;
@@ -109,6 +120,7 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     if (j > i) { S.Lc[i * KP + j] = 0.0; S.Lr[i * KP + j] = 0.0; }
   }
   __syncthreads();
+  }
   // Core M = Lc^T diag(d) Lr : M[p][q] = sum_{i >= max(p,q)} Lc[i][p] d_i Lr[i][q].
   const int ke = k + (k & 1);  // even number of columns for the pairing
   for (int idx = tid; idx < ke * ke; idx += NT) {
@@ -191,7 +203,9 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     double acc = 0.0;
     for (int i = lane; i < k; i += 32) acc += (double)S.Mx[qq * KP + i] * (double)S.Mx[qq * KP + i];
     acc = warp_sum_t(acc);
-    if (lane == 0) S.sig[qq] = sqrt(acc);
+    // A non-finite value (overflow or 0/0 upstream) is ranked last as -1, so
+    // the ordering below stays a permutation; the solve is then failed.
+    if (lane == 0) S.sig[qq] = isfinite(acc) ? sqrt(acc) : -1.0;
   }
   __syncthreads();
   for (int qq = tid; qq < k; qq += NT) {
@@ -205,8 +219,9 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     double total = 0.0;
     for (int p = 0; p < k; ++p) total += S.sig[p] * S.sig[p];
     int K;
-    if (S.sig[S.perm[0]] == 0.0) {
+    if (S.sig[S.perm[0]] == 0.0 || S.sig[S.perm[k - 1]] < 0.0) {
       K = 0;
+      if (S.sig[S.perm[k - 1]] < 0.0) A.st->status = LR_ENONFINITE;
     } else {
       const double lim = A.eps * sqrt(total);
       double tail2 = 0.0;
@@ -224,7 +239,7 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     S.K = K;
     A.st->rank = K;
     A.st->cut = cut;
-    A.st->sigma0 = S.sig[S.perm[0]];
+    A.st->sigma0 = K > 0 ? S.sig[S.perm[0]] : 0.0;
   }
   __syncthreads();
   const int K = S.K;
@@ -238,6 +253,10 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     T* out = side == 0 ? A.Tc : A.Tr;
     const double inv = side == 0 ? (S.sig[src] > 0.0 ? 1.0 / S.sig[src] : 0.0) : 1.0;
     const JT* col = side == 0 ? S.Mx + src * KP : S.Zm + src * KP;
+    if (A.tri_given) {  // the factors are already orthonormal: T = W_K, Z_K
+      for (int i = 0; i < k; ++i) out[i + (size_t)p * KMAX] = (T)((double)col[i] * inv);
+      continue;
+    }
     // back substitution with L^T (upper triangular): x_i = (w_i - sum_{j>i} L[j][i] x_j) / L[i][i]
     double xs[KMAX];
     for (int i = k - 1; i >= 0; --i) {

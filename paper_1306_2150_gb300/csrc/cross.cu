@@ -568,11 +568,13 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
     if (tid == 0) {
       const T delta = sh.delta;
       const T csq = sh.sumsq;
-      const T rr = sh.rsq / (delta * delta);
+      // |r|^2 = |row|^2 / delta^2 <= m (delta is the row's largest entry);
+      // divided twice so that delta^2 never underflows.
+      const T rr = (sh.rsq / delta) / delta;
       T cs = T(0);
       for (int l = 0; l < k; ++l) cs += sh.d[l] * sh.dots[l] * sh.gr[l];
-      sh.norm2 += T(2) * delta * cs + delta * delta * csq * rr;
-      const T term2 = delta * delta * csq * rr;       // |d|^2 |c|^2 |r|^2
+      const T term2 = csq * sh.rsq;                   // |d|^2 |c|^2 |r|^2
+      sh.norm2 += T(2) * delta * cs + term2;
       sh.small = (term2 <= tol2 * sh.norm2) ? sh.small + 1 : 0;
       if (q == 0) {
         A.GC[k + (size_t)k * A.kcap] = (double)csq;

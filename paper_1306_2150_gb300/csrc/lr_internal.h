@@ -121,6 +121,8 @@ struct CoreArgs {
   T* Tr;
   double* s_out;    // R singular values
   SolveState* st;
+  int tri_given = 0; // 1: GC, GR are upper-triangular QR factors (column-major,
+                     // ldg), d may be null (ones); T = W_K, Z_K directly
 };
 template <typename T>
 cudaError_t launch_core(const CoreArgs<T>& a, bool jacobi_fp32, cudaStream_t st);
@@ -134,5 +136,26 @@ template <typename TI, typename TO>
 cudaError_t launch_rotate(const TI* in, int ld_in, int rows, const int* k_dev, int k_host,
                           const void* Tm, bool tm_f32, const int* rank_dev, TO* out, int ld_out,
                           cudaStream_t st);
+
+// Iterative refinement helpers (float64): the residual F - A X as factors
+// [UF, -c P U s, -c Q U s], [VF, Q V, P V] (r + 2R columns, leading dim ldo).
+cudaError_t launch_residual_factors(int m, int r, int R, const double* UF, const double* VF, int ldf,
+                                    const double* U, const double* s, const double* V, int ldx, int op,
+                                    double* L, double* Rt, int ldo, cudaStream_t st);
+// One shifted/plain Cholesky QR step on two factors (see refine.cu).
+struct CholQrArgs {
+  const double* G[2];  // q x q Gram matrices (ld q)
+  double* T[2];        // KMAX x KMAX: X T has orthonormal columns
+  double* Racc[2];     // KMAX x KMAX: accumulated upper-triangular R
+  int* qout;           // [2], set to q (rotation column count)
+  int q;
+  int first;           // 1: Racc = this step's R
+  double shift;        // added to the equilibrated Gram diagonal
+  double floor_rel;    // Cholesky pivots at or below are dropped columns
+};
+cudaError_t launch_cholqr_step(const CholQrArgs& a, cudaStream_t st);
+cudaError_t launch_fold_weights(int m, int kmax, const int* K, double* U, int ld, const double* s, bool unit,
+                                cudaStream_t st);
+cudaError_t launch_scale_weights(int n, double* w, const double* s, cudaStream_t st);
 
 }  // namespace lrp

@@ -166,5 +166,6 @@ extern "C" lr_status lr_truncate_noalloc(lr_mat* X, double eps, int rmax, void* 
   if (cudaMemcpyAsync(&hs, state, sizeof(SolveState), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LR_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return LR_ECUDA;
   X->r = hs.rank;
+  if (hs.status) return static_cast<lr_status>(hs.status);
   return hs.cut ? LR_ENOCONV : LR_OK;
 }

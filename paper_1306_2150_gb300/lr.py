@@ -17,7 +17,7 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblrpoisson.so")
 
-LR_OK, LR_EINVAL, LR_ENOMEM, LR_ENOCONV, LR_ETIMEOUT, LR_ECUDA = range(6)
+LR_OK, LR_EINVAL, LR_ENOMEM, LR_ENOCONV, LR_ETIMEOUT, LR_ECUDA, LR_ENONFINITE = range(7)
 LR_FP64, LR_MIXED = 0, 1
 LR_OP_5PT, LR_OP_SEMISTAGGERED = 0, 1
 LR_FLAG_ASYNC = 1
@@ -45,7 +45,7 @@ class LrOptions(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("op", ctypes.c_int), ("eps", ctypes.c_double),
                 ("rmax", ctypes.c_int), ("aca_tol_factor", ctypes.c_double),
                 ("probes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-                ("flags", ctypes.c_uint), ("cluster_size", ctypes.c_int)]
+                ("flags", ctypes.c_uint), ("cluster_size", ctypes.c_int), ("refine", ctypes.c_int)]
 
 
 class LrInfo(ctypes.Structure):
@@ -54,7 +54,9 @@ class LrInfo(ctypes.Structure):
                 ("probe_rounds", ctypes.c_int), ("zero_rows", ctypes.c_int),
                 ("cluster_size", ctypes.c_int), ("launches", ctypes.c_int),
                 ("norm_est", ctypes.c_double),
-                ("sigma0", ctypes.c_double)]
+                ("sigma0", ctypes.c_double),
+                ("refine_rounds", ctypes.c_int), ("pad", ctypes.c_int),
+                ("refine_corr", ctypes.c_double)]
 
 
 _lib = None
@@ -199,8 +201,9 @@ class SolveResult:
     pivots_J: list
 
 
-def _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size) -> LrOptions:
+def _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size, refine=0) -> LrOptions:
     o = lr_options_default()
+    o.refine = int(refine)
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     o.op = OPERATORS[op] if isinstance(op, str) else int(op)
     o.eps = float(eps)
@@ -216,7 +219,7 @@ def _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_s
 def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rmax: int = 64,
                  rmax_out: int = 64, aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
                  cluster_size: int = 0, async_: bool = False, out=None, check: bool = True,
-                 timing: bool = False, graph: bool = False):
+                 timing: bool = False, graph: bool = False, refine: int = 0):
     """Low-rank solve of A X = U V^T.  Returns SolveResult with the solution
     factors (views of rank R) unless ``async_`` (then read lr_get_info after
     synchronising the stream).  ``out`` = (Uo, s, Vo) preallocated outputs."""
@@ -246,7 +249,7 @@ def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rma
         raise ValueError("output factors need the same leading dimension")
     flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_TIMING if timing else 0) | \
         (LR_FLAG_GRAPH if graph else 0)
-    o = _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size)
+    o = _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size, refine)
     st = load().lr_poisson2d(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o))
     if async_:
         if st != LR_OK:

@@ -274,3 +274,39 @@ def test_truncate_matches_oracle(lr, h):
     Xg = (npy(Ut) * npy(st)) @ npy(Vt).T
     assert np.linalg.norm(Xg - X) <= 1.01e-6 * np.linalg.norm(X)
     assert np.abs(npy(Ut).T @ npy(Ut) - np.eye(len(so))).max() < 1e-10
+
+
+# ------------------------------------------------------------------ refinement
+@pytest.mark.parametrize("m,kind", [(256, "random"), (1024, "smooth"), (4096, "smooth"), (16384, "smooth")])
+def test_mixed_with_refinement_reaches_1e10(lr, h, m, kind):
+    # float32 sampling alone stalls near 1e-7; float64 residual refinement
+    # (automatic below eps = 1e-7) brings the mixed path to 10 eps
+    eps = 1e-10
+    U, V = inputs.separable_random(m, 8, seed=0) if kind == "random" else inputs.smooth_sum(m, eps)
+    res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="mixed")
+    assert res.status == lr.LR_OK
+    assert 1 <= res.info.refine_rounds <= 3
+    rows = None if m <= 4096 else np.unique(np.linspace(0, m - 1, 512).astype(int))
+    assert O.rel_error_freq(Uo, s, Vo, U, V, "5pt", rows=rows) <= 10 * eps
+    assert np.abs(Uo.T @ Uo - np.eye(len(s))).max() < 1e-10
+    assert np.abs(Vo.T @ Vo - np.eye(len(s))).max() < 1e-10
+    assert np.all(np.diff(s) <= 0)
+
+
+def test_refinement_off_is_limited_by_float32(lr, h):
+    m, eps = 1024, 1e-10
+    U, V = inputs.smooth_sum(m, eps)
+    res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="mixed", refine=-1)
+    assert res.info.refine_rounds == 0
+    e_plain = O.rel_error_freq(Uo, s, Vo, U, V, "5pt")
+    res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="mixed", refine=2)
+    e_ref = O.rel_error_freq(Uo, s, Vo, U, V, "5pt")
+    assert e_ref <= 10 * eps < e_plain
+
+
+def test_refinement_semistaggered(lr, h):
+    m, eps = 2048, 1e-10
+    U, V = inputs.smooth_sum(m, eps)
+    res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="mixed", op="semi")
+    assert res.status == lr.LR_OK and res.info.refine_rounds >= 1
+    assert O.rel_error_freq(Uo, s, Vo, U, V, "semi") <= 10 * eps
