@@ -109,15 +109,16 @@ typedef struct {
   unsigned int flags;    /* LR_FLAG_* */
   int cluster_size;      /* CTAs per cross cluster (0 = automatic, 1..16) */
   int refine;            /* LR_MIXED only: maximum rounds of iterative
-                            refinement in float64 (0 = automatic: up to 3
+                            refinement in float64 (0 = automatic: up to 6
                             rounds when eps < 1e-7, none otherwise; -1 =
                             none).  A round forms the residual F - A X
                             exactly in float64 as a low-rank matrix, rounds
                             it with a shifted Cholesky QR, solves for the
                             correction D in mixed precision and rounds X + D
-                            at eps.  Rounds stop early once the correction
-                            is below eps / 10 of X.  Refined solves are
-                            synchronous. */
+                            at eps.  Rounds stop once the correction times
+                            the ratio of the last two corrections is below
+                            eps / 2 relative to X, or when the corrections
+                            stop shrinking.  Refined solves are synchronous. */
 } lr_options;
 
 /* Result details of the last solve on a handle. */

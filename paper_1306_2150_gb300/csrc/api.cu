@@ -26,6 +26,7 @@ struct lr_handle_s {
   size_t ws_bytes = 0;
   SolveState* h_state = nullptr;  // pinned
   int* h_piv = nullptr;           // pinned, 2 * KMAX
+  double* h_w = nullptr;          // pinned, 2 * KMAX (weights read back by refinement)
   lr_info info{};
   int last_kcap = 0;
   cudaEvent_t ev[LR_NUM_PHASES + 1] = {};
@@ -356,7 +357,8 @@ lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options&
 //           Res <- QR-round(Res, 1e-8)    (shifted Cholesky QR + core SVD)
 //           D   = s0 solve(Res / s0)      (mixed, at 1e-6, at unit scale)
 //           X   <- round(X + D, eps)      (float64 rounding, Section 3)
-//   until sigma_0(D) <= sigma_0(X) eps / 10.
+//   until the error estimate sigma_0(D) / sigma_0(X) * (ratio of successive
+//   corrections) is below eps / 2, or the corrections stop shrinking.
 // The float32 error of X lives in its factors, so Res stays low rank; each
 // round multiplies the error by about the accuracy of the correction solve.
 struct RefineBufs {
@@ -394,6 +396,8 @@ void carve_refine(Carve& c, RefineBufs& b, int ld, int m) {
   b.st = c.take<SolveState>(sizeof(SolveState));
 }
 
+constexpr int kQrSteps = 4;
+
 // Rounding of L diag(d) Rt^T (q <= 64 columns, d = null: ones) through QR
 // factors of L and Rt by shifted Cholesky QR and the SVD of the core
 // R_L diag(d) R_R^T (Section 3).  Backward stable, so it keeps a product far
@@ -403,17 +407,22 @@ void carve_refine(Carve& c, RefineBufs& b, int ld, int m) {
 // Scratch: b.L, b.Rt, b.Lb, b.Rb, the small matrices and b.st.
 lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const double* Rin, int ldin, int m, int q,
                    const double* d, double eps, int rmax, double* U, double* V, double* s_out, int ldo, int fold,
-                   int* K, double* sigma0) {
+                   bool jacobi_fp32, int* K, double* sigma0) {
   cudaStream_t stm = h->stream;
   const int ld = m + (m & 1);
   const double* Xl = Lin;
   const double* Xr = Rin;
   int ldx = ldin;
-  double* Yl = b.Lb;
-  double* Yr = b.Rb;
-  // Shift of the first step (equilibrated Gram matrix, ||G|| <= q).
+  // Shift of the first two steps (equilibrated Gram matrix, ||G|| <= q).
+  // Each shifted step maps a singular value sigma to sigma / sqrt(sigma^2 +
+  // shift) and loses nothing (Q = X R^-1 exactly), so two of them bring a
+  // factor of condition up to 1 / eps64 within reach of the two plain steps
+  // that make Q orthonormal; no column is ever dropped but an exactly zero
+  // one.
   const double shift = 11.0 * ((double)m * q + (double)q * (q + 1)) * (DBL_EPSILON / 2) * q;
-  for (int step = 0; step < 3; ++step) {
+  for (int step = 0; step < kQrSteps; ++step) {
+    double* Yl = (step & 1) ? b.L : b.Lb;   // ping-pong: Lin -> Lb -> L -> Lb -> L
+    double* Yr = (step & 1) ? b.Rt : b.Rb;
     LR_CUDA(h, launch_gram(Xl, m, ldx, q, b.G0, q, b.part, h->num_sms, stm), "gram");
     LR_CUDA(h, launch_gram(Xr, m, ldx, q, b.G1, q, b.part, h->num_sms, stm), "gram");
     CholQrArgs a;
@@ -423,17 +432,14 @@ lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const do
     a.qout = b.qout;
     a.q = q;
     a.first = step == 0;
-    a.shift = step == 0 ? shift : 0.0;
-    a.floor_rel = step == 0 ? 0.5 * shift : 1e-15;
+    a.shift = step < 2 ? shift : 0.0;
+    a.floor_rel = 0.0;
     LR_CUDA(h, launch_cholqr_step(a, stm), "cholesky qr");
     LR_CUDA(h, (launch_rotate<double, double>(Xl, ldx, m, nullptr, q, b.T0, false, &b.qout[0], Yl, ld, stm)), "qr");
     LR_CUDA(h, (launch_rotate<double, double>(Xr, ldx, m, nullptr, q, b.T1, false, &b.qout[1], Yr, ld, stm)), "qr");
-    // ping-pong: Lb -> L -> Lb
     Xl = Yl;
     Xr = Yr;
     ldx = ld;
-    Yl = step == 0 ? b.L : b.Lb;
-    Yr = step == 0 ? b.Rt : b.Rb;
   }
   LR_CUDA(h, cudaMemsetAsync(b.st, 0, sizeof(SolveState), stm), "state reset");
   CoreArgs<double> co;
@@ -442,7 +448,7 @@ lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const do
   co.eps = eps; co.rmax_out = rmax;
   co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = s_out; co.st = b.st;
   co.tri_given = 1;
-  LR_CUDA(h, launch_core<double>(co, false, stm), "qr rounding core");
+  LR_CUDA(h, launch_core<double>(co, jacobi_fp32, stm), "qr rounding core");
   LR_CUDA(h, (launch_rotate<double, double>(Xl, ld, m, nullptr, q, b.Tc, false, &b.st->rank, U, ldo, stm)), "rot");
   LR_CUDA(h, (launch_rotate<double, double>(Xr, ld, m, nullptr, q, b.Tr, false, &b.st->rank, V, ldo, stm)), "rot");
   if (fold) LR_CUDA(h, launch_fold_weights(m, q, &b.st->rank, U, ldo, s_out, fold == 2, stm), "fold");
@@ -454,7 +460,7 @@ lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const do
   if (h->h_state->cut) return fail(h, LR_ENOCONV, "rank exceeds rmax; result truncated");
   return LR_OK;
 }
-constexpr int kQrRoundLaunches = 3 * 7 + 4;
+constexpr int kQrRoundLaunches = kQrSteps * 7 + 4;
 
 lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options& o, Plan* plan,
                           int rounds) {
@@ -486,7 +492,7 @@ lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   std::memcpy(piv, h->h_piv, sizeof piv);
   const int cs_first = h->info.cluster_size;
   int launches = h->info.launches;
-  double sigX = first.sigma0, corr = 0.0;
+  double sigX = first.sigma0, corr = 0.0, prev = 0.0;
   int done = 0;
   for (int it = 0; it < rounds && X.r > 0; ++it) {
     const int R1 = X.r;
@@ -510,8 +516,10 @@ lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
       // Intermediate sums are kept to 1e-12 of their size (F - A X_1 is
       // already far below F); the last one only to the accuracy the float32
       // correction solve can use.
+      // The last sum feeds a float32 solve, so its core may be diagonalised
+      // in float32 too.
       s = qr_round(h, b, b.L, b.Rt, ld, m, q, nullptr, last ? 1e-8 : 1e-12, KMAX, b.FU, b.FV, b.rs, ld,
-                   last ? 2 : 1, &Kres, &rs0);
+                   last ? 2 : 1, last, &Kres, &rs0);
       if (s != LR_OK) return s;
       launches += 1 + kQrRoundLaunches;
       FUp = b.FU;
@@ -530,15 +538,31 @@ lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
     s = solve2d<float>(h, &res, &D, o1, plan);
     if (s != LR_OK && s != LR_ENOCONV) return s;  // ENOCONV: D cut to the room left, or cross cap
     launches += h->info.launches;
-    const int R2 = D.r;
     const double sd = h->h_state->sigma0 * rs0;
+    // Keep the correction's columns down to a tail below eps / 20 of X: the
+    // rounding of X + D at eps drops them anyway, and a narrower core is
+    // cheaper to diagonalise.
+    int R2 = D.r;
+    LR_CUDA(h, cudaMemcpyAsync(h->h_w, X.s, sizeof(double) * (R1 + R2), cudaMemcpyDeviceToHost, stm), "weights");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "weights");
+    {
+      double nx = 0.0, tail = 0.0;
+      for (int j = 0; j < R1; ++j) nx += h->h_w[j] * h->h_w[j];
+      const double lim = 0.05 * o.eps * std::sqrt(nx);
+      while (R2 > 0) {
+        const double v = h->h_w[R1 + R2 - 1] * rs0;
+        if (std::sqrt(tail + v * v) > lim) break;
+        tail += v * v;
+        --R2;
+      }
+    }
     LR_CUDA(h, launch_scale_weights(R2, X.s + R1, b.rs, stm), "scale");
     // X + D = [XU, DU] diag(Xs, Ds) [XV, DV]^T, rounded at eps.  D lies
     // mostly in X's column space, which a Gram-based rounding would resolve
     // only to sqrt(eps64); the QR rounding keeps the factors orthonormal.
     int Rn = 0;
     double sig_new = 0.0;
-    s = qr_round(h, b, X.U, X.V, ld, m, R1 + R2, X.s, o.eps, KMAX, X.U, X.V, X.s, ld, 0, &Rn, &sig_new);
+    s = qr_round(h, b, X.U, X.V, ld, m, R1 + R2, X.s, o.eps, KMAX, X.U, X.V, X.s, ld, 0, false, &Rn, &sig_new);
     if (s != LR_OK && s != LR_ENOCONV) return s;
     if (s != LR_OK) worst = s;
     launches += 1 + kQrRoundLaunches;
@@ -546,7 +570,14 @@ lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
     corr = sigX > 0.0 ? sd / sigX : 0.0;
     sigX = sig_new;
     ++done;
-    if (corr <= 0.1 * o.eps) break;
+    // The error left after this round is about the correction times the
+    // relative accuracy of the correction, estimated by the ratio of
+    // successive corrections (0.05 before there is one: a float32 solve of
+    // the residual loses accuracy to cancellation as the grid grows).
+    const double rate = prev > 0.0 ? std::min(1.0, corr / prev) : 0.05;
+    if (corr * rate <= 0.5 * o.eps) break;
+    if (prev > 0.0 && corr > 0.5 * prev) break;  // no longer converging
+    prev = corr;
   }
   // Copy the result into the caller's buffers.
   int R = X.r;
@@ -719,9 +750,11 @@ lr_status lr_create(lr_handle* out, void* stream) {
     return LR_ECUDA;
   }
   if (cudaMallocHost(&h->h_state, sizeof(SolveState)) != cudaSuccess ||
-      cudaMallocHost(&h->h_piv, sizeof(int) * 2 * KMAX) != cudaSuccess) {
+      cudaMallocHost(&h->h_piv, sizeof(int) * 2 * KMAX) != cudaSuccess ||
+      cudaMallocHost(&h->h_w, sizeof(double) * 2 * KMAX) != cudaSuccess) {
     cudaGetLastError();
     if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->h_piv) cudaFreeHost(h->h_piv);
     delete h;
     return LR_ENOMEM;
   }
@@ -755,6 +788,7 @@ lr_status lr_destroy(lr_handle h) {
   if (h->ws2) cudaFree(h->ws2);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_piv) cudaFreeHost(h->h_piv);
+  if (h->h_w) cudaFreeHost(h->h_w);
   delete h;
   return LR_OK;
 }
@@ -798,7 +832,7 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
   if (s != LR_OK) return s;
   h->info = lr_info{};
   int rounds = o.refine;
-  if (rounds == 0) rounds = o.eps < 1e-7 ? 3 : 0;
+  if (rounds == 0) rounds = o.eps < 1e-7 ? 6 : 0;
   if (o.prec == LR_MIXED && rounds > 0)
     s = solve2d_refined(h, rhs, sol, o, plan, rounds);
   else

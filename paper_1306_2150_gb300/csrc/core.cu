@@ -34,6 +34,11 @@ struct CoreSmem {
   int perm[KMAX];
   int flag;
   int K;
+  // float64 cores only: float32 copies of the core and its rotations, then
+  // an orthogonalised rotation and a product temporary (re-basing steps)
+  double scrA[sizeof(JT) == 8 ? KMAX * KP : 1];
+  double scrB[sizeof(JT) == 8 ? KMAX * KP : 1];
+  double amax;
 };
 
 template <typename JT>
@@ -43,12 +48,162 @@ __device__ __forceinline__ JT warp_sum_t(JT v) {
   return v;
 }
 
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Maximum of non-negative doubles: their bit patterns order like integers.
+__device__ __forceinline__ void atomic_max_pos(double* a, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
 template <typename JT> __device__ __forceinline__ JT rsqrt_t(JT x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
 template <typename JT> __device__ __forceinline__ JT fdiv_t(JT a, JT b);
 template <> __device__ __forceinline__ float fdiv_t<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double fdiv_t<double>(double a, double b) { return a / b; }
+
+
+// Sweeps of one-sided (Hestenes) Jacobi with round-robin pair ordering on
+// the ke columns of X (column c at X[c * KP + i], ke rows), accumulating the
+// rotations in Z, until a sweep rotates nothing (at most max_sweeps).  One
+// warp per pair: lanes hold rows (ke <= 64: two per lane) of both columns in
+// registers for the inner products and the update.
+// A pair is left alone when it is orthogonal to tol: the rounding error of
+// the computed inner product itself is about k ulps, so a tighter test would
+// rotate rounding noise forever.  Whatever the sweep count, the discarded
+// columns' norms are exactly the error of the truncated product, because
+// every rotation is orthogonal.
+template <typename JT>
+__device__ void jacobi_sweeps(JT* X, JT* Z, int ke, JT tol, int max_sweeps,
+                              const unsigned char (*pc0)[KMAX / 2], const unsigned char (*pc1)[KMAX / 2],
+                              int* flag) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = blockDim.x >> 5;
+  const int npairs = ke / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+    for (int round = 0; round < ke - 1; ++round) {
+      for (int pr = warp; pr < npairs; pr += NW) {
+        const int c0 = pc0[round][pr], c1 = pc1[round][pr];
+        JT* x = X + c0 * KP;
+        JT* y = X + c1 * KP;
+        const int i0 = lane, i1 = lane + 32;
+        const JT x0 = i0 < ke ? x[i0] : JT(0), y0 = i0 < ke ? y[i0] : JT(0);
+        const JT x1 = i1 < ke ? x[i1] : JT(0), y1 = i1 < ke ? y[i1] : JT(0);
+        JT al = x0 * x0 + x1 * x1, be = y0 * y0 + y1 * y1, ga = x0 * y0 + x1 * y1;
+        al = warp_sum_t(al);
+        be = warp_sum_t(be);
+        ga = warp_sum_t(ga);
+        if (ga != JT(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const JT zeta = fdiv_t<JT>(be - al, JT(2) * ga);
+          const JT t = fdiv_t<JT>(zeta >= JT(0) ? JT(1) : JT(-1), fabs(zeta) + sqrt(JT(1) + zeta * zeta));
+          const JT c = rsqrt_t<JT>(JT(1) + t * t);
+          const JT s = c * t;
+          JT* zx = Z + c0 * KP;
+          JT* zy = Z + c1 * KP;
+          if (i0 < ke) {
+            x[i0] = c * x0 - s * y0;
+            y[i0] = s * x0 + c * y0;
+            const JT a = zx[i0], b = zy[i0];
+            zx[i0] = c * a - s * b;
+            zy[i0] = s * a + c * b;
+          }
+          if (i1 < ke) {
+            x[i1] = c * x1 - s * y1;
+            y[i1] = s * x1 + c * y1;
+            const JT a = zx[i1], b = zy[i1];
+            zx[i1] = c * a - s * b;
+            zy[i1] = s * a + c * b;
+          }
+          if (lane == 0) *flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (*flag == 0) break;
+    __syncthreads();
+  }
+  __syncthreads();
+}
+
+// X <- X P in place (ke x ke, column c at X[c * KP + i]): row i of the
+// result depends only on row i of X, so a warp computes a row into
+// registers and writes it back.
+__device__ void rowwise_product(double* X, const double* P, int ke) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  for (int i = warp; i < ke; i += NW) {
+    double a0 = 0.0, a1 = 0.0;
+    const int j0 = lane, j1 = lane + 32;
+    for (int l = 0; l < ke; ++l) {
+      const double x = X[l * KP + i];
+      if (j0 < ke) a0 += x * P[j0 * KP + l];
+      if (j1 < ke) a1 += x * P[j1 * KP + l];
+    }
+    __syncwarp();
+    if (j0 < ke) X[j0 * KP + i] = a0;
+    if (j1 < ke) X[j1 * KP + i] = a1;
+  }
+  __syncthreads();
+}
+
+constexpr int kMixedJacobiMin = 12;  // below, plain float64 sweeps are cheap
+
+// One float32 pass of the mixed Jacobi on a float64 core (see the caller).
+__device__ void mixed_rebase_pass(CoreSmem<double>& S, int ke, const unsigned char (*pc0)[KMAX / 2],
+                                  const unsigned char (*pc1)[KMAX / 2]) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  float* M32 = reinterpret_cast<float*>(S.scrA);
+  float* Z32 = M32 + KMAX * KP;
+  // scale by a power of two so the largest entry is O(1) in float32
+  if (tid == 0) S.amax = 0.0;
+  __syncthreads();
+  double am = 0.0;
+  for (int idx = tid; idx < ke * ke; idx += NT) {
+    const int c = idx / ke, i = idx % ke;
+    am = fmax(am, fabs(S.Mx[c * KP + i]));
+  }
+  am = warp_max(am);
+  if ((tid & 31) == 0) atomic_max_pos(&S.amax, am);
+  __syncthreads();
+  const double sc = S.amax > 0.0 ? ldexp(1.0, -ilogb(S.amax)) : 1.0;
+  for (int idx = tid; idx < ke * ke; idx += NT) {
+    const int c = idx / ke, i = idx % ke;
+    M32[c * KP + i] = (float)(S.Mx[c * KP + i] * sc);
+    Z32[c * KP + i] = c == i ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const float tol32 = (float)((ke < 4 ? 8 : 2 * ke) * (double)FLT_EPSILON);
+  jacobi_sweeps<float>(M32, Z32, ke, tol32, 40, pc0, pc1, &S.flag);
+  // Z (float64, in scrB) from the float32 rotations, then two Newton-Schulz
+  // steps with the product temporary in scrA (the float32 copies are done).
+  double* Zp = S.scrB;
+  double* T = S.scrA;
+  for (int idx = tid; idx < ke * ke; idx += NT) {
+    const int c = idx / ke, i = idx % ke;
+    Zp[c * KP + i] = (double)Z32[c * KP + i];
+  }
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    // T = (3 I - Z^T Z) / 2, symmetric
+    for (int idx = tid; idx < ke * ke; idx += NT) {
+      const int a = idx / ke, b = idx % ke;
+      if (b > a) continue;
+      double g = 0.0;
+      for (int i = 0; i < ke; ++i) g += Zp[a * KP + i] * Zp[b * KP + i];
+      const double t = (a == b ? 1.5 : 0.0) - 0.5 * g;
+      T[a * KP + b] = t;
+      T[b * KP + a] = t;
+    }
+    __syncthreads();
+    rowwise_product(Zp, T, ke);
+  }
+  rowwise_product(S.Mx, Zp, ke);
+  rowwise_product(S.Zm, Zp, ke);
+}
 
 template <typename T, typename JT>
 __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
@@ -134,13 +289,6 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     S.Zm[qq * KP + p] = (JT)(p == qq ? 1.0 : 0.0);
   }
   __syncthreads();
-  // One-sided (Hestenes) Jacobi with round-robin pair ordering.
-  // Stop when every pair is orthogonal to 2k ulps: the rounding error of the
-  // computed inner product itself is about k ulps, so a tighter test would
-  // rotate rounding noise forever.  Whatever the sweep count, the discarded
-  // columns' norms are exactly the error of the truncated product, because
-  // every rotation is orthogonal.
-  const JT tol = (JT)((k < 4 ? 8 : 2 * k) * ((sizeof(JT) == 8) ? DBL_EPSILON : (double)FLT_EPSILON));
   // Round-robin (circle) pair schedule: in round t, position p meets
   // position ke-1-p; position 0 holds column 0, the others rotate.
   const int npairs = ke / 2;
@@ -152,52 +300,22 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     pair_c1[round][pr] = (unsigned char)(1 + (pos1 - 1 + round) % (ke - 1));
   }
   __syncthreads();
-  // One warp per pair: lanes hold rows (k <= 64: two per lane) of both
-  // columns in registers for the inner products and the update.
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) S.flag = 0;
-    __syncthreads();
-    for (int round = 0; round < ke - 1; ++round) {
-      for (int pr = warp; pr < npairs; pr += NW) {
-        const int c0 = pair_c0[round][pr], c1 = pair_c1[round][pr];
-        JT* x = S.Mx + c0 * KP;
-        JT* y = S.Mx + c1 * KP;
-        const int i0 = lane, i1 = lane + 32;
-        const JT x0 = i0 < ke ? x[i0] : JT(0), y0 = i0 < ke ? y[i0] : JT(0);
-        const JT x1 = i1 < ke ? x[i1] : JT(0), y1 = i1 < ke ? y[i1] : JT(0);
-        JT al = x0 * x0 + x1 * x1, be = y0 * y0 + y1 * y1, ga = x0 * y0 + x1 * y1;
-        al = warp_sum_t(al);
-        be = warp_sum_t(be);
-        ga = warp_sum_t(ga);
-        if (ga != JT(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          const JT zeta = fdiv_t<JT>(be - al, JT(2) * ga);
-          const JT t = fdiv_t<JT>(zeta >= JT(0) ? JT(1) : JT(-1), fabs(zeta) + sqrt(JT(1) + zeta * zeta));
-          const JT c = rsqrt_t<JT>(JT(1) + t * t);
-          const JT s = c * t;
-          JT* zx = S.Zm + c0 * KP;
-          JT* zy = S.Zm + c1 * KP;
-          if (i0 < ke) {
-            x[i0] = c * x0 - s * y0;
-            y[i0] = s * x0 + c * y0;
-            const JT a = zx[i0], b = zy[i0];
-            zx[i0] = c * a - s * b;
-            zy[i0] = s * a + c * b;
-          }
-          if (i1 < ke) {
-            x[i1] = c * x1 - s * y1;
-            y[i1] = s * x1 + c * y1;
-            const JT a = zx[i1], b = zy[i1];
-            zx[i1] = c * a - s * b;
-            zy[i1] = s * a + c * b;
-          }
-          if (lane == 0) S.flag = 1;
-        }
-      }
-      __syncthreads();
+  if constexpr (sizeof(JT) == 8) {
+    // float64 core: GB300 runs float64 at a small fraction of its float32
+    // rate, so most of the iteration runs in float32 on a scaled copy, and
+    // float64 only re-bases and polishes:
+    //   pass (x2): Z32 = Jacobi_f32(M / 2^e);  Z = NS(NS(Z32))  (Newton-Schulz,
+    //              Z <- Z (3 I - Z^T Z) / 2, orthogonal to float64 accuracy);
+    //              M <- M Z, Zm <- Zm Z   (float64)
+    // The first pass resolves the singular values above ~1e-7 of the largest;
+    // after re-basing the small ones sit in columns of their own size, which
+    // the second float32 pass resolves in turn; float64 sweeps then finish.
+    if (k >= kMixedJacobiMin) {
+      for (int pass = 0; pass < 2; ++pass) mixed_rebase_pass(S, ke, pair_c0, pair_c1);
     }
-    if (S.flag == 0) break;
-    __syncthreads();
   }
+  const JT tol = (JT)((k < 4 ? 8 : 2 * k) * ((sizeof(JT) == 8) ? DBL_EPSILON : (double)FLT_EPSILON));
+  jacobi_sweeps<JT>(S.Mx, S.Zm, ke, tol, 40, pair_c0, pair_c1, &S.flag);
   // Singular values (column norms) and their descending order.
   for (int qq = warp; qq < k; qq += NW) {
     double acc = 0.0;

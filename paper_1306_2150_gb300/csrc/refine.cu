@@ -11,13 +11,14 @@
 // Its factors are each of the size of F while the product is of the size of
 // the error of X, so rounding it through Gram matrices (which resolve only
 // sqrt(eps64) of a factor) would lose it.  It is rounded instead through a
-// QR factorisation of each factor by shifted Cholesky QR (three Cholesky QR
-// steps, the first on a shifted, column-equilibrated Gram matrix: Fukaya,
-// Kannan, Nakatsukasa, Zhang and Yamamoto, SIAM J. Sci. Comput. 42 (2020)),
-// which gives orthonormal Q and a backward-stable R for factors of
-// condition up to 1/eps64; columns that are dependent to working accuracy
-// are dropped (zero in Q and R).  The small core R_L R_R^T then goes to the
-// SVD of the rounding core (Section 3).
+// QR factorisation of each factor by shifted Cholesky QR (Cholesky QR steps
+// on column-equilibrated Gram matrices, the first ones shifted: Fukaya,
+// Kannan, Nakatsukasa, Zhang and Yamamoto, SIAM J. Sci. Comput. 42 (2020)).
+// Two shifted and two plain steps give orthonormal Q and a backward-stable R
+// for factors of condition up to about 1/eps64 (the residual's factors come
+// close: P V is nearly in the span of V); only exactly zero columns are
+// dropped.  The small core R_L R_R^T then goes to the SVD of the rounding
+// core (Section 3).
 #include <cfloat>
 
 #include "lr_internal.h"
@@ -151,19 +152,23 @@ __global__ void __launch_bounds__(256) cholqr_step_kernel(CholQrArgs a) {
     }
   }
   __syncthreads();
-  // T = D Rs^-1 = D V^T;  Racc <- (Rs D^-1) Racc with Rs = L^T.
+  // R_step = Rs D^-1 with Rs = L^T, in place over L (row-major Rstep[l][i]
+  // at A[l * KP2 + i], l >= i: column l of R_step is row l of L over d_l).
+  for (int idx = tid; idx < q * q; idx += NT) {
+    const int l = idx / q, i = idx % q;
+    if (i <= l) S.A[l * KP2 + i] = S.dsc[l] > 0.0 ? S.A[l * KP2 + i] * (1.0 / S.dsc[l]) : 0.0;
+  }
+  __syncthreads();
+  // T = D Rs^-1 = D V^T;  Racc <- R_step Racc.
   for (int idx = tid; idx < KMAX * KMAX; idx += NT) {
     const int i = idx % KMAX, j = idx / KMAX;  // column-major position (i, j)
     double t = 0.0, rn = 0.0;
     if (i < q && j < q && i <= j) {
       t = S.dsc[i] * S.V[j * KP2 + i];
       if (a.first) {
-        rn = S.dsc[j] > 0.0 ? S.A[j * KP2 + i] / S.dsc[j] : 0.0;
+        rn = S.A[j * KP2 + i];
       } else {
-        for (int l = i; l <= j; ++l) {
-          const double rs = S.dsc[l] > 0.0 ? S.A[l * KP2 + i] / S.dsc[l] : 0.0;
-          rn += rs * S.Ro[l * KP2 + j];
-        }
+        for (int l = i; l <= j; ++l) rn += S.A[l * KP2 + i] * S.Ro[l * KP2 + j];
       }
     }
     T[idx] = t;

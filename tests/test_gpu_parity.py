@@ -285,7 +285,7 @@ def test_mixed_with_refinement_reaches_1e10(lr, h, m, kind):
     U, V = inputs.separable_random(m, 8, seed=0) if kind == "random" else inputs.smooth_sum(m, eps)
     res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="mixed")
     assert res.status == lr.LR_OK
-    assert 1 <= res.info.refine_rounds <= 3
+    assert 1 <= res.info.refine_rounds <= 6
     rows = None if m <= 4096 else np.unique(np.linspace(0, m - 1, 512).astype(int))
     assert O.rel_error_freq(Uo, s, Vo, U, V, "5pt", rows=rows) <= 10 * eps
     assert np.abs(Uo.T @ Uo - np.eye(len(s))).max() < 1e-10
