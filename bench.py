@@ -193,7 +193,10 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     h = lr.Handle(stream)
     out = (lr.colmajor_empty(n, 64), torch.empty(64, dtype=torch.float64, device="cuda"),
            lr.colmajor_empty(n, 64))
-    results = {}
+    results = {"autotune": {}}
+    # launch shapes tuned on this problem before anything is timed (T0/T7)
+    for prec in ("mixed", "fp64"):
+        results["autotune"][prec] = lr.lr_autotune(h, Ud, Vd, eps=EPS, prec=prec, reps=3)
     for prec in ("mixed", "fp64"):
         for _ in range(args.warmup):
             lr.lr_poisson2d(h, Ud, Vd, eps=EPS, prec=prec, out=out)
@@ -277,6 +280,7 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     probs = [(torch.from_numpy(U) * (1.0 + p / B), torch.from_numpy(V)) for p in range(B)]
     for prec in ("mixed", "fp64"):
         batch = lr.Batch(probs)
+        results["autotune"]["batch_" + prec] = lr.lr_autotune_batched(h, batch, eps=EPS, prec=prec, reps=2)
         for _ in range(args.warmup):
             lr.lr_poisson2d_batched(h, batch, eps=EPS, prec=prec, graph=True)
         torch.cuda.synchronize()
@@ -425,6 +429,8 @@ def main():
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 5),
                      "traffic": committed_traffic(dom), "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": byts, "launch_ms": round(ph[dom], 4)},
+        "autotune": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                     for k, v in res["autotune"].items()},
         "e2e": {"value": round(eb["ms_step"] / eb["batch"], 5), "unit": "ms", "h2d_bytes_per_step": eb["h2d"],
                 "d2h_bytes_per_step": eb["d2h"]},
         "gpu_launches": bm["launches"] * args.steps,

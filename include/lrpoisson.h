@@ -200,6 +200,38 @@ lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, 
  * last solve was not timed. */
 lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
 
+/* Autotuning of the launch shapes (the paper has no counterpart; step T0's
+ * tuned-configuration lookup and T7's tuned tiles and cluster sizes).
+ *
+ * lr_autotune times lr_poisson2d on the caller's problem rhs (device buffers
+ * as for lr_poisson2d; the trial solutions go to internal scratch) with CUDA
+ * events on the handle's stream, one warm-up and `reps` timed solves per
+ * candidate (median), and keeps the fastest in the handle for the order m,
+ * precision and operator kind of opt.  Later solves on this handle with
+ * opt->cluster_size = 0 use it.  Candidates: the transform tile (1024, 2048
+ * or 4096 complex elements; orders whose transform takes the four-step path,
+ * 2m - 1 > 4096) and then the cross cluster size (1, 2, 4, 8, 12, 16 CTAs,
+ * those the order admits).  Refinement is not run while tuning.
+ *
+ * lr_autotune_batched times lr_poisson2d_batched on the given batch (its
+ * sol buffers receive the trial results) for 1024, 2048, 4096 and 8192
+ * indices per cross CTA and keeps the fastest for batched solves of that
+ * precision on this handle (default 2048).
+ *
+ * Both synchronise and return LR_EINVAL for bad arguments.  `out` (host, may
+ * be NULL) receives the choice and the times. */
+typedef struct {
+  int cluster_size;          /* tuned CTAs per cross cluster (single solves) */
+  int log_tile;              /* log2 of the tuned transform tile (0: heuristic) */
+  int batch_indices_per_cta; /* tuned indices per cross CTA (batched solves) */
+  int candidates;            /* configurations timed */
+  double ms_best;            /* median ms of the chosen configuration */
+  double ms_default;         /* median ms of the untuned configuration */
+} lr_tune;
+lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int reps, lr_tune* out);
+lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options* opt,
+                              int reps, lr_tune* out);
+
 /* lr_truncate without any allocation (the paper has no counterpart; this is
  * a deployment variant of lr_truncate above, same arithmetic and results).
  *

@@ -10,6 +10,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lr_internal.h"
@@ -45,6 +46,10 @@ struct lr_handle_s {
   // float64 buffers of iterative refinement (solution, correction, residual)
   void* ws2 = nullptr;
   size_t ws2_bytes = 0;
+  // autotuned cluster sizes of single solves, keyed (m, precision, operator),
+  // and indices per cross CTA of batched solves, per precision
+  std::map<std::tuple<int, int, int>, int> tuned_cs;
+  int batch_ipc[2] = {2048, 2048};
 };
 
 namespace {
@@ -656,13 +661,15 @@ lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol
   int launches = 0;
   for (int i = 0; i < batch; ++i) launches += launches_of(geo[i]);
   // Throughput mode: unless the caller fixed it, give each cross about 2048
-  // indices per CTA.  Its per-step cost is mostly a fixed latency, so fewer,
-  // fuller CTAs per problem spend less SM time and let more problems run at
-  // once (a single solve uses about 1024 indices per CTA for latency).
+  // indices per CTA (or the autotuned number).  Its per-step cost is mostly a
+  // fixed latency, so fewer, fuller CTAs per problem spend less SM time and
+  // let more problems run at once (a single solve uses about 1024 indices per
+  // CTA for latency).
   std::vector<lr_options> popt(batch, o);
+  const int ipc = h->batch_ipc[sizeof(T) == 4 ? 1 : 0];
   if (o.cluster_size == 0)
     for (int i = 0; i < batch; ++i) {
-      int cs = (geo[i].m + 2047) / 2048;
+      int cs = (geo[i].m + ipc - 1) / ipc;
       popt[i].cluster_size = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
     }
   const bool graph = (o.flags & LR_FLAG_GRAPH) != 0;
@@ -831,6 +838,10 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
   s = get_plan(h, m, &plan);
   if (s != LR_OK) return s;
   h->info = lr_info{};
+  if (o.cluster_size == 0) {  // T0: autotuned configuration of this order, if any
+    auto it = h->tuned_cs.find(std::make_tuple(m, (int)o.prec, (int)o.op));
+    if (it != h->tuned_cs.end()) o.cluster_size = it->second;
+  }
   int rounds = o.refine;
   if (rounds == 0) rounds = o.eps < 1e-7 ? 6 : 0;
   if (o.prec == LR_MIXED && rounds > 0)
@@ -865,6 +876,141 @@ lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat
                          : solve2d_batched<double>(h, batch, rhs, sol, o, plans, per_problem);
   h->info.status = s;
   return s;
+}
+
+// Autotuning: time candidate launch shapes on the caller's problem (CUDA
+// events on the handle's stream, median of reps after a warm-up).
+lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int reps, lr_tune* out) {
+  if (!h) return LR_EINVAL;
+  lr_options o;
+  if (opt) o = *opt; else lr_options_default(&o);
+  lr_status s = check_opts(h, o);
+  if (s != LR_OK) return s;
+  if (!rhs) return fail(h, LR_EINVAL, "null rhs");
+  if (reps < 1 || reps > 100) return fail(h, LR_EINVAL, "reps must be in [1, 100]");
+  const int m = rhs->n1;
+  const int ld = m + (m & 1);
+  double* buf = nullptr;
+  if (m < 1 || m > 131072) return fail(h, LR_EINVAL, "m must be in [1, 131072]");
+  if (cudaMalloc(&buf, sizeof(double) * ((size_t)2 * ld * KMAX + KMAX)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, LR_ENOMEM, "autotune scratch");
+  }
+  struct Free { double* p; ~Free() { cudaFree(p); } } guard{buf};
+  lr_mat sol = {m, m, 0, KMAX, ld, buf, buf + (size_t)2 * ld * KMAX, buf + (size_t)ld * KMAX};
+  if ((s = check_problem(h, rhs, &sol)) != LR_OK) return s;
+  Plan* plan = nullptr;
+  if ((s = get_plan(h, m, &plan)) != LR_OK) return s;
+  if ((s = ensure_events(h)) != LR_OK) return s;
+  o.flags = LR_FLAG_TIMING;
+  o.refine = -1;
+  const int pi = o.prec == LR_MIXED ? 1 : 0;
+  int ncand = 0;
+  auto timed = [&](int cs, int tile, double* ms, int* used) -> lr_status {
+    plan->log_tile[pi] = tile;
+    o.cluster_size = cs;
+    std::vector<double> t;
+    for (int i = 0; i <= reps; ++i) {
+      const lr_status st = o.prec == LR_MIXED ? solve2d<float>(h, rhs, &sol, o, plan)
+                                              : solve2d<double>(h, rhs, &sol, o, plan);
+      if (st != LR_OK && st != LR_ENOCONV) return st;
+      float e = 0.f;
+      LR_CUDA(h, cudaEventElapsedTime(&e, h->ev[0], h->ev[LR_NUM_PHASES]), "event time");
+      if (i > 0) t.push_back(e);
+    }
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    *used = h->last_cs;
+    ++ncand;
+    return LR_OK;
+  };
+  double ms_def = 0.0, ms = 0.0;
+  int used = 0, best_cs = 0, best_tile = 0;
+  if ((s = timed(0, 0, &ms_def, &best_cs)) != LR_OK) return s;
+  double best = ms_def;
+  const int logM = plan->logM;
+  if (((size_t)1 << logM) > (size_t)kSmallM) {  // four-step transform: tile 2^10 .. 2^12
+    const int logMin = std::max((logM + 1) / 2, 10);
+    for (int t = logMin; t <= 12; ++t) {
+      if ((s = timed(0, t, &ms, &used)) != LR_OK) return s;
+      if (ms < best) { best = ms; best_tile = t; best_cs = used; }
+    }
+  }
+  const int cs_min = (m + 8191) / 8192;
+  const int cs_max = std::min(16, std::max(1, (m + 127) / 128));
+  for (int cs : {1, 2, 4, 8, 12, 16}) {
+    if (cs < cs_min || cs > cs_max) continue;
+    if ((s = timed(cs, best_tile, &ms, &used)) != LR_OK) return s;
+    if (ms < best) { best = ms; best_cs = used; }
+  }
+  plan->log_tile[pi] = best_tile;
+  h->tuned_cs[std::make_tuple(m, (int)o.prec, (int)o.op)] = best_cs;
+  h->timed = false;
+  if (out) {
+    out->cluster_size = best_cs;
+    out->log_tile = best_tile;
+    out->batch_indices_per_cta = h->batch_ipc[pi];
+    out->candidates = ncand;
+    out->ms_best = best;
+    out->ms_default = ms_def;
+  }
+  return LR_OK;
+}
+
+lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options* opt,
+                              int reps, lr_tune* out) {
+  if (!h) return LR_EINVAL;
+  lr_options o;
+  if (opt) o = *opt; else lr_options_default(&o);
+  lr_status s = check_opts(h, o);
+  if (s != LR_OK) return s;
+  if (batch < 1 || !rhs || !sol) return fail(h, LR_EINVAL, "bad batch arguments");
+  if (reps < 1 || reps > 100) return fail(h, LR_EINVAL, "reps must be in [1, 100]");
+  std::vector<Plan*> plans(batch);
+  for (int i = 0; i < batch; ++i) {
+    if ((s = check_problem(h, &rhs[i], &sol[i])) != LR_OK) return s;
+    if ((s = get_plan(h, rhs[i].n1, &plans[i])) != LR_OK) return s;
+  }
+  if ((s = ensure_events(h)) != LR_OK) return s;
+  o.flags = 0;
+  o.cluster_size = 0;
+  const int pi = o.prec == LR_MIXED ? 1 : 0;
+  const int before = h->batch_ipc[pi];
+  double best = 0.0, ms_def = 0.0;
+  int best_ipc = before, ncand = 0;
+  for (int ipc : {2048, 1024, 4096, 8192}) {  // the default first
+    h->batch_ipc[pi] = ipc;
+    std::vector<double> t;
+    for (int i = 0; i <= reps; ++i) {
+      LR_CUDA(h, cudaEventRecord(h->ev[0], h->stream), "event");
+      const lr_status st = o.prec == LR_MIXED ? solve2d_batched<float>(h, batch, rhs, sol, o, plans, nullptr)
+                                              : solve2d_batched<double>(h, batch, rhs, sol, o, plans, nullptr);
+      if (st != LR_OK && st != LR_ENOCONV) { h->batch_ipc[pi] = before; return st; }
+      LR_CUDA(h, cudaEventRecord(h->ev[1], h->stream), "event");
+      LR_CUDA(h, cudaEventSynchronize(h->ev[1]), "event");
+      float e = 0.f;
+      LR_CUDA(h, cudaEventElapsedTime(&e, h->ev[0], h->ev[1]), "event time");
+      if (i > 0) t.push_back(e);
+    }
+    std::sort(t.begin(), t.end());
+    const double ms = t[t.size() / 2];
+    if (ncand == 0) ms_def = ms;
+    ++ncand;
+    if (ncand == 1 || ms < best) { best = ms; best_ipc = ipc; }
+  }
+  h->batch_ipc[pi] = best_ipc;
+  h->timed = false;
+  if (out) {
+    auto it = h->tuned_cs.find(std::make_tuple(rhs[0].n1, (int)o.prec, (int)o.op));
+    out->cluster_size = it != h->tuned_cs.end() ? it->second : 0;
+    Plan* p0 = plans[0];
+    out->log_tile = p0->log_tile[pi];
+    out->batch_indices_per_cta = best_ipc;
+    out->candidates = ncand;
+    out->ms_best = best;
+    out->ms_default = ms_def;
+  }
+  return LR_OK;
 }
 
 lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, int cap) {

@@ -443,7 +443,12 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
   GeomArgs g2 = g;
   g2.logTile = 12;
   const int logMin = g.logM1 > 10 ? g.logM1 : 10;
-  while (g2.logTile > logMin && (g.ncols << (g.logM - g2.logTile)) < 2 * num_sms) --g2.logTile;
+  const int tuned = p.log_tile[sizeof(T) == 4 ? 1 : 0];
+  if (tuned) {
+    g2.logTile = tuned < logMin ? logMin : (tuned > 12 ? 12 : tuned);
+  } else {
+    while (g2.logTile > logMin && (g.ncols << (g.logM - g2.logTile)) < 2 * num_sms) --g2.logTile;
+  }
   const int tile = 1 << g2.logTile;
   const int threads = tile / EPT;
   const size_t smem = (size_t)(tile + (1 << g.logM1)) * sizeof(cpx<T>);

@@ -42,6 +42,7 @@ struct Plan {
   double* sym_b64[2] = {nullptr, nullptr};
   float* sym_a32[2] = {nullptr, nullptr};
   float* sym_b32[2] = {nullptr, nullptr};
+  int log_tile[2] = {0, 0};                 // tuned four-step tile (0: heuristic), [fp64, fp32]
   std::vector<void*> allocations;
   ~Plan();
 };

@@ -32,7 +32,7 @@ OPERATORS = {"5pt": LR_OP_5PT, "semi": LR_OP_SEMISTAGGERED}
 EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
-           "lr_poisson2d_batched")
+           "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched")
 
 
 class LrMat(ctypes.Structure):
@@ -46,6 +46,15 @@ class LrOptions(ctypes.Structure):
                 ("rmax", ctypes.c_int), ("aca_tol_factor", ctypes.c_double),
                 ("probes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("flags", ctypes.c_uint), ("cluster_size", ctypes.c_int), ("refine", ctypes.c_int)]
+
+
+class LrTune(ctypes.Structure):
+    _fields_ = [("cluster_size", ctypes.c_int), ("log_tile", ctypes.c_int),
+                ("batch_indices_per_cta", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("ms_best", ctypes.c_double), ("ms_default", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class LrInfo(ctypes.Structure):
@@ -106,6 +115,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_poisson2d_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                          ctypes.POINTER(LrOptions), ctypes.POINTER(c_int)]
     lib.lr_poisson2d_batched.restype = c_int
+    lib.lr_autotune.argtypes = [c_void_p, ctypes.POINTER(LrMat), ctypes.POINTER(LrOptions), c_int,
+                                ctypes.POINTER(LrTune)]
+    lib.lr_autotune.restype = c_int
+    lib.lr_autotune_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
+                                        ctypes.POINTER(LrOptions), c_int, ctypes.POINTER(LrTune)]
+    lib.lr_autotune_batched.restype = c_int
     if path is None:
         _lib = lib
     return lib
@@ -368,3 +383,36 @@ def lr_poisson2d_batched(h: Handle, batch: Batch, eps: float = 1e-6, prec="mixed
     if check and st not in (LR_OK, LR_ENOCONV):
         raise LrError(st, h.last_error())
     return st
+
+
+def lr_autotune(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rmax: int = 64,
+                reps: int = 5) -> dict:
+    """Time launch-shape candidates of lr_poisson2d on (U, V) and keep the
+    fastest in the handle for this order, precision and operator kind."""
+    U = as_colmajor(U)
+    V = as_colmajor(V)
+    if U.stride(1) != V.stride(1):
+        V2 = colmajor_empty(V.shape[0], V.shape[1], V.device)
+        V2.copy_(V)
+        V = V2
+    m, r = U.shape
+    rhs = LrMat(m, m, r, r, _ld(U), U.data_ptr(), None, V.data_ptr())
+    o = _options(eps, prec, op, rmax, 1.0, 16, 0, 0, 0)
+    t = LrTune()
+    st = load().lr_autotune(h.ptr, ctypes.byref(rhs), ctypes.byref(o), int(reps), ctypes.byref(t))
+    if st != LR_OK:
+        raise LrError(st, h.last_error())
+    return t.as_dict()
+
+
+def lr_autotune_batched(h: Handle, batch: Batch, eps: float = 1e-6, prec="mixed", op="5pt", rmax: int = 64,
+                        reps: int = 3) -> dict:
+    """Time the indices-per-CTA candidates of lr_poisson2d_batched on ``batch``
+    and keep the fastest in the handle for this precision."""
+    o = _options(eps, prec, op, rmax, 1.0, 16, 0, 0, 0)
+    t = LrTune()
+    st = load().lr_autotune_batched(h.ptr, len(batch), batch.c_rhs, batch.c_sol, ctypes.byref(o), int(reps),
+                                    ctypes.byref(t))
+    if st != LR_OK:
+        raise LrError(st, h.last_error())
+    return t.as_dict()

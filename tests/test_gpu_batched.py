@@ -100,3 +100,34 @@ def test_batch_of_config3_recipe_converges(lr, h):
         Ub, sb, Vb = (npy(t) for t in batch.result(i))
         rows = np.unique(np.linspace(0, U.shape[0] - 1, 128).astype(int))
         assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt", rows=rows) <= 1e-5
+
+
+# ------------------------------------------------------------------ autotuning (T0 lookup, T7 tiles)
+def test_autotune_single_then_lookup(lr, h):
+    m, eps = 16384, 1e-6
+    U, V = inputs.smooth_sum(m, eps)
+    Ud, Vd = torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda()
+    t = lr.lr_autotune(h, Ud, Vd, eps=eps, prec="mixed", reps=3)
+    assert 1 <= t["cluster_size"] <= 16 and t["log_tile"] in (0, 10, 11, 12)
+    assert t["candidates"] >= 2 and 0 < t["ms_best"] <= t["ms_default"] * 1.0001
+    # a solve with cluster_size 0 now uses the tuned size, and gives bitwise
+    # the result of an explicit solve with that size
+    a = lr.lr_poisson2d(h, Ud, Vd, eps=eps, prec="mixed")
+    assert a.info.cluster_size == t["cluster_size"]
+    b = lr.lr_poisson2d(h, Ud, Vd, eps=eps, prec="mixed", cluster_size=t["cluster_size"])
+    assert np.array_equal(npy(a.U), npy(b.U)) and np.array_equal(npy(a.s), npy(b.s))
+    rows = np.unique(np.linspace(0, m - 1, 256).astype(int))
+    assert O.rel_error_freq(npy(a.U), npy(a.s), npy(a.V), U, V, "5pt", rows=rows) <= 10 * eps
+
+
+def test_autotune_batched(lr, h):
+    probs = _problems(16, 512, 4096, 16, seed=5)
+    batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
+    t = lr.lr_autotune_batched(h, batch, eps=1e-6, prec="mixed", reps=2)
+    assert t["batch_indices_per_cta"] in (1024, 2048, 4096, 8192) and t["candidates"] == 4
+    st = lr.lr_poisson2d_batched(h, batch, eps=1e-6, prec="mixed")
+    torch.cuda.synchronize()
+    assert st == lr.LR_OK
+    for i, (U, V) in enumerate(probs):
+        Ub, sb, Vb = (npy(x) for x in batch.result(i))
+        assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt") <= 1e-5
