@@ -73,6 +73,10 @@ typedef enum {
 #define LR_FLAG_GRAPH 4u   /* capture the enqueued work once as a CUDA graph
                               (keyed by every pointer, size and option) and
                               replay it on later calls with the same key */
+#define LR_FLAG_CLUSTER_DST 8u  /* lr_poisson2d: run both transforms with the
+                                   cluster variant (one thread-block cluster
+                                   per column, 8192 <= M <= 131072) for this
+                                   call, whatever the tuned choice */
 
 /* Phases of lr_poisson2d timed under LR_FLAG_TIMING. */
 #define LR_PHASE_FORWARD_DST 0  /* DST of the right-hand side factors      */
@@ -208,10 +212,12 @@ lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
  * events on the handle's stream, one warm-up and `reps` timed solves per
  * candidate (median), and keeps the fastest in the handle for the order m,
  * precision and operator kind of opt.  Later solves on this handle with
- * opt->cluster_size = 0 use it.  Candidates: the transform tile (1024, 2048
- * or 4096 complex elements; orders whose transform takes the four-step path,
- * 2m - 1 > 4096) and then the cross cluster size (1, 2, 4, 8, 12, 16 CTAs,
- * those the order admits).  Refinement is not run while tuning.
+ * opt->cluster_size = 0 use it.  Candidates, for orders whose transform is
+ * not a single-CTA one (2m - 1 > 4096): the four-step transform's tile (1024,
+ * 2048 or 4096 complex elements) and the cluster transform (one thread-block
+ * cluster per column, 8192 <= M <= 131072); then the cross cluster size (1,
+ * 2, 4, 8, 12, 16 CTAs, those the order admits).  Refinement is not run
+ * while tuning.
  *
  * lr_autotune_batched times lr_poisson2d_batched on the given batch (its
  * sol buffers receive the trial results) for 1024, 2048, 4096 and 8192
@@ -223,6 +229,7 @@ lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
 typedef struct {
   int cluster_size;          /* tuned CTAs per cross cluster (single solves) */
   int log_tile;              /* log2 of the tuned transform tile (0: heuristic) */
+  int transform;             /* tuned transform variant: 0 four-step, 1 cluster */
   int batch_indices_per_cta; /* tuned indices per cross CTA (batched solves) */
   int candidates;            /* configurations timed */
   double ms_best;            /* median ms of the chosen configuration */

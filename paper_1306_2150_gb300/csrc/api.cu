@@ -331,6 +331,10 @@ lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options&
   if (timing && (s = ensure_events(h)) != LR_OK) return s;
   h->timed = timing;
   int used_cs = 0;
+  // transform variant for this call (restored on return)
+  const int pi = sizeof(T) == 4 ? 1 : 0;
+  struct Restore { Plan* p; int i, v; ~Restore() { p->use_cluster[i] = v; } } restore{plan, pi, plan->use_cluster[pi]};
+  if (o.flags & LR_FLAG_CLUSTER_DST) plan->use_cluster[pi] = 1;
   s = run_maybe_graph(h, graph, key_of("single", rhs, 1, sol, o), [&](cudaStream_t stm) -> cudaError_t {
     cudaError_t e = enqueue_solve<T>(h, rhs, sol, o, *plan, g, w, st, stm, timing ? h->ev : nullptr, &used_cs);
     if (e != cudaSuccess) return e;
@@ -360,7 +364,7 @@ lr_status solve2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options&
 //   X  <- solve(F)                        (mixed, at max(eps, 1e-6))
 //   repeat: Res = F - A X                 (exact, low rank r + 2R, float64)
 //           Res <- QR-round(Res, 1e-8)    (shifted Cholesky QR + core SVD)
-//           D   = s0 solve(Res / s0)      (mixed, at 1e-6, at unit scale)
+//           D   = s0 solve(Res / s0)      (mixed, at 1e-5, at unit scale)
 //           X   <- round(X + D, eps)      (float64 rounding, Section 3)
 //   until the error estimate sigma_0(D) / sigma_0(X) * (ratio of successive
 //   corrections) is below eps / 2, or the corrections stop shrinking.
@@ -540,7 +544,12 @@ lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
     // Correction D, written after X's R1 columns (room KMAX - R1).
     lr_mat res = {m, m, Kres, Kres, ld, Yl, nullptr, Yr};
     lr_mat D = {m, m, 0, KMAX - R1, ld, X.U + (size_t)R1 * ld, X.s + R1, X.V + (size_t)R1 * ld};
-    s = solve2d<float>(h, &res, &D, o1, plan);
+    // The correction is needed to a few digits only (a round cannot gain more
+    // than the float32 solve resolves under the residual's cancellation), and
+    // a looser tolerance keeps its rank well inside the 64-step cap.
+    lr_options oc = o1;
+    oc.eps = std::max(o1.eps, 1e-5);
+    s = solve2d<float>(h, &res, &D, oc, plan);
     if (s != LR_OK && s != LR_ENOCONV) return s;  // ENOCONV: D cut to the room left, or cross cap
     launches += h->info.launches;
     const double sd = h->h_state->sigma0 * rs0;
@@ -907,7 +916,9 @@ lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int
   const int pi = o.prec == LR_MIXED ? 1 : 0;
   int ncand = 0;
   auto timed = [&](int cs, int tile, double* ms, int* used) -> lr_status {
-    plan->log_tile[pi] = tile;
+    // tile -1: the cluster transform; otherwise the four-step tile (0: heuristic)
+    plan->use_cluster[pi] = tile < 0 ? 1 : 0;
+    plan->log_tile[pi] = tile < 0 ? 0 : tile;
     o.cluster_size = cs;
     std::vector<double> t;
     for (int i = 0; i <= reps; ++i) {
@@ -935,6 +946,10 @@ lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int
       if ((s = timed(0, t, &ms, &used)) != LR_OK) return s;
       if (ms < best) { best = ms; best_tile = t; best_cs = used; }
     }
+    if (plan->logN2cl) {
+      if ((s = timed(0, -1, &ms, &used)) != LR_OK) return s;
+      if (ms < best) { best = ms; best_tile = -1; best_cs = used; }
+    }
   }
   const int cs_min = (m + 8191) / 8192;
   const int cs_max = std::min(16, std::max(1, (m + 127) / 128));
@@ -943,12 +958,14 @@ lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int
     if ((s = timed(cs, best_tile, &ms, &used)) != LR_OK) return s;
     if (ms < best) { best = ms; best_cs = used; }
   }
-  plan->log_tile[pi] = best_tile;
+  plan->use_cluster[pi] = best_tile < 0 ? 1 : 0;
+  plan->log_tile[pi] = best_tile < 0 ? 0 : best_tile;
   h->tuned_cs[std::make_tuple(m, (int)o.prec, (int)o.op)] = best_cs;
   h->timed = false;
   if (out) {
     out->cluster_size = best_cs;
-    out->log_tile = best_tile;
+    out->log_tile = best_tile < 0 ? 0 : best_tile;
+    out->transform = best_tile < 0 ? 1 : 0;
     out->batch_indices_per_cta = h->batch_ipc[pi];
     out->candidates = ncand;
     out->ms_best = best;
@@ -1005,6 +1022,7 @@ lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat*
     out->cluster_size = it != h->tuned_cs.end() ? it->second : 0;
     Plan* p0 = plans[0];
     out->log_tile = p0->log_tile[pi];
+    out->transform = p0->use_cluster[pi];
     out->batch_indices_per_cta = best_ipc;
     out->candidates = ncand;
     out->ms_best = best;

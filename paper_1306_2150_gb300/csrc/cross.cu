@@ -108,6 +108,7 @@ struct Shared {
   T norm2;                 // ||S_k||_F^2 of the skeleton
   T rsq;                   // |rho|^2 of the current step
   T delta;                 // pivot value of the current step
+  T pfloor;                // pivots at or below are treated as zero (noise floor)
   int idx;
   int flag;
   int win;                 // rank whose candidate won the last reduction
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
       }
   }
   for (int i = tid; i < SP * KS; i += NT) { cc.C[i] = T(0); cc.R[i] = T(0); }
-  if (tid == 0) { sh.norm2 = T(0); sh.small = 0; }
+  if (tid == 0) { sh.norm2 = T(0); sh.small = 0; sh.pfloor = T(0); }
   __syncthreads();
   // Every CTA must be running before anyone pushes into its inbox.
   cl.sync();
@@ -517,7 +518,9 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
     const int jstar = sh.idx;
     if (tid == 0) {
       const T dv = jstar >= 0 ? sh.val : T(0);
-      sh.flag = dv == T(0);
+      // A pivot far below the working precision's rounding noise (relative to
+      // the first pivot) is a zero row: dividing by it would only overflow.
+      sh.flag = !(fabs(dv) > sh.pfloor);
       sh.delta = dv;
       sh.rsq = sh.sumsq;
       if (jstar >= row0 && jstar < row1) cc.used_c[jstar - row0] = 1;
@@ -576,6 +579,7 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
       const T term2 = csq * sh.rsq;                   // |d|^2 |c|^2 |r|^2
       sh.norm2 += T(2) * delta * cs + term2;
       sh.small = (term2 <= tol2 * sh.norm2) ? sh.small + 1 : 0;
+      if (k == 0) sh.pfloor = fabs(delta) * (T)(sizeof(T) == 4 ? 1e-9 : 1e-20);
       if (q == 0) {
         A.GC[k + (size_t)k * A.kcap] = (double)csq;
         A.GR[k + (size_t)k * A.kcap] = (double)rr;

@@ -21,6 +21,12 @@
 //     col_inv : per t1, inverse length-M2 FFT over k2 -> t2, chirp, store.
 //   The frequency-domain product is taken in the permuted order the forward
 //   passes leave, so no transposition pass is needed.
+//   cluster path (8192 <= M <= 131072, a variant the autotuner may pick):
+//   one thread-block cluster per column holds the whole sequence in
+//   distributed shared memory (see dst_cluster_kernel).  On GB300 it is
+//   slower than the four-step path as measured (float64: its per-CTA work
+//   lands on a few SMs' small FP64 units; float32: latency-bound at 8 warps
+//   per CTA), so the four-step path is the default.
 // Shared-memory FFTs are in-place Stockham radix-4 (one radix-2 pass when
 // log2 L is odd): every thread keeps its 16 elements in registers between the
 // read and the write phase of a pass.
@@ -29,7 +35,11 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "lr_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace lrp {
 
@@ -408,6 +418,114 @@ static const TablesT& tables_of(const Plan& p);
 template <> const TablesT& tables_of<double>(const Plan& p) { return p.t64; }
 template <> const TablesT& tables_of<float>(const Plan& p) { return p.t32; }
 
+// ---------------------------------------------------------------------------
+// Cluster path (8192 <= M <= 131072): one thread-block cluster of CS = M / N2
+// CTAs per column; CTA k1 ends up holding the length-N2 sub-spectrum k = k1 +
+// CS k2 (N2 = 4096, or 8192 at M = 131072).  With t = t2 + N2 t1:
+//   CTA c takes the t2 of its slice [c N2/CS, (c+1) N2/CS), reads a[t2 + N2 t1]
+//   for every t1 from global memory, forms the CS-point DFTs in registers and
+//   the twiddle, b_k1[t2] = w_M^(t2 k1) sum_t1 a[t2 + N2 t1] w_CS^(t1 k1), and
+//   stores b_k1[t2] into CTA k1's shared memory (distributed shared memory);
+//   CTA k1: A[k1 + CS k2] = FFT_N2(b_k1)[k2], times the kernel spectrum
+//   (stored per CTA as [k1][k2]), d_k1 = conj(w_M^(t2 k1)) IFFT_N2(...);
+//   CTA c again takes its slice, gathers d_k1[t2] from every CTA, forms the
+//   inverse CS-point DFTs z[t2 + N2 t1] and stores Im(w_t z_t) for t < m.
+// A transform is one launch, no scratch in global memory, inputs read and
+// outputs written once (coalesced runs of N2/CS), and each value crosses the
+// cluster network twice.
+// ---------------------------------------------------------------------------
+template <typename T, int INM, bool OUT64>
+__global__ void __launch_bounds__(512) dst_cluster_kernel(ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp,
+                                                          const cpx<T>* __restrict__ tw,
+                                                          const cpx<T>* __restrict__ bcl, int logN2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int logCS = g.logM - logN2;
+  const int me = (int)cl.block_rank();
+  const int col = blockIdx.x >> logCS;
+  const int NT = blockDim.x;        // N2 / EPT
+  const int G = EPT >> logCS;       // slice positions per thread (EPT / CS)
+  int seg, cc;
+  const bool live = col < g.ncols && col_live(c, col, seg, cc);  // uniform over the cluster
+  if (!live) return;
+  const int slice0 = me << (logN2 - logCS);
+  // Distributed shared memory may be written only once every CTA of the
+  // cluster is running.
+  cl.sync();
+  // 1-2. a[t2 + N2 t1] of the slice from global memory, CS-point DFTs, twiddle,
+  // scatter to the owners of the sub-spectra.
+  for (int q = 0; q < G; ++q) {
+    const int t2 = slice0 + threadIdx.x + q * NT;
+    cpx<T> a[EPT];
+#pragma unroll
+    for (int t1 = 0; t1 < EPT; ++t1) {
+      a[t1] = {T(0), T(0)};
+      if (t1 < CS) {
+        const int t = t2 + (t1 << logN2);
+        if (t < g.m) {
+          const T x = load_in<T, INM>(c, seg, cc, t);
+          const cpx<T> w = chirp[t];
+          a[t1] = {x * w.re, x * w.im};
+        }
+      }
+    }
+    for (int k1 = 0; k1 < CS; ++k1) {
+      cpx<T> acc = a[0];
+#pragma unroll
+      for (int t1 = 1; t1 < EPT; ++t1)
+        if (t1 < CS) acc = cadd(acc, cmul(a[t1], tw[((t1 * k1) & (CS - 1)) << logN2]));  // w_CS^(t1 k1)
+      acc = cmul(acc, tw[(size_t)t2 * k1]);  // w_M^(t2 k1)
+      cl.map_shared_rank(S, k1)[t2] = acc;
+    }
+  }
+  cl.sync();
+  // 3-5. local FFT, kernel spectrum, inverse FFT, conjugate twiddle
+  smem_fft<T, false>(S, logN2, 0, 1, 0, tw, g.logM, false);
+  {
+    const cpx<T>* bk = bcl + ((size_t)me << logN2);
+#pragma unroll
+    for (int s = 0; s < EPT; ++s) {
+      const int k2 = threadIdx.x + s * NT;
+      S[k2] = cmul(S[k2], bk[k2]);
+    }
+  }
+  __syncthreads();
+  smem_fft<T, false>(S, logN2, 0, 1, 0, tw, g.logM, true);
+#pragma unroll
+  for (int s = 0; s < EPT; ++s) {
+    const int t2 = threadIdx.x + s * NT;
+    cpx<T> w = tw[(size_t)t2 * me];
+    w.im = -w.im;
+    S[t2] = cmul(S[t2], w);
+  }
+  cl.sync();
+  // 6-7. gather the slice from every sub-spectrum owner, inverse CS-point
+  // DFTs, chirp, store.
+  for (int q = 0; q < G; ++q) {
+    const int t2 = slice0 + threadIdx.x + q * NT;
+    cpx<T> d[EPT];
+#pragma unroll
+    for (int k1 = 0; k1 < EPT; ++k1) d[k1] = k1 < CS ? cl.map_shared_rank(S, k1)[t2] : cpx<T>{T(0), T(0)};
+    for (int t1 = 0; t1 < CS; ++t1) {
+      const int t = t2 + (t1 << logN2);
+      if (t >= g.m) break;  // t grows with t1
+      cpx<T> z = d[0];
+#pragma unroll
+      for (int k1 = 1; k1 < EPT; ++k1)
+        if (k1 < CS) {
+          cpx<T> w = tw[((t1 * k1) & (CS - 1)) << logN2];
+          w.im = -w.im;
+          z = cadd(z, cmul(d[k1], w));
+        }
+      const cpx<T> w = chirp[t];
+      store_out<T, OUT64>(c, seg, cc, t, w.re * z.im + w.im * z.re);  // Im(w z)
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 template <typename T, int INM, bool OUT64>
 static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs& g, void* work,
                                 int num_sms, cudaStream_t st) {
@@ -437,6 +555,40 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
     }
     kern<<<grid, threads, smem, st>>>(c, g, chirp, tw, bhat, lognf);
     return cudaGetLastError();
+  }
+  // Cluster path: one cluster per column, no global scratch.
+  if (p.logN2cl && p.use_cluster[sizeof(T) == 4 ? 1 : 0] &&
+      (size_t)(1 << p.logN2cl) * sizeof(cpx<T>) <= 64 * 1024) {
+    const int logN2 = p.logN2cl;
+    const int CS = 1 << (g.logM - logN2);
+    auto kern = dst_cluster_kernel<T, INM, OUT64>;
+    const size_t smem = (size_t)(1 << logN2) * sizeof(cpx<T>);
+    static cudaError_t attr = [&] {
+      cudaError_t e1 = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      return e1 != cudaSuccess ? e1 : e2;
+    }();
+    if (attr == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(g.ncols * CS));
+      cfg.blockDim = dim3((unsigned)((1 << logN2) / EPT));
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = CS;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cpx<T>* bcl = static_cast<const cpx<T>*>(tb.bhat_cl);
+      cudaError_t e = cudaLaunchKernelEx(&cfg, kern, c, g, chirp, tw, bcl, logN2);
+      if (e == cudaSuccess) return cudaSuccess;
+      if (e != cudaErrorInvalidClusterSize && e != cudaErrorLaunchOutOfResources &&
+          e != cudaErrorInvalidConfiguration)
+        return e;
+      cudaGetLastError();  // cluster does not fit: use the four-step path
+    }
   }
   // Tile of 4096 elements, halved (down to 1024, and not below either
   // sub-length) while that still leaves fewer than two tiles per SM.
@@ -627,6 +779,17 @@ std::string build_plan(int m, Plan& p) {
   if (!(e = upload<float>(p, chirp, &p.t32.chirp)).empty()) return e;
   if (!(e = upload<float>(p, tw, &p.t32.tw)).empty()) return e;
   if (!(e = upload<float>(p, bh, &p.t32.bhat)).empty()) return e;
+  // cluster path: chunks of N2 = 4096 (8192 at M = 131072), spectrum stored
+  // per CTA as [k1][k2] = b[k1 + CS k2]
+  if (logM >= 13 && logM <= 17) {
+    p.logN2cl = logM <= 16 ? 12 : 13;
+    const size_t N2c = (size_t)1 << p.logN2cl, CSc = M / N2c;
+    std::vector<std::complex<double>> bc(M);
+    for (size_t k1 = 0; k1 < CSc; ++k1)
+      for (size_t k2 = 0; k2 < N2c; ++k2) bc[k1 * N2c + k2] = b[k1 + CSc * k2];
+    if (!(e = upload<double>(p, bc, &p.t64.bhat_cl)).empty()) return e;
+    if (!(e = upload<float>(p, bc, &p.t32.bhat_cl)).empty()) return e;
+  }
   // Symbol: lambda_i = 4 sin^2(i pi/(2N)), 4 - lambda_i = 4 cos^2(i pi/(2N)).
   std::vector<double> a5(m), b5(m, 1.0), as(m), bs(m);
   const double N2 = (double)N * (double)N;

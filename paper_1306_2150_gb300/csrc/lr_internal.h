@@ -30,6 +30,7 @@ struct TablesT {
   void* chirp = nullptr;  // cpx<T>[m]
   void* tw = nullptr;     // cpx<T>[M]
   void* bhat = nullptr;   // cpx<T>[M]
+  void* bhat_cl = nullptr;  // cpx<T>[M], cluster order [k1][k2] (cluster path only)
   void* a = nullptr;      // T[m] per operator kind (index by op)
   void* b = nullptr;
 };
@@ -43,6 +44,8 @@ struct Plan {
   float* sym_a32[2] = {nullptr, nullptr};
   float* sym_b32[2] = {nullptr, nullptr};
   int log_tile[2] = {0, 0};                 // tuned four-step tile (0: heuristic), [fp64, fp32]
+  int logN2cl = 0;                          // cluster-path chunk (0: no cluster path)
+  int use_cluster[2] = {0, 0};              // transform variant: 1 = cluster path, [fp64, fp32]
   std::vector<void*> allocations;
   ~Plan();
 };

@@ -23,6 +23,7 @@ LR_OP_5PT, LR_OP_SEMISTAGGERED = 0, 1
 LR_FLAG_ASYNC = 1
 LR_FLAG_TIMING = 2
 LR_FLAG_GRAPH = 4
+LR_FLAG_CLUSTER_DST = 8
 PHASES = ("forward_dst", "cross", "rounding", "inverse_dst")
 
 PRECISIONS = {"fp64": LR_FP64, "mixed": LR_MIXED}
@@ -49,7 +50,7 @@ class LrOptions(ctypes.Structure):
 
 
 class LrTune(ctypes.Structure):
-    _fields_ = [("cluster_size", ctypes.c_int), ("log_tile", ctypes.c_int),
+    _fields_ = [("cluster_size", ctypes.c_int), ("log_tile", ctypes.c_int), ("transform", ctypes.c_int),
                 ("batch_indices_per_cta", ctypes.c_int), ("candidates", ctypes.c_int),
                 ("ms_best", ctypes.c_double), ("ms_default", ctypes.c_double)]
 
@@ -234,7 +235,7 @@ def _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_s
 def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rmax: int = 64,
                  rmax_out: int = 64, aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
                  cluster_size: int = 0, async_: bool = False, out=None, check: bool = True,
-                 timing: bool = False, graph: bool = False, refine: int = 0):
+                 timing: bool = False, graph: bool = False, refine: int = 0, cluster_dst: bool = False):
     """Low-rank solve of A X = U V^T.  Returns SolveResult with the solution
     factors (views of rank R) unless ``async_`` (then read lr_get_info after
     synchronising the stream).  ``out`` = (Uo, s, Vo) preallocated outputs."""
@@ -263,7 +264,7 @@ def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rma
     if _ld(Vo) != _ld(Uo):
         raise ValueError("output factors need the same leading dimension")
     flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_TIMING if timing else 0) | \
-        (LR_FLAG_GRAPH if graph else 0)
+        (LR_FLAG_GRAPH if graph else 0) | (LR_FLAG_CLUSTER_DST if cluster_dst else 0)
     o = _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size, refine)
     st = load().lr_poisson2d(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o))
     if async_:

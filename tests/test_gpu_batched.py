@@ -108,7 +108,7 @@ def test_autotune_single_then_lookup(lr, h):
     U, V = inputs.smooth_sum(m, eps)
     Ud, Vd = torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda()
     t = lr.lr_autotune(h, Ud, Vd, eps=eps, prec="mixed", reps=3)
-    assert 1 <= t["cluster_size"] <= 16 and t["log_tile"] in (0, 10, 11, 12)
+    assert 1 <= t["cluster_size"] <= 16 and t["log_tile"] in (0, 10, 11, 12) and t["transform"] in (0, 1)
     assert t["candidates"] >= 2 and 0 < t["ms_best"] <= t["ms_default"] * 1.0001
     # a solve with cluster_size 0 now uses the tuned size, and gives bitwise
     # the result of an explicit solve with that size

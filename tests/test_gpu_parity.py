@@ -310,3 +310,20 @@ def test_refinement_semistaggered(lr, h):
     res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="mixed", op="semi")
     assert res.status == lr.LR_OK and res.info.refine_rounds >= 1
     assert O.rel_error_freq(Uo, s, Vo, U, V, "semi") <= 10 * eps
+
+
+# ------------------------------------------------------------------ cluster transform variant
+@pytest.mark.parametrize("m", [2049, 4096, 5000, 16384, 65536])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cluster_transform_variant(lr, h, m, prec):
+    # one thread-block cluster per column (CS = 2, 2, 4, 8, 16 CTAs; float64 at
+    # m = 65536 needs more shared memory than the variant uses and falls back
+    # to the four-step transform)
+    eps = 1e-6 if prec == "mixed" else 1e-10
+    U, V = inputs.smooth_sum(m, eps)
+    res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec=prec, cluster_dst=True)
+    assert res.status == lr.LR_OK
+    rows = None if m <= 5000 else np.unique(np.linspace(0, m - 1, 256).astype(int))
+    assert O.rel_error_freq(Uo, s, Vo, U, V, "5pt", rows=rows) <= 10 * eps
+    ref, Ur, sr, Vr = solve(lr, h, U, V, eps=eps, prec=prec)
+    assert abs(len(s) - len(sr)) <= 1
