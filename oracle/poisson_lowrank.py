@@ -181,7 +181,11 @@ def symbol(m: int, kind: str):
     if kind == "5pt":
         return lam / (h * h), np.ones(m)
     if kind == "semi":          # S (G G^T) S = diag(lam), S (H H^T) S = diag(4 - lam)
-        return lam / (16.0 * h * h), 4.0 - lam
+        # 4 - lam_k = 4 cos^2(k pi / (2(m+1))), the eigenvalues of H H^T =
+        # tridiag(1, 2, 1), evaluated directly: the subtraction cancels for k
+        # near m (relative error up to ~1e-10 at m = 2049)
+        k = np.arange(1, m + 1, dtype=np.float64)
+        return lam / (16.0 * h * h), 4.0 * np.cos(k * np.pi / (2.0 * (m + 1))) ** 2
     raise ValueError(kind)
 
 
