@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--batch", type=int, default=64)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--crossover", type=int, nargs="*", default=[256, 1024, 4096, 16384],
+                   help="grid sizes of the full-grid vs low-rank comparison")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -275,6 +277,35 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
             per.append(a.elapsed_time(b))
         results["tight_" + prec] = {"ms": statistics.median(per), "rank": rr.info.rank, "r": U2.shape[1],
                                     "refine_rounds": rr.info.refine_rounds, "status": rr.status}
+    # ---- crossover against the full-grid solver X = S((S F S)/Lambda)S on the
+    # dense grid (same smooth right-hand side, single solves, 3 timed each)
+    results["crossover"] = []
+    for nc in args.crossover:
+        Uc, Vc = inputs.smooth_sum(nc, EPS)
+        Ucd, Vcd = torch.from_numpy(Uc).cuda(), torch.from_numpy(Vc).cuda()
+        Fc = lr.as_colmajor(Ucd @ Vcd.T)
+        Xc = lr.colmajor_empty(nc, nc)
+        outc = (lr.colmajor_empty(nc, 64), torch.empty(64, dtype=torch.float64, device="cuda"),
+                lr.colmajor_empty(nc, 64))
+        row = {"n": nc}
+        for prec in ("mixed", "fp64"):
+            for kind, fn in (("full_grid", lambda: lr.lr_poisson2d_full(h, Fc, prec=prec, out=Xc)),
+                             ("lowrank", lambda: lr.lr_poisson2d(h, Ucd, Vcd, eps=EPS, prec=prec, out=outc))):
+                fn()
+                per = []
+                for i in range(3):
+                    flush.fill_(i & 0xFF)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    b.record(stream)
+                    stream.synchronize()
+                    per.append(a.elapsed_time(b))
+                row[f"{kind}_{prec}_ms"] = round(statistics.median(per), 4)
+        results["crossover"].append(row)
+        del Fc, Xc
+        torch.cuda.empty_cache()
     # ---- throughput: batches of independent solves, one CUDA graph per batch
     B = args.batch
     probs = [(torch.from_numpy(U) * (1.0 + p / B), torch.from_numpy(V)) for p in range(B)]
@@ -423,6 +454,7 @@ def main():
             "refine_rounds": res["tight_mixed"]["refine_rounds"],
             "rank": {"fp64": res["tight_fp64"]["rank"], "mixed": res["tight_mixed"]["rank"]},
             "rhs_rank": res["tight_fp64"]["r"]},
+        "crossover_full_grid_vs_lowrank": res["crossover"],
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2),

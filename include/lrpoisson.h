@@ -204,6 +204,19 @@ lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, 
  * last solve was not timed. */
 lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
 
+/* Full-grid solve of A X = F on the m x m grid (Section 4.1, Eq. flr:diag:
+ * X = S ((S F S) / Lambda) S, the fast Poisson solver the low-rank method is
+ * compared with; no truncation).  F and X are dense column-major float64
+ * device matrices (leading dimensions ldf, ldx >= m, 16-byte aligned; X may
+ * not alias F).  opt->prec picks the transforms' precision (LR_MIXED: float32
+ * transforms), opt->op the operator kind; eps, rmax and the cross options are
+ * ignored.  Work: four DST-I passes over m columns, two transposes, the
+ * division by Lambda fused into the third transform's input.  Workspace:
+ * about 2 m^2 + 2 M m working-precision words (M = next power of two >= 2m - 1)
+ * in the handle.  Synchronises. */
+lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double* X, int ldx,
+                            const lr_options* opt);
+
 /* Autotuning of the launch shapes (the paper has no counterpart; step T0's
  * tuned-configuration lookup and T7's tuned tiles and cluster sizes).
  *

@@ -46,6 +46,9 @@ struct lr_handle_s {
   // float64 buffers of iterative refinement (solution, correction, residual)
   void* ws2 = nullptr;
   size_t ws2_bytes = 0;
+  // workspace of full-grid solves (two m x m buffers and the transform scratch)
+  void* ws3 = nullptr;
+  size_t ws3_bytes = 0;
   // autotuned cluster sizes of single solves, keyed (m, precision, operator),
   // and indices per cross CTA of batched solves, per precision
   std::map<std::tuple<int, int, int>, int> tuned_cs;
@@ -620,6 +623,52 @@ lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   return worst;
 }
 
+// Full-grid solve X = S ((S F S) / Lambda) S (Eq. flr:diag) with column
+// transforms and transposes:
+//   W1 = S F;  W2 = W1^T;  W1 = S W2 = (S F S)^T;
+//   W2 = S (W1 / Lambda) = S Xh^T  (division fused into the transform input;
+//                                   Lambda is symmetric);
+//   W1 = W2^T = Xh S;  X = S W1.
+template <typename T>
+lr_status solve2d_full(lr_handle h, int m, const double* F, int ldf, double* X, int ldx, const lr_options& o,
+                       Plan* plan) {
+  const int ldw = round_up(m, 32);
+  const size_t M = (size_t)1 << plan->logM;
+  const size_t wbytes = align256(sizeof(T) * (size_t)ldw * m);
+  const size_t sbytes = M > (size_t)kSmallM ? align256(sizeof(cpx<T>) * M * (size_t)m) : 256;
+  const size_t need = 2 * wbytes + sbytes;
+  if (need > h->ws3_bytes) {
+    if (h->ws3) { cudaStreamSynchronize(h->stream); cudaFree(h->ws3); h->ws3 = nullptr; h->ws3_bytes = 0; }
+    if (cudaMalloc(&h->ws3, need) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "full-grid workspace"); }
+    h->ws3_bytes = need;
+  }
+  char* base = static_cast<char*>(h->ws3);
+  T* W1 = reinterpret_cast<T*>(base);
+  T* W2 = reinterpret_cast<T*>(base + wbytes);
+  void* scratch = base + 2 * wbytes;
+  cudaStream_t stm = h->stream;
+  const bool f32 = sizeof(T) == 4;
+  auto cols = [&](const void* in, int ldi, void* out, int ldo) {
+    ColumnSet cs;
+    cs.in[0] = in; cs.ld_in[0] = ldi; cs.out[0] = out; cs.ld_out[0] = ldo; cs.ncol[0] = m;
+    return cs;
+  };
+  ColumnSet c1 = cols(F, ldf, W1, ldw);
+  LR_CUDA(h, launch_dst<T>(*plan, c1, IoType::F64, IoType::WORK, scratch, h->num_sms, stm), "full: S F");
+  LR_CUDA(h, launch_transpose<T>(W1, ldw, m, m, W2, ldw, stm), "full: transpose");
+  ColumnSet c2 = cols(W2, ldw, W1, ldw);
+  LR_CUDA(h, launch_dst<T>(*plan, c2, IoType::WORK, IoType::WORK, scratch, h->num_sms, stm), "full: S F S");
+  ColumnSet c3 = cols(W1, ldw, W2, ldw);
+  c3.sym_a = f32 ? (const void*)plan->sym_a32[o.op] : (const void*)plan->sym_a64[o.op];
+  c3.sym_b = f32 ? (const void*)plan->sym_b32[o.op] : (const void*)plan->sym_b64[o.op];
+  LR_CUDA(h, launch_dst<T>(*plan, c3, IoType::DIV, IoType::WORK, scratch, h->num_sms, stm), "full: S Xh^T");
+  LR_CUDA(h, launch_transpose<T>(W2, ldw, m, m, W1, ldw, stm), "full: transpose");
+  ColumnSet c4 = cols(W1, ldw, X, ldx);
+  LR_CUDA(h, launch_dst<T>(*plan, c4, IoType::WORK, IoType::F64, scratch, h->num_sms, stm), "full: S Xh S");
+  LR_CUDA(h, cudaStreamSynchronize(stm), "full-grid solve");
+  return LR_OK;
+}
+
 constexpr int kBatchStreams = 32;
 
 lr_status ensure_batch_streams(lr_handle h) {
@@ -802,6 +851,7 @@ lr_status lr_destroy(lr_handle h) {
   h->plans.clear();
   if (h->ws) cudaFree(h->ws);
   if (h->ws2) cudaFree(h->ws2);
+  if (h->ws3) cudaFree(h->ws3);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_piv) cudaFreeHost(h->h_piv);
   if (h->h_w) cudaFreeHost(h->h_w);
@@ -833,6 +883,24 @@ lr_status lr_dst1(lr_handle h, int m, int ncols, const double* in, int ld_in, do
   if (e != cudaSuccess) return cuda_fail(h, e, "lr_dst1");
   LR_CUDA(h, cudaStreamSynchronize(h->stream), "lr_dst1");
   return LR_OK;
+}
+
+lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double* X, int ldx,
+                            const lr_options* opt) {
+  if (!h) return LR_EINVAL;
+  lr_options o;
+  if (opt) o = *opt; else lr_options_default(&o);
+  if (o.prec != LR_FP64 && o.prec != LR_MIXED) return fail(h, LR_EINVAL, "unknown precision");
+  if (o.op != LR_OP_5PT && o.op != LR_OP_SEMISTAGGERED) return fail(h, LR_EINVAL, "unknown operator");
+  if (m < 1 || m > 65536) return fail(h, LR_EINVAL, "m must be in [1, 65536]");
+  if (ldf < m || ldx < m) return fail(h, LR_EINVAL, "leading dimension smaller than m");
+  if (!F || !X || !aligned16(F) || !aligned16(X)) return fail(h, LR_EINVAL, "null or unaligned pointer");
+  if (F == X) return fail(h, LR_EINVAL, "X may not alias F");
+  Plan* plan = nullptr;
+  lr_status s = get_plan(h, m, &plan);
+  if (s != LR_OK) return s;
+  return o.prec == LR_MIXED ? solve2d_full<float>(h, m, F, ldf, X, ldx, o, plan)
+                            : solve2d_full<double>(h, m, F, ldf, X, ldx, o, plan);
 }
 
 lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt) {

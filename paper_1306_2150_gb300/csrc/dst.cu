@@ -136,9 +136,11 @@ struct ColArgs {
   const int* dyn_count;
   const void* tm[2];
   const int* k_dev;
+  const void* sym_a;
+  const void* sym_b;
 };
 
-enum : int { IN_F64 = 0, IN_WORK = 1, IN_ROT = 2 };
+enum : int { IN_F64 = 0, IN_WORK = 1, IN_ROT = 2, IN_DIV = 3 };
 
 __device__ __forceinline__ bool col_live(const ColArgs& c, int col, int& seg, int& cc) {
   seg = col < c.ncol[0] ? 0 : 1;
@@ -154,6 +156,11 @@ template <typename T, int INM>
 __device__ __forceinline__ T load_in(const ColArgs& c, int seg, int cc, int t) {
   if (INM == IN_F64) return (T)(static_cast<const double*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t]);
   if (INM == IN_WORK) return static_cast<const T*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t];
+  if (INM == IN_DIV) {
+    const T* a = static_cast<const T*>(c.sym_a);
+    const T* b = static_cast<const T*>(c.sym_b);
+    return static_cast<const T*>(c.in[seg])[(size_t)cc * c.ld_in[seg] + t] / (a[t] * b[cc] + b[t] * a[cc]);
+  }
   const T* X = static_cast<const T*>(c.in[seg]);
   const T* tm = static_cast<const T*>(c.tm[seg]) + (size_t)cc * KMAX;
   const int k = *c.k_dev;
@@ -640,6 +647,8 @@ cudaError_t launch_dst(const Plan& p, const ColumnSet& cs, IoType in_t, IoType o
   c.tm[0] = cs.tm[0];
   c.tm[1] = cs.tm[1];
   c.k_dev = cs.k_dev;
+  c.sym_a = cs.sym_a;
+  c.sym_b = cs.sym_b;
   GeomArgs g{p.m, p.logM, p.logM1, p.logM2, cs.ncol[0] + cs.ncol[1], 12};
   if (g.ncols == 0) return cudaSuccess;
   const bool o64 = out_t == IoType::F64;
@@ -650,12 +659,46 @@ cudaError_t launch_dst(const Plan& p, const ColumnSet& cs, IoType in_t, IoType o
     if (!o64) return cudaErrorInvalidValue;
     return launch_dst_t<T, IN_ROT, true>(p, c, g, work, num_sms, st);
   }
+  if (in_t == IoType::DIV) {
+    if (o64) return cudaErrorInvalidValue;
+    return launch_dst_t<T, IN_DIV, false>(p, c, g, work, num_sms, st);
+  }
   return o64 ? launch_dst_t<T, IN_WORK, true>(p, c, g, work, num_sms, st)
              : launch_dst_t<T, IN_WORK, false>(p, c, g, work, num_sms, st);
 }
 
 template cudaError_t launch_dst<double>(const Plan&, const ColumnSet&, IoType, IoType, void*, int, cudaStream_t);
 template cudaError_t launch_dst<float>(const Plan&, const ColumnSet&, IoType, IoType, void*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Tiled transpose (the full-grid solve transforms rows as columns of the
+// transpose): 32 x 32 tiles through shared memory, padded against bank
+// conflicts, coalesced on both sides.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_kernel(const T* __restrict__ in, int ldi, int m, int n,
+                                                        T* __restrict__ out, int ldo) {
+  __shared__ T tile[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int i = i0 + threadIdx.x, j = j0 + r;
+    if (i < m && j < n) tile[r][threadIdx.x] = in[i + (size_t)j * ldi];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int j = j0 + threadIdx.x, i = i0 + r;
+    if (i < m && j < n) out[j + (size_t)i * ldo] = tile[threadIdx.x][r];
+  }
+}
+
+template <typename T>
+cudaError_t launch_transpose(const T* in, int ldi, int m, int n, T* out, int ldo, cudaStream_t st) {
+  dim3 grid((m + 31) / 32, (n + 31) / 32), block(32, 8);
+  transpose_kernel<T><<<grid, block, 0, st>>>(in, ldi, m, n, out, ldo);
+  return cudaGetLastError();
+}
+template cudaError_t launch_transpose<float>(const float*, int, int, int, float*, int, cudaStream_t);
+template cudaError_t launch_transpose<double>(const double*, int, int, int, double*, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Plan tables (built once per order m on the host in float64, uploaded).

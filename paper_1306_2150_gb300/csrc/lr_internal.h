@@ -66,11 +66,16 @@ struct ColumnSet {
   // (working precision, k read from *k_dev on the device).
   const void* tm[2] = {nullptr, nullptr};
   const int* k_dev = nullptr;
+  // IoType::DIV input: element t of column q is in[s][t + q ld] / (a_t b_q + b_t a_q)
+  // (working-precision symbol tables a, b: the division by Lambda of Eq. flr:diag)
+  const void* sym_a = nullptr;
+  const void* sym_b = nullptr;
 };
 
 // Input/output kinds: caller float64 buffers, working-precision buffers, or
-// (input only) working-precision columns rotated on the fly.
-enum class IoType { F64, WORK, ROT };
+// (input only) working-precision columns rotated on the fly, or divided by
+// the symbol on the fly.
+enum class IoType { F64, WORK, ROT, DIV };
 
 // Launch the DST-I of every column of cs (forward and inverse are the same
 // orthonormal, symmetric S).  work: complex scratch of M * (ncol0 + ncol1)
@@ -140,6 +145,10 @@ template <typename TI, typename TO>
 cudaError_t launch_rotate(const TI* in, int ld_in, int rows, const int* k_dev, int k_host,
                           const void* Tm, bool tm_f32, const int* rank_dev, TO* out, int ld_out,
                           cudaStream_t st);
+
+// out[j + i ldo] = in[i + j ldi] for an m x n working-precision matrix.
+template <typename T>
+cudaError_t launch_transpose(const T* in, int ldi, int m, int n, T* out, int ldo, cudaStream_t st);
 
 // Iterative refinement helpers (float64): the residual F - A X as factors
 // [UF, -c P U s, -c Q U s], [VF, Q V, P V] (r + 2R columns, leading dim ldo).

@@ -33,7 +33,7 @@ OPERATORS = {"5pt": LR_OP_5PT, "semi": LR_OP_SEMISTAGGERED}
 EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
-           "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched")
+           "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full")
 
 
 class LrMat(ctypes.Structure):
@@ -119,6 +119,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_autotune.argtypes = [c_void_p, ctypes.POINTER(LrMat), ctypes.POINTER(LrOptions), c_int,
                                 ctypes.POINTER(LrTune)]
     lib.lr_autotune.restype = c_int
+    lib.lr_poisson2d_full.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
+                                      ctypes.POINTER(LrOptions)]
+    lib.lr_poisson2d_full.restype = c_int
     lib.lr_autotune_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                         ctypes.POINTER(LrOptions), c_int, ctypes.POINTER(LrTune)]
     lib.lr_autotune_batched.restype = c_int
@@ -417,3 +420,18 @@ def lr_autotune_batched(h: Handle, batch: Batch, eps: float = 1e-6, prec="mixed"
     if st != LR_OK:
         raise LrError(st, h.last_error())
     return t.as_dict()
+
+
+def lr_poisson2d_full(h: Handle, F, prec="mixed", op="5pt", out=None):
+    """Full-grid solve of A X = F (dense m x m, float64 on the device):
+    X = S ((S F S) / Lambda) S.  Returns X (column-major float64)."""
+    F = as_colmajor(F)
+    m = F.shape[0]
+    if F.shape != (m, m):
+        raise ValueError("F must be square")
+    X = colmajor_empty(m, m, F.device) if out is None else out
+    o = _options(1e-6, prec, op, 64, 1.0, 16, 0, 0, 0)
+    st = load().lr_poisson2d_full(h.ptr, m, F.data_ptr(), _ld(F), X.data_ptr(), _ld(X), ctypes.byref(o))
+    if st != LR_OK:
+        raise LrError(st, h.last_error())
+    return X

@@ -327,3 +327,36 @@ def test_cluster_transform_variant(lr, h, m, prec):
     assert O.rel_error_freq(Uo, s, Vo, U, V, "5pt", rows=rows) <= 10 * eps
     ref, Ur, sr, Vr = solve(lr, h, U, V, eps=eps, prec=prec)
     assert abs(len(s) - len(sr)) <= 1
+
+
+# ------------------------------------------------------------------ full-grid solver (crossover reference)
+@pytest.mark.parametrize("m", [1, 2, 3, 31, 256, 1000, 2049, 5000])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind", ["5pt", "semi"])
+def test_full_grid_matches_oracle(lr, h, m, prec, kind):
+    F = np.random.default_rng(m + 7).standard_normal((m, m))
+    X = npy(lr.lr_poisson2d_full(h, cuda(F), prec=prec, op=kind))
+    Xo = O.solve_full(F, kind)
+    err = np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
+    tol = 1e-13 * max(1.0, math.log2(m)) if prec == "fp64" else 3e-6
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_grid_agrees_with_lowrank_at_16384(lr, h, prec):
+    m = 16384
+    U, V = inputs.smooth_sum(m, 1e-12)
+    Ud, Vd = cuda(U), cuda(V)
+    F = torch.from_numpy(np.asfortranarray(U @ V.T)).T.cuda().T   # exact float64 product on the host
+    X = lr.lr_poisson2d_full(h, F, prec=prec)
+    del F
+    res = lr.lr_poisson2d(h, Ud, Vd, eps=1e-12, prec="fp64")
+    # whole sampled rows: the low-rank solution's error (<= 10 eps in the
+    # Frobenius norm) is not uniform over single entries (it is relatively
+    # largest in the corners, where X is smallest)
+    rows = np.unique(np.linspace(0, m - 1, 300).astype(np.int64))
+    Xs = npy(X[torch.from_numpy(rows).cuda()])
+    Ul, sl, Vl = npy(res.U), npy(res.s), npy(res.V)
+    Xl = (Ul[rows] * sl) @ Vl.T                # sampled rows of the low-rank solution, on the host
+    err = np.linalg.norm(Xs - Xl) / np.linalg.norm(Xl)
+    assert err <= (1e-10 if prec == "fp64" else 1e-5), err
