@@ -204,6 +204,32 @@ lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, 
  * last solve was not timed. */
 lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
 
+/* Low-rank Uzawa solve of the 2D Stokes problem on semi-staggered grids
+ * (Section 2: Eq. flr:stprob with A = I_2 (x) Delta, B = [B_x; B_y],
+ * B_x = G (x) H / (4h), B_y = H (x) G / (4h), h = 1/n; Section 5: the Uzawa
+ * iteration in low-rank format).  Conjugate gradients on the Schur equation
+ * (B^T A^-1 B) p = B^T A^-1 f (Eq. flr:schur) with every iterate in low-rank
+ * format: each Schur product applies B to the factors (bidiagonal maps, rank
+ * kept), runs the two velocity Poisson solves (semi-staggered kind, m = n - 1,
+ * batched, opt->prec) and rounds B^T of the result; every CG update is
+ * rounded in float64 at opt->eps; the CG scalars are float64.  The
+ * pressure's two kernel modes (constant, checkerboard) are projected out of
+ * p.  Stops when ||r|| <= tol_div ||B^T A^-1 f|| (r the Schur residual) or
+ * after maxit iterations (LR_ENOCONV, best iterate written).
+ *   d     : 2 (the only dimension built)
+ *   n     : cells per direction; velocity on the (n-1) x (n-1) interior
+ *           vertices, pressure on the n x n cell centres (first index x)
+ *   f     : 2 body-force components, (n-1) x (n-1), rank 1..64, s = NULL
+ *   g     : must be NULL (divergence-free)
+ *   u     : 2 velocity outputs (n-1) x (n-1), U, s, V capacity rmax
+ *   p     : pressure output n x n (U, s, V capacity rmax)
+ *   iters : CG iterations taken (may be NULL)
+ *   resid : ||B^T u|| / ||B^T A^-1 f|| of the returned velocity (may be NULL)
+ * LR_EINVAL for bad arguments, LR_ENOCONV if tol_div was not reached or a
+ * low-rank sum needed more than 64 columns.  Synchronises. */
+lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p,
+                          double tol_div, int maxit, const lr_options* opt, int* iters, double* resid);
+
 /* Full-grid solve of A X = F on the m x m grid (Section 4.1, Eq. flr:diag:
  * X = S ((S F S) / Lambda) S, the fast Poisson solver the low-rank method is
  * compared with; no truncation).  F and X are dense column-major float64

@@ -10,6 +10,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <initializer_list>
 #include <tuple>
 #include <vector>
 
@@ -49,6 +50,10 @@ struct lr_handle_s {
   // workspace of full-grid solves (two m x m buffers and the transform scratch)
   void* ws3 = nullptr;
   size_t ws3_bytes = 0;
+  // Stokes workspace and a pinned buffer for its Gram matrices
+  void* ws4 = nullptr;
+  size_t ws4_bytes = 0;
+  double* h_big = nullptr;
   // autotuned cluster sizes of single solves, keyed (m, precision, operator),
   // and indices per cross CTA of batched solves, per precision
   std::map<std::tuple<int, int, int>, int> tuned_cs;
@@ -419,7 +424,7 @@ constexpr int kQrSteps = 4;
 // Scratch: b.L, b.Rt, b.Lb, b.Rb, the small matrices and b.st.
 lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const double* Rin, int ldin, int m, int q,
                    const double* d, double eps, int rmax, double* U, double* V, double* s_out, int ldo, int fold,
-                   bool jacobi_fp32, int* K, double* sigma0) {
+                   bool jacobi_fp32, int* K, double* sigma0, double eps_abs = 0.0) {
   cudaStream_t stm = h->stream;
   const int ld = m + (m & 1);
   const double* Xl = Lin;
@@ -458,6 +463,7 @@ lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const do
   co.GC = b.Ra0; co.GR = b.Ra1; co.ldg = KMAX; co.d = d;
   co.k_dev = nullptr; co.k_host = q;
   co.eps = eps; co.rmax_out = rmax;
+  co.eps_abs = eps_abs;
   co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = s_out; co.st = b.st;
   co.tri_given = 1;
   LR_CUDA(h, launch_core<double>(co, jacobi_fp32, stm), "qr rounding core");
@@ -769,6 +775,407 @@ lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol
   return worst;
 }
 
+// ---------------------------------------------------------------------------
+// Low-rank Uzawa solve of the 2D Stokes problem on semi-staggered grids
+// (Section 2, Eq. flr:stprob and Eq. flr:schur; Section 5): conjugate
+// gradients on (B^T A^-1 B) p = B^T A^-1 f with every iterate in low-rank
+// format, every sum rounded in float64 at eps, the d = 2 velocity solves of a
+// Schur product batched, the CG scalars in float64.
+// ---------------------------------------------------------------------------
+struct LrDev {
+  double *U = nullptr, *s = nullptr, *V = nullptr;
+  int r = 0;
+};
+
+struct StokesCtx {
+  lr_handle h;
+  int n, ldp, ldv;
+  RefineBufs b;
+  LrDev P, R, D, Q, T;               // pressure-sized (n x KMAX), T: scratch result
+  double *RU[2], *RV[2];             // velocity right-hand sides ((n-1) x KMAX, weights folded)
+  double *WU[2], *Ws[2], *WV[2];     // velocity solutions
+  double *wts, *gm0, *gm1, *cs, *E;  // weights, cross Gram matrices, column sums, kernel modes
+  double* xpart;                     // cross Gram partials (32-row blocks)
+  double* hbuf;                      // pinned host: 2 KMAX^2 + 4 KMAX
+  Plan* plan;
+  lr_options oin;                    // inner solves
+  double eps;
+  int launches = 0;
+};
+
+void carve_stokes(Carve& c, StokesCtx& x) {
+  carve_refine(c, x.b, x.ldp, x.n);
+  const size_t cp = sizeof(double) * (size_t)x.ldp * KMAX, cv = sizeof(double) * (size_t)x.ldv * KMAX;
+  for (LrDev* d : {&x.P, &x.R, &x.D, &x.Q, &x.T}) {
+    d->U = c.take<double>(cp);
+    d->V = c.take<double>(cp);
+    d->s = c.take<double>(sizeof(double) * KMAX);
+  }
+  for (int k = 0; k < 2; ++k) {
+    x.RU[k] = c.take<double>(cv);
+    x.RV[k] = c.take<double>(cv);
+    x.WU[k] = c.take<double>(cv);
+    x.WV[k] = c.take<double>(cv);
+    x.Ws[k] = c.take<double>(sizeof(double) * KMAX);
+  }
+  x.wts = c.take<double>(sizeof(double) * 2 * KMAX);
+  x.gm0 = c.take<double>(sizeof(double) * KMAX * KMAX);
+  x.gm1 = c.take<double>(sizeof(double) * KMAX * KMAX);
+  x.cs = c.take<double>(sizeof(double) * 4 * KMAX);
+  x.E = c.take<double>(sizeof(double) * 2 * x.ldp);
+  x.xpart = c.take<double>(sizeof(double) * KMAX * KMAX * (size_t)((x.n + 31) / 32));
+}
+
+// A term U diag(coef s) V^T of a sum (s null: ones; U, V leading dim ld).
+struct Term {
+  const double* U;
+  const double* s;
+  const double* V;
+  int r, ld;
+  double coef;
+};
+
+// dst = round(sum of terms, eps), rows x rows matrices, dst orthonormal with
+// leading dimension ldo; abs_tol > 0 also allows an absolute dropped tail.
+lr_status sum_round(StokesCtx& x, int rows, std::initializer_list<Term> terms, LrDev& dst, int ldo,
+                    double abs_tol = 0.0) {
+  lr_handle h = x.h;
+  cudaStream_t stm = h->stream;
+  int q = 0;
+  std::vector<Term> tv(terms);
+  for (const Term& t : tv) q += t.r;
+  if (q == 0) { dst.r = 0; return LR_OK; }
+  if (q > KMAX) {
+    // Too wide for one rounding: drop the smallest weighted singular triplets
+    // (every term's weights are in descending order) until 64 columns remain.
+    std::vector<double> w(q);
+    int o2 = 0;
+    for (const Term& t : tv) {
+      if (t.s) LR_CUDA(h, cudaMemcpyAsync(x.hbuf + o2, t.s, sizeof(double) * t.r, cudaMemcpyDeviceToHost, stm), "copy");
+      o2 += t.r;
+    }
+    LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
+    o2 = 0;
+    std::vector<int> keep(tv.size());
+    for (size_t i = 0; i < tv.size(); ++i) {
+      keep[i] = tv[i].r;
+      for (int k = 0; k < tv[i].r; ++k) w[o2 + k] = std::fabs(tv[i].coef) * (tv[i].s ? x.hbuf[o2 + k] : 1.0);
+      o2 += tv[i].r;
+    }
+    while (q > KMAX) {
+      int best = -1;
+      double bw = 0.0;
+      o2 = 0;
+      for (size_t i = 0; i < tv.size(); ++i) {
+        if (keep[i] > 0 && (best < 0 || w[o2 + keep[i] - 1] < bw)) { best = (int)i; bw = w[o2 + keep[i] - 1]; }
+        o2 += tv[i].r;
+      }
+      --keep[best];
+      --q;
+    }
+    for (size_t i = 0; i < tv.size(); ++i) tv[i].r = keep[i];
+  }
+  int off = 0;
+  for (const Term& t : tv) {
+    if (t.r == 0) continue;
+    LR_CUDA(h, cudaMemcpy2DAsync(x.b.L + (size_t)off * x.ldp, sizeof(double) * x.ldp, t.U, sizeof(double) * t.ld,
+                                 sizeof(double) * rows, t.r, cudaMemcpyDeviceToDevice, stm), "stack");
+    LR_CUDA(h, cudaMemcpy2DAsync(x.b.Rt + (size_t)off * x.ldp, sizeof(double) * x.ldp, t.V, sizeof(double) * t.ld,
+                                 sizeof(double) * rows, t.r, cudaMemcpyDeviceToDevice, stm), "stack");
+    LR_CUDA(h, launch_scale_copy(t.r, t.s, t.coef, x.wts + off, stm), "weights");
+    off += t.r;
+  }
+  int K = 0;
+  double sig = 0.0;
+  lr_status s = qr_round(h, x.b, x.b.L, x.b.Rt, x.ldp, rows, q, x.wts, x.eps, KMAX, dst.U, dst.V, dst.s, ldo, 0,
+                         false, &K, &sig, abs_tol);
+  x.launches += 3 + kQrRoundLaunches;
+  if (s != LR_OK && s != LR_ENOCONV) return s;
+  dst.r = K;
+  return LR_OK;
+}
+
+// Squared Frobenius norm of an orthonormal-factor matrix (sum of s^2).
+lr_status norm2_of(StokesCtx& x, const LrDev& a, double* out) {
+  *out = 0.0;
+  if (a.r == 0) return LR_OK;
+  LR_CUDA(x.h, cudaMemcpyAsync(x.hbuf, a.s, sizeof(double) * a.r, cudaMemcpyDeviceToHost, x.h->stream), "copy");
+  LR_CUDA(x.h, cudaStreamSynchronize(x.h->stream), "sync");
+  for (int k = 0; k < a.r; ++k) *out += x.hbuf[k] * x.hbuf[k];
+  return LR_OK;
+}
+
+// <A, B> = sum_kl sa_k sb_l (Ua^T Ub)_kl (Va^T Vb)_kl, float64.
+lr_status inner(StokesCtx& x, int rows, const LrDev& a, const LrDev& b, double* out) {
+  *out = 0.0;
+  if (a.r == 0 || b.r == 0) return LR_OK;
+  cudaStream_t stm = x.h->stream;
+  LR_CUDA(x.h, launch_cross_gram(a.U, x.ldp, b.U, x.ldp, rows, a.r, b.r, x.gm0, x.xpart, stm), "gram");
+  LR_CUDA(x.h, launch_cross_gram(a.V, x.ldp, b.V, x.ldp, rows, a.r, b.r, x.gm1, x.xpart, stm), "gram");
+  x.launches += 4;
+  double* hg0 = x.hbuf;
+  double* hg1 = x.hbuf + KMAX * KMAX;
+  double* hsa = x.hbuf + 2 * KMAX * KMAX;
+  double* hsb = hsa + KMAX;
+  const size_t gb = sizeof(double) * a.r * b.r;
+  LR_CUDA(x.h, cudaMemcpyAsync(hg0, x.gm0, gb, cudaMemcpyDeviceToHost, stm), "copy");
+  LR_CUDA(x.h, cudaMemcpyAsync(hg1, x.gm1, gb, cudaMemcpyDeviceToHost, stm), "copy");
+  LR_CUDA(x.h, cudaMemcpyAsync(hsa, a.s, sizeof(double) * a.r, cudaMemcpyDeviceToHost, stm), "copy");
+  LR_CUDA(x.h, cudaMemcpyAsync(hsb, b.s, sizeof(double) * b.r, cudaMemcpyDeviceToHost, stm), "copy");
+  LR_CUDA(x.h, cudaStreamSynchronize(stm), "sync");
+  double acc = 0.0;
+  for (int l = 0; l < b.r; ++l)
+    for (int k = 0; k < a.r; ++k) acc += hsa[k] * hsb[l] * hg0[k + l * a.r] * hg1[k + l * a.r];
+  *out = acc;
+  return LR_OK;
+}
+
+// W = A^-1 (B_x X, B_y X) for a pressure X: the d = 2 velocity solves of a
+// Schur product, batched.  *rx, *ry: the ranks of the two solutions.
+lr_status velocity_solves(StokesCtx& x, const lr_mat* rhs, int* rx, int* ry) {
+  lr_handle h = x.h;
+  const int m = x.n - 1;
+  lr_mat sol[2];
+  for (int k = 0; k < 2; ++k) sol[k] = {m, m, 0, KMAX, x.ldv, x.WU[k], x.Ws[k], x.WV[k]};
+  std::vector<Plan*> plans(2, x.plan);
+  lr_status s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, sol, x.oin, plans, nullptr)
+                                       : solve2d_batched<double>(h, 2, rhs, sol, x.oin, plans, nullptr);
+  x.launches += h->info.launches;
+  if (s != LR_OK && s != LR_ENOCONV) return s;
+  *rx = sol[0].r;
+  *ry = sol[1].r;
+  return LR_OK;
+}
+
+lr_status grad_solve(StokesCtx& x, const LrDev& X, int* rx, int* ry) {
+  lr_handle h = x.h;
+  cudaStream_t stm = h->stream;
+  const int n = x.n, m = n - 1;
+  if (X.r == 0) { *rx = *ry = 0; return LR_OK; }
+  // The directions shrink with the residual: solve at unit scale (divide by
+  // sigma_0 of X, multiply the solutions back) so float32 solves stay far
+  // from the ends of their range.
+  LR_CUDA(h, cudaMemcpyAsync(x.hbuf, X.s, sizeof(double), cudaMemcpyDeviceToHost, stm), "copy");
+  LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
+  const double s0 = x.hbuf[0] > 0.0 ? x.hbuf[0] : 1.0;
+  const double c = n / 4.0 / s0;  // 1 / (4h), at unit scale
+  LR_CUDA(h, launch_gh(OP_G, n, X.U, x.ldp, X.r, X.s, c, x.RU[0], x.ldv, stm), "grad");
+  LR_CUDA(h, launch_gh(OP_H, n, X.V, x.ldp, X.r, nullptr, 1.0, x.RV[0], x.ldv, stm), "grad");
+  LR_CUDA(h, launch_gh(OP_H, n, X.U, x.ldp, X.r, X.s, c, x.RU[1], x.ldv, stm), "grad");
+  LR_CUDA(h, launch_gh(OP_G, n, X.V, x.ldp, X.r, nullptr, 1.0, x.RV[1], x.ldv, stm), "grad");
+  x.launches += 4;
+  lr_mat rhs[2];
+  for (int k = 0; k < 2; ++k) rhs[k] = {m, m, X.r, X.r, x.ldv, x.RU[k], nullptr, x.RV[k]};
+  lr_status s = velocity_solves(x, rhs, rx, ry);
+  if (s != LR_OK) return s;
+  LR_CUDA(h, launch_scale_copy(*rx, x.Ws[0], s0, x.Ws[0], stm), "rescale");
+  LR_CUDA(h, launch_scale_copy(*ry, x.Ws[1], s0, x.Ws[1], stm), "rescale");
+  x.launches += 2;
+  return LR_OK;
+}
+
+// dst = round(B^T W) for the velocity solutions of grad_solve (ranks rx, ry).
+lr_status div_round(StokesCtx& x, int rx, int ry, LrDev& dst, double abs_tol = 0.0) {
+  lr_handle h = x.h;
+  cudaStream_t stm = h->stream;
+  const int n = x.n;
+  const double c = n / 4.0;
+  if (rx + ry > KMAX) {
+    // Keep the 64 largest singular triplets of the pair (each solution's
+    // weights are in descending order): the Schur product becomes inexact by
+    // the dropped tail, which CG tolerates at that level.
+    LR_CUDA(h, cudaMemcpyAsync(x.hbuf, x.Ws[0], sizeof(double) * rx, cudaMemcpyDeviceToHost, stm), "copy");
+    LR_CUDA(h, cudaMemcpyAsync(x.hbuf + KMAX, x.Ws[1], sizeof(double) * ry, cudaMemcpyDeviceToHost, stm), "copy");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
+    while (rx + ry > KMAX) {
+      if (ry == 0 || (rx > 0 && x.hbuf[rx - 1] <= x.hbuf[KMAX + ry - 1])) --rx;
+      else --ry;
+    }
+  }
+  // stack [G^T Wx sx c, H^T Wy sy c] and [H^T Zx, G^T Zy] directly into the rounding input
+  LR_CUDA(h, launch_gh(OP_GT, n, x.WU[0], x.ldv, rx, x.Ws[0], c, x.b.L, x.ldp, stm), "div");
+  LR_CUDA(h, launch_gh(OP_HT, n, x.WV[0], x.ldv, rx, nullptr, 1.0, x.b.Rt, x.ldp, stm), "div");
+  LR_CUDA(h, launch_gh(OP_HT, n, x.WU[1], x.ldv, ry, x.Ws[1], c, x.b.L + (size_t)rx * x.ldp, x.ldp, stm), "div");
+  LR_CUDA(h, launch_gh(OP_GT, n, x.WV[1], x.ldv, ry, nullptr, 1.0, x.b.Rt + (size_t)rx * x.ldp, x.ldp, stm), "div");
+  x.launches += 4;
+  if (rx + ry == 0) { dst.r = 0; return LR_OK; }
+  int K = 0;
+  double sig = 0.0;
+  lr_status s = qr_round(h, x.b, x.b.L, x.b.Rt, x.ldp, n, rx + ry, nullptr, x.eps, KMAX, dst.U, dst.V, dst.s, x.ldp, 0,
+                         false, &K, &sig, abs_tol);
+  x.launches += kQrRoundLaunches;
+  if (s != LR_OK && s != LR_ENOCONV) return s;
+  dst.r = K;
+  return LR_OK;
+}
+
+lr_status copy_lr(StokesCtx& x, int rows, const LrDev& a, LrDev& dst) {
+  dst.r = a.r;
+  if (a.r == 0) return LR_OK;
+  cudaStream_t stm = x.h->stream;
+  const size_t bytes = sizeof(double) * (size_t)x.ldp * a.r;
+  (void)rows;
+  LR_CUDA(x.h, cudaMemcpyAsync(dst.U, a.U, bytes, cudaMemcpyDeviceToDevice, stm), "copy");
+  LR_CUDA(x.h, cudaMemcpyAsync(dst.V, a.V, bytes, cudaMemcpyDeviceToDevice, stm), "copy");
+  LR_CUDA(x.h, cudaMemcpyAsync(dst.s, a.s, sizeof(double) * a.r, cudaMemcpyDeviceToDevice, stm), "copy");
+  return LR_OK;
+}
+
+lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p, double tol, int maxit,
+                       const lr_options& o, int* iters, double* resid) {
+  StokesCtx x;
+  x.h = h;
+  x.n = n;
+  x.ldp = n + (n & 1);
+  x.ldv = (n - 1) + ((n - 1) & 1);
+  x.eps = o.eps;
+  x.oin = o;
+  x.oin.flags = 0;
+  x.oin.refine = -1;
+  x.oin.op = LR_OP_SEMISTAGGERED;
+  if (o.prec == LR_MIXED && x.oin.eps < 1e-7) x.oin.eps = 1e-7;  // float32 solves: no refinement inside CG
+  lr_status s = get_plan(h, n - 1, &x.plan);
+  if (s != LR_OK) return s;
+  Carve sizing;
+  carve_stokes(sizing, x);
+  if (sizing.off > h->ws4_bytes) {
+    if (h->ws4) { cudaStreamSynchronize(h->stream); cudaFree(h->ws4); h->ws4 = nullptr; h->ws4_bytes = 0; }
+    if (cudaMalloc(&h->ws4, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "Stokes workspace"); }
+    h->ws4_bytes = sizing.off;
+  }
+  if (!h->h_big && cudaMallocHost(&h->h_big, sizeof(double) * (2 * KMAX * KMAX + 4 * KMAX)) != cudaSuccess) {
+    cudaGetLastError();
+    h->h_big = nullptr;
+    return fail(h, LR_ENOMEM, "pinned buffer");
+  }
+  x.hbuf = h->h_big;
+  Carve cv;
+  cv.base = static_cast<char*>(h->ws4);
+  carve_stokes(cv, x);
+  cudaStream_t stm = h->stream;
+  // r0 = B^T A^-1 f
+  int rx = 0, ry = 0;
+  if ((s = velocity_solves(x, f, &rx, &ry)) != LR_OK) return s;
+  if ((s = div_round(x, rx, ry, x.R)) != LR_OK) return s;
+  double rr = 0.0;
+  if ((s = norm2_of(x, x.R, &rr)) != LR_OK) return s;
+  const double nr0 = std::sqrt(rr);
+  x.P.r = 0;
+  if ((s = copy_lr(x, n, x.R, x.D)) != LR_OK) return s;
+  int it = 0;
+  while (it < maxit && nr0 > 0.0 && std::sqrt(rr) > tol * nr0 && x.D.r > 0) {
+    // q = (B^T A^-1 B) d
+    if ((s = grad_solve(x, x.D, &rx, &ry)) != LR_OK) return s;
+    // q enters r - alpha q with alpha = O(1) (the Schur spectrum lies in
+    // (0, 1]): rounded to a tenth of the residual's absolute level
+    if ((s = div_round(x, rx, ry, x.Q, 0.1 * x.eps * nr0)) != LR_OK) return s;
+    double dq = 0.0;
+    if ((s = inner(x, n, x.D, x.Q, &dq)) != LR_OK) return s;
+    if (!(dq > 0.0)) break;  // d in the kernel (round-off): nothing left to gain
+    const double alpha = rr / dq;
+    // p <- p + alpha d, r <- r - alpha q, d <- r + beta d (each rounded at eps)
+    if ((s = sum_round(x, n, {{x.P.U, x.P.s, x.P.V, x.P.r, x.ldp, 1.0}, {x.D.U, x.D.s, x.D.V, x.D.r, x.ldp, alpha}},
+                       x.T, x.ldp)) != LR_OK) return s;
+    std::swap(x.P, x.T);
+    // The residual and the direction shrink by orders of magnitude while
+    // their terms do not: they are rounded to the absolute level eps ||r0||
+    // (relative rounding would keep ever more columns of cancellation noise).
+    if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, -alpha}},
+                       x.T, x.ldp, x.eps * nr0)) != LR_OK) return s;
+    std::swap(x.R, x.T);
+    double rr_new = 0.0;
+    if ((s = norm2_of(x, x.R, &rr_new)) != LR_OK) return s;
+    const double beta = rr_new / rr;
+    if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.D.U, x.D.s, x.D.V, x.D.r, x.ldp, beta}},
+                       x.T, x.ldp, x.eps * nr0)) != LR_OK) return s;
+    std::swap(x.D, x.T);
+    rr = rr_new;
+    ++it;
+  }
+  // Project the pressure's kernel modes (constant, checkerboard) out of p.
+  if (x.P.r > 0) {
+    LR_CUDA(h, launch_colsums(x.P.U, x.ldp, n, x.P.r, x.cs, stm), "colsums");
+    LR_CUDA(h, launch_colsums(x.P.V, x.ldp, n, x.P.r, x.cs + 2 * KMAX, stm), "colsums");
+    LR_CUDA(h, launch_kernel_modes(n, x.E, x.ldp, stm), "modes");
+    LR_CUDA(h, cudaMemcpyAsync(x.hbuf, x.cs, sizeof(double) * 4 * KMAX, cudaMemcpyDeviceToHost, stm), "copy");
+    LR_CUDA(h, cudaMemcpyAsync(x.hbuf + 4 * KMAX, x.P.s, sizeof(double) * x.P.r, cudaMemcpyDeviceToHost, stm), "copy");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
+    const int r = x.P.r;
+    const double* cu = x.hbuf;            // [sum U_k, sum (-1)^i U_k]
+    const double* cw = x.hbuf + 2 * KMAX; // the same for V
+    const double* sp = x.hbuf + 4 * KMAX;
+    double a = 0.0, b2 = 0.0;
+    for (int k = 0; k < r; ++k) {
+      a += sp[k] * cu[k] * cw[k];
+      b2 += sp[k] * cu[r + k] * cw[r + k];
+    }
+    a /= (double)n * n;
+    b2 /= (double)n * n;
+    if ((s = sum_round(x, n, {{x.P.U, x.P.s, x.P.V, x.P.r, x.ldp, 1.0}, {x.E, nullptr, x.E, 1, x.ldp, -a},
+                              {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -b2}}, x.T, x.ldp)) != LR_OK) return s;
+    std::swap(x.P, x.T);
+  }
+  // Velocity u = A^-1 (f - B p), the right-hand sides rounded first (f and
+  // B p cancel in part) with their weights folded into U.
+  lr_mat rhs[2];
+  const int m = n - 1;
+  const double c = n / 4.0;
+  for (int k = 0; k < 2; ++k) {
+    double* GU = x.b.FU;  // gradient factors of this component (scratch)
+    double* GV = x.b.FV;
+    LR_CUDA(h, launch_gh(k == 0 ? OP_G : OP_H, n, x.P.U, x.ldp, x.P.r, x.P.s, c, GU, x.ldv, stm), "grad");
+    LR_CUDA(h, launch_gh(k == 0 ? OP_H : OP_G, n, x.P.V, x.ldp, x.P.r, nullptr, 1.0, GV, x.ldv, stm), "grad");
+    LrDev out{x.RU[k], x.T.s, x.RV[k], 0};
+    if ((s = sum_round(x, m, {{f[k].U, nullptr, f[k].V, f[k].r, f[k].ld, 1.0}, {GU, nullptr, GV, x.P.r, x.ldv, -1.0}},
+                       out, x.ldv)) != LR_OK) return s;
+    rhs[k] = {m, m, out.r, out.r, x.ldv, x.RU[k], nullptr, x.RV[k]};
+    if (out.r == 0) {  // f = B p: a zero column, whose solve is rank 0
+      LR_CUDA(h, cudaMemsetAsync(x.RU[k], 0, sizeof(double) * m, stm), "zero");
+      LR_CUDA(h, cudaMemsetAsync(x.RV[k], 0, sizeof(double) * m, stm), "zero");
+      rhs[k].r = rhs[k].rmax = 1;
+    } else {
+      LR_CUDA(h, launch_fold_weights(m, KMAX, &x.b.st->rank, x.RU[k], x.ldv, x.T.s, false, stm), "fold");
+    }
+  }
+  // the solutions go straight into the caller's buffers
+  lr_options of = x.oin;
+  std::vector<Plan*> plans(2, x.plan);
+  s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, u, of, plans, nullptr)
+                             : solve2d_batched<double>(h, 2, rhs, u, of, plans, nullptr);
+  if (s != LR_OK && s != LR_ENOCONV) return s;
+  // divergence of the final velocity, relative to ||B^T A^-1 f||
+  for (int k = 0; k < 2; ++k) {
+    LR_CUDA(h, cudaMemcpy2DAsync(x.WU[k], sizeof(double) * x.ldv, u[k].U, sizeof(double) * u[k].ld,
+                                 sizeof(double) * m, u[k].r, cudaMemcpyDeviceToDevice, stm), "copy");
+    LR_CUDA(h, cudaMemcpy2DAsync(x.WV[k], sizeof(double) * x.ldv, u[k].V, sizeof(double) * u[k].ld,
+                                 sizeof(double) * m, u[k].r, cudaMemcpyDeviceToDevice, stm), "copy");
+    LR_CUDA(h, cudaMemcpyAsync(x.Ws[k], u[k].s, sizeof(double) * u[k].r, cudaMemcpyDeviceToDevice, stm), "copy");
+  }
+  if ((s = div_round(x, u[0].r, u[1].r, x.T)) != LR_OK) return s;
+  double dv = 0.0;
+  if ((s = norm2_of(x, x.T, &dv)) != LR_OK) return s;
+  // pressure out
+  if (x.P.r > p->rmax) return fail(h, LR_ENOCONV, "pressure rank exceeds p->rmax");
+  if (x.P.r > 0) {
+    LR_CUDA(h, cudaMemcpy2DAsync(p->U, sizeof(double) * p->ld, x.P.U, sizeof(double) * x.ldp, sizeof(double) * n,
+                                 x.P.r, cudaMemcpyDeviceToDevice, stm), "copy");
+    LR_CUDA(h, cudaMemcpy2DAsync(p->V, sizeof(double) * p->ld, x.P.V, sizeof(double) * x.ldp, sizeof(double) * n,
+                                 x.P.r, cudaMemcpyDeviceToDevice, stm), "copy");
+    LR_CUDA(h, cudaMemcpyAsync(p->s, x.P.s, sizeof(double) * x.P.r, cudaMemcpyDeviceToDevice, stm), "copy");
+  }
+  LR_CUDA(h, cudaStreamSynchronize(stm), "Stokes");
+  p->r = x.P.r;
+  if (iters) *iters = it;
+  const double res = nr0 > 0.0 ? std::sqrt(dv) / nr0 : 0.0;
+  if (resid) *resid = res;
+  h->info = lr_info{};
+  h->info.launches = x.launches;
+  h->info.rank = x.P.r;
+  if (!(std::sqrt(rr) <= tol * nr0) && nr0 > 0.0)
+    return fail(h, LR_ENOCONV, "Uzawa did not reach tol_div within maxit");
+  return LR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -852,6 +1259,8 @@ lr_status lr_destroy(lr_handle h) {
   if (h->ws) cudaFree(h->ws);
   if (h->ws2) cudaFree(h->ws2);
   if (h->ws3) cudaFree(h->ws3);
+  if (h->ws4) cudaFree(h->ws4);
+  if (h->h_big) cudaFreeHost(h->h_big);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_piv) cudaFreeHost(h->h_piv);
   if (h->h_w) cudaFreeHost(h->h_w);
@@ -957,6 +1366,30 @@ lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat
 
 // Autotuning: time candidate launch shapes on the caller's problem (CUDA
 // events on the handle's stream, median of reps after a warm-up).
+lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p,
+                          double tol_div, int maxit, const lr_options* opt, int* iters, double* resid) {
+  if (!h) return LR_EINVAL;
+  lr_options o;
+  if (opt) o = *opt; else lr_options_default(&o);
+  lr_status s = check_opts(h, o);
+  if (s != LR_OK) return s;
+  if (d != 2) return fail(h, LR_EINVAL, "lr_stokes_uzawa: only d = 2 is built");
+  if (g) return fail(h, LR_EINVAL, "lr_stokes_uzawa: g must be NULL (divergence-free constraint)");
+  if (n < 3 || n > 32768) return fail(h, LR_EINVAL, "lr_stokes_uzawa: n must be in [3, 32768]");
+  if (!f || !u || !p) return fail(h, LR_EINVAL, "lr_stokes_uzawa: null f, u or p");
+  if (!(tol_div > 0.0) || tol_div >= 1.0 || maxit < 1) return fail(h, LR_EINVAL, "lr_stokes_uzawa: bad tol_div or maxit");
+  const int m = n - 1;
+  for (int k = 0; k < 2; ++k) {
+    if (f[k].n1 != m || f[k].n2 != m || u[k].n1 != m || u[k].n2 != m)
+      return fail(h, LR_EINVAL, "lr_stokes_uzawa: f and u components must be (n-1) x (n-1)");
+    if ((s = check_problem(h, &f[k], &u[k])) != LR_OK) return s;
+  }
+  if (p->n1 != n || p->n2 != n || p->ld < n || p->rmax < 1 || !p->U || !p->V || !p->s ||
+      !aligned16(p->U) || !aligned16(p->V) || !aligned16(p->s))
+    return fail(h, LR_EINVAL, "lr_stokes_uzawa: p must be n x n with U, s, V set and aligned");
+  return stokes_uzawa(h, n, f, u, p, tol_div, maxit, o, iters, resid);
+}
+
 lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int reps, lr_tune* out) {
   if (!h) return LR_EINVAL;
   lr_options o;

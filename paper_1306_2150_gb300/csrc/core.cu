@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
       K = 0;
       if (S.sig[S.perm[k - 1]] < 0.0) A.st->status = LR_ENONFINITE;
     } else {
-      const double lim = A.eps * sqrt(total);
+      const double lim = fmax(A.eps * sqrt(total), A.eps_abs);
       double tail2 = 0.0;
       K = k;
       for (int p = k - 1; p >= 1; --p) {

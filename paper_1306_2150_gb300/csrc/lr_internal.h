@@ -130,6 +130,8 @@ struct CoreArgs {
   T* Tr;
   double* s_out;    // R singular values
   SolveState* st;
+  double eps_abs = 0.0; // if > 0: also drop singular values while the dropped
+                        // tail stays within eps_abs (absolute)
   int tri_given = 0; // 1: GC, GR are upper-triangular QR factors (column-major,
                      // ldg), d may be null (ones); T = W_K, Z_K directly
 };
@@ -145,6 +147,17 @@ template <typename TI, typename TO>
 cudaError_t launch_rotate(const TI* in, int ld_in, int rows, const int* k_dev, int k_host,
                           const void* Tm, bool tm_f32, const int* rank_dev, TO* out, int ld_out,
                           cudaStream_t st);
+
+// Stokes (Section 2): bidiagonal maps of factor columns, cross Gram matrices,
+// column sums against the pressure's kernel modes.
+enum : int { OP_G = 0, OP_H = 1, OP_GT = 2, OP_HT = 3 };
+cudaError_t launch_gh(int op, int n, const double* in, int ldi, int r, const double* w, double scale,
+                      double* out, int ldo, cudaStream_t st);
+cudaError_t launch_cross_gram(const double* X, int ldx, const double* Y, int ldy, int rows, int kx, int ky,
+                              double* C, double* partial, cudaStream_t st);
+cudaError_t launch_colsums(const double* X, int ld, int rows, int r, double* out, cudaStream_t st);
+cudaError_t launch_kernel_modes(int rows, double* e, int ld, cudaStream_t st);
+cudaError_t launch_scale_copy(int n, const double* src, double coef, double* dst, cudaStream_t st);
 
 // out[j + i ldo] = in[i + j ldi] for an m x n working-precision matrix.
 template <typename T>

@@ -33,7 +33,8 @@ OPERATORS = {"5pt": LR_OP_5PT, "semi": LR_OP_SEMISTAGGERED}
 EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
-           "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full")
+           "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full",
+           "lr_stokes_uzawa")
 
 
 class LrMat(ctypes.Structure):
@@ -122,6 +123,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_poisson2d_full.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                       ctypes.POINTER(LrOptions)]
     lib.lr_poisson2d_full.restype = c_int
+    lib.lr_stokes_uzawa.argtypes = [c_void_p, c_int, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
+                                    ctypes.POINTER(LrMat), ctypes.POINTER(LrMat), c_double, c_int,
+                                    ctypes.POINTER(LrOptions), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]
+    lib.lr_stokes_uzawa.restype = c_int
     lib.lr_autotune_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                         ctypes.POINTER(LrOptions), c_int, ctypes.POINTER(LrTune)]
     lib.lr_autotune_batched.restype = c_int
@@ -435,3 +440,50 @@ def lr_poisson2d_full(h: Handle, F, prec="mixed", op="5pt", out=None):
     if st != LR_OK:
         raise LrError(st, h.last_error())
     return X
+
+
+@dataclass
+class StokesResult:
+    u: list          # [(U, s, V) for the x and y velocity components]
+    p: tuple         # (U, s, V) of the pressure
+    iters: int
+    resid: float
+    status: int
+
+
+def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 200, eps: float = 1e-7,
+                    prec="mixed", rmax_out: int = 64, check: bool = True) -> StokesResult:
+    """Low-rank Uzawa solve of the 2D Stokes problem on n x n cells; ``f`` is
+    [(U1, V1), (U2, V2)], the body-force components at the (n-1)^2 interior
+    vertices in factored form (device float64)."""
+    import torch
+    m = n - 1
+    c_f = (LrMat * 2)()
+    c_u = (LrMat * 2)()
+    keep, outs = [], []
+    for k, (U, V) in enumerate(f):
+        U = as_colmajor(U)
+        V = as_colmajor(V)
+        if U.stride(1) != V.stride(1):
+            V2 = colmajor_empty(V.shape[0], V.shape[1], V.device)
+            V2.copy_(V)
+            V = V2
+        keep += [U, V]
+        c_f[k] = LrMat(m, m, U.shape[1], U.shape[1], _ld(U), U.data_ptr(), None, V.data_ptr())
+        Uo, Vo = colmajor_empty(m, rmax_out, U.device), colmajor_empty(m, rmax_out, U.device)
+        so = torch.empty(rmax_out, dtype=torch.float64, device=U.device)
+        outs.append((Uo, so, Vo))
+        c_u[k] = LrMat(m, m, 0, rmax_out, _ld(Uo), Uo.data_ptr(), so.data_ptr(), Vo.data_ptr())
+    dev = keep[0].device
+    Up, Vp = colmajor_empty(n, rmax_out, dev), colmajor_empty(n, rmax_out, dev)
+    sp = torch.empty(rmax_out, dtype=torch.float64, device=dev)
+    c_p = LrMat(n, n, 0, rmax_out, _ld(Up), Up.data_ptr(), sp.data_ptr(), Vp.data_ptr())
+    o = _options(eps, prec, "semi", 64, 1.0, 16, 0, 0, 0)
+    iters = ctypes.c_int(0)
+    resid = ctypes.c_double(0.0)
+    st = load().lr_stokes_uzawa(h.ptr, 2, n, c_f, None, c_u, ctypes.byref(c_p), float(tol_div), int(maxit),
+                                ctypes.byref(o), ctypes.byref(iters), ctypes.byref(resid))
+    if check and st not in (LR_OK, LR_ENOCONV):
+        raise LrError(st, h.last_error())
+    u = [(Uo[:, :c_u[k].r], so[:c_u[k].r], Vo[:, :c_u[k].r]) for k, (Uo, so, Vo) in enumerate(outs)]
+    return StokesResult(u, (Up[:, :c_p.r], sp[:c_p.r], Vp[:, :c_p.r]), iters.value, resid.value, st)

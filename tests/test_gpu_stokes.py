@@ -1,0 +1,74 @@
+"""Low-rank Uzawa Stokes solve (Section 2, Section 5) through the C ABI
+against the full-format oracle (oracle/stokes.py)."""
+import numpy as np
+import pytest
+
+from oracle import stokes as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    from paper_1306_2150_gb300 import build, lr as lrmod
+    build.build()
+    lrmod.load()
+    return lrmod
+
+
+@pytest.fixture(scope="module")
+def h(lr):
+    handle = lr.Handle()
+    yield handle
+    handle.close()
+
+
+def dense(t):
+    U, s, V = (x.detach().cpu().numpy() for x in t)
+    return (U * s) @ V.T
+
+
+def body_force_dev(n):
+    (a1, b1), (a2, b2) = S.body_force(n)
+    return [(torch.from_numpy(a1).cuda(), torch.from_numpy(b1).cuda()),
+            (torch.from_numpy(a2).cuda(), torch.from_numpy(b2).cuda())], (a1 @ b1.T, a2 @ b2.T)
+
+
+@pytest.mark.parametrize("n", [16, 64, 256])
+@pytest.mark.parametrize("prec,eps,tol,acc", [("fp64", 1e-10, 1e-9, 1e-7), ("mixed", 1e-7, 1e-6, 2e-5)])
+def test_stokes_matches_oracle(lr, h, n, prec, eps, tol, acc):
+    fdev, (f1, f2) = body_force_dev(n)
+    res = lr.lr_stokes_uzawa(h, n, fdev, tol_div=tol, eps=eps, prec=prec)
+    assert res.status == lr.LR_OK, h.last_error()
+    ref = S.uzawa_cg(f1, f2, n, tol=1e-13)
+    u, v, p = dense(res.u[0]), dense(res.u[1]), dense(res.p)
+    for a, b in ((u, ref.u), (v, ref.v), (p, ref.p)):
+        assert np.linalg.norm(a - b) <= acc * np.linalg.norm(b), (np.linalg.norm(a - b) / np.linalg.norm(b))
+    # divergence of the returned velocity, recomputed by the oracle: the CG
+    # stops on the Schur residual (tol); the velocity's own rounding at eps
+    # adds up to about n eps through B^T (a difference over h)
+    div = np.linalg.norm(S.bt(u, v, n)) / np.linalg.norm(S.bt(S.laplace_solve(f1, n), S.laplace_solve(f2, n), n))
+    bound = 5 * tol + 2 * n * eps
+    assert div <= bound and res.resid <= bound, (div, res.resid)
+    # the pressure has no kernel component
+    for K in S.kernel_modes(n):
+        assert abs(np.sum(p * K)) <= 1e-8 * np.linalg.norm(p)
+
+
+def test_stokes_iterations_independent_of_h(lr, h):
+    its = []
+    for n in (64, 256, 1024):
+        fdev, _ = body_force_dev(n)
+        res = lr.lr_stokes_uzawa(h, n, fdev, tol_div=1e-6, eps=1e-8, prec="fp64")
+        assert res.status == lr.LR_OK
+        its.append(res.iters)
+    assert max(its) <= min(its) + 6, its
+
+
+def test_stokes_rejects_bad_arguments(lr, h):
+    import ctypes
+    fdev, _ = body_force_dev(16)
+    o = lr._options(1e-7, "fp64", "semi", 64, 1.0, 16, 0, 0, 0)
+    st = lr.load().lr_stokes_uzawa(h.ptr, 3, 16, None, None, None, None, 1e-6, 10, ctypes.byref(o), None, None)
+    assert st == lr.LR_EINVAL
