@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--crossover", type=int, nargs="*", default=[256, 1024, 4096, 16384],
                    help="grid sizes of the full-grid vs low-rank comparison")
+    p.add_argument("--stokes", type=int, nargs="*", default=[1024, 4096, 8192],
+                   help="cells per direction of the low-rank Uzawa Stokes runs")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -306,6 +308,28 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         results["crossover"].append(row)
         del Fc, Xc
         torch.cuda.empty_cache()
+    # ---- low-rank Uzawa Stokes (semi-staggered grids, body force of rank 1
+    # per component, truncation eps = 1e-7, stop at the Schur residual 1e-6)
+    results["stokes"] = []
+    for ns in args.stokes:
+        x = np.arange(1, ns) / ns
+        fs = [(torch.from_numpy(np.sin(np.pi * x)[:, None]).cuda(), torch.from_numpy(np.cos(np.pi * x)[:, None]).cuda()),
+              (torch.from_numpy(-np.cos(np.pi * x)[:, None]).cuda(),
+               torch.from_numpy((np.sin(np.pi * x) * (1.0 + x))[:, None]).cuda())]
+        row = {"n": ns}
+        for prec in ("mixed", "fp64"):
+            lr.lr_stokes_uzawa(h, ns, fs, tol_div=1e-6, eps=1e-7, prec=prec, check=False)  # warm-up
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            flush.fill_(1)
+            a.record(stream)
+            rs = lr.lr_stokes_uzawa(h, ns, fs, tol_div=1e-6, eps=1e-7, prec=prec, check=False)
+            b.record(stream)
+            stream.synchronize()
+            row[prec] = {"ms": round(a.elapsed_time(b), 3), "iters": rs.iters, "status": rs.status,
+                         "velocity_divergence": rs.resid, "pressure_rank": int(rs.p[1].shape[0]),
+                         "velocity_ranks": [int(c[1].shape[0]) for c in rs.u]}
+        results["stokes"].append(row)
     # ---- throughput: batches of independent solves, one CUDA graph per batch
     B = args.batch
     probs = [(torch.from_numpy(U) * (1.0 + p / B), torch.from_numpy(V)) for p in range(B)]
@@ -455,6 +479,7 @@ def main():
             "rank": {"fp64": res["tight_fp64"]["rank"], "mixed": res["tight_mixed"]["rank"]},
             "rhs_rank": res["tight_fp64"]["r"]},
         "crossover_full_grid_vs_lowrank": res["crossover"],
+        "stokes_uzawa_lowrank": res["stokes"],
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2),

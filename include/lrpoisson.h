@@ -138,7 +138,9 @@ typedef struct {
   int launches;          /* kernels launched by the solve */
   double norm_est;       /* cross estimate of ||Xh||_F */
   double sigma0;         /* largest singular value kept */
-  int refine_rounds;     /* refinement rounds taken (LR_MIXED, eps < 1e-7) */
+  int refine_rounds;     /* refinement rounds taken (LR_MIXED, eps < 1e-7);
+                            after lr_stokes_uzawa: mixed velocity solves that
+                            broke down in float32 and were repeated in float64 */
   int pad;
   double refine_corr;    /* sigma_0 of the last correction / sigma_0 of X */
 } lr_info;

@@ -801,6 +801,7 @@ struct StokesCtx {
   lr_options oin;                    // inner solves
   double eps;
   int launches = 0;
+  int escalations = 0;               // mixed velocity solves repeated in float64
 };
 
 void carve_stokes(Carve& c, StokesCtx& x) {
@@ -938,9 +939,23 @@ lr_status velocity_solves(StokesCtx& x, const lr_mat* rhs, int* rx, int* ry) {
   lr_mat sol[2];
   for (int k = 0; k < 2; ++k) sol[k] = {m, m, 0, KMAX, x.ldv, x.WU[k], x.Ws[k], x.WV[k]};
   std::vector<Plan*> plans(2, x.plan);
-  lr_status s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, sol, x.oin, plans, nullptr)
-                                       : solve2d_batched<double>(h, 2, rhs, sol, x.oin, plans, nullptr);
+  lr_status per[2] = {LR_OK, LR_OK};
+  lr_status s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, sol, x.oin, plans, per)
+                                       : solve2d_batched<double>(h, 2, rhs, sol, x.oin, plans, per);
   x.launches += h->info.launches;
+  if (s == LR_ENONFINITE && x.oin.prec == LR_MIXED) {
+    // A float32 solve broke down (noise-level pivots on a direction whose
+    // solution float32 cannot resolve): solve that problem again in float64.
+    s = LR_OK;
+    for (int k = 0; k < 2; ++k) {
+      if (per[k] != LR_ENONFINITE) continue;
+      lr_options o64 = x.oin;
+      o64.prec = LR_FP64;
+      const lr_status s2 = solve2d<double>(h, &rhs[k], &sol[k], o64, x.plan);
+      if (s2 != LR_OK && s2 != LR_ENOCONV) return s2;
+      ++x.escalations;
+    }
+  }
   if (s != LR_OK && s != LR_ENOCONV) return s;
   *rx = sol[0].r;
   *ry = sol[1].r;
@@ -1021,6 +1036,32 @@ lr_status copy_lr(StokesCtx& x, int rows, const LrDev& a, LrDev& dst) {
   return LR_OK;
 }
 
+// coef * <X, 1 1^T> / n^2 and coef * <X, c c^T> / n^2 (c = (-1)^i): the
+// weights of the two kernel modes (as the columns 1 and c of x.E) in X.
+lr_status kernel_coeffs(StokesCtx& x, const LrDev& X, double coef, double* a, double* b) {
+  *a = *b = 0.0;
+  if (X.r == 0) return LR_OK;
+  lr_handle h = x.h;
+  cudaStream_t stm = h->stream;
+  const int n = x.n, r = X.r;
+  LR_CUDA(h, launch_colsums(X.U, x.ldp, n, r, x.cs, stm), "colsums");
+  LR_CUDA(h, launch_colsums(X.V, x.ldp, n, r, x.cs + 2 * KMAX, stm), "colsums");
+  LR_CUDA(h, cudaMemcpyAsync(x.hbuf, x.cs, sizeof(double) * 4 * KMAX, cudaMemcpyDeviceToHost, stm), "copy");
+  LR_CUDA(h, cudaMemcpyAsync(x.hbuf + 4 * KMAX, X.s, sizeof(double) * r, cudaMemcpyDeviceToHost, stm), "copy");
+  LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
+  x.launches += 2;
+  const double* cu = x.hbuf;             // [sum U_k, sum (-1)^i U_k]
+  const double* cw = x.hbuf + 2 * KMAX;  // the same for V
+  const double* sp = x.hbuf + 4 * KMAX;
+  for (int k = 0; k < r; ++k) {
+    *a += sp[k] * cu[k] * cw[k];
+    *b += sp[k] * cu[r + k] * cw[r + k];
+  }
+  *a *= coef / ((double)n * n);
+  *b *= coef / ((double)n * n);
+  return LR_OK;
+}
+
 lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p, double tol, int maxit,
                        const lr_options& o, int* iters, double* resid) {
   StokesCtx x;
@@ -1033,7 +1074,9 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   x.oin.flags = 0;
   x.oin.refine = -1;
   x.oin.op = LR_OP_SEMISTAGGERED;
-  if (o.prec == LR_MIXED && x.oin.eps < 1e-7) x.oin.eps = 1e-7;  // float32 solves: no refinement inside CG
+  // float32 solves: at 1e-7 the float32 cross sits on its own rounding noise
+  // and does not converge, so the inner solves run at 1e-6 at least
+  if (o.prec == LR_MIXED && x.oin.eps < 1e-6) x.oin.eps = 1e-6;
   lr_status s = get_plan(h, n - 1, &x.plan);
   if (s != LR_OK) return s;
   Carve sizing;
@@ -1053,6 +1096,7 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   cv.base = static_cast<char*>(h->ws4);
   carve_stokes(cv, x);
   cudaStream_t stm = h->stream;
+  LR_CUDA(h, launch_kernel_modes(n, x.E, x.ldp, stm), "modes");
   // r0 = B^T A^-1 f
   int rx = 0, ry = 0;
   if ((s = velocity_solves(x, f, &rx, &ry)) != LR_OK) return s;
@@ -1080,7 +1124,19 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
     // The residual and the direction shrink by orders of magnitude while
     // their terms do not: they are rounded to the absolute level eps ||r0||
     // (relative rounding would keep ever more columns of cancellation noise).
-    if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, -alpha}},
+    // The new residual also loses its components along the pressure's kernel
+    // modes (round-off of the truncations would otherwise accumulate there
+    // and stall CG): r - alpha q - a 1 1^T - b c c^T.
+    double ka = 0.0, kb = 0.0;
+    if ((s = kernel_coeffs(x, x.R, 1.0, &ka, &kb)) != LR_OK) return s;
+    {
+      double qa = 0.0, qb = 0.0;
+      if ((s = kernel_coeffs(x, x.Q, -alpha, &qa, &qb)) != LR_OK) return s;
+      ka += qa;
+      kb += qb;
+    }
+    if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, -alpha},
+                              {x.E, nullptr, x.E, 1, x.ldp, -ka}, {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -kb}},
                        x.T, x.ldp, x.eps * nr0)) != LR_OK) return s;
     std::swap(x.R, x.T);
     double rr_new = 0.0;
@@ -1094,23 +1150,8 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   }
   // Project the pressure's kernel modes (constant, checkerboard) out of p.
   if (x.P.r > 0) {
-    LR_CUDA(h, launch_colsums(x.P.U, x.ldp, n, x.P.r, x.cs, stm), "colsums");
-    LR_CUDA(h, launch_colsums(x.P.V, x.ldp, n, x.P.r, x.cs + 2 * KMAX, stm), "colsums");
-    LR_CUDA(h, launch_kernel_modes(n, x.E, x.ldp, stm), "modes");
-    LR_CUDA(h, cudaMemcpyAsync(x.hbuf, x.cs, sizeof(double) * 4 * KMAX, cudaMemcpyDeviceToHost, stm), "copy");
-    LR_CUDA(h, cudaMemcpyAsync(x.hbuf + 4 * KMAX, x.P.s, sizeof(double) * x.P.r, cudaMemcpyDeviceToHost, stm), "copy");
-    LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
-    const int r = x.P.r;
-    const double* cu = x.hbuf;            // [sum U_k, sum (-1)^i U_k]
-    const double* cw = x.hbuf + 2 * KMAX; // the same for V
-    const double* sp = x.hbuf + 4 * KMAX;
     double a = 0.0, b2 = 0.0;
-    for (int k = 0; k < r; ++k) {
-      a += sp[k] * cu[k] * cw[k];
-      b2 += sp[k] * cu[r + k] * cw[r + k];
-    }
-    a /= (double)n * n;
-    b2 /= (double)n * n;
+    if ((s = kernel_coeffs(x, x.P, 1.0, &a, &b2)) != LR_OK) return s;
     if ((s = sum_round(x, n, {{x.P.U, x.P.s, x.P.V, x.P.r, x.ldp, 1.0}, {x.E, nullptr, x.E, 1, x.ldp, -a},
                               {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -b2}}, x.T, x.ldp)) != LR_OK) return s;
     std::swap(x.P, x.T);
@@ -1171,6 +1212,7 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   h->info = lr_info{};
   h->info.launches = x.launches;
   h->info.rank = x.P.r;
+  h->info.refine_rounds = x.escalations;  // reused: velocity solves escalated to float64
   if (!(std::sqrt(rr) <= tol * nr0) && nr0 > 0.0)
     return fail(h, LR_ENOCONV, "Uzawa did not reach tol_div within maxit");
   return LR_OK;

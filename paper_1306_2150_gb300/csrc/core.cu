@@ -39,6 +39,8 @@ struct CoreSmem {
   double scrA[sizeof(JT) == 8 ? KMAX * KP : 1];
   double scrB[sizeof(JT) == 8 ? KMAX * KP : 1];
   double amax;
+  double scale;  // power of two applied to M before the Jacobi iteration
+  double red[3][8];  // per-warp partials (fixed summation order)
 };
 
 template <typename JT>
@@ -276,6 +278,31 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
   }
   __syncthreads();
   }
+  // Scale M by a power of two (exact) so that its entries are at most about
+  // 1 (|M_pq| <= ||Lc||_F max|d| ||Lr||_F): the iteration in the working
+  // precision then never meets values near the ends of its range.
+  {
+    double a = 0.0, b = 0.0, dm = 0.0;
+    for (int idx = tid; idx < k * k; idx += NT) {
+      const int i = idx / k, j = idx % k;
+      a += S.Lc[i * KP + j] * S.Lc[i * KP + j];
+      b += S.Lr[i * KP + j] * S.Lr[i * KP + j];
+    }
+    for (int i = tid; i < k; i += NT) dm = fmax(dm, fabs(S.d[i]));
+    a = warp_sum_t(a);
+    b = warp_sum_t(b);
+    dm = warp_max(dm);
+    if (lane == 0) { S.red[0][warp] = a; S.red[1][warp] = b; S.red[2][warp] = dm; }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0, dm = 0.0;
+    for (int w = 0; w < NW; ++w) { a += S.red[0][w]; b += S.red[1][w]; dm = fmax(dm, S.red[2][w]); }
+    const double bound = sqrt(a) * sqrt(b) * dm;
+    S.scale = (bound > 0.0 && isfinite(bound)) ? ldexp(1.0, -ilogb(bound)) : 1.0;
+  }
+  __syncthreads();
+  const double msc = S.scale;
   // Core M = Lc^T diag(d) Lr : M[p][q] = sum_{i >= max(p,q)} Lc[i][p] d_i Lr[i][q].
   const int ke = k + (k & 1);  // even number of columns for the pairing
   for (int idx = tid; idx < ke * ke; idx += NT) {
@@ -285,7 +312,7 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
       const int i0 = p > qq ? p : qq;
       for (int i = i0; i < k; ++i) acc += S.Lc[i * KP + p] * S.d[i] * S.Lr[i * KP + qq];
     }
-    S.Mx[qq * KP + p] = (JT)acc;
+    S.Mx[qq * KP + p] = (JT)(acc * msc);
     S.Zm[qq * KP + p] = (JT)(p == qq ? 1.0 : 0.0);
   }
   __syncthreads();
@@ -323,7 +350,7 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     acc = warp_sum_t(acc);
     // A non-finite value (overflow or 0/0 upstream) is ranked last as -1, so
     // the ordering below stays a permutation; the solve is then failed.
-    if (lane == 0) S.sig[qq] = isfinite(acc) ? sqrt(acc) : -1.0;
+    if (lane == 0) S.sig[qq] = isfinite(acc) ? sqrt(acc) / msc : -1.0;
   }
   __syncthreads();
   for (int qq = tid; qq < k; qq += NT) {
@@ -369,7 +396,7 @@ __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
     const double* L = side == 0 ? S.Lc : S.Lr;
     const double* inv_diag = side == 0 ? S.invc : S.invr;
     T* out = side == 0 ? A.Tc : A.Tr;
-    const double inv = side == 0 ? (S.sig[src] > 0.0 ? 1.0 / S.sig[src] : 0.0) : 1.0;
+    const double inv = side == 0 ? (S.sig[src] > 0.0 ? 1.0 / (S.sig[src] * msc) : 0.0) : 1.0;
     const JT* col = side == 0 ? S.Mx + src * KP : S.Zm + src * KP;
     if (A.tri_given) {  // the factors are already orthonormal: T = W_K, Z_K
       for (int i = 0; i < k; ++i) out[i + (size_t)p * KMAX] = (T)((double)col[i] * inv);

@@ -49,7 +49,7 @@ def test_stokes_matches_oracle(lr, h, n, prec, eps, tol, acc):
     # stops on the Schur residual (tol); the velocity's own rounding at eps
     # adds up to about n eps through B^T (a difference over h)
     div = np.linalg.norm(S.bt(u, v, n)) / np.linalg.norm(S.bt(S.laplace_solve(f1, n), S.laplace_solve(f2, n), n))
-    bound = 5 * tol + 2 * n * eps
+    bound = 5 * tol + 2 * n * (max(eps, 1e-6) if prec == "mixed" else eps)  # mixed inner solves run at >= 1e-6
     assert div <= bound and res.resid <= bound, (div, res.resid)
     # the pressure has no kernel component
     for K in S.kernel_modes(n):
