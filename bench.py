@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--crossover", type=int, nargs="*", default=[256, 1024, 4096, 16384],
                    help="grid sizes of the full-grid vs low-rank comparison")
+    p.add_argument("--expsum", type=int, nargs="*", default=[1024, 16384],
+                   help="grid sizes of the exponential-sum vs cross comparison")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the untuned launch shapes (for profiler runs, whose per-launch overhead "
                         "would skew the tuner's timings)")
@@ -201,7 +203,7 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     out = (lr.colmajor_empty(n, 64), torch.empty(64, dtype=torch.float64, device="cuda"),
            lr.colmajor_empty(n, 64))
     results = {"autotune": {}}
-    # launch shapes tuned on this problem before anything is timed (T0/T7)
+    # launch shapes tuned on this problem before anything is timed
     for prec in ("mixed", "fp64"):
         if not args.no_autotune:
             results["autotune"][prec] = lr.lr_autotune(h, Ud, Vd, eps=EPS, prec=prec, reps=3)
@@ -335,6 +337,35 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                          "velocity_divergence": rs.resid, "pressure_rank": int(rs.p[1].shape[0]),
                          "velocity_ranks": [int(c[1].shape[0]) for c in rs.u]}
         results["stokes"].append(row)
+    # ---- exponential-sum baseline against the cross (n = 1024, eps = 1e-7,
+    # float64, the paper's comparison point)
+    results["expsum"] = []
+    for ne in args.expsum:
+        Ue, Ve = inputs.smooth_sum(ne, 1e-7)
+        Ued, Ved = torch.from_numpy(Ue).cuda(), torch.from_numpy(Ve).cuda()
+        oute = (lr.colmajor_empty(ne, 64), torch.empty(64, dtype=torch.float64, device="cuda"),
+                lr.colmajor_empty(ne, 64))
+        row = {"n": ne, "eps": 1e-7}
+        for kind, fn in (("expsum_fp64", lambda: lr.lr_poisson2d_expsum(h, Ued, Ved, eps=1e-7)),
+                         ("cross_fp64", lambda: lr.lr_poisson2d(h, Ued, Ved, eps=1e-7, prec="fp64", out=oute)),
+                         ("cross_mixed", lambda: lr.lr_poisson2d(h, Ued, Ved, eps=1e-7, prec="mixed", out=oute,
+                                                                 refine=-1))):
+            r0 = fn()
+            per = []
+            for i in range(3):
+                flush.fill_(i & 0xFF)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r0 = fn()
+                b.record(stream)
+                stream.synchronize()
+                per.append(a.elapsed_time(b))
+            row[kind + "_ms"] = round(statistics.median(per), 4)
+            if kind == "expsum_fp64":
+                row["expsum_terms"] = r0[3]
+                row["expsum_rank"] = int(r0[1].shape[0])
+        results["expsum"].append(row)
     # ---- throughput: batches of independent solves, one CUDA graph per batch
     B = args.batch
     probs = [(torch.from_numpy(U) * (1.0 + p / B), torch.from_numpy(V)) for p in range(B)]
@@ -486,6 +517,7 @@ def main():
             "rhs_rank": res["tight_fp64"]["r"]},
         "crossover_full_grid_vs_lowrank": res["crossover"],
         "stokes_uzawa_lowrank": res["stokes"],
+        "expsum_vs_cross": res["expsum"],
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2),

@@ -232,6 +232,19 @@ lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
 lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p,
                           double tol_div, int maxit, const lr_options* opt, int* iters, double* resid);
 
+/* Exponential-sum solve of the 5-point problem (Section 4.1, the known
+ * approach the cross method is compared with): 1/lambda is approximated on
+ * the spectrum [2 mu_1, 2 mu_m] by the sinc (trapezoidal) quadrature of
+ * int exp(s - lambda e^s) ds at eps / 10, so that
+ *   Xh ~ sum_q w_q (E_q Uh)(E_q Vh)^T,  E_q = diag(exp(-t_q mu)),
+ * accumulated in chunks and rounded at eps in float64 (shifted Cholesky QR
+ * and the core SVD, Section 3); float64 transforms.  Arguments as
+ * lr_poisson2d; opt->op must be LR_OP_5PT (the semi-staggered symbol does
+ * not split into a sum); nterms (may be NULL) receives the number of
+ * quadrature terms.  LR_EINVAL for eps < 1e-12 or the other operator kind.
+ * Synchronises. */
+lr_status lr_poisson2d_expsum(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt, int* nterms);
+
 /* Full-grid solve of A X = F on the m x m grid (Section 4.1, Eq. flr:diag:
  * X = S ((S F S) / Lambda) S, the fast Poisson solver the low-rank method is
  * compared with; no truncation).  F and X are dense column-major float64
@@ -245,8 +258,8 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
 lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double* X, int ldx,
                             const lr_options* opt);
 
-/* Autotuning of the launch shapes (the paper has no counterpart; step T0's
- * tuned-configuration lookup and T7's tuned tiles and cluster sizes).
+/* Autotuning of the launch shapes (the paper has no counterpart): the tiles
+ * and cluster sizes a solve looks up for its order before launching.
  *
  * lr_autotune times lr_poisson2d on the caller's problem rhs (device buffers
  * as for lr_poisson2d; the trial solutions go to internal scratch) with CUDA

@@ -94,7 +94,7 @@ def project_kernel(Pm: np.ndarray, n: int) -> np.ndarray:
 
 
 def body_force(n: int):
-    """The config-4 body force at the interior vertices, as rank-1 factors:
+    """The benchmark body force at the interior vertices, as rank-1 factors:
     f1 = sin(pi x) cos(pi y), f2 = -cos(pi x) sin(pi y) (1 + y)."""
     x = np.arange(1, n) / n
     f1 = (np.sin(np.pi * x)[:, None], np.cos(np.pi * x)[:, None])

@@ -203,7 +203,7 @@ Slice<T> carve_slice(Carve& cv, const SolveGeom& g) {
 
 int launches_of(const SolveGeom& g) { return 2 * (g.four_step ? 3 : 1) + 2; }
 
-// Enqueue T1-T6 of one solve on stream stm.  ev (optional) receives the
+// Enqueue the steps of one solve (forward DST to inverse DST) on stream stm.  ev (optional) receives the
 // phase boundaries.
 template <typename T>
 cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options& o, const Plan& plan,
@@ -213,7 +213,7 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   cudaError_t e;
   if ((e = cudaMemsetAsync(st, 0, sizeof(SolveState), stm)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], stm)) != cudaSuccess) return e;
-  // T1: forward DST of both factors.
+  // Forward DST of both factors.
   ColumnSet fw;
   fw.in[0] = rhs->U; fw.in[1] = rhs->V;
   fw.ld_in[0] = rhs->ld; fw.ld_in[1] = rhs->ld;
@@ -222,7 +222,7 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   fw.ncol[0] = g.r; fw.ncol[1] = g.r;
   if ((e = launch_dst<T>(plan, fw, IoType::F64, IoType::WORK, w.work, h->num_sms, stm)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stm)) != cudaSuccess) return e;
-  // T2-T4: cross approximation in frequency space.
+  // Cross approximation in frequency space (symbol, pivots, skeleton).
   CrossArgs<T> ca;
   ca.m = g.m; ca.r = g.r; ca.kcap = g.kcap; ca.ld = g.ldw;
   ca.Uh = w.Uh; ca.Vh = w.Vh; ca.C = w.C; ca.R = w.R;
@@ -236,7 +236,7 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   ca.max_zero_rows = 16;
   if ((e = launch_cross<T>(ca, o.cluster_size, stm, used_cs)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], stm)) != cudaSuccess) return e;
-  // T5: rounding core.
+  // Rounding core.
   CoreArgs<T> co;
   co.GC = w.GC; co.GR = w.GR; co.ldg = g.kcap; co.d = w.d;
   co.k_dev = &st->k; co.k_host = 0;
@@ -244,7 +244,7 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   co.Tc = w.Tc; co.Tr = w.Tr; co.s_out = sol->s; co.st = st;
   if ((e = launch_core<T>(co, f32, stm)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], stm)) != cudaSuccess) return e;
-  // T6: inverse DST of the kept columns into the caller's float64 factors;
+  // Inverse DST of the kept columns into the caller's float64 factors;
   // the rotation of the skeleton by Tc, Tr (the last step of the rounding) is
   // applied as the transform loads its input.
   ColumnSet iv;
@@ -385,6 +385,7 @@ struct RefineBufs {
   double *G0, *G1, *T0, *T1, *Ra0, *Ra1, *Tc, *Tr, *rs, *part;
   int* qout;
   SolveState* st;
+  double* aux;  // 4 KMAX scratch values (quadrature nodes, weights)
 };
 
 void carve_refine(Carve& c, RefineBufs& b, int ld, int m) {
@@ -411,9 +412,11 @@ void carve_refine(Carve& c, RefineBufs& b, int ld, int m) {
   b.part = c.take<double>(sq * (size_t)((m + 63) / 64));
   b.qout = c.take<int>(sizeof(int) * 2);
   b.st = c.take<SolveState>(sizeof(SolveState));
+  b.aux = c.take<double>(sizeof(double) * 4 * KMAX);
 }
 
-constexpr int kQrSteps = 4;
+constexpr int kQrSteps = 5;
+constexpr int kQrShiftedSteps = 3;
 
 // Rounding of L diag(d) Rt^T (q <= 64 columns, d = null: ones) through QR
 // factors of L and Rt by shifted Cholesky QR and the SVD of the core
@@ -430,15 +433,16 @@ lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const do
   const double* Xl = Lin;
   const double* Xr = Rin;
   int ldx = ldin;
-  // Shift of the first two steps (equilibrated Gram matrix, ||G|| <= q).
+  // Shift of the first three steps (equilibrated Gram matrix, ||G|| <= q).
   // Each shifted step maps a singular value sigma to sigma / sqrt(sigma^2 +
-  // shift) and loses nothing (Q = X R^-1 exactly), so two of them bring a
-  // factor of condition up to 1 / eps64 within reach of the two plain steps
-  // that make Q orthonormal; no column is ever dropped but an exactly zero
-  // one.
+  // shift) and loses nothing (Q = X R^-1 exactly), so three of them bring a
+  // factor of condition beyond 1 / eps64 (columns nearly in the span of the
+  // others, as the terms of an exponential sum at neighbouring nodes are)
+  // within reach of the two plain steps that make Q orthonormal; no column
+  // is ever dropped but an exactly zero one.
   const double shift = 11.0 * ((double)m * q + (double)q * (q + 1)) * (DBL_EPSILON / 2) * q;
   for (int step = 0; step < kQrSteps; ++step) {
-    double* Yl = (step & 1) ? b.L : b.Lb;   // ping-pong: Lin -> Lb -> L -> Lb -> L
+    double* Yl = (step & 1) ? b.L : b.Lb;   // ping-pong: Lin -> Lb -> L -> Lb -> L -> Lb
     double* Yr = (step & 1) ? b.Rt : b.Rb;
     LR_CUDA(h, launch_gram(Xl, m, ldx, q, b.G0, q, b.part, h->num_sms, stm), "gram");
     LR_CUDA(h, launch_gram(Xr, m, ldx, q, b.G1, q, b.part, h->num_sms, stm), "gram");
@@ -449,7 +453,7 @@ lr_status qr_round(lr_handle h, const RefineBufs& b, const double* Lin, const do
     a.qout = b.qout;
     a.q = q;
     a.first = step == 0;
-    a.shift = step < 2 ? shift : 0.0;
+    a.shift = step < kQrShiftedSteps ? shift : 0.0;
     a.floor_rel = 0.0;
     LR_CUDA(h, launch_cholqr_step(a, stm), "cholesky qr");
     LR_CUDA(h, (launch_rotate<double, double>(Xl, ldx, m, nullptr, q, b.T0, false, &b.qout[0], Yl, ld, stm)), "qr");
@@ -672,6 +676,105 @@ lr_status solve2d_full(lr_handle h, int m, const double* F, int ldf, double* X, 
   ColumnSet c4 = cols(W1, ldw, X, ldx);
   LR_CUDA(h, launch_dst<T>(*plan, c4, IoType::WORK, IoType::F64, scratch, h->num_sms, stm), "full: S Xh S");
   LR_CUDA(h, cudaStreamSynchronize(stm), "full-grid solve");
+  return LR_OK;
+}
+
+// Exponential-sum solve of the 5-point problem (Section 4.1, the "known
+// approaches" the cross is compared with): with 1/lambda ~ sum_q w_q
+// exp(-t_q lambda) (sinc quadrature of int exp(s - lambda e^s) ds) and
+// Lambda_ij = mu_i + mu_j,
+//   Xh ~ sum_q w_q (E_q Uh) (E_q Vh)^T,  E_q = diag(exp(-t_q mu)),
+// accumulated in chunks of terms (each rounding sees at most 64 columns) by
+// float64 QR rounding; float64 transforms.
+lr_status solve2d_expsum(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options& o, Plan* plan,
+                         int* nterms) {
+  const int m = rhs->n1, r = rhs->r;
+  const int ld = m + (m & 1);
+  RefineBufs b;
+  Carve sizing;
+  carve_refine(sizing, b, ld, m);
+  if (sizing.off > h->ws2_bytes) {
+    if (h->ws2) { cudaStreamSynchronize(h->stream); cudaFree(h->ws2); h->ws2 = nullptr; h->ws2_bytes = 0; }
+    if (cudaMalloc(&h->ws2, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "exp-sum buffers"); }
+    h->ws2_bytes = sizing.off;
+  }
+  Carve cv;
+  cv.base = static_cast<char*>(h->ws2);
+  carve_refine(cv, b, ld, m);
+  cudaStream_t stm = h->stream;
+  // Quadrature over the spectrum [2 mu_1, 2 mu_m] at eps / 10 (nodes on the
+  // host: step, ends and weights as stated for the sinc rule).
+  const double N = m + 1.0;
+  const double mu1 = 4.0 * N * N * std::pow(std::sin(M_PI / (2.0 * N)), 2);
+  const double mum = 4.0 * N * N * std::pow(std::cos(M_PI / (2.0 * N)), 2);
+  const double lo = 2.0 * mu1, hi = 2.0 * mum, eq = o.eps / 10.0;
+  const double tau = M_PI * M_PI / (std::log(1.0 / eq) + std::log(32.0));
+  const double s_min = std::log(eq / (4.0 * hi));
+  const double s_max = std::log((std::log(hi / eq) + 2.0) / lo);
+  const int Q = (int)std::ceil((s_max - s_min) / tau) + 1;
+  if (Q > 2 * KMAX) return fail(h, LR_EINVAL, "exp-sum: too many quadrature terms (eps too small)");
+  std::vector<double> tw(2 * Q);
+  for (int k = 0; k < Q; ++k) {
+    tw[k] = std::exp(s_min + k * tau);
+    tw[Q + k] = tau * tw[k];
+  }
+  // forward transforms of the factors (float64) into FU, FV
+  const size_t M = (size_t)1 << plan->logM;
+  // four-step scratch for the larger of the two transforms (2r and 2R <= 2 KMAX columns)
+  lr_status s = ensure_ws(h, M > (size_t)kSmallM ? M * 2 * (size_t)KMAX * sizeof(cpx<double>) + 256 : 256);
+  if (s != LR_OK) return s;
+  {
+    ColumnSet cs;
+    cs.in[0] = rhs->U; cs.in[1] = rhs->V;
+    cs.ld_in[0] = rhs->ld; cs.ld_in[1] = rhs->ld;
+    cs.out[0] = b.FU; cs.out[1] = b.FV;
+    cs.ld_out[0] = ld; cs.ld_out[1] = ld;
+    cs.ncol[0] = r; cs.ncol[1] = r;
+    LR_CUDA(h, launch_dst<double>(*plan, cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm), "exp-sum: forward");
+  }
+  double* dt = nullptr;
+  double* dw = nullptr;
+  if (Q <= 2 * KMAX) {  // nodes and weights in b.aux (4 KMAX values)
+    dt = b.aux;
+    dw = b.aux + 2 * KMAX;
+    LR_CUDA(h, cudaMemcpyAsync(dt, tw.data(), sizeof(double) * Q, cudaMemcpyHostToDevice, stm), "nodes");
+    LR_CUDA(h, cudaMemcpyAsync(dw, tw.data() + Q, sizeof(double) * Q, cudaMemcpyHostToDevice, stm), "weights");
+  }
+  const double* mu = plan->sym_a64[LR_OP_5PT];
+  int K = 0;
+  double sig = 0.0;
+  for (int k = 0; k < Q;) {
+    const int c = std::min(Q - k, (KMAX - K) / r);
+    if (c < 1) return fail(h, LR_ENOCONV, "exp-sum: running rank leaves no room for a term");
+    if (K > 0) {
+      LR_CUDA(h, cudaMemcpyAsync(b.L, b.XU, sizeof(double) * (size_t)ld * K, cudaMemcpyDeviceToDevice, stm), "stack");
+      LR_CUDA(h, cudaMemcpyAsync(b.Rt, b.XV, sizeof(double) * (size_t)ld * K, cudaMemcpyDeviceToDevice, stm), "stack");
+    }
+    LR_CUDA(h, launch_scale_copy(K, b.Xs, 1.0, b.rs, stm), "weights");
+    LR_CUDA(h, launch_scale_copy(c * r, nullptr, 1.0, b.rs + K, stm), "weights");
+    LR_CUDA(h, launch_expsum_cols(m, r, c, b.FU, b.FV, ld, mu, dt + k, dw + k, b.L, b.Rt, ld, K, stm), "terms");
+    const bool last = k + c == Q;
+    s = qr_round(h, b, b.L, b.Rt, ld, m, K + c * r, b.rs, last ? o.eps : o.eps / 4.0, KMAX, b.XU, b.XV, b.Xs, ld,
+                 0, false, &K, &sig);
+    if (s != LR_OK && s != LR_ENOCONV) return s;
+    k += c;
+  }
+  // inverse transforms into the caller's factors
+  const int R = std::min(K, sol->rmax);
+  if (R > 0) {
+    ColumnSet cs;
+    cs.in[0] = b.XU; cs.in[1] = b.XV;
+    cs.ld_in[0] = ld; cs.ld_in[1] = ld;
+    cs.out[0] = sol->U; cs.out[1] = sol->V;
+    cs.ld_out[0] = sol->ld; cs.ld_out[1] = sol->ld;
+    cs.ncol[0] = R; cs.ncol[1] = R;
+    LR_CUDA(h, launch_dst<double>(*plan, cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm), "exp-sum: inverse");
+    LR_CUDA(h, cudaMemcpyAsync(sol->s, b.Xs, sizeof(double) * R, cudaMemcpyDeviceToDevice, stm), "copy s");
+  }
+  LR_CUDA(h, cudaStreamSynchronize(stm), "exp-sum solve");
+  sol->r = R;
+  if (nterms) *nterms = Q;
+  if (R < K) return fail(h, LR_ENOCONV, "solution rank exceeds sol->rmax; result truncated");
   return LR_OK;
 }
 
@@ -1366,7 +1469,7 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
   s = get_plan(h, m, &plan);
   if (s != LR_OK) return s;
   h->info = lr_info{};
-  if (o.cluster_size == 0) {  // T0: autotuned configuration of this order, if any
+  if (o.cluster_size == 0) {  // autotuned configuration of this order, if any
     auto it = h->tuned_cs.find(std::make_tuple(m, (int)o.prec, (int)o.op));
     if (it != h->tuned_cs.end()) o.cluster_size = it->second;
   }
@@ -1430,6 +1533,20 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
       !aligned16(p->U) || !aligned16(p->V) || !aligned16(p->s))
     return fail(h, LR_EINVAL, "lr_stokes_uzawa: p must be n x n with U, s, V set and aligned");
   return stokes_uzawa(h, n, f, u, p, tol_div, maxit, o, iters, resid);
+}
+
+lr_status lr_poisson2d_expsum(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt, int* nterms) {
+  if (!h) return LR_EINVAL;
+  lr_options o;
+  if (opt) o = *opt; else lr_options_default(&o);
+  lr_status s = check_opts(h, o);
+  if (s != LR_OK) return s;
+  if (o.op != LR_OP_5PT) return fail(h, LR_EINVAL, "exp-sum: the 5-point kind only (the other symbol does not split)");
+  if (!(o.eps >= 1e-12)) return fail(h, LR_EINVAL, "exp-sum: eps must be >= 1e-12");
+  if ((s = check_problem(h, rhs, sol)) != LR_OK) return s;
+  Plan* plan = nullptr;
+  if ((s = get_plan(h, rhs->n1, &plan)) != LR_OK) return s;
+  return solve2d_expsum(h, rhs, sol, o, plan, nterms);
 }
 
 lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int reps, lr_tune* out) {

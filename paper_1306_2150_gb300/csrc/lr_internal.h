@@ -183,5 +183,8 @@ cudaError_t launch_cholqr_step(const CholQrArgs& a, cudaStream_t st);
 cudaError_t launch_fold_weights(int m, int kmax, const int* K, double* U, int ld, const double* s, bool unit,
                                 cudaStream_t st);
 cudaError_t launch_scale_weights(int n, double* w, const double* s, cudaStream_t st);
+cudaError_t launch_expsum_cols(int m, int r, int nterms, const double* Uh, const double* Vh, int ldh,
+                               const double* mu, const double* t, const double* w, double* L, double* R, int ldo,
+                               int off, cudaStream_t st);
 
 }  // namespace lrp

@@ -217,4 +217,29 @@ cudaError_t launch_scale_weights(int n, double* w, const double* s, cudaStream_t
   return cudaGetLastError();
 }
 
+// Columns of the exponential-sum solve (Section 4.1, known approaches): for
+// term q of the quadrature, L[:, off + q r + a] = w_q exp(-t_q mu_i) Uh[i, a],
+// R[:, off + q r + a] = exp(-t_q mu_i) Vh[i, a].
+__global__ void expsum_cols_kernel(int m, int r, const double* __restrict__ Uh, const double* __restrict__ Vh,
+                                   int ldh, const double* __restrict__ mu, const double* __restrict__ t,
+                                   const double* __restrict__ w, double* __restrict__ L, double* __restrict__ R,
+                                   int ldo, int off) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int col = blockIdx.y;  // q r + a
+  if (i >= m) return;
+  const int q = col / r, a = col % r;
+  const double e = exp(-t[q] * mu[i]);
+  L[i + (size_t)(off + col) * ldo] = w[q] * e * Uh[i + (size_t)a * ldh];
+  R[i + (size_t)(off + col) * ldo] = e * Vh[i + (size_t)a * ldh];
+}
+
+cudaError_t launch_expsum_cols(int m, int r, int nterms, const double* Uh, const double* Vh, int ldh,
+                               const double* mu, const double* t, const double* w, double* L, double* R, int ldo,
+                               int off, cudaStream_t st) {
+  if (nterms <= 0) return cudaSuccess;
+  dim3 grid((m + 255) / 256, nterms * r);
+  expsum_cols_kernel<<<grid, 256, 0, st>>>(m, r, Uh, Vh, ldh, mu, t, w, L, R, ldo, off);
+  return cudaGetLastError();
+}
+
 }  // namespace lrp

@@ -34,7 +34,7 @@ EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
            "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full",
-           "lr_stokes_uzawa")
+           "lr_stokes_uzawa", "lr_poisson2d_expsum")
 
 
 class LrMat(ctypes.Structure):
@@ -127,6 +127,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                     ctypes.POINTER(LrMat), ctypes.POINTER(LrMat), c_double, c_int,
                                     ctypes.POINTER(LrOptions), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]
     lib.lr_stokes_uzawa.restype = c_int
+    lib.lr_poisson2d_expsum.argtypes = [c_void_p, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
+                                        ctypes.POINTER(LrOptions), ctypes.POINTER(c_int)]
+    lib.lr_poisson2d_expsum.restype = c_int
     lib.lr_autotune_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                         ctypes.POINTER(LrOptions), c_int, ctypes.POINTER(LrTune)]
     lib.lr_autotune_batched.restype = c_int
@@ -487,3 +490,27 @@ def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 20
         raise LrError(st, h.last_error())
     u = [(Uo[:, :c_u[k].r], so[:c_u[k].r], Vo[:, :c_u[k].r]) for k, (Uo, so, Vo) in enumerate(outs)]
     return StokesResult(u, (Up[:, :c_p.r], sp[:c_p.r], Vp[:, :c_p.r]), iters.value, resid.value, st)
+
+
+def lr_poisson2d_expsum(h: Handle, U, V, eps: float = 1e-7, rmax_out: int = 64):
+    """Exponential-sum solve of the 5-point problem (float64); returns
+    (U, s, V, number of quadrature terms)."""
+    import torch
+    U = as_colmajor(U)
+    V = as_colmajor(V)
+    if U.stride(1) != V.stride(1):
+        V2 = colmajor_empty(V.shape[0], V.shape[1], V.device)
+        V2.copy_(V)
+        V = V2
+    m, r = U.shape
+    Uo, Vo = colmajor_empty(m, rmax_out, U.device), colmajor_empty(m, rmax_out, U.device)
+    so = torch.empty(rmax_out, dtype=torch.float64, device=U.device)
+    rhs = LrMat(m, m, r, r, _ld(U), U.data_ptr(), None, V.data_ptr())
+    sol = LrMat(m, m, 0, rmax_out, _ld(Uo), Uo.data_ptr(), so.data_ptr(), Vo.data_ptr())
+    o = _options(eps, "fp64", "5pt", 64, 1.0, 16, 0, 0, 0)
+    q = ctypes.c_int(0)
+    st = load().lr_poisson2d_expsum(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o), ctypes.byref(q))
+    if st not in (LR_OK,):
+        raise LrError(st, h.last_error())
+    R = sol.r
+    return Uo[:, :R], so[:R], Vo[:, :R], q.value

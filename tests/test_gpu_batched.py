@@ -87,7 +87,7 @@ def test_single_solve_graph_replay(lr, h):
         assert np.array_equal(npy(res.U), npy(ref.U)) and np.array_equal(npy(res.s), npy(ref.s))
 
 
-def test_batch_of_config3_recipe_converges(lr, h):
+def test_batch_of_uneven_log_uniform_problems_converges(lr, h):
     # the 512-problem batch recipe, scaled to 64 problems for test time:
     # n log-uniform in [512, 16384], r uniform in {1..32}, eps = 1e-6
     probs = _problems(64, 512, 16384, 32, seed=3)
@@ -102,7 +102,7 @@ def test_batch_of_config3_recipe_converges(lr, h):
         assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt", rows=rows) <= 1e-5
 
 
-# ------------------------------------------------------------------ autotuning (T0 lookup, T7 tiles)
+# ------------------------------------------------------------------ autotuning (tuned-shape lookup, tiles, cluster sizes)
 def test_autotune_single_then_lookup(lr, h):
     m, eps = 16384, 1e-6
     U, V = inputs.smooth_sum(m, eps)

@@ -46,7 +46,7 @@ def solve(lr, h, U, V, **kw):
     return res, npy(res.U), npy(res.s), npy(res.V)
 
 
-# ------------------------------------------------------------------ T1 / T6
+# ------------------------------------------------------------------ forward / inverse DST
 @pytest.mark.parametrize("m", [1, 2, 3, 31, 256, 1000, 2048, 2049, 5000])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_dst1_matches_oracle(lr, h, m, prec):
@@ -73,7 +73,7 @@ def test_dst1_full_size_sampled(lr, h, m, prec):
 
 
 # ------------------------------------------------------------------ solve
-def test_config0_fp64_pivots_ranks_bitexact(lr, h):
+def test_m256_r8_fp64_pivots_ranks_bitexact(lr, h):
     m, r, eps = 256, 8, 1e-10
     U, V = inputs.separable_random(m, r, seed=0)
     res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="fp64")
@@ -89,8 +89,8 @@ def test_config0_fp64_pivots_ranks_bitexact(lr, h):
     assert np.abs(Uo.T @ Uo - np.eye(len(s))).max() < 1e-12
 
 
-def test_config0_dense_lu_n32(lr, h):
-    # the n = 32 dense LU check of the smallest configuration, on the GPU result
+def test_dense_lu_n32(lr, h):
+    # the n = 32 dense LU check, on the GPU result
     m, r, eps = 32, 8, 1e-10
     U, V = inputs.separable_random(m, r, seed=0)
     res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="fp64")
@@ -360,3 +360,16 @@ def test_full_grid_agrees_with_lowrank_at_16384(lr, h, prec):
     Xl = (Ul[rows] * sl) @ Vl.T                # sampled rows of the low-rank solution, on the host
     err = np.linalg.norm(Xs - Xl) / np.linalg.norm(Xl)
     assert err <= (1e-10 if prec == "fp64" else 1e-5), err
+
+
+# ------------------------------------------------------------------ exponential-sum baseline
+@pytest.mark.parametrize("m,kind", [(64, "random"), (255, "random"), (1024, "smooth"), (4096, "smooth")])
+def test_expsum_matches_oracle(lr, h, m, kind):
+    from oracle import expsum as E
+    eps = 1e-7
+    U, V = inputs.separable_random(m, 4, seed=3) if kind == "random" else inputs.smooth_sum(m, eps)
+    Ux, s, Vx, q = lr.lr_poisson2d_expsum(h, cuda(U), cuda(V), eps=eps)
+    t, _ = E.sinc_exp_sum(2 * O.symbol(m, "5pt")[0].min(), 2 * O.symbol(m, "5pt")[0].max(), eps / 10)
+    assert q == len(t)
+    assert O.rel_error_freq(npy(Ux), npy(s), npy(Vx), U, V, "5pt") <= 10 * eps
+    assert np.abs(npy(Ux).T @ npy(Ux) - np.eye(len(s))).max() < 1e-10

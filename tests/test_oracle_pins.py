@@ -291,7 +291,7 @@ def test_lowrank_residual_matches_dense_residual():
 
 
 @pytest.mark.parametrize("kind", O.KINDS)
-def test_lowrank_solve_config0_accuracy_and_rank(kind):
+def test_lowrank_solve_m256_accuracy_and_rank(kind):
     # n = 256, rank-8 random separable RHS, eps = 1e-10: error <= 10 eps against
     # the full-grid solve, and the rank is within a few of the optimal eps-rank.
     m, eps = 256, 1e-10
