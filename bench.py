@@ -334,6 +334,7 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
             b.record(stream)
             stream.synchronize()
             row[prec] = {"ms": round(a.elapsed_time(b), 3), "iters": rs.iters, "status": rs.status,
+                         "cg_residual": rs.history[-1],
                          "velocity_divergence": rs.resid, "pressure_rank": int(rs.p[1].shape[0]),
                          "velocity_ranks": [int(c[1].shape[0]) for c in rs.u]}
         results["stokes"].append(row)

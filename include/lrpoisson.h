@@ -227,10 +227,13 @@ lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
  *   p     : pressure output n x n (U, s, V capacity rmax)
  *   iters : CG iterations taken (may be NULL)
  *   resid : ||B^T u|| / ||B^T A^-1 f|| of the returned velocity (may be NULL)
+ *   history: host array of maxit + 1 doubles (may be NULL): ||r_k|| / ||r_0||
+ *           of the CG residual for k = 0..iters (the rest untouched)
  * LR_EINVAL for bad arguments, LR_ENOCONV if tol_div was not reached or a
  * low-rank sum needed more than 64 columns.  Synchronises. */
 lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p,
-                          double tol_div, int maxit, const lr_options* opt, int* iters, double* resid);
+                          double tol_div, int maxit, const lr_options* opt, int* iters, double* resid,
+                          double* history);
 
 /* Exponential-sum solve of the 5-point problem (Section 4.1, the known
  * approach the cross method is compared with): 1/lambda is approximated on

@@ -905,6 +905,7 @@ struct StokesCtx {
   double eps;
   int launches = 0;
   int escalations = 0;               // mixed velocity solves repeated in float64
+  bool cut = false;                  // a low-rank sum needed more than 64 columns
 };
 
 void carve_stokes(Carve& c, StokesCtx& x) {
@@ -939,67 +940,71 @@ struct Term {
   double coef;
 };
 
-// dst = round(sum of terms, eps), rows x rows matrices, dst orthonormal with
-// leading dimension ldo; abs_tol > 0 also allows an absolute dropped tail.
+// dst = round(sum of terms), rows x rows matrices, dst orthonormal with
+// leading dimension ldo: relative tolerance eps, and abs_tol > 0 also allows
+// an absolute dropped tail.  Up to 64 columns the sum is rounded at once; a
+// wider one is accumulated in chunks, the running result plus as many further
+// columns as fit in 64, each partial rounding at eps / 4 and abs_tol / 2.  An
+// absolute truncation does not depend on how much the terms cancel (the CG
+// update r - alpha q cancels to a fraction of both), so the result stays
+// within max(eps ||sum||, abs_tol) of the exact sum, where dropping columns
+// by weight before the rounding would not.  Columns enter in term order, each
+// term's in descending weight.  dst must not alias a term; x.cut is set if
+// the running rank leaves no room for the rest.
 lr_status sum_round(StokesCtx& x, int rows, std::initializer_list<Term> terms, LrDev& dst, int ldo,
                     double abs_tol = 0.0) {
   lr_handle h = x.h;
   cudaStream_t stm = h->stream;
+  std::vector<Term> tv;
   int q = 0;
-  std::vector<Term> tv(terms);
-  for (const Term& t : tv) q += t.r;
+  for (const Term& t : terms)
+    if (t.r > 0) {
+      tv.push_back(t);
+      q += t.r;
+    }
   if (q == 0) { dst.r = 0; return LR_OK; }
-  if (q > KMAX) {
-    // Too wide for one rounding: drop the smallest weighted singular triplets
-    // (every term's weights are in descending order) until 64 columns remain.
-    std::vector<double> w(q);
-    int o2 = 0;
-    for (const Term& t : tv) {
-      if (t.s) LR_CUDA(h, cudaMemcpyAsync(x.hbuf + o2, t.s, sizeof(double) * t.r, cudaMemcpyDeviceToHost, stm), "copy");
-      o2 += t.r;
+  const bool single = q <= KMAX;
+  size_t ti = 0;  // next column: term ti, column tj
+  int tj = 0;
+  int K = 0;      // rank of the running result (in dst)
+  while (ti < tv.size()) {
+    if (K >= KMAX) { x.cut = true; break; }
+    int off = 0;
+    if (K > 0) {
+      LR_CUDA(h, cudaMemcpy2DAsync(x.b.L, sizeof(double) * x.ldp, dst.U, sizeof(double) * ldo, sizeof(double) * rows, K,
+                                   cudaMemcpyDeviceToDevice, stm), "stack");
+      LR_CUDA(h, cudaMemcpy2DAsync(x.b.Rt, sizeof(double) * x.ldp, dst.V, sizeof(double) * ldo, sizeof(double) * rows, K,
+                                   cudaMemcpyDeviceToDevice, stm), "stack");
+      LR_CUDA(h, launch_scale_copy(K, dst.s, 1.0, x.wts, stm), "weights");
+      off = K;
+      x.launches += 1;
     }
-    LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
-    o2 = 0;
-    std::vector<int> keep(tv.size());
-    for (size_t i = 0; i < tv.size(); ++i) {
-      keep[i] = tv[i].r;
-      for (int k = 0; k < tv[i].r; ++k) w[o2 + k] = std::fabs(tv[i].coef) * (tv[i].s ? x.hbuf[o2 + k] : 1.0);
-      o2 += tv[i].r;
+    while (off < KMAX && ti < tv.size()) {
+      const Term& t = tv[ti];
+      const int c = std::min(KMAX - off, t.r - tj);
+      LR_CUDA(h, cudaMemcpy2DAsync(x.b.L + (size_t)off * x.ldp, sizeof(double) * x.ldp, t.U + (size_t)tj * t.ld,
+                                   sizeof(double) * t.ld, sizeof(double) * rows, c, cudaMemcpyDeviceToDevice, stm),
+             "stack");
+      LR_CUDA(h, cudaMemcpy2DAsync(x.b.Rt + (size_t)off * x.ldp, sizeof(double) * x.ldp, t.V + (size_t)tj * t.ld,
+                                   sizeof(double) * t.ld, sizeof(double) * rows, c, cudaMemcpyDeviceToDevice, stm),
+             "stack");
+      LR_CUDA(h, launch_scale_copy(c, t.s ? t.s + tj : nullptr, t.coef, x.wts + off, stm), "weights");
+      x.launches += 1;
+      off += c;
+      tj += c;
+      if (tj == t.r) { ++ti; tj = 0; }
     }
-    while (q > KMAX) {
-      int best = -1;
-      double bw = 0.0;
-      o2 = 0;
-      for (size_t i = 0; i < tv.size(); ++i) {
-        if (keep[i] > 0 && (best < 0 || w[o2 + keep[i] - 1] < bw)) { best = (int)i; bw = w[o2 + keep[i] - 1]; }
-        o2 += tv[i].r;
-      }
-      --keep[best];
-      --q;
-    }
-    for (size_t i = 0; i < tv.size(); ++i) tv[i].r = keep[i];
+    const bool last = ti == tv.size();
+    double sig = 0.0;
+    lr_status s = qr_round(h, x.b, x.b.L, x.b.Rt, x.ldp, rows, off, x.wts, last ? x.eps : x.eps / 4.0, KMAX, dst.U,
+                           dst.V, dst.s, ldo, 0, false, &K, &sig, single ? abs_tol : abs_tol / 2.0);
+    x.launches += kQrRoundLaunches;
+    if (s != LR_OK && s != LR_ENOCONV) return s;
   }
-  int off = 0;
-  for (const Term& t : tv) {
-    if (t.r == 0) continue;
-    LR_CUDA(h, cudaMemcpy2DAsync(x.b.L + (size_t)off * x.ldp, sizeof(double) * x.ldp, t.U, sizeof(double) * t.ld,
-                                 sizeof(double) * rows, t.r, cudaMemcpyDeviceToDevice, stm), "stack");
-    LR_CUDA(h, cudaMemcpy2DAsync(x.b.Rt + (size_t)off * x.ldp, sizeof(double) * x.ldp, t.V, sizeof(double) * t.ld,
-                                 sizeof(double) * rows, t.r, cudaMemcpyDeviceToDevice, stm), "stack");
-    LR_CUDA(h, launch_scale_copy(t.r, t.s, t.coef, x.wts + off, stm), "weights");
-    off += t.r;
-  }
-  int K = 0;
-  double sig = 0.0;
-  lr_status s = qr_round(h, x.b, x.b.L, x.b.Rt, x.ldp, rows, q, x.wts, x.eps, KMAX, dst.U, dst.V, dst.s, ldo, 0,
-                         false, &K, &sig, abs_tol);
-  x.launches += 3 + kQrRoundLaunches;
-  if (s != LR_OK && s != LR_ENOCONV) return s;
   dst.r = K;
   return LR_OK;
 }
 
-// Squared Frobenius norm of an orthonormal-factor matrix (sum of s^2).
 lr_status norm2_of(StokesCtx& x, const LrDev& a, double* out) {
   *out = 0.0;
   if (a.r == 0) return LR_OK;
@@ -1092,39 +1097,21 @@ lr_status grad_solve(StokesCtx& x, const LrDev& X, int* rx, int* ry) {
   return LR_OK;
 }
 
-// dst = round(B^T W) for the velocity solutions of grad_solve (ranks rx, ry).
+// dst = round(B^T W) for the velocity solutions of grad_solve (ranks rx, ry):
+// the sum of (G^T Wx c)(H^T Zx)^T diag(sx) and (H^T Wy c)(G^T Zy)^T diag(sy),
+// c = 1 / (4h), built in x.b.XU / XV and x.b.FU / FV.
 lr_status div_round(StokesCtx& x, int rx, int ry, LrDev& dst, double abs_tol = 0.0) {
   lr_handle h = x.h;
   cudaStream_t stm = h->stream;
   const int n = x.n;
   const double c = n / 4.0;
-  if (rx + ry > KMAX) {
-    // Keep the 64 largest singular triplets of the pair (each solution's
-    // weights are in descending order): the Schur product becomes inexact by
-    // the dropped tail, which CG tolerates at that level.
-    LR_CUDA(h, cudaMemcpyAsync(x.hbuf, x.Ws[0], sizeof(double) * rx, cudaMemcpyDeviceToHost, stm), "copy");
-    LR_CUDA(h, cudaMemcpyAsync(x.hbuf + KMAX, x.Ws[1], sizeof(double) * ry, cudaMemcpyDeviceToHost, stm), "copy");
-    LR_CUDA(h, cudaStreamSynchronize(stm), "sync");
-    while (rx + ry > KMAX) {
-      if (ry == 0 || (rx > 0 && x.hbuf[rx - 1] <= x.hbuf[KMAX + ry - 1])) --rx;
-      else --ry;
-    }
-  }
-  // stack [G^T Wx sx c, H^T Wy sy c] and [H^T Zx, G^T Zy] directly into the rounding input
-  LR_CUDA(h, launch_gh(OP_GT, n, x.WU[0], x.ldv, rx, x.Ws[0], c, x.b.L, x.ldp, stm), "div");
-  LR_CUDA(h, launch_gh(OP_HT, n, x.WV[0], x.ldv, rx, nullptr, 1.0, x.b.Rt, x.ldp, stm), "div");
-  LR_CUDA(h, launch_gh(OP_HT, n, x.WU[1], x.ldv, ry, x.Ws[1], c, x.b.L + (size_t)rx * x.ldp, x.ldp, stm), "div");
-  LR_CUDA(h, launch_gh(OP_GT, n, x.WV[1], x.ldv, ry, nullptr, 1.0, x.b.Rt + (size_t)rx * x.ldp, x.ldp, stm), "div");
+  LR_CUDA(h, launch_gh(OP_GT, n, x.WU[0], x.ldv, rx, nullptr, 1.0, x.b.XU, x.ldp, stm), "div");
+  LR_CUDA(h, launch_gh(OP_HT, n, x.WV[0], x.ldv, rx, nullptr, 1.0, x.b.XV, x.ldp, stm), "div");
+  LR_CUDA(h, launch_gh(OP_HT, n, x.WU[1], x.ldv, ry, nullptr, 1.0, x.b.FU, x.ldp, stm), "div");
+  LR_CUDA(h, launch_gh(OP_GT, n, x.WV[1], x.ldv, ry, nullptr, 1.0, x.b.FV, x.ldp, stm), "div");
   x.launches += 4;
-  if (rx + ry == 0) { dst.r = 0; return LR_OK; }
-  int K = 0;
-  double sig = 0.0;
-  lr_status s = qr_round(h, x.b, x.b.L, x.b.Rt, x.ldp, n, rx + ry, nullptr, x.eps, KMAX, dst.U, dst.V, dst.s, x.ldp, 0,
-                         false, &K, &sig, abs_tol);
-  x.launches += kQrRoundLaunches;
-  if (s != LR_OK && s != LR_ENOCONV) return s;
-  dst.r = K;
-  return LR_OK;
+  return sum_round(x, n, {{x.b.XU, x.Ws[0], x.b.XV, rx, x.ldp, c}, {x.b.FU, x.Ws[1], x.b.FV, ry, x.ldp, c}}, dst,
+                   x.ldp, abs_tol);
 }
 
 lr_status copy_lr(StokesCtx& x, int rows, const LrDev& a, LrDev& dst) {
@@ -1165,8 +1152,12 @@ lr_status kernel_coeffs(StokesCtx& x, const LrDev& X, double coef, double* a, do
   return LR_OK;
 }
 
+// Absolute rounding level of the CG residual and direction, in units of
+// eps ||r0|| (the Schur product q: a tenth of it).
+constexpr double kCgFloor = 0.3;
+
 lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p, double tol, int maxit,
-                       const lr_options& o, int* iters, double* resid) {
+                       const lr_options& o, int* iters, double* resid, double* history) {
   StokesCtx x;
   x.h = h;
   x.n = n;
@@ -1177,8 +1168,12 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   x.oin.flags = 0;
   x.oin.refine = -1;
   x.oin.op = LR_OP_SEMISTAGGERED;
-  // float32 solves: at 1e-7 the float32 cross sits on its own rounding noise
-  // and does not converge, so the inner solves run at 1e-6 at least
+  // The velocity solves run at eps / 10: B^T is a difference over h and
+  // amplifies the high-frequency part of their error, which the Schur
+  // product q would otherwise carry into the CG recursion.  float32 solves:
+  // below 1e-6 the float32 cross sits on its own rounding noise and does not
+  // converge, so they run at 1e-6 at least.
+  x.oin.eps = 0.1 * o.eps;
   if (o.prec == LR_MIXED && x.oin.eps < 1e-6) x.oin.eps = 1e-6;
   lr_status s = get_plan(h, n - 1, &x.plan);
   if (s != LR_OK) return s;
@@ -1207,6 +1202,7 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   double rr = 0.0;
   if ((s = norm2_of(x, x.R, &rr)) != LR_OK) return s;
   const double nr0 = std::sqrt(rr);
+  if (history) history[0] = nr0 > 0.0 ? 1.0 : 0.0;
   x.P.r = 0;
   if ((s = copy_lr(x, n, x.R, x.D)) != LR_OK) return s;
   int it = 0;
@@ -1215,7 +1211,7 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
     if ((s = grad_solve(x, x.D, &rx, &ry)) != LR_OK) return s;
     // q enters r - alpha q with alpha = O(1) (the Schur spectrum lies in
     // (0, 1]): rounded to a tenth of the residual's absolute level
-    if ((s = div_round(x, rx, ry, x.Q, 0.1 * x.eps * nr0)) != LR_OK) return s;
+    if ((s = div_round(x, rx, ry, x.Q, 0.1 * kCgFloor * x.eps * nr0)) != LR_OK) return s;
     double dq = 0.0;
     if ((s = inner(x, n, x.D, x.Q, &dq)) != LR_OK) return s;
     if (!(dq > 0.0)) break;  // d in the kernel (round-off): nothing left to gain
@@ -1225,8 +1221,11 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
                        x.T, x.ldp)) != LR_OK) return s;
     std::swap(x.P, x.T);
     // The residual and the direction shrink by orders of magnitude while
-    // their terms do not: they are rounded to the absolute level eps ||r0||
-    // (relative rounding would keep ever more columns of cancellation noise).
+    // their terms do not: they are rounded to the absolute level
+    // kCgFloor eps ||r0|| (relative rounding would keep ever more columns of
+    // cancellation noise; the floor sits well below the stopping level
+    // tol_div ||r0|| for the workloads' tol_div = 10 eps, so that the
+    // truncations do not slow CG down near the end).
     // The new residual also loses its components along the pressure's kernel
     // modes (round-off of the truncations would otherwise accumulate there
     // and stall CG): r - alpha q - a 1 1^T - b c c^T.
@@ -1240,16 +1239,17 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
     }
     if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, -alpha},
                               {x.E, nullptr, x.E, 1, x.ldp, -ka}, {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -kb}},
-                       x.T, x.ldp, x.eps * nr0)) != LR_OK) return s;
+                       x.T, x.ldp, kCgFloor * x.eps * nr0)) != LR_OK) return s;
     std::swap(x.R, x.T);
     double rr_new = 0.0;
     if ((s = norm2_of(x, x.R, &rr_new)) != LR_OK) return s;
     const double beta = rr_new / rr;
     if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.D.U, x.D.s, x.D.V, x.D.r, x.ldp, beta}},
-                       x.T, x.ldp, x.eps * nr0)) != LR_OK) return s;
+                       x.T, x.ldp, kCgFloor * x.eps * nr0)) != LR_OK) return s;
     std::swap(x.D, x.T);
     rr = rr_new;
     ++it;
+    if (history) history[it] = std::sqrt(rr) / nr0;
   }
   // Project the pressure's kernel modes (constant, checkerboard) out of p.
   if (x.P.r > 0) {
@@ -1318,6 +1318,7 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   h->info.refine_rounds = x.escalations;  // reused: velocity solves escalated to float64
   if (!(std::sqrt(rr) <= tol * nr0) && nr0 > 0.0)
     return fail(h, LR_ENOCONV, "Uzawa did not reach tol_div within maxit");
+  if (x.cut) return fail(h, LR_ENOCONV, "a low-rank sum needed more than 64 columns; columns were dropped");
   return LR_OK;
 }
 
@@ -1512,7 +1513,8 @@ lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat
 // Autotuning: time candidate launch shapes on the caller's problem (CUDA
 // events on the handle's stream, median of reps after a warm-up).
 lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p,
-                          double tol_div, int maxit, const lr_options* opt, int* iters, double* resid) {
+                          double tol_div, int maxit, const lr_options* opt, int* iters, double* resid,
+                          double* history) {
   if (!h) return LR_EINVAL;
   lr_options o;
   if (opt) o = *opt; else lr_options_default(&o);
@@ -1532,7 +1534,7 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
   if (p->n1 != n || p->n2 != n || p->ld < n || p->rmax < 1 || !p->U || !p->V || !p->s ||
       !aligned16(p->U) || !aligned16(p->V) || !aligned16(p->s))
     return fail(h, LR_EINVAL, "lr_stokes_uzawa: p must be n x n with U, s, V set and aligned");
-  return stokes_uzawa(h, n, f, u, p, tol_div, maxit, o, iters, resid);
+  return stokes_uzawa(h, n, f, u, p, tol_div, maxit, o, iters, resid, history);
 }
 
 lr_status lr_poisson2d_expsum(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt, int* nterms) {

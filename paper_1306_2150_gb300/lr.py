@@ -125,7 +125,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_poisson2d_full.restype = c_int
     lib.lr_stokes_uzawa.argtypes = [c_void_p, c_int, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                     ctypes.POINTER(LrMat), ctypes.POINTER(LrMat), c_double, c_int,
-                                    ctypes.POINTER(LrOptions), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]
+                                    ctypes.POINTER(LrOptions), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
+                                    ctypes.POINTER(c_double)]
     lib.lr_stokes_uzawa.restype = c_int
     lib.lr_poisson2d_expsum.argtypes = [c_void_p, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                         ctypes.POINTER(LrOptions), ctypes.POINTER(c_int)]
@@ -452,6 +453,7 @@ class StokesResult:
     iters: int
     resid: float
     status: int
+    history: list    # ||r_k|| / ||r_0|| of the CG residual, k = 0..iters
 
 
 def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 200, eps: float = 1e-7,
@@ -484,12 +486,14 @@ def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 20
     o = _options(eps, prec, "semi", 64, 1.0, 16, 0, 0, 0)
     iters = ctypes.c_int(0)
     resid = ctypes.c_double(0.0)
+    hist = (ctypes.c_double * (int(maxit) + 1))()
     st = load().lr_stokes_uzawa(h.ptr, 2, n, c_f, None, c_u, ctypes.byref(c_p), float(tol_div), int(maxit),
-                                ctypes.byref(o), ctypes.byref(iters), ctypes.byref(resid))
+                                ctypes.byref(o), ctypes.byref(iters), ctypes.byref(resid), hist)
     if check and st not in (LR_OK, LR_ENOCONV):
         raise LrError(st, h.last_error())
     u = [(Uo[:, :c_u[k].r], so[:c_u[k].r], Vo[:, :c_u[k].r]) for k, (Uo, so, Vo) in enumerate(outs)]
-    return StokesResult(u, (Up[:, :c_p.r], sp[:c_p.r], Vp[:, :c_p.r]), iters.value, resid.value, st)
+    return StokesResult(u, (Up[:, :c_p.r], sp[:c_p.r], Vp[:, :c_p.r]), iters.value, resid.value, st,
+                        list(hist[:iters.value + 1]))
 
 
 def lr_poisson2d_expsum(h: Handle, U, V, eps: float = 1e-7, rmax_out: int = 64):

@@ -41,6 +41,7 @@ def test_stokes_matches_oracle(lr, h, n, prec, eps, tol, acc):
     fdev, (f1, f2) = body_force_dev(n)
     res = lr.lr_stokes_uzawa(h, n, fdev, tol_div=tol, eps=eps, prec=prec)
     assert res.status == lr.LR_OK, h.last_error()
+    assert len(res.history) == res.iters + 1 and res.history[0] == 1.0 and res.history[-1] <= tol
     ref = S.uzawa_cg(f1, f2, n, tol=1e-13)
     u, v, p = dense(res.u[0]), dense(res.u[1]), dense(res.p)
     for a, b in ((u, ref.u), (v, ref.v), (p, ref.p)):
@@ -70,5 +71,5 @@ def test_stokes_rejects_bad_arguments(lr, h):
     import ctypes
     fdev, _ = body_force_dev(16)
     o = lr._options(1e-7, "fp64", "semi", 64, 1.0, 16, 0, 0, 0)
-    st = lr.load().lr_stokes_uzawa(h.ptr, 3, 16, None, None, None, None, 1e-6, 10, ctypes.byref(o), None, None)
+    st = lr.load().lr_stokes_uzawa(h.ptr, 3, 16, None, None, None, None, 1e-6, 10, ctypes.byref(o), None, None, None)
     assert st == lr.LR_EINVAL
