@@ -135,3 +135,89 @@ def batch_problems(count: int, n_lo: int, n_hi: int, r_hi: int, seed: int):
         r = 1 + min(int(u[2 * p + 1] * r_hi), r_hi - 1)
         out.append((n, r, (seed * 1000003 + p) & _MASK))
     return out
+
+
+# ---------------------------------------------------------------- 3D (Tucker)
+# Tensors in Tucker format (Section 3, Eq. flr:tucker): a core G of shape
+# (r1, r2, r3), C-ordered (G[a, b, c] at (a r2 + b) r3 + c), and factors U_k,
+# n_k x r_k, Fortran-ordered; A = G x_1 U1 x_2 U2 x_3 U3.
+
+def _orth_trunc(A: np.ndarray, tol: float):
+    """Orthonormal basis of the columns of A up to relative size tol (numpy SVD;
+    input preparation only)."""
+    w, s, _ = np.linalg.svd(A, full_matrices=False)
+    keep = max(1, int(np.sum(s > tol * s[0])))
+    return w[:, :keep]
+
+
+def _cp_to_tucker(A1: np.ndarray, A2: np.ndarray, A3: np.ndarray, lam: np.ndarray, tol: float):
+    """The CP tensor sum_q lam_q A1[:, q] o A2[:, q] o A3[:, q] re-expressed in
+    Tucker format with relative Frobenius error <= tol: a basis of each factor
+    matrix's columns (to 1e-15), the core in those bases, then the core's
+    higher-order SVD truncated with tol / sqrt(3) per mode (De Lathauwer, De
+    Moor, Vandewalle 2000).  Input preparation only."""
+    W = [_orth_trunc(A, 1e-15) for A in (A1, A2, A3)]
+    B = [w.T @ A for w, A in zip(W, (A1, A2, A3))]
+    core = np.einsum("q,aq,bq,cq->abc", lam, B[0], B[1], B[2], optimize=True)
+    total = np.linalg.norm(core)
+    Z = []
+    for mode in range(3):
+        unf = np.moveaxis(core, mode, 0).reshape(core.shape[mode], -1)
+        z, s, _ = np.linalg.svd(unf, full_matrices=False)
+        keep = len(s)
+        tail = 0.0
+        for k in range(len(s) - 1, 0, -1):
+            tail_new = math.sqrt(tail * tail + s[k] * s[k])
+            if tail_new > tol / math.sqrt(3.0) * total:
+                break
+            tail = tail_new
+            keep = k
+        Z.append(z[:, :keep])
+    G = np.einsum("abc,ai,bj,ck->ijk", core, Z[0], Z[1], Z[2], optimize=True)
+    Us = [np.asfortranarray(w @ z) for w, z in zip(W, Z)]
+    return np.ascontiguousarray(G), Us[0], Us[1], Us[2]
+
+
+def smooth3d(n: int, tol: float):
+    """f(x,y,z) = exp(-(x+2y+3z)) + 1/sqrt(x^2+y^2+z^2+0.01) on the n^3 interior
+    grid in Tucker format, relative Frobenius tolerance ``tol``.
+
+    1/sqrt(s) = (2/sqrt(pi)) int_R exp(-s e^{2t}) e^t dt (s = x^2+y^2+z^2+0.01 in
+    [0.01, 3.01]), discretised by the trapezoidal rule with step 0.15 on
+    [-34, 5] (261 nodes; relative error below 1e-13 on that interval): each
+    node is the separable term e^{-0.01 e^{2t}} e^{-x^2 e^{2t}} e^{-y^2 e^{2t}}
+    e^{-z^2 e^{2t}}.  With the separable first term this is a CP tensor of 262
+    terms, compressed to Tucker format.
+    Returns (G, U1, U2, U3)."""
+    x = grid(n)
+    t = np.arange(-34.0, 5.0 + 1e-9, 0.15)
+    e2 = np.exp(2.0 * t)
+    lam = (2.0 / math.sqrt(math.pi)) * 0.15 * np.exp(t) * np.exp(-0.01 * e2)
+    E = np.exp(-np.outer(x * x, e2))
+    A1 = np.hstack([E, np.exp(-x)[:, None]])
+    A2 = np.hstack([E, np.exp(-2.0 * x)[:, None]])
+    A3 = np.hstack([E, np.exp(-3.0 * x)[:, None]])
+    return _cp_to_tucker(A1, A2, A3, np.append(lam, 1.0), tol)
+
+
+def smooth3d_dense(n: int) -> np.ndarray:
+    """The same f sampled directly on the grid (small n only), C-ordered
+    [i, j, k] with i along x."""
+    x = grid(n)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    return np.exp(-(X + 2.0 * Y + 3.0 * Z)) + 1.0 / np.sqrt(X * X + Y * Y + Z * Z + 0.01)
+
+
+def tucker_random(n, r, seed: int = 0):
+    """Random Tucker tensor with separable factor columns like separable_random:
+    mode 1 cos(b x + c), mode 2 exp(d y), mode 3 cos(b' z + c'), coefficients in
+    [0, 4); core entries N(0, 1).  n and r are ints or 3-tuples.
+    Returns (G, U1, U2, U3)."""
+    ns = (n, n, n) if np.isscalar(n) else tuple(n)
+    rs = (r, r, r) if np.isscalar(r) else tuple(r)
+    u = uniform01(seed, 5 * max(rs)).reshape(max(rs), 5) * 4.0
+    U1 = np.cos(np.outer(grid(ns[0]), u[:rs[0], 0]) + u[:rs[0], 1])
+    U2 = np.exp(np.outer(grid(ns[1]), u[:rs[1], 2]) * 0.5)
+    U3 = np.cos(np.outer(grid(ns[2]), u[:rs[2], 3]) + u[:rs[2], 4])
+    G = normal(seed ^ 0x3C6EF372, rs[0] * rs[1] * rs[2]).reshape(rs)
+    return (np.ascontiguousarray(G), np.asfortranarray(U1), np.asfortranarray(U2), np.asfortranarray(U3))
