@@ -57,6 +57,8 @@ def parse():
                         "would skew the tuner's timings)")
     p.add_argument("--stokes", type=int, nargs="*", default=[1024, 4096, 8192],
                    help="cells per direction of the low-rank Uzawa Stokes runs")
+    p.add_argument("--tucker", type=int, nargs="*", default=[128, 256, 512, 1024],
+                   help="grid sizes of the 3D Tucker solves (eps = 1e-6, float64)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -338,6 +340,26 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                          "velocity_divergence": rs.resid, "pressure_rank": int(rs.p[1].shape[0]),
                          "velocity_ranks": [int(c[1].shape[0]) for c in rs.u]}
         results["stokes"].append(row)
+    # ---- 3D Poisson in Tucker format (7-point operator, smooth right-hand
+    # side exp(-(x+2y+3z)) + 1/sqrt(r^2 + 0.01), eps = 1e-6, float64)
+    results["tucker"] = []
+    for nt in args.tucker:
+        G3, A1, A2, A3 = inputs.smooth3d(nt, 1e-6)
+        d3 = (torch.from_numpy(G3).cuda(), *[torch.from_numpy(np.asfortranarray(A)).cuda() for A in (A1, A2, A3)])
+        r0 = lr.lr_poisson3d_tucker(h, *d3, eps=1e-6, check=False)
+        per = []
+        for i in range(3):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r0 = lr.lr_poisson3d_tucker(h, *d3, eps=1e-6, check=False)
+            b.record(stream)
+            stream.synchronize()
+            per.append(a.elapsed_time(b))
+        results["tucker"].append({"n": nt, "ms": round(statistics.median(per), 3), "status": r0.status,
+                                  "rhs_ranks": list(G3.shape), "solution_ranks": list(r0.G.shape),
+                                  "cross_steps": r0.steps, "probe_rounds": r0.probe_rounds})
     # ---- exponential-sum baseline against the cross (n = 1024, eps = 1e-7,
     # float64, the paper's comparison point)
     results["expsum"] = []
@@ -519,6 +541,7 @@ def main():
         "crossover_full_grid_vs_lowrank": res["crossover"],
         "stokes_uzawa_lowrank": res["stokes"],
         "expsum_vs_cross": res["expsum"],
+        "tucker3d_fp64": res["tucker"],
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2),

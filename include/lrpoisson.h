@@ -235,6 +235,44 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
                           double tol_div, int maxit, const lr_options* opt, int* iters, double* resid,
                           double* history);
 
+/* A three-dimensional tensor in Tucker format (Section 3, Eq. flr:tucker):
+ * A(i, j, k) = sum_{a,b,c} G(a, b, c) U[0](i, a) U[1](j, b) U[2](k, c).
+ * Device pointers; factors column-major n[k] x r[k] with leading dimension
+ * ld[k] (even, >= n[k], 16-byte aligned); the core in C order,
+ * G[(a r[1] + b) r[2] + c].  rmax[k] is the output capacity of a solution
+ * (its core must hold rmax[0] rmax[1] rmax[2] doubles, U[k] rmax[k] columns). */
+typedef struct {
+  int n[3];
+  int r[3];
+  int rmax[3];
+  int ld[3];
+  double* G;
+  double* U[3];
+} lr_tucker;
+
+/* Low-rank 3D Poisson solve in Tucker format (Section 3, Eq. flr:tucker;
+ * Sections 4.1 and 4.2 in three dimensions): A X = F for the 7-point
+ * Laplacian of the unit cube with homogeneous Dirichlet conditions, n[k]
+ * interior points in direction k (h_k = 1/(n[k] + 1)), F = rhs in Tucker
+ * format.  X-hat = F-hat / (mu_i + mu_j + mu_k) (F-hat = G x_k (S U_k), S the
+ * DST-I) is approximated by a Tucker fibre cross: each step finds a pivot by
+ * alternating maximisation of the residual along fibres, adds the residual
+ * fibres through it to per-mode orthonormal bases Q_k with DEIM
+ * interpolation indices I_k, and takes the core by cross interpolation
+ * C = X-hat(I_1, I_2, I_3) x_k Q_k(I_k, :)^-1; the stop test (the step's
+ * rank-one size below tol ||C||_F twice) is confirmed by probe rounds
+ * (opt->probes random fibres per mode drawn by splitmix64 from opt->seed,
+ * and every fibre through the other modes' index sets), tol =
+ * 0.1 aca_tol_factor eps.  Then the higher-order SVD of C, each mode
+ * truncated with a tail <= eps ||C|| / sqrt(3), and the inverse DST of the
+ * kept factors.  Output: sol->G, sol->U[k] (orthonormal columns), sol->r.
+ * Requirements: opt->prec == LR_FP64, opt->op == LR_OP_5PT (its 3D
+ * analogue), 1 <= n[k] <= 16384, 1 <= r[k] <= 64, opt->rmax <= 64 cross
+ * steps.  LR_EINVAL for bad arguments, LR_ENOCONV if the cross did not
+ * converge within opt->rmax steps or a rank exceeded sol->rmax (result
+ * truncated), LR_ENONFINITE for a non-finite value.  Synchronises. */
+lr_status lr_poisson3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options* opt);
+
 /* Exponential-sum solve of the 5-point problem (Section 4.1, the known
  * approach the cross method is compared with): 1/lambda is approximated on
  * the spectrum [2 mu_1, 2 mu_m] by the sinc (trapezoidal) quadrature of

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -54,6 +55,9 @@ struct lr_handle_s {
   void* ws4 = nullptr;
   size_t ws4_bytes = 0;
   double* h_big = nullptr;
+  // workspace of 3D Tucker solves
+  void* ws5 = nullptr;
+  size_t ws5_bytes = 0;
   // autotuned cluster sizes of single solves, keyed (m, precision, operator),
   // and indices per cross CTA of batched solves, per precision
   std::map<std::tuple<int, int, int>, int> tuned_cs;
@@ -1152,6 +1156,310 @@ lr_status kernel_coeffs(StokesCtx& x, const LrDev& X, double coef, double* a, do
   return LR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Low-rank 3D solve in Tucker format (Section 3, Eq. flr:tucker; Sections 4.1
+// and 4.2 in three dimensions): forward DST of the three factors, Tucker
+// fibre cross of Xh = Fh / (mu_i + mu_j + mu_k) (kernels in tucker.cu), the
+// higher-order SVD of its core (shifted Cholesky QR of each unfolding and the
+// rounding core), inverse DST of the kept factors.  float64 throughout.
+// ---------------------------------------------------------------------------
+
+// Output t (1-based) of splitmix64 started at state seed (Steele, Lea and
+// Flood 2014): the probe positions of the 3D cross.
+unsigned long long splitmix64_at(unsigned long long seed, unsigned long long t) {
+  unsigned long long z = seed + t * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+constexpr int kT3ProbeRounds = 4;
+
+lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options& o) {
+  cudaStream_t stm = h->stream;
+  Plan* plan[3];
+  int n[3], r[3], ldq[3];
+  int nmax = 0;
+  size_t Mmax = 0;
+  for (int k = 0; k < 3; ++k) {
+    n[k] = rhs->n[k];
+    r[k] = rhs->r[k];
+    ldq[k] = n[k] + (n[k] & 1);
+    nmax = std::max(nmax, n[k]);
+    lr_status s = get_plan(h, n[k], &plan[k]);
+    if (s != LR_OK) return s;
+    Mmax = std::max(Mmax, (size_t)1 << plan[k]->logM);
+  }
+  const int probes = std::max(0, o.probes);
+  const int maxjobs = 3 * (probes + T3P * T3P);
+  const int lda = T3P * T3P;  // unfoldings: at most 64 x 64 rows
+  const size_t cube = sizeof(double) * (size_t)T3P * T3P * T3P;
+  T3Dev d{};
+  double *T1 = nullptr, *T2 = nullptr, *E = nullptr, *ident = nullptr, *W[3] = {}, *sig = nullptr, *XU = nullptr;
+  int *jobs = nullptr, *pam = nullptr;
+  double* pn2 = nullptr;
+  RefineBufs b;
+  auto layout = [&](Carve& c) {
+    for (int k = 0; k < 3; ++k) {
+      d.Uh[k] = c.take<double>(sizeof(double) * (size_t)ldq[k] * r[k]);
+      d.Q[k] = c.take<double>(sizeof(double) * (size_t)ldq[k] * T3P);
+      d.e[k] = c.take<double>(sizeof(double) * ldq[k]);
+      d.v[k] = c.take<double>(sizeof(double) * ldq[k]);
+      d.inI[k] = c.take<unsigned char>(n[k]);
+      d.Minv[k] = c.take<double>(sizeof(double) * T3P * T3P);
+      d.I[k] = c.take<int>(sizeof(int) * T3P);
+      d.h[k] = c.take<double>(sizeof(double) * (T3P + 1));
+      d.y[k] = c.take<double>(sizeof(double) * T3P);
+      W[k] = c.take<double>(sizeof(double) * KMAX * KMAX);
+    }
+    d.C = c.take<double>(cube);
+    T1 = c.take<double>(cube);
+    T2 = c.take<double>(cube);
+    E = c.take<double>(cube);
+    d.st = c.take<T3State>(sizeof(T3State));
+    jobs = c.take<int>(sizeof(int) * 3 * (size_t)maxjobs);
+    pn2 = c.take<double>(sizeof(double) * (size_t)maxjobs);
+    pam = c.take<int>(sizeof(int) * (size_t)maxjobs);
+    ident = c.take<double>(sizeof(double) * KMAX * KMAX);
+    sig = c.take<double>(sizeof(double) * KMAX);
+    XU = c.take<double>(sizeof(double) * (size_t)(nmax + 1) * KMAX);
+    carve_refine(c, b, lda, lda);  // Cholesky QR of the unfoldings (b.L, b.Lb: lda x 64)
+  };
+  Carve sizing;
+  layout(sizing);
+  if (sizing.off > h->ws5_bytes) {
+    if (h->ws5) { cudaStreamSynchronize(stm); cudaFree(h->ws5); h->ws5 = nullptr; h->ws5_bytes = 0; }
+    if (cudaMalloc(&h->ws5, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "3D workspace"); }
+    h->ws5_bytes = sizing.off;
+  }
+  if (!h->h_big && cudaMallocHost(&h->h_big, sizeof(double) * (2 * KMAX * KMAX + 4 * KMAX)) != cudaSuccess) {
+    cudaGetLastError();
+    h->h_big = nullptr;
+    return fail(h, LR_ENOMEM, "pinned buffer");
+  }
+  Carve cv;
+  cv.base = static_cast<char*>(h->ws5);
+  layout(cv);
+  for (int k = 0; k < 3; ++k) {
+    d.n[k] = n[k];
+    d.r[k] = r[k];
+    d.ldu[k] = ldq[k];
+    d.ldq[k] = ldq[k];
+    d.mu[k] = plan[k]->sym_a64[LR_OP_5PT];
+  }
+  d.G = rhs->G;
+  int launches = 0;
+  // forward transforms of the factors
+  lr_status s = ensure_ws(h, Mmax > (size_t)kSmallM ? Mmax * 2 * (size_t)KMAX * sizeof(cpx<double>) + 256 : 256);
+  if (s != LR_OK) return s;
+  for (int k = 0; k < 3; ++k) {
+    ColumnSet cs;
+    cs.in[0] = rhs->U[k];
+    cs.ld_in[0] = rhs->ld[k];
+    cs.out[0] = const_cast<double*>(d.Uh[k]);
+    cs.ld_out[0] = ldq[k];
+    cs.ncol[0] = r[k];
+    LR_CUDA(h, launch_dst<double>(*plan[k], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm), "3D: forward");
+    ++launches;
+  }
+  // state
+  for (int k = 0; k < 3; ++k) {
+    LR_CUDA(h, cudaMemsetAsync(d.inI[k], 0, n[k], stm), "3D: init");
+    LR_CUDA(h, cudaMemsetAsync(d.Minv[k], 0, sizeof(double) * T3P * T3P, stm), "3D: init");
+  }
+  T3State* hs = reinterpret_cast<T3State*>(h->h_big);
+  std::memset(hs, 0, sizeof(T3State));
+  hs->rho0 = -1.0;
+  LR_CUDA(h, cudaMemcpyAsync(d.st, hs, sizeof(T3State), cudaMemcpyHostToDevice, stm), "3D: init");
+  const double tol = 0.1 * o.aca_tol_factor * o.eps;
+  auto read_state = [&]() -> lr_status {
+    LR_CUDA(h, cudaMemcpyAsync(hs, d.st, sizeof(T3State), cudaMemcpyDeviceToHost, stm), "3D: state");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "3D: cross");
+    if (hs->status) return fail(h, static_cast<lr_status>(hs->status), "3D: non-finite value in the cross");
+    return LR_OK;
+  };
+  const size_t P = T3P, P2 = (size_t)T3P * T3P;
+  auto mp = [&](const double* in, std::array<size_t, 3> is, double* out, std::array<size_t, 3> os,
+                std::array<int, 3> od, int mode, int K, const double* A, const int* rowmap, int ars, int acs,
+                int divlam) -> cudaError_t {
+    T3ModeProd a;
+    a.in = in;
+    a.out = out;
+    for (int k = 0; k < 3; ++k) { a.is[k] = (int)is[k]; a.os[k] = (int)os[k]; a.od[k] = od[k]; }
+    a.mode = mode;
+    a.K = K;
+    a.A = A;
+    a.rowmap = rowmap;
+    a.ars = ars;
+    a.acs = acs;
+    a.divlam = divlam;
+    ++launches;
+    return launch_t3_modeprod(a, d, stm);
+  };
+  bool converged = false;
+  std::vector<int> hjobs;
+  std::vector<int> hI(3 * T3P);
+  for (int step = 0; step < o.rmax; ++step) {
+    // pivot search: two rounds of mode-2, mode-3, mode-1 fibres, then the
+    // mode-2 and mode-3 fibres through the pivot
+    for (int rd = 0; rd < 2; ++rd)
+      for (int m : {1, 2, 0}) LR_CUDA(h, launch_t3_search(d, m, 0, stm), "3D: search");
+    LR_CUDA(h, launch_t3_search(d, 1, 1, stm), "3D: fibre");
+    LR_CUDA(h, launch_t3_search(d, 2, 1, stm), "3D: fibre");
+    LR_CUDA(h, launch_t3_pivot(d, stm), "3D: pivot");
+    LR_CUDA(h, launch_t3_basis_update(d, nmax, stm), "3D: bases");
+    launches += 9 + 7;
+    if ((s = read_state()) != LR_OK) return s;
+    if (hs->done) { converged = hs->converged != 0; break; }
+    if (!hs->negl) {
+      // C = Xh(I1, I2, I3) x_k M_k: Fh on the index grid by three mode
+      // products of G (the last one divided by Lambda), then the inverses
+      const int p0 = hs->p[0], p1 = hs->p[1], p2 = hs->p[2];
+      const std::array<size_t, 3> sg{(size_t)r[1] * r[2], (size_t)r[2], 1}, sc{1, P, P2};
+      LR_CUDA(h, mp(d.G, sg, T1, sc, {p0, r[1], r[2]}, 0, r[0], d.Uh[0], d.I[0], 1, ldq[0], 0), "3D: core");
+      LR_CUDA(h, mp(T1, sc, T2, sc, {p0, p1, r[2]}, 1, r[1], d.Uh[1], d.I[1], 1, ldq[1], 0), "3D: core");
+      LR_CUDA(h, mp(T2, sc, E, sc, {p0, p1, p2}, 2, r[2], d.Uh[2], d.I[2], 1, ldq[2], 1), "3D: core");
+      LR_CUDA(h, mp(E, sc, T1, sc, {p0, p1, p2}, 0, p0, d.Minv[0], nullptr, 1, T3P, 0), "3D: core");
+      LR_CUDA(h, mp(T1, sc, T2, sc, {p0, p1, p2}, 1, p1, d.Minv[1], nullptr, 1, T3P, 0), "3D: core");
+      LR_CUDA(h, mp(T2, sc, d.C, sc, {p0, p1, p2}, 2, p2, d.Minv[2], nullptr, 1, T3P, 0), "3D: core");
+    }
+    LR_CUDA(h, launch_t3_decide(d, tol, stm), "3D: step test");
+    ++launches;
+    if ((s = read_state()) != LR_OK) return s;
+    if (hs->small < 2) continue;
+    if (probes == 0 || hs->probe_rounds >= kT3ProbeRounds) { converged = true; break; }
+    // probe round: random fibres of every mode, then the fibres through the
+    // other two modes' index sets
+    for (int k = 0; k < 3; ++k)
+      if (hs->p[k] > 0)
+        LR_CUDA(h, cudaMemcpyAsync(hI.data() + k * T3P, d.I[k], sizeof(int) * hs->p[k], cudaMemcpyDeviceToHost, stm),
+                "3D: indices");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "3D: indices");
+    const unsigned long long seed = o.seed + (unsigned long long)hs->probe_rounds;
+    hjobs.clear();
+    T3ProbeCounts cnt{};
+    for (int m = 0; m < 3; ++m) {
+      const int oa = m == 0 ? 1 : 0, ob = m == 2 ? 1 : 2;
+      for (int t = 0; t < probes; ++t) {
+        const unsigned long long z = splitmix64_at(seed, (unsigned long long)(m * probes + t + 1));
+        hjobs.insert(hjobs.end(), {m, (int)((z >> 32) % (unsigned long long)n[oa]),
+                                   (int)((z & 0xFFFFFFFFull) % (unsigned long long)n[ob])});
+      }
+      cnt.nrand[m] = probes;
+      for (int x = 0; x < hs->p[oa]; ++x)
+        for (int y = 0; y < hs->p[ob]; ++y) hjobs.insert(hjobs.end(), {m, hI[oa * T3P + x], hI[ob * T3P + y]});
+      cnt.ncross[m] = hs->p[oa] * hs->p[ob];
+    }
+    const int nfib = (int)hjobs.size() / 3;
+    LR_CUDA(h, cudaMemcpyAsync(jobs, hjobs.data(), sizeof(int) * hjobs.size(), cudaMemcpyHostToDevice, stm), "3D: jobs");
+    LR_CUDA(h, launch_t3_probe(d, nfib, jobs, pn2, pam, stm), "3D: probes");
+    LR_CUDA(h, launch_t3_probe_reduce(d, jobs, pn2, pam, cnt, tol, stm), "3D: probes");
+    launches += 2;
+    if ((s = read_state()) != LR_OK) return s;
+    if (hs->done) { converged = true; break; }
+  }
+  // Rounding: higher-order SVD of the core.  For each mode the unfolding's
+  // transpose C_(m)^T = Q R (shifted Cholesky QR); the rounding core on
+  // M = I R^T gives the left singular vectors W_m of C_(m) and its singular
+  // values, truncated with a tail <= eps ||C|| / sqrt(3).
+  const int p[3] = {hs->p[0], hs->p[1], hs->p[2]};
+  {
+    std::vector<double> id(KMAX * KMAX, 0.0);
+    for (int i = 0; i < KMAX; ++i) id[i + i * KMAX] = 1.0;
+    LR_CUDA(h, cudaMemcpyAsync(ident, id.data(), sizeof(double) * id.size(), cudaMemcpyHostToDevice, stm), "3D: identity");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "3D: identity");
+  }
+  int R[3] = {0, 0, 0};
+  bool cut = false;
+  double* A = b.XU;  // lda x 64
+  for (int m = 0; m < 3 && p[0] * p[1] * p[2] > 0; ++m) {
+    const int oa = m == 0 ? 1 : 0, ob = m == 2 ? 1 : 2;
+    const int q = p[m], rows = p[oa] * p[ob];
+    LR_CUDA(h, launch_t3_unfold(d, m, q * rows, A, lda, stm), "3D: unfold");
+    const double shift = 11.0 * ((double)rows * q + (double)q * (q + 1)) * (DBL_EPSILON / 2) * q;
+    const double* X = A;
+    for (int step = 0; step < kQrSteps; ++step) {
+      LR_CUDA(h, launch_gram(X, rows, lda, q, b.G0, q, b.part, h->num_sms, stm), "3D: gram");
+      CholQrArgs a;
+      a.G[0] = b.G0; a.G[1] = b.G0;
+      a.T[0] = b.T0; a.T[1] = b.T1;
+      a.Racc[0] = b.Ra0; a.Racc[1] = b.Ra1;
+      a.qout = b.qout;
+      a.q = q;
+      a.first = step == 0;
+      a.shift = step < kQrShiftedSteps ? shift : 0.0;
+      a.floor_rel = 0.0;
+      LR_CUDA(h, launch_cholqr_step(a, stm), "3D: cholesky qr");
+      launches += 3;
+      if (step + 1 < kQrSteps) {
+        double* Y = (step & 1) ? b.L : b.Lb;
+        LR_CUDA(h, (launch_rotate<double, double>(X, lda, rows, nullptr, q, b.T0, false, &b.qout[0], Y, lda, stm)), "3D: qr");
+        ++launches;
+        X = Y;
+      }
+    }
+    LR_CUDA(h, cudaMemsetAsync(b.st, 0, sizeof(SolveState), stm), "state reset");
+    CoreArgs<double> co;
+    co.GC = ident; co.GR = b.Ra0; co.ldg = KMAX; co.d = nullptr;
+    co.k_dev = nullptr; co.k_host = q;
+    co.eps = o.eps / std::sqrt(3.0); co.rmax_out = std::min(sol->rmax[m], KMAX);
+    co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = sig; co.st = b.st;
+    co.tri_given = 1;
+    LR_CUDA(h, launch_core<double>(co, false, stm), "3D: core SVD");
+    LR_CUDA(h, cudaMemcpyAsync(W[m], b.Tc, sizeof(double) * KMAX * KMAX, cudaMemcpyDeviceToDevice, stm), "3D: W");
+    // kept factor Q_m W_m, transformed back into the caller's U_m
+    LR_CUDA(h, (launch_rotate<double, double>(d.Q[m], ldq[m], n[m], nullptr, q, W[m], false, &b.st->rank, XU, ldq[m], stm)), "3D: rot");
+    launches += 3;
+    LR_CUDA(h, cudaMemcpyAsync(h->h_state, b.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm), "state copy");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "3D: core SVD");
+    if (h->h_state->status) return fail(h, static_cast<lr_status>(h->h_state->status), kNonFiniteMsg);
+    R[m] = h->h_state->rank;
+    if (h->h_state->cut) cut = true;
+    if (R[m] > 0) {
+      ColumnSet cs;
+      cs.in[0] = XU;
+      cs.ld_in[0] = ldq[m];
+      cs.out[0] = sol->U[m];
+      cs.ld_out[0] = sol->ld[m];
+      cs.ncol[0] = R[m];
+      LR_CUDA(h, launch_dst<double>(*plan[m], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm), "3D: inverse");
+      ++launches;
+    }
+  }
+  if (R[0] * R[1] * R[2] > 0) {
+    // G_out = C x_1 W_1^T x_2 W_2^T x_3 W_3^T, written in C order
+    const std::array<size_t, 3> sc{1, P, P2};
+    const std::array<size_t, 3> so{(size_t)R[1] * R[2], (size_t)R[2], 1};
+    LR_CUDA(h, mp(d.C, sc, T1, sc, {R[0], p[1], p[2]}, 0, p[0], W[0], nullptr, KMAX, 1, 0), "3D: core out");
+    LR_CUDA(h, mp(T1, sc, T2, sc, {R[0], R[1], p[2]}, 1, p[1], W[1], nullptr, KMAX, 1, 0), "3D: core out");
+    LR_CUDA(h, mp(T2, sc, sol->G, so, {R[0], R[1], R[2]}, 2, p[2], W[2], nullptr, KMAX, 1, 0), "3D: core out");
+  } else {
+    R[0] = R[1] = R[2] = 0;
+  }
+  LR_CUDA(h, cudaStreamSynchronize(stm), "3D solve");
+  for (int k = 0; k < 3; ++k) sol->r[k] = R[k];
+  h->info = lr_info{};
+  h->info.aca_steps = hs->steps;
+  h->info.probe_rounds = hs->probe_rounds;
+  h->info.converged = converged ? 1 : 0;
+  h->info.rank = std::max(R[0], std::max(R[1], R[2]));
+  h->info.cut = cut ? 1 : 0;
+  h->info.launches = launches;
+  h->info.norm_est = hs->nrmC;
+  // lr_get_info reports from the solve state record
+  SolveState& ss = *h->h_state;
+  ss.k = hs->steps;
+  ss.rank = h->info.rank;
+  ss.converged = h->info.converged;
+  ss.cut = h->info.cut;
+  ss.probe_rounds = hs->probe_rounds;
+  ss.zero_rows = 0;
+  ss.norm2 = hs->nrmC * hs->nrmC;
+  if (cut) return fail(h, LR_ENOCONV, "a Tucker rank exceeds sol->rmax; result truncated");
+  if (!converged) return fail(h, LR_ENOCONV, "3D cross did not converge within rmax steps");
+  return LR_OK;
+}
+
 // Absolute rounding level of the CG residual and direction, in units of
 // eps ||r0|| (the Schur product q: a tenth of it).
 constexpr double kCgFloor = 0.3;
@@ -1406,6 +1714,7 @@ lr_status lr_destroy(lr_handle h) {
   if (h->ws2) cudaFree(h->ws2);
   if (h->ws3) cudaFree(h->ws3);
   if (h->ws4) cudaFree(h->ws4);
+  if (h->ws5) cudaFree(h->ws5);
   if (h->h_big) cudaFreeHost(h->h_big);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_piv) cudaFreeHost(h->h_piv);
@@ -1535,6 +1844,29 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
       !aligned16(p->U) || !aligned16(p->V) || !aligned16(p->s))
     return fail(h, LR_EINVAL, "lr_stokes_uzawa: p must be n x n with U, s, V set and aligned");
   return stokes_uzawa(h, n, f, u, p, tol_div, maxit, o, iters, resid, history);
+}
+
+lr_status lr_poisson3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options* opt) {
+  if (!h) return LR_EINVAL;
+  lr_options o;
+  if (opt) o = *opt; else lr_options_default(&o);
+  lr_status s = check_opts(h, o);
+  if (s != LR_OK) return s;
+  if (o.prec != LR_FP64) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: LR_FP64 only");
+  if (o.op != LR_OP_5PT) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: the 7-point operator (LR_OP_5PT kind) only");
+  if (!rhs || !sol || !rhs->G || !sol->G) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: null rhs, sol or core");
+  for (int k = 0; k < 3; ++k) {
+    if (rhs->n[k] < 1 || rhs->n[k] > 16384) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: n[k] must be in [1, 16384]");
+    if (rhs->r[k] < 1 || rhs->r[k] > KMAX) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: r[k] must be in [1, 64]");
+    if (rhs->ld[k] < rhs->n[k] || sol->ld[k] < rhs->n[k]) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: ld[k] < n[k]");
+    if (sol->n[k] != rhs->n[k]) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: sol->n must equal rhs->n");
+    if (sol->rmax[k] < 1 || sol->rmax[k] > KMAX) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: sol->rmax[k] must be in [1, 64]");
+    if (!rhs->U[k] || !sol->U[k] || !aligned16(rhs->U[k]) || !aligned16(sol->U[k]) || (rhs->ld[k] & 1) ||
+        (sol->ld[k] & 1))
+      return fail(h, LR_EINVAL, "lr_poisson3d_tucker: factors must be 16-byte aligned with even ld");
+  }
+  if (!aligned16(rhs->G) || !aligned16(sol->G)) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: cores must be 16-byte aligned");
+  return solve3d_tucker(h, rhs, sol, o);
 }
 
 lr_status lr_poisson2d_expsum(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt, int* nterms) {

@@ -187,4 +187,70 @@ cudaError_t launch_expsum_cols(int m, int r, int nterms, const double* Uh, const
                                const double* mu, const double* t, const double* w, double* L, double* R, int ldo,
                                int off, cudaStream_t st);
 
+// ---- 3D Tucker solve (tucker.cu) -------------------------------------------
+constexpr int T3P = KMAX;  // largest basis size per mode; stride of core-sized tensors
+
+// Device state of one Tucker cross.
+struct T3State {
+  int pos[3];        // search position (i, j, k)
+  int p[3];          // basis sizes
+  int add[3];        // the step's fibre of this mode enters the basis
+  int negl;          // the step's pivot is negligible
+  int done, converged;
+  int small;         // consecutive steps that passed the step test (2: probe)
+  int probe_rounds;
+  int steps;
+  int status;        // lr_status of a failure (LR_ENONFINITE)
+  double fval[3];    // value at the argmax of the last fibre of each mode
+  double fnrm2[3];   // square norm of that fibre
+  double rho, rho0;  // pivot of the step, size of the first pivot (-1: none yet)
+  double upd, nrmC, est;
+};
+
+struct T3Dev {
+  int n[3], r[3], ldu[3], ldq[3];
+  const double* Uh[3];    // transformed factors of the right-hand side, n_k x r_k (ld ldu)
+  const double* G;        // its core, C order: G[(a r1 + b) r2 + c]
+  const double* mu[3];    // 1D symbols (n_k)
+  double* Q[3];           // bases n_k x T3P (ld ldq)
+  double* Minv[3];        // Q_k(I_k, :)^-1, T3P x T3P column-major
+  int* I[3];              // interpolation indices
+  unsigned char* inI[3];  // membership of I_k (n_k bytes)
+  double* e[3];           // residual fibres of the step
+  double* v[3];           // their working copies (orthogonalisation, DEIM residual)
+  double* h[3];           // Gram-Schmidt coefficients (T3P)
+  double* y[3];           // M_k Q_k(I_k, p_k) (T3P)
+  double* C;              // core, C[x0 + T3P (x1 + T3P x2)]
+  T3State* st;
+};
+
+// out = in x_mode A (see t3_modeprod_kernel).
+struct T3ModeProd {
+  const double* in;
+  int is[3];
+  double* out;
+  int os[3];
+  int od[3];
+  int mode, K;
+  const double* A;
+  const int* rowmap;
+  int ars, acs;
+  int divlam;
+};
+
+struct T3ProbeCounts {
+  int nrand[3];
+  int ncross[3];
+};
+
+cudaError_t launch_t3_search(const T3Dev& d, int m, int keep_pos, cudaStream_t st);
+cudaError_t launch_t3_probe(const T3Dev& d, int nfib, const int* jobs, double* nrm2, int* amax, cudaStream_t st);
+cudaError_t launch_t3_pivot(const T3Dev& d, cudaStream_t st);
+cudaError_t launch_t3_basis_update(const T3Dev& d, int nmax, cudaStream_t st);
+cudaError_t launch_t3_modeprod(const T3ModeProd& a, const T3Dev& d, cudaStream_t st);
+cudaError_t launch_t3_decide(const T3Dev& d, double tol, cudaStream_t st);
+cudaError_t launch_t3_probe_reduce(const T3Dev& d, const int* jobs, const double* nrm2, const int* amax,
+                                   const T3ProbeCounts& c, double tol, cudaStream_t st);
+cudaError_t launch_t3_unfold(const T3Dev& d, int m, int total, double* A, int lda, cudaStream_t st);
+
 }  // namespace lrp

@@ -34,13 +34,18 @@ EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
            "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full",
-           "lr_stokes_uzawa", "lr_poisson2d_expsum")
+           "lr_stokes_uzawa", "lr_poisson2d_expsum", "lr_poisson3d_tucker")
 
 
 class LrMat(ctypes.Structure):
     _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("r", ctypes.c_int),
                 ("rmax", ctypes.c_int), ("ld", ctypes.c_int),
                 ("U", ctypes.c_void_p), ("s", ctypes.c_void_p), ("V", ctypes.c_void_p)]
+
+
+class LrTucker(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("r", ctypes.c_int * 3), ("rmax", ctypes.c_int * 3),
+                ("ld", ctypes.c_int * 3), ("G", ctypes.c_void_p), ("U", ctypes.c_void_p * 3)]
 
 
 class LrOptions(ctypes.Structure):
@@ -128,6 +133,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                     ctypes.POINTER(LrOptions), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
                                     ctypes.POINTER(c_double)]
     lib.lr_stokes_uzawa.restype = c_int
+    lib.lr_poisson3d_tucker.argtypes = [c_void_p, ctypes.POINTER(LrTucker), ctypes.POINTER(LrTucker),
+                                        ctypes.POINTER(LrOptions)]
+    lib.lr_poisson3d_tucker.restype = c_int
     lib.lr_poisson2d_expsum.argtypes = [c_void_p, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                         ctypes.POINTER(LrOptions), ctypes.POINTER(c_int)]
     lib.lr_poisson2d_expsum.restype = c_int
@@ -518,3 +526,51 @@ def lr_poisson2d_expsum(h: Handle, U, V, eps: float = 1e-7, rmax_out: int = 64):
         raise LrError(st, h.last_error())
     R = sol.r
     return Uo[:, :R], so[:R], Vo[:, :R], q.value
+
+
+@dataclass
+class TuckerResult:
+    G: object        # core (R0, R1, R2), device float64
+    U: list          # factors n_k x R_k with orthonormal columns
+    steps: int       # cross steps
+    probe_rounds: int
+    status: int
+
+
+def lr_poisson3d_tucker(h: Handle, G, U1, U2, U3, eps: float = 1e-6, rmax: int = 64, rmax_out: int = 64,
+                        aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
+                        check: bool = True) -> TuckerResult:
+    """Low-rank 3D solve (float64): the right-hand side in Tucker format, core
+    G (r0, r1, r2) and factors U_k (n_k x r_k), device float64 tensors."""
+    import torch
+    G = G.contiguous()
+    Us = []
+    for U in (U1, U2, U3):
+        U = as_colmajor(U)
+        if _ld(U) % 2:
+            U2_ = colmajor_empty(U.shape[0], U.shape[1], U.device)
+            U2_.copy_(U)
+            U = U2_
+        Us.append(U)
+    dev = G.device
+    ns = [U.shape[0] for U in Us]
+    rs = list(G.shape)
+    outs = [colmajor_empty(n, rmax_out, dev) for n in ns]
+    Go = torch.empty(rmax_out ** 3, dtype=torch.float64, device=dev)
+    rhs = LrTucker()
+    sol = LrTucker()
+    for k in range(3):
+        rhs.n[k] = ns[k]; rhs.r[k] = rs[k]; rhs.rmax[k] = rs[k]; rhs.ld[k] = _ld(Us[k]); rhs.U[k] = Us[k].data_ptr()
+        sol.n[k] = ns[k]; sol.r[k] = 0; sol.rmax[k] = rmax_out; sol.ld[k] = _ld(outs[k]); sol.U[k] = outs[k].data_ptr()
+    rhs.G = G.data_ptr()
+    sol.G = Go.data_ptr()
+    o = _options(eps, "fp64", "5pt", rmax, aca_tol_factor, probes, seed, 0, 0)
+    st = load().lr_poisson3d_tucker(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o))
+    if check and st not in (LR_OK,):
+        raise LrError(st, h.last_error())
+    R = [sol.r[k] for k in range(3)]
+    info = LrInfo()
+    load().lr_get_info(h.ptr, ctypes.byref(info), None, None, 0)
+    steps, pr = info.aca_steps, info.probe_rounds
+    return TuckerResult(Go[:R[0] * R[1] * R[2]].view(R[0], R[1], R[2]) if min(R) > 0 else Go[:0].view(0, 0, 0),
+                        [outs[k][:, :R[k]] for k in range(3)], steps, pr, st)
