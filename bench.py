@@ -352,10 +352,12 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
             flush.fill_(i & 0xFF)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push(f"tucker3d_n{nt}")  # profiler range (ncu --nvtx-include)
             a.record(stream)
             r0 = lr.lr_poisson3d_tucker(h, *d3, eps=1e-6, check=False)
             b.record(stream)
             stream.synchronize()
+            torch.cuda.nvtx.range_pop()
             per.append(a.elapsed_time(b))
         results["tucker"].append({"n": nt, "ms": round(statistics.median(per), 3), "status": r0.status,
                                   "rhs_ranks": list(G3.shape), "solution_ranks": list(r0.G.shape),

@@ -1175,6 +1175,8 @@ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long t) 
 
 constexpr int kT3ProbeRounds = 4;
 
+int q_cap(int p) { return p < 1 ? 1 : p; }
+
 lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options& o) {
   cudaStream_t stm = h->stream;
   Plan* plan[3];
@@ -1195,10 +1197,10 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
   const int lda = T3P * T3P;  // unfoldings: at most 64 x 64 rows
   const size_t cube = sizeof(double) * (size_t)T3P * T3P * T3P;
   T3Dev d{};
-  double *T1 = nullptr, *T2 = nullptr, *E = nullptr, *ident = nullptr, *W[3] = {}, *sig = nullptr, *XU = nullptr;
+  double *T1 = nullptr, *T2 = nullptr, *E = nullptr, *ident = nullptr, *W[3] = {}, *sig[3] = {}, *XU[3] = {};
   int *jobs = nullptr, *pam = nullptr;
   double* pn2 = nullptr;
-  RefineBufs b;
+  RefineBufs b3[3];
   auto layout = [&](Carve& c) {
     for (int k = 0; k < 3; ++k) {
       d.Uh[k] = c.take<double>(sizeof(double) * (size_t)ldq[k] * r[k]);
@@ -1221,9 +1223,11 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
     pn2 = c.take<double>(sizeof(double) * (size_t)maxjobs);
     pam = c.take<int>(sizeof(int) * (size_t)maxjobs);
     ident = c.take<double>(sizeof(double) * KMAX * KMAX);
-    sig = c.take<double>(sizeof(double) * KMAX);
-    XU = c.take<double>(sizeof(double) * (size_t)(nmax + 1) * KMAX);
-    carve_refine(c, b, lda, lda);  // Cholesky QR of the unfoldings (b.L, b.Lb: lda x 64)
+    for (int k = 0; k < 3; ++k) {
+      sig[k] = c.take<double>(sizeof(double) * KMAX);
+      XU[k] = c.take<double>(sizeof(double) * (size_t)ldq[k] * KMAX);
+      carve_refine(c, b3[k], lda, lda);  // Cholesky QR of unfolding k (XU: the unfolding, L, Lb: lda x 64)
+    }
   };
   Carve sizing;
   layout(sizing);
@@ -1299,33 +1303,50 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
   bool converged = false;
   std::vector<int> hjobs;
   std::vector<int> hI(3 * T3P);
+  // One step of the cross as a fixed launch sequence (every size it depends
+  // on is read from the device state), captured once as a CUDA graph: the
+  // pivot search, the pivot, the basis updates, the core C = Xh(I1, I2, I3)
+  // x_k M_k (Fh on the index grid by three mode products of G, the last one
+  // divided by Lambda, then the inverses) and the step test.
+  auto step_body = [&](cudaStream_t sq) -> cudaError_t {
+    cudaError_t e;
+    if ((e = launch_t3_search(d, sq)) != cudaSuccess) return e;
+    if ((e = launch_t3_pivot(d, sq)) != cudaSuccess) return e;
+    if ((e = launch_t3_basis_update(d, nmax, sq)) != cudaSuccess) return e;
+    const std::array<size_t, 3> sg{(size_t)r[1] * r[2], (size_t)r[2], 1}, sc{1, P, P2};
+    const int P0 = -1, P1 = -2, P2d = -3;  // device basis sizes p_0, p_1, p_2
+    auto prod = [&](const double* in, std::array<size_t, 3> is, double* out, std::array<int, 3> od, int mode, int K,
+                    const double* Am, const int* rowmap, int acs, int divlam) {
+      T3ModeProd a;
+      a.in = in;
+      a.out = out;
+      for (int k = 0; k < 3; ++k) { a.is[k] = (int)is[k]; a.os[k] = (int)sc[k]; a.od[k] = od[k]; }
+      a.mode = mode;
+      a.K = K;
+      a.A = Am;
+      a.rowmap = rowmap;
+      a.ars = 1;
+      a.acs = acs;
+      a.divlam = divlam;
+      a.skip_negl = 1;
+      return launch_t3_modeprod(a, d, sq);
+    };
+    if ((e = prod(d.G, sg, T1, {P0, r[1], r[2]}, 0, r[0], d.Uh[0], d.I[0], ldq[0], 0)) != cudaSuccess) return e;
+    if ((e = prod(T1, sc, T2, {P0, P1, r[2]}, 1, r[1], d.Uh[1], d.I[1], ldq[1], 0)) != cudaSuccess) return e;
+    if ((e = prod(T2, sc, E, {P0, P1, P2d}, 2, r[2], d.Uh[2], d.I[2], ldq[2], 1)) != cudaSuccess) return e;
+    if ((e = prod(E, sc, T1, {P0, P1, P2d}, 0, P0, d.Minv[0], nullptr, T3P, 0)) != cudaSuccess) return e;
+    if ((e = prod(T1, sc, T2, {P0, P1, P2d}, 1, P1, d.Minv[1], nullptr, T3P, 0)) != cudaSuccess) return e;
+    if ((e = prod(T2, sc, d.C, {P0, P1, P2d}, 2, P2d, d.Minv[2], nullptr, T3P, 0)) != cudaSuccess) return e;
+    return launch_t3_decide(d, tol, sq);
+  };
+  char key[512];
+  snprintf(key, sizeof key, "t3step|%p,%zu|%p|%d,%d,%d|%d,%d,%d|%.17g|%d|%d", h->ws5, h->ws5_bytes, (void*)rhs->G,
+           n[0], n[1], n[2], r[0], r[1], r[2], tol, nmax, probes);
   for (int step = 0; step < o.rmax; ++step) {
-    // pivot search: two rounds of mode-2, mode-3, mode-1 fibres, then the
-    // mode-2 and mode-3 fibres through the pivot
-    for (int rd = 0; rd < 2; ++rd)
-      for (int m : {1, 2, 0}) LR_CUDA(h, launch_t3_search(d, m, 0, stm), "3D: search");
-    LR_CUDA(h, launch_t3_search(d, 1, 1, stm), "3D: fibre");
-    LR_CUDA(h, launch_t3_search(d, 2, 1, stm), "3D: fibre");
-    LR_CUDA(h, launch_t3_pivot(d, stm), "3D: pivot");
-    LR_CUDA(h, launch_t3_basis_update(d, nmax, stm), "3D: bases");
-    launches += 9 + 7;
+    if ((s = run_maybe_graph(h, true, key, step_body)) != LR_OK) return s;
+    launches += 16;
     if ((s = read_state()) != LR_OK) return s;
     if (hs->done) { converged = hs->converged != 0; break; }
-    if (!hs->negl) {
-      // C = Xh(I1, I2, I3) x_k M_k: Fh on the index grid by three mode
-      // products of G (the last one divided by Lambda), then the inverses
-      const int p0 = hs->p[0], p1 = hs->p[1], p2 = hs->p[2];
-      const std::array<size_t, 3> sg{(size_t)r[1] * r[2], (size_t)r[2], 1}, sc{1, P, P2};
-      LR_CUDA(h, mp(d.G, sg, T1, sc, {p0, r[1], r[2]}, 0, r[0], d.Uh[0], d.I[0], 1, ldq[0], 0), "3D: core");
-      LR_CUDA(h, mp(T1, sc, T2, sc, {p0, p1, r[2]}, 1, r[1], d.Uh[1], d.I[1], 1, ldq[1], 0), "3D: core");
-      LR_CUDA(h, mp(T2, sc, E, sc, {p0, p1, p2}, 2, r[2], d.Uh[2], d.I[2], 1, ldq[2], 1), "3D: core");
-      LR_CUDA(h, mp(E, sc, T1, sc, {p0, p1, p2}, 0, p0, d.Minv[0], nullptr, 1, T3P, 0), "3D: core");
-      LR_CUDA(h, mp(T1, sc, T2, sc, {p0, p1, p2}, 1, p1, d.Minv[1], nullptr, 1, T3P, 0), "3D: core");
-      LR_CUDA(h, mp(T2, sc, d.C, sc, {p0, p1, p2}, 2, p2, d.Minv[2], nullptr, 1, T3P, 0), "3D: core");
-    }
-    LR_CUDA(h, launch_t3_decide(d, tol, stm), "3D: step test");
-    ++launches;
-    if ((s = read_state()) != LR_OK) return s;
     if (hs->small < 2) continue;
     if (probes == 0 || hs->probe_rounds >= kT3ProbeRounds) { converged = true; break; }
     // probe round: random fibres of every mode, then the fibres through the
@@ -1371,59 +1392,76 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
   }
   int R[3] = {0, 0, 0};
   bool cut = false;
-  double* A = b.XU;  // lda x 64
-  for (int m = 0; m < 3 && p[0] * p[1] * p[2] > 0; ++m) {
-    const int oa = m == 0 ? 1 : 0, ob = m == 2 ? 1 : 2;
-    const int q = p[m], rows = p[oa] * p[ob];
-    LR_CUDA(h, launch_t3_unfold(d, m, q * rows, A, lda, stm), "3D: unfold");
-    const double shift = 11.0 * ((double)rows * q + (double)q * (q + 1)) * (DBL_EPSILON / 2) * q;
-    const double* X = A;
-    for (int step = 0; step < kQrSteps; ++step) {
-      LR_CUDA(h, launch_gram(X, rows, lda, q, b.G0, q, b.part, h->num_sms, stm), "3D: gram");
-      CholQrArgs a;
-      a.G[0] = b.G0; a.G[1] = b.G0;
-      a.T[0] = b.T0; a.T[1] = b.T1;
-      a.Racc[0] = b.Ra0; a.Racc[1] = b.Ra1;
-      a.qout = b.qout;
-      a.q = q;
-      a.first = step == 0;
-      a.shift = step < kQrShiftedSteps ? shift : 0.0;
-      a.floor_rel = 0.0;
-      LR_CUDA(h, launch_cholqr_step(a, stm), "3D: cholesky qr");
-      launches += 3;
-      if (step + 1 < kQrSteps) {
-        double* Y = (step & 1) ? b.L : b.Lb;
-        LR_CUDA(h, (launch_rotate<double, double>(X, lda, rows, nullptr, q, b.T0, false, &b.qout[0], Y, lda, stm)), "3D: qr");
-        ++launches;
-        X = Y;
+  if (p[0] * p[1] * p[2] > 0) {
+    // the three modes are independent: one stream each, with their own scratch
+    if ((s = ensure_batch_streams(h)) != LR_OK) return s;
+    LR_CUDA(h, cudaEventRecord(h->bfork, stm), "3D: fork");
+    for (int m = 0; m < 3; ++m) {
+      cudaStream_t sm = h->bstreams[m];
+      const RefineBufs& b = b3[m];
+      double* A = b.XU;  // lda x 64
+      LR_CUDA(h, cudaStreamWaitEvent(sm, h->bfork, 0), "3D: fork");
+      const int oa = m == 0 ? 1 : 0, ob = m == 2 ? 1 : 2;
+      const int q = p[m], rows = p[oa] * p[ob];
+      LR_CUDA(h, launch_t3_unfold(d, m, q * rows, A, lda, sm), "3D: unfold");
+      const double shift = 11.0 * ((double)rows * q + (double)q * (q + 1)) * (DBL_EPSILON / 2) * q;
+      const double* X = A;
+      for (int step = 0; step < kQrSteps; ++step) {
+        LR_CUDA(h, launch_gram(X, rows, lda, q, b.G0, q, b.part, h->num_sms, sm), "3D: gram");
+        CholQrArgs a;
+        a.G[0] = b.G0; a.G[1] = b.G0;
+        a.T[0] = b.T0; a.T[1] = b.T1;
+        a.Racc[0] = b.Ra0; a.Racc[1] = b.Ra1;
+        a.qout = b.qout;
+        a.q = q;
+        a.first = step == 0;
+        a.shift = step < kQrShiftedSteps ? shift : 0.0;
+        a.floor_rel = 0.0;
+        LR_CUDA(h, launch_cholqr_step(a, sm), "3D: cholesky qr");
+        launches += 3;
+        if (step + 1 < kQrSteps) {
+          double* Y = (step & 1) ? b.L : b.Lb;
+          LR_CUDA(h, (launch_rotate<double, double>(X, lda, rows, nullptr, q, b.T0, false, &b.qout[0], Y, lda, sm)), "3D: qr");
+          ++launches;
+          X = Y;
+        }
       }
+      LR_CUDA(h, cudaMemsetAsync(b.st, 0, sizeof(SolveState), sm), "state reset");
+      CoreArgs<double> co;
+      co.GC = ident; co.GR = b.Ra0; co.ldg = KMAX; co.d = nullptr;
+      co.k_dev = nullptr; co.k_host = q;
+      co.eps = o.eps / std::sqrt(3.0); co.rmax_out = std::min(sol->rmax[m], KMAX);
+      co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = sig[m]; co.st = b.st;
+      co.tri_given = 1;
+      LR_CUDA(h, launch_core<double>(co, false, sm), "3D: core SVD");
+      LR_CUDA(h, cudaMemcpyAsync(W[m], b.Tc, sizeof(double) * KMAX * KMAX, cudaMemcpyDeviceToDevice, sm), "3D: W");
+      // kept factor Q_m W_m (its rank read on the device)
+      LR_CUDA(h, (launch_rotate<double, double>(d.Q[m], ldq[m], n[m], nullptr, q, W[m], false, &b.st->rank, XU[m], ldq[m], sm)), "3D: rot");
+      launches += 3;
+      LR_CUDA(h, cudaEventRecord(h->bjoin[m], sm), "3D: join");
+      LR_CUDA(h, cudaStreamWaitEvent(stm, h->bjoin[m], 0), "3D: join");
     }
-    LR_CUDA(h, cudaMemsetAsync(b.st, 0, sizeof(SolveState), stm), "state reset");
-    CoreArgs<double> co;
-    co.GC = ident; co.GR = b.Ra0; co.ldg = KMAX; co.d = nullptr;
-    co.k_dev = nullptr; co.k_host = q;
-    co.eps = o.eps / std::sqrt(3.0); co.rmax_out = std::min(sol->rmax[m], KMAX);
-    co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = sig; co.st = b.st;
-    co.tri_given = 1;
-    LR_CUDA(h, launch_core<double>(co, false, stm), "3D: core SVD");
-    LR_CUDA(h, cudaMemcpyAsync(W[m], b.Tc, sizeof(double) * KMAX * KMAX, cudaMemcpyDeviceToDevice, stm), "3D: W");
-    // kept factor Q_m W_m, transformed back into the caller's U_m
-    LR_CUDA(h, (launch_rotate<double, double>(d.Q[m], ldq[m], n[m], nullptr, q, W[m], false, &b.st->rank, XU, ldq[m], stm)), "3D: rot");
-    launches += 3;
-    LR_CUDA(h, cudaMemcpyAsync(h->h_state, b.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm), "state copy");
-    LR_CUDA(h, cudaStreamSynchronize(stm), "3D: core SVD");
-    if (h->h_state->status) return fail(h, static_cast<lr_status>(h->h_state->status), kNonFiniteMsg);
-    R[m] = h->h_state->rank;
-    if (h->h_state->cut) cut = true;
-    if (R[m] > 0) {
+    // inverse transforms of the kept factors into the caller's U_m (on the
+    // handle's stream: they share the transform scratch)
+    for (int m = 0; m < 3; ++m) {
       ColumnSet cs;
-      cs.in[0] = XU;
+      cs.in[0] = XU[m];
       cs.ld_in[0] = ldq[m];
       cs.out[0] = sol->U[m];
       cs.ld_out[0] = sol->ld[m];
-      cs.ncol[0] = R[m];
+      cs.ncol[0] = std::min(sol->rmax[m], q_cap(p[m]));
+      cs.dyn_count = &b3[m].st->rank;
       LR_CUDA(h, launch_dst<double>(*plan[m], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm), "3D: inverse");
       ++launches;
+    }
+    SolveState* hst = reinterpret_cast<SolveState*>(h->h_big + 512);
+    for (int m = 0; m < 3; ++m)
+      LR_CUDA(h, cudaMemcpyAsync(hst + m, b3[m].st, sizeof(SolveState), cudaMemcpyDeviceToHost, stm), "state copy");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "3D: rounding");
+    for (int m = 0; m < 3; ++m) {
+      if (hst[m].status) return fail(h, static_cast<lr_status>(hst[m].status), kNonFiniteMsg);
+      R[m] = hst[m].rank;
+      if (hst[m].cut) cut = true;
     }
   }
   if (R[0] * R[1] * R[2] > 0) {

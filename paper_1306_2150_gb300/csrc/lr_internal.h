@@ -236,6 +236,7 @@ struct T3ModeProd {
   const int* rowmap;
   int ars, acs;
   int divlam;
+  int skip_negl = 0;
 };
 
 struct T3ProbeCounts {
@@ -243,7 +244,7 @@ struct T3ProbeCounts {
   int ncross[3];
 };
 
-cudaError_t launch_t3_search(const T3Dev& d, int m, int keep_pos, cudaStream_t st);
+cudaError_t launch_t3_search(const T3Dev& d, cudaStream_t st);
 cudaError_t launch_t3_probe(const T3Dev& d, int nfib, const int* jobs, double* nrm2, int* amax, cudaStream_t st);
 cudaError_t launch_t3_pivot(const T3Dev& d, cudaStream_t st);
 cudaError_t launch_t3_basis_update(const T3Dev& d, int nmax, cudaStream_t st);

@@ -14,7 +14,13 @@
 //     Q_3(k, :)) costs O(p^3 + r^3 + n (p + r)).
 // float64 throughout.  Tensors of the core's size are stored with mode 0
 // fastest and stride T3P per mode: X[x0 + T3P (x1 + T3P x2)].
+#include <algorithm>
+
+#include <cooperative_groups.h>
+
 #include "lr_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace lrp {
 
@@ -148,22 +154,164 @@ __device__ void t3_fibre(const T3Dev& d, FibreSmem& S, int m, int a, int b, cons
   }
 }
 
-// The search fibre of mode m at the current position; its argmax becomes the
-// position's mode-m coordinate unless keep_pos.
-__global__ void __launch_bounds__(FT) t3_search_kernel(T3Dev d, int m, int keep_pos) {
-  __shared__ FibreSmem S;
-  if (d.st->done || d.st->status) return;
+// ---------------------------------------------------------------------------
+// The pivot search of one step, on one thread-block cluster of SCS CTAs:
+// two rounds of the mode-2, mode-3 and mode-1 fibres (each fibre's argmax
+// becoming the position's coordinate in its mode), then the mode-2 and
+// mode-3 fibres through the pivot.  Per fibre, the contraction outputs
+// c = C x qa x qb and g = G x ua x ub are spread over the cluster's warps and
+// gathered through distributed shared memory, the n entries are split in
+// contiguous chunks over the CTAs, and the per-CTA (square norm, argmax)
+// partials are combined in rank order by every CTA, so all take the same
+// decision.  float64 runs at a few FMAs per clock per SM on this part: one
+// SM per fibre would make the search the slowest step of the solve.
+// ---------------------------------------------------------------------------
+constexpr int SCS = 8;          // CTAs in the search cluster
+constexpr int SNW = FT / 32;    // warps per CTA
+
+struct SearchSmem {
+  double qa[T3P], qb[T3P], ua[T3P], ub[T3P];
+  double item[2 * T3P];         // contraction outputs computed here (c, then g)
+  double cvec[T3P], gvec[T3P];
+  RedSmem red;
+  double ps, pa, pv;            // this CTA's partial: square norm, |max|, value
+  int pi;                       // and index of the max
+  int pos[3];
+  int bad;
+};
+
+__device__ void cluster_fibre(const T3Dev& d, SearchSmem& S, cg::cluster_group& cl, int m, int a, int b,
+                              double* e_out, double* v_out, double* nrm2, int* amax, double* vmax) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rank = (int)cl.block_rank();
   int oa, ob;
   other_modes(m, oa, ob);
-  const int a = d.st->pos[oa], b = d.st->pos[ob];
-  double nrm2 = 0.0, v = 0.0;
-  int am = 0;
-  t3_fibre(d, S, m, a, b, nullptr, d.e[m], d.v[m], &nrm2, &am, &v);
-  if (threadIdx.x == 0) {
-    d.st->fnrm2[m] = nrm2;
-    d.st->fval[m] = v;
-    if (!keep_pos) d.st->pos[m] = am;
+  const int pm = d.st->p[m], pa = d.st->p[oa], pb = d.st->p[ob];
+  const int rm = d.r[m], ra = d.r[oa], rb = d.r[ob];
+  if (tid == 0) S.bad = 0;
+  for (int x = tid; x < T3P; x += FT) {
+    S.qa[x] = x < pa ? d.Q[oa][a + (size_t)x * d.ldq[oa]] : 0.0;
+    S.qb[x] = x < pb ? d.Q[ob][b + (size_t)x * d.ldq[ob]] : 0.0;
+    S.ua[x] = x < ra ? d.Uh[oa][a + (size_t)x * d.ldu[oa]] : 0.0;
+    S.ub[x] = x < rb ? d.Uh[ob][b + (size_t)x * d.ldu[ob]] : 0.0;
   }
+  __syncthreads();
+  // item t < pm: c[t]; pm <= t < pm + rm: g[t - pm]; one warp per item
+  const size_t sc[3] = {1, (size_t)T3P, (size_t)T3P * T3P};
+  const size_t sg[3] = {(size_t)d.r[1] * d.r[2], (size_t)d.r[2], 1};
+  const int items = pm + rm;
+  for (int t = rank * SNW + warp; t < items; t += SCS * SNW) {
+    double acc = 0.0;
+    if (t < pm) {
+      const double* c = d.C + t * sc[m];
+      for (int w = lane; w < pa * pb; w += 32) {
+        const int xa = w % pa, xb = w / pa;
+        acc += c[xa * sc[oa] + xb * sc[ob]] * S.qa[xa] * S.qb[xb];
+      }
+    } else {
+      const double* g = d.G + (t - pm) * sg[m];
+      for (int w = lane; w < ra * rb; w += 32) {
+        const int ya = w % ra, yb = w / ra;
+        acc += g[ya * sg[oa] + yb * sg[ob]] * S.ua[ya] * S.ub[yb];
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) S.item[t] = acc;
+  }
+  cl.sync();
+  for (int t = tid; t < items; t += FT) {
+    const int owner = (t % (SCS * SNW)) / SNW;
+    const double v = *cl.map_shared_rank(&S.item[t], owner);
+    if (t < pm) S.cvec[t] = v;
+    else S.gvec[t - pm] = v;
+  }
+  __syncthreads();
+  const int n = d.n[m];
+  const int chunk = (n + SCS - 1) / SCS;
+  const int i0 = rank * chunk, i1 = min(n, i0 + chunk);
+  const double lab = d.mu[oa][a] + d.mu[ob][b];
+  const double* U = d.Uh[m];
+  const double* Qm = d.Q[m];
+  const double* mu = d.mu[m];
+  double s2 = 0.0, best = -1.0, bestv = 0.0;
+  int besti = -1;
+  for (int i = i0 + tid; i < i1; i += FT) {
+    double f = 0.0;
+    for (int y = 0; y < rm; ++y) f += U[i + (size_t)y * d.ldu[m]] * S.gvec[y];
+    double yv = 0.0;
+    for (int x = 0; x < pm; ++x) yv += Qm[i + (size_t)x * d.ldq[m]] * S.cvec[x];
+    const double val = f / (mu[i] + lab) - yv;
+    if (!isfinite(val)) S.bad = 1;
+    e_out[i] = val;
+    v_out[i] = val;
+    s2 += val * val;
+    const double av = fabs(val);
+    if (av > best) { best = av; bestv = val; besti = i; }
+  }
+  block_reduce(S.red, s2, best, bestv, besti);
+  if (tid == 0) {
+    S.ps = S.red.s[0];
+    S.pa = S.red.a[0];
+    S.pv = S.red.v[0];
+    S.pi = S.red.i[0];
+    if (S.bad) d.st->status = LR_ENONFINITE;
+  }
+  cl.sync();
+  if (tid < 32) {
+    // lane r < SCS reads rank r's partial; then a fixed tree over the lanes
+    // (rank order: the chunks of lower ranks hold the lower indices)
+    double ps = 0.0, ar = -1.0, vr = 0.0;
+    int ir = -1;
+    if (lane < SCS) {
+      ps = *cl.map_shared_rank(&S.ps, lane);
+      ar = *cl.map_shared_rank(&S.pa, lane);
+      vr = *cl.map_shared_rank(&S.pv, lane);
+      ir = *cl.map_shared_rank(&S.pi, lane);
+    }
+    for (int o = 1; o < SCS; o <<= 1) {
+      const double ps2 = __shfl_down_sync(0xffffffffu, ps, o);
+      const double a2 = __shfl_down_sync(0xffffffffu, ar, o);
+      const double v2 = __shfl_down_sync(0xffffffffu, vr, o);
+      const int i2 = __shfl_down_sync(0xffffffffu, ir, o);
+      if ((lane & (2 * o - 1)) == 0) {
+        ps += ps2;
+        if (a2 > ar || (a2 == ar && i2 >= 0 && (ir < 0 || i2 < ir))) { ar = a2; vr = v2; ir = i2; }
+      }
+    }
+    if (lane == 0) {
+      *nrm2 = ps;
+      *amax = ir >= 0 ? ir : 0;
+      *vmax = vr;
+    }
+  }
+  cl.sync();  // partials and items read before the next fibre overwrites them
+}
+
+__global__ void __launch_bounds__(FT) t3_search_kernel(T3Dev d) {
+  __shared__ SearchSmem S;
+  cg::cluster_group cl = cg::this_cluster();
+  if (d.st->done || d.st->status) return;  // the same for every CTA of the cluster
+  const int rank = (int)cl.block_rank();
+  if (threadIdx.x < 3) S.pos[threadIdx.x] = d.st->pos[threadIdx.x];
+  __syncthreads();
+  const int seq[8] = {1, 2, 0, 1, 2, 0, 1, 2};
+  for (int t = 0; t < 8; ++t) {
+    const int m = seq[t];
+    int oa, ob;
+    other_modes(m, oa, ob);
+    double nrm2 = 0.0, v = 0.0;
+    int a2 = 0;
+    cluster_fibre(d, S, cl, m, S.pos[oa], S.pos[ob], d.e[m], d.v[m], &nrm2, &a2, &v);
+    if (threadIdx.x == 0) {
+      if (rank == 0) {
+        d.st->fnrm2[m] = nrm2;
+        d.st->fval[m] = v;
+      }
+      if (t < 6) S.pos[m] = a2;
+    }
+    __syncthreads();
+  }
+  if (rank == 0 && threadIdx.x < 3) d.st->pos[threadIdx.x] = S.pos[threadIdx.x];
 }
 
 // Probe fibres from a job list (mode, a, b): square norm and argmax of each.
@@ -309,13 +457,20 @@ __global__ void __launch_bounds__(FT) t3_deimpick_kernel(T3Dev d) {
 // out = in x_mode A: out[.., i, ..] = sum_{x < K} A(i, x) in[.., x, ..] with
 // A(i, x) = A[rowmap(i) * ars + x * acs] (rowmap null: i); optionally divided
 // by mu0[I0[x0]] + mu1[I1[x1]] + mu2[I2[x2]].
+// A negative dimension -1 - k (od or K) stands for the basis size p_k of the
+// state; with skip_negl the product is not formed on a step whose pivot was
+// negligible (the core is unchanged).
 __global__ void t3_modeprod_kernel(T3ModeProd a, T3Dev d) {
-  const size_t total = (size_t)a.od[0] * a.od[1] * a.od[2];
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total || d.st->status) return;
-  const int x0 = (int)(t % a.od[0]);
-  const int x1 = (int)((t / a.od[0]) % a.od[1]);
-  const int x2 = (int)(t / ((size_t)a.od[0] * a.od[1]));
+  const T3State* s = d.st;
+  if (s->status || (a.skip_negl && (s->negl || s->done))) return;
+  int od[3];
+  for (int k = 0; k < 3; ++k) od[k] = a.od[k] >= 0 ? a.od[k] : s->p[-1 - a.od[k]];
+  const int K = a.K >= 0 ? a.K : s->p[-1 - a.K];
+  const size_t total = (size_t)od[0] * od[1] * od[2];
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+  const int x0 = (int)(t % od[0]);
+  const int x1 = (int)((t / od[0]) % od[1]);
+  const int x2 = (int)(t / ((size_t)od[0] * od[1]));
   const int xo[3] = {x0, x1, x2};
   const int i = xo[a.mode];
   size_t base = 0;
@@ -323,9 +478,10 @@ __global__ void t3_modeprod_kernel(T3ModeProd a, T3Dev d) {
     if (k != a.mode) base += (size_t)xo[k] * a.is[k];
   const size_t arow = (size_t)(a.rowmap ? a.rowmap[i] : i) * a.ars;
   double acc = 0.0;
-  for (int x = 0; x < a.K; ++x) acc += a.A[arow + (size_t)x * a.acs] * a.in[base + (size_t)x * a.is[a.mode]];
+  for (int x = 0; x < K; ++x) acc += a.A[arow + (size_t)x * a.acs] * a.in[base + (size_t)x * a.is[a.mode]];
   if (a.divlam) acc /= d.mu[0][d.I[0][x0]] + d.mu[1][d.I[1][x1]] + d.mu[2][d.I[2][x2]];
   a.out[(size_t)x0 * a.os[0] + (size_t)x1 * a.os[1] + (size_t)x2 * a.os[2]] = acc;
+  }
 }
 
 // End of a step: ||C||_F, the step test, and the next search start (the
@@ -367,31 +523,41 @@ __global__ void __launch_bounds__(FT) t3_decide_kernel(T3Dev d, double tol) {
 
 // Probe round: the estimates of ||R||_F from the random fibres (mean square
 // norm times the number of fibres of the mode) and from the cross fibres
-// (root of the sum), the largest fibre, and the decision.  counts[m] =
-// {random fibres, cross fibres} of mode m, in job order.
-__global__ void t3_probe_reduce_kernel(T3Dev d, const int* __restrict__ jobs, const double* __restrict__ nrm2,
-                                       const int* __restrict__ amax, T3ProbeCounts cnt, double tol) {
-  if (threadIdx.x != 0) return;
+// (root of the sum), the largest fibre (first in job order on ties), and the
+// decision.  counts: random and cross fibres of each mode, in job order.
+// One CTA; every sum is a fixed-order block reduction.
+__global__ void __launch_bounds__(FT) t3_probe_reduce_kernel(T3Dev d, const int* __restrict__ jobs,
+                                                               const double* __restrict__ nrm2,
+                                                               const int* __restrict__ amax, T3ProbeCounts cnt,
+                                                               double tol) {
+  __shared__ RedSmem R;
+  __shared__ double est;
+  const int tid = threadIdx.x;
   T3State* s = d.st;
-  double est = 0.0, worst = -1.0;
-  int wf = -1;
-  int f = 0;
-  for (int m = 0; m < 3; ++m) {
-    int oa, ob;
-    other_modes(m, oa, ob);
-    double ss = 0.0;
-    for (int t = 0; t < cnt.nrand[m]; ++t, ++f) {
-      ss += nrm2[f];
-      if (nrm2[f] > worst) { worst = nrm2[f]; wf = f; }
+  if (tid == 0) est = 0.0;
+  int f0 = 0;
+  for (int seg = 0; seg < 6; ++seg) {
+    const int m = seg / 2;
+    const int len = (seg & 1) ? cnt.ncross[m] : cnt.nrand[m];
+    double acc = 0.0;
+    for (int f = f0 + tid; f < f0 + len; f += FT) acc += nrm2[f];
+    block_reduce(R, acc, 0.0, 0.0, -1);
+    if (tid == 0 && len > 0) {
+      int oa, ob;
+      other_modes(m, oa, ob);
+      const double e = (seg & 1) ? sqrt(R.s[0]) : sqrt(R.s[0] * (double)d.n[oa] * (double)d.n[ob] / len);
+      est = fmax(est, e);
     }
-    if (cnt.nrand[m] > 0) est = fmax(est, sqrt(ss * (double)d.n[oa] * (double)d.n[ob] / cnt.nrand[m]));
-    ss = 0.0;
-    for (int t = 0; t < cnt.ncross[m]; ++t, ++f) {
-      ss += nrm2[f];
-      if (nrm2[f] > worst) { worst = nrm2[f]; wf = f; }
-    }
-    est = fmax(est, sqrt(ss));
+    __syncthreads();
+    f0 += len;
   }
+  double best = -1.0;
+  int bi = -1;
+  for (int f = tid; f < f0; f += FT)
+    if (nrm2[f] > best) { best = nrm2[f]; bi = f; }
+  block_reduce(R, 0.0, best, 0.0, bi);
+  if (tid != 0) return;
+  const int wf = R.i[0];
   s->est = est;
   s->probe_rounds += 1;
   if (est <= tol * s->nrmC) {
@@ -430,9 +596,20 @@ __global__ void t3_unfold_kernel(T3Dev d, int m, double* __restrict__ A, int lda
 
 #define T3_LAUNCH_CHECK() return cudaGetLastError()
 
-cudaError_t launch_t3_search(const T3Dev& d, int m, int keep_pos, cudaStream_t st) {
-  t3_search_kernel<<<1, FT, 0, st>>>(d, m, keep_pos);
-  T3_LAUNCH_CHECK();
+cudaError_t launch_t3_search(const T3Dev& d, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(SCS, 1, 1);
+  cfg.blockDim = dim3(FT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = SCS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, t3_search_kernel, d);
 }
 
 cudaError_t launch_t3_probe(const T3Dev& d, int nfib, const int* jobs, double* nrm2, int* amax, cudaStream_t st) {
@@ -459,9 +636,13 @@ cudaError_t launch_t3_basis_update(const T3Dev& d, int nmax, cudaStream_t st) {
 }
 
 cudaError_t launch_t3_modeprod(const T3ModeProd& a, const T3Dev& d, cudaStream_t st) {
-  const size_t total = (size_t)a.od[0] * a.od[1] * a.od[2];
+  size_t total = 1;  // upper bound: a basis size is at most T3P
+  for (int k = 0; k < 3; ++k) total *= (size_t)(a.od[k] >= 0 ? a.od[k] : T3P);
   if (total == 0) return cudaSuccess;
-  t3_modeprod_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a, d);
+  // grid-stride over a grid of at most 256 CTAs (the sizes read on the device
+  // are usually far below the bound)
+  const size_t blocks = std::min<size_t>((total + 255) / 256, 256);
+  t3_modeprod_kernel<<<(unsigned)blocks, 256, 0, st>>>(a, d);
   T3_LAUNCH_CHECK();
 }
 
@@ -472,7 +653,7 @@ cudaError_t launch_t3_decide(const T3Dev& d, double tol, cudaStream_t st) {
 
 cudaError_t launch_t3_probe_reduce(const T3Dev& d, const int* jobs, const double* nrm2, const int* amax,
                                    const T3ProbeCounts& c, double tol, cudaStream_t st) {
-  t3_probe_reduce_kernel<<<1, 32, 0, st>>>(d, jobs, nrm2, amax, c, tol);
+  t3_probe_reduce_kernel<<<1, FT, 0, st>>>(d, jobs, nrm2, amax, c, tol);
   T3_LAUNCH_CHECK();
 }
 
