@@ -57,6 +57,10 @@ def parse():
                         "would skew the tuner's timings)")
     p.add_argument("--stokes", type=int, nargs="*", default=[1024, 4096, 8192],
                    help="cells per direction of the low-rank Uzawa Stokes runs")
+    p.add_argument("--stokes-gmres", type=int, nargs="*", default=[],
+                   help="cells per direction of the Stokes runs with inexact GMRES (Section 5) besides CG")
+    p.add_argument("--uneven", type=int, default=512,
+                   help="problems in the uneven batch (n log-uniform in [512, 16384], r in 1..32; 0: skip)")
     p.add_argument("--tucker", type=int, nargs="*", default=[128, 256, 512, 1024],
                    help="grid sizes of the 3D Tucker solves (eps = 1e-6, float64)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
@@ -319,23 +323,27 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     # ---- low-rank Uzawa Stokes (semi-staggered grids, body force of rank 1
     # per component, truncation eps = 1e-7, stop at the Schur residual 1e-6)
     results["stokes"] = []
-    for ns in args.stokes:
+    for ns in list(args.stokes) + [g for g in args.stokes_gmres if g not in args.stokes]:
         x = np.arange(1, ns) / ns
         fs = [(torch.from_numpy(np.sin(np.pi * x)[:, None]).cuda(), torch.from_numpy(np.cos(np.pi * x)[:, None]).cuda()),
               (torch.from_numpy(-np.cos(np.pi * x)[:, None]).cuda(),
                torch.from_numpy((np.sin(np.pi * x) * (1.0 + x))[:, None]).cuda())]
         row = {"n": ns}
-        for prec in ("mixed", "fp64"):
+        variants = [("mixed", False), ("fp64", False)]
+        if ns in args.stokes_gmres:
+            variants += [("fp64", True), ("mixed", True)]
+        for prec, gm in variants:
             mi = 60 if prec == "mixed" else 200  # mixed stalls above n = 256 (float32 noise through B^T)
-            lr.lr_stokes_uzawa(h, ns, fs, tol_div=1e-6, eps=1e-7, prec=prec, maxit=mi, check=False)  # warm-up
+            lr.lr_stokes_uzawa(h, ns, fs, tol_div=1e-6, eps=1e-7, prec=prec, maxit=mi, check=False,
+                               gmres=gm)  # warm-up
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             flush.fill_(1)
             a.record(stream)
-            rs = lr.lr_stokes_uzawa(h, ns, fs, tol_div=1e-6, eps=1e-7, prec=prec, maxit=mi, check=False)
+            rs = lr.lr_stokes_uzawa(h, ns, fs, tol_div=1e-6, eps=1e-7, prec=prec, maxit=mi, check=False, gmres=gm)
             b.record(stream)
             stream.synchronize()
-            row[prec] = {"ms": round(a.elapsed_time(b), 3), "iters": rs.iters, "status": rs.status,
+            row[prec + ("_gmres" if gm else "")] = {"ms": round(a.elapsed_time(b), 3), "iters": rs.iters, "status": rs.status,
                          "cg_residual": rs.history[-1],
                          "velocity_divergence": rs.resid, "pressure_rank": int(rs.p[1].shape[0]),
                          "velocity_ranks": [int(c[1].shape[0]) for c in rs.u]}
@@ -391,6 +399,50 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                 row["expsum_terms"] = r0[3]
                 row["expsum_rank"] = int(r0[1].shape[0])
         results["expsum"].append(row)
+    # ---- the uneven batch: problems with n log-uniform in [512, 16384], r
+    # uniform in 1..32 and random separable factors (seed 3), eps = 1e-6; one
+    # batched call (one CUDA graph) in each precision against a loop of
+    # single float64 solves
+    results["uneven"] = {}
+    if args.uneven > 0:
+        specs = inputs.batch_problems(args.uneven, 512, 16384, 32, seed=3)
+        uprobs = []
+        for (nn, rr, sd) in specs:
+            Uu, Vu = inputs.separable_random(nn, rr, seed=sd)
+            uprobs.append((torch.from_numpy(Uu), torch.from_numpy(Vu)))
+        ub = lr.Batch(uprobs)
+        row = {"problems": len(specs), "n_min": min(x[0] for x in specs), "n_max": max(x[0] for x in specs),
+               "r_min": min(x[1] for x in specs), "r_max": max(x[1] for x in specs),
+               "unknowns_total": int(sum(x[0] * x[0] for x in specs))}
+        for prec in ("mixed", "fp64"):
+            for _ in range(2):
+                lr.lr_poisson2d_batched(h, ub, eps=EPS, prec=prec, graph=True)
+            per = []
+            for i in range(3):
+                flush.fill_(i & 0xFF)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lr.lr_poisson2d_batched(h, ub, eps=EPS, prec=prec, graph=True, async_=True)
+                b.record(stream)
+                stream.synchronize()
+                per.append(a.elapsed_time(b))
+            row["batched_" + prec + "_ms"] = round(statistics.median(per), 3)
+            row["status_" + prec] = sorted(set(int(ub.status[i]) for i in range(len(specs))))
+        flush.fill_(7)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record(stream)
+        for (Uu, Vu), o in zip(ub.rhs, ub.out):
+            lr.lr_poisson2d(h, Uu, Vu, eps=EPS, prec="fp64", out=o, check=False)
+        b.record(stream)
+        stream.synchronize()
+        row["loop_single_fp64_ms"] = round(a.elapsed_time(b), 3)
+        row["loop_single_fp64_wall_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+        row["batched_mixed_speedup_over_loop"] = round(row["loop_single_fp64_ms"] / row["batched_mixed_ms"], 2)
+        results["uneven"] = row
+        del ub, uprobs
     # ---- throughput: batches of independent solves, one CUDA graph per batch
     B = args.batch
     probs = [(torch.from_numpy(U) * (1.0 + p / B), torch.from_numpy(V)) for p in range(B)]
@@ -544,6 +596,7 @@ def main():
         "stokes_uzawa_lowrank": res["stokes"],
         "expsum_vs_cross": res["expsum"],
         "tucker3d_fp64": res["tucker"],
+        "uneven_batch": res["uneven"],
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2),

@@ -73,7 +73,9 @@ typedef enum {
 #define LR_FLAG_GRAPH 4u   /* capture the enqueued work once as a CUDA graph
                               (keyed by every pointer, size and option) and
                               replay it on later calls with the same key */
-#define LR_FLAG_CLUSTER_DST 8u  /* lr_poisson2d: run both transforms with the
+#define LR_FLAG_CLUSTER_DST 8u
+#define LR_FLAG_GMRES 16u       /* lr_stokes_uzawa: restarted inexact GMRES with adaptive
+                                   accuracy (Section 5) instead of conjugate gradients */  /* lr_poisson2d: run both transforms with the
                                    cluster variant (one thread-block cluster
                                    per column, 8192 <= M <= 131072) for this
                                    call, whatever the tuned choice */

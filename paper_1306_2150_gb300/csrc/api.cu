@@ -910,7 +910,14 @@ struct StokesCtx {
   int launches = 0;
   int escalations = 0;               // mixed velocity solves repeated in float64
   bool cut = false;                  // a low-rank sum needed more than 64 columns
+  bool gmres = false;                // inexact GMRES instead of CG
+  std::vector<LrDev> K;              // GMRES: Krylov basis (kGmresRestart + 1 vectors)
 };
+
+constexpr int kGmresRestart = 20;
+// Loosest relative accuracy of a relaxed GMRES product: looser products lose
+// the Krylov relation through the amplification of B^T.
+constexpr double kGmresMaxDelta = 1e-4;
 
 void carve_stokes(Carve& c, StokesCtx& x) {
   carve_refine(c, x.b, x.ldp, x.n);
@@ -933,6 +940,12 @@ void carve_stokes(Carve& c, StokesCtx& x) {
   x.cs = c.take<double>(sizeof(double) * 4 * KMAX);
   x.E = c.take<double>(sizeof(double) * 2 * x.ldp);
   x.xpart = c.take<double>(sizeof(double) * KMAX * KMAX * (size_t)((x.n + 31) / 32));
+  x.K.assign(x.gmres ? kGmresRestart + 1 : 0, LrDev{});
+  for (LrDev& d : x.K) {
+    d.U = c.take<double>(cp);
+    d.V = c.take<double>(cp);
+    d.s = c.take<double>(sizeof(double) * KMAX);
+  }
 }
 
 // A term U diag(coef s) V^T of a sum (s null: ones; U, V leading dim ld).
@@ -955,7 +968,7 @@ struct Term {
 // by weight before the rounding would not.  Columns enter in term order, each
 // term's in descending weight.  dst must not alias a term; x.cut is set if
 // the running rank leaves no room for the rest.
-lr_status sum_round(StokesCtx& x, int rows, std::initializer_list<Term> terms, LrDev& dst, int ldo,
+lr_status sum_round(StokesCtx& x, int rows, const std::vector<Term>& terms, LrDev& dst, int ldo,
                     double abs_tol = 0.0) {
   lr_handle h = x.h;
   cudaStream_t stm = h->stream;
@@ -1007,6 +1020,11 @@ lr_status sum_round(StokesCtx& x, int rows, std::initializer_list<Term> terms, L
   }
   dst.r = K;
   return LR_OK;
+}
+
+lr_status sum_round(StokesCtx& x, int rows, std::initializer_list<Term> terms, LrDev& dst, int ldo,
+                    double abs_tol = 0.0) {
+  return sum_round(x, rows, std::vector<Term>(terms), dst, ldo, abs_tol);
 }
 
 lr_status norm2_of(StokesCtx& x, const LrDev& a, double* out) {
@@ -1498,6 +1516,170 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
   return LR_OK;
 }
 
+// w = (B^T A^-1 B) v with the velocity solves and the rounding of B^T u at
+// relative accuracy delta.  In LR_MIXED a product asked for below 1e-6 (what
+// float32 solves resolve) runs its velocity solves in float64: with the
+// relaxed accuracies of GMRES that is the first product of a cycle and the
+// residuals of the restarts, the rest stays in float32.
+lr_status schur_product(StokesCtx& x, const LrDev& v, LrDev& w, double delta) {
+  const double e_in = x.oin.eps, e_r = x.eps;
+  const lr_precision p_in = x.oin.prec;
+  // velocity solves a tenth tighter than the product (B^T, a difference over
+  // h, amplifies their high-frequency error)
+  const double d_in = 0.1 * delta;
+  if (x.oin.prec == LR_MIXED && d_in < 1e-6) x.oin.prec = LR_FP64;
+  x.oin.eps = d_in;
+  x.eps = delta;
+  int rx = 0, ry = 0;
+  lr_status s = grad_solve(x, v, &rx, &ry);
+  if (s == LR_OK) s = div_round(x, rx, ry, w);
+  x.oin.eps = e_in;
+  x.oin.prec = p_in;
+  x.eps = e_r;
+  return s;
+}
+
+// Restarted inexact GMRES(kGmresRestart) on the Schur equation (Section 5: the
+// paper's Stokes solver; adaptive accuracy of the products after Simoncini
+// and Szyld 2003): the product with the j-th Krylov vector is formed at
+// relative accuracy min(kGmresMaxDelta, tol ||r0|| / (2 ||r_j||)), exact early
+// and relaxed as the residual falls; the new vector w - sum_i h_ij V_i is formed
+// by modified Gram-Schmidt, each step rounded at that accuracy (kernel modes
+// of the pressure projected out at the last); the small least-squares problem
+// is solved by Givens rotations on the host; at a restart p <- p + y_i V_i is
+// rounded at eps term by term and the residual rhs - S p recomputed.  x.R holds the
+// right-hand side B^T A^-1 f; the result goes to x.P.
+lr_status stokes_gmres(StokesCtx& x, double tol, int maxit, double nr0, int* it_out, double* res_out,
+                       double* history) {
+  const int n = x.n, m = kGmresRestart;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), y(m, 0.0);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i + (size_t)j * (m + 1)]; };
+  int it = 0;
+  double res = nr0;
+  x.P.r = 0;
+  lr_status s;
+  // Only a cut of the pressure update counts (x.cut on return): a Krylov
+  // vector or a product that needed more than 64 columns only changes the
+  // space searched, and the result is certified by its true residual.
+  const bool cut_in = x.cut;
+  bool pcut = false;
+  auto scale_vec = [&](LrDev& v, double c) -> lr_status {
+    if (v.r > 0) LR_CUDA(x.h, launch_scale_copy(v.r, v.s, c, v.s, x.h->stream), "scale");
+    return LR_OK;
+  };
+  while (it < maxit) {
+    // r = rhs - S p, kernel modes projected out
+    if (x.P.r == 0) {
+      if ((s = copy_lr(x, n, x.R, x.K[0])) != LR_OK) return s;
+    } else {
+      if ((s = schur_product(x, x.P, x.Q, 0.1 * x.eps)) != LR_OK) return s;
+      double ka = 0.0, kb = 0.0, qa = 0.0, qb = 0.0;
+      if ((s = kernel_coeffs(x, x.R, 1.0, &ka, &kb)) != LR_OK) return s;
+      if ((s = kernel_coeffs(x, x.Q, -1.0, &qa, &qb)) != LR_OK) return s;
+      if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, -1.0},
+                                {x.E, nullptr, x.E, 1, x.ldp, -(ka + qa)},
+                                {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -(kb + qb)}},
+                         x.K[0], x.ldp, 0.1 * x.eps * nr0)) != LR_OK)
+        return s;
+    }
+    double b2 = 0.0;
+    if ((s = norm2_of(x, x.K[0], &b2)) != LR_OK) return s;
+    const double beta = std::sqrt(b2);
+    res = beta;
+    if (!(beta > tol * nr0)) break;
+    if ((s = scale_vec(x.K[0], 1.0 / beta)) != LR_OK) return s;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    while (j < m && it < maxit) {
+      const double delta = std::min(kGmresMaxDelta, 0.5 * tol * nr0 / res);
+      if ((s = schur_product(x, x.K[j], x.Q, delta)) != LR_OK) return s;
+      // modified Gram-Schmidt, each subtraction rounded at delta (a single sum
+      // of all terms has partial sums of far higher rank than the result);
+      // the last one also removes the kernel modes
+      const double e_r = x.eps;
+      x.eps = delta;
+      for (int i = 0; i <= j && s == LR_OK; ++i) {
+        if ((s = inner(x, n, x.Q, x.K[i], &Hij(i, j))) != LR_OK) break;
+        std::vector<Term> terms;
+        terms.push_back({x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, 1.0});
+        terms.push_back({x.K[i].U, x.K[i].s, x.K[i].V, x.K[i].r, x.ldp, -Hij(i, j)});
+        LrDev& dst = i == j ? x.K[j + 1] : x.T;
+        if (i == j) {
+          double ka = 0.0, kb = 0.0;
+          if ((s = kernel_coeffs(x, x.Q, -1.0, &ka, &kb)) != LR_OK) break;
+          terms.push_back({x.E, nullptr, x.E, 1, x.ldp, ka});
+          terms.push_back({x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, kb});
+        }
+        if ((s = sum_round(x, n, terms, dst, x.ldp)) != LR_OK) break;
+        if (i != j) std::swap(x.Q, x.T);
+      }
+      x.eps = e_r;
+      if (s != LR_OK) return s;
+      double hn2 = 0.0;
+      if ((s = norm2_of(x, x.K[j + 1], &hn2)) != LR_OK) return s;
+      const double hn = std::sqrt(hn2);
+      Hij(j + 1, j) = hn;
+      if (hn > 0.0 && (s = scale_vec(x.K[j + 1], 1.0 / hn)) != LR_OK) return s;
+      // Givens rotations: apply the previous ones to column j, then a new one
+      for (int i = 0; i < j; ++i) {
+        const double a = Hij(i, j), b = Hij(i + 1, j);
+        Hij(i, j) = cs[i] * a + sn[i] * b;
+        Hij(i + 1, j) = -sn[i] * a + cs[i] * b;
+      }
+      const double a = Hij(j, j), b = Hij(j + 1, j);
+      const double rho = std::hypot(a, b);
+      cs[j] = rho > 0.0 ? a / rho : 1.0;
+      sn[j] = rho > 0.0 ? b / rho : 0.0;
+      Hij(j, j) = rho;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      res = std::fabs(g[j + 1]);
+      ++j;
+      ++it;
+      if (history) history[it] = res / nr0;
+      if (res <= tol * nr0 || hn == 0.0) break;
+    }
+    // y = R^-1 g (upper triangular j x j), p <- round(p + sum_i y_i V_i)
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int l = i + 1; l < j; ++l) acc -= Hij(i, l) * y[l];
+      y[i] = Hij(i, i) != 0.0 ? acc / Hij(i, i) : 0.0;
+    }
+    for (int i = 0; i < j; ++i) {
+      x.cut = false;
+      if ((s = sum_round(x, n, {{x.P.U, x.P.s, x.P.V, x.P.r, x.ldp, 1.0},
+                                {x.K[i].U, x.K[i].s, x.K[i].V, x.K[i].r, x.ldp, y[i]}},
+                         x.T, x.ldp)) != LR_OK)
+        return s;
+      pcut = pcut || x.cut;
+      std::swap(x.P, x.T);
+    }
+    if (res <= tol * nr0) {
+      // the recursion's estimate met the tolerance: confirm on the true residual
+      if ((s = schur_product(x, x.P, x.Q, 0.1 * x.eps)) != LR_OK) return s;
+      double ka = 0.0, kb = 0.0, qa = 0.0, qb = 0.0;
+      if ((s = kernel_coeffs(x, x.R, 1.0, &ka, &kb)) != LR_OK) return s;
+      if ((s = kernel_coeffs(x, x.Q, -1.0, &qa, &qb)) != LR_OK) return s;
+      if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, -1.0},
+                                {x.E, nullptr, x.E, 1, x.ldp, -(ka + qa)},
+                                {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -(kb + qb)}},
+                         x.K[0], x.ldp, 0.1 * x.eps * nr0)) != LR_OK)
+        return s;
+      double t2 = 0.0;
+      if ((s = norm2_of(x, x.K[0], &t2)) != LR_OK) return s;
+      res = std::sqrt(t2);
+      if (res <= tol * nr0) break;
+      // otherwise the next cycle restarts from the true residual
+    }
+  }
+  x.cut = cut_in || pcut;
+  *it_out = it;
+  *res_out = res;
+  return LR_OK;
+}
+
 // Absolute rounding level of the CG residual and direction, in units of
 // eps ||r0|| (the Schur product q: a tenth of it).
 constexpr double kCgFloor = 0.3;
@@ -1514,6 +1696,7 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   x.oin.flags = 0;
   x.oin.refine = -1;
   x.oin.op = LR_OP_SEMISTAGGERED;
+  x.gmres = (o.flags & LR_FLAG_GMRES) != 0;
   // The velocity solves run at eps / 10: B^T is a difference over h and
   // amplifies the high-frequency part of their error, which the Schur
   // product q would otherwise carry into the CG recursion.  float32 solves:
@@ -1550,9 +1733,14 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   const double nr0 = std::sqrt(rr);
   if (history) history[0] = nr0 > 0.0 ? 1.0 : 0.0;
   x.P.r = 0;
-  if ((s = copy_lr(x, n, x.R, x.D)) != LR_OK) return s;
   int it = 0;
-  while (it < maxit && nr0 > 0.0 && std::sqrt(rr) > tol * nr0 && x.D.r > 0) {
+  if (x.gmres && nr0 > 0.0) {
+    double res = 0.0;
+    if ((s = stokes_gmres(x, tol, maxit, nr0, &it, &res, history)) != LR_OK) return s;
+    rr = res * res;
+  }
+  if (!x.gmres && (s = copy_lr(x, n, x.R, x.D)) != LR_OK) return s;
+  while (!x.gmres && it < maxit && nr0 > 0.0 && std::sqrt(rr) > tol * nr0 && x.D.r > 0) {
     // q = (B^T A^-1 B) d
     if ((s = grad_solve(x, x.D, &rx, &ry)) != LR_OK) return s;
     // q enters r - alpha q with alpha = O(1) (the Schur spectrum lies in

@@ -24,6 +24,7 @@ LR_FLAG_ASYNC = 1
 LR_FLAG_TIMING = 2
 LR_FLAG_GRAPH = 4
 LR_FLAG_CLUSTER_DST = 8
+LR_FLAG_GMRES = 16
 PHASES = ("forward_dst", "cross", "rounding", "inverse_dst")
 
 PRECISIONS = {"fp64": LR_FP64, "mixed": LR_MIXED}
@@ -465,7 +466,7 @@ class StokesResult:
 
 
 def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 200, eps: float = 1e-7,
-                    prec="mixed", rmax_out: int = 64, check: bool = True) -> StokesResult:
+                    prec="mixed", rmax_out: int = 64, check: bool = True, gmres: bool = False) -> StokesResult:
     """Low-rank Uzawa solve of the 2D Stokes problem on n x n cells; ``f`` is
     [(U1, V1), (U2, V2)], the body-force components at the (n-1)^2 interior
     vertices in factored form (device float64)."""
@@ -491,7 +492,7 @@ def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 20
     Up, Vp = colmajor_empty(n, rmax_out, dev), colmajor_empty(n, rmax_out, dev)
     sp = torch.empty(rmax_out, dtype=torch.float64, device=dev)
     c_p = LrMat(n, n, 0, rmax_out, _ld(Up), Up.data_ptr(), sp.data_ptr(), Vp.data_ptr())
-    o = _options(eps, prec, "semi", 64, 1.0, 16, 0, 0, 0)
+    o = _options(eps, prec, "semi", 64, 1.0, 16, 0, LR_FLAG_GMRES if gmres else 0, 0)
     iters = ctypes.c_int(0)
     resid = ctypes.c_double(0.0)
     hist = (ctypes.c_double * (int(maxit) + 1))()
