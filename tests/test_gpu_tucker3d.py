@@ -72,7 +72,7 @@ def test_tucker3d_matches_the_full_solve(lr, h, case, eps):
         assert abs(G.shape[k] - ref.G.shape[k]) <= 3, (G.shape, ref.G.shape)
 
 
-@pytest.mark.parametrize("n", [256, 512])
+@pytest.mark.parametrize("n", [256, 512, 1024])
 def test_tucker3d_benchmark_sizes_on_sampled_slices(lr, h, n):
     eps = 1e-6
     rhs = inputs.smooth3d(n, eps)
