@@ -354,22 +354,25 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     for nt in args.tucker:
         G3, A1, A2, A3 = inputs.smooth3d(nt, 1e-6)
         d3 = (torch.from_numpy(G3).cuda(), *[torch.from_numpy(np.asfortranarray(A)).cuda() for A in (A1, A2, A3)])
-        r0 = lr.lr_poisson3d_tucker(h, *d3, eps=1e-6, check=False)
-        per = []
-        for i in range(3):
-            flush.fill_(i & 0xFF)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            torch.cuda.nvtx.range_push(f"tucker3d_n{nt}")  # profiler range (ncu --nvtx-include)
-            a.record(stream)
-            r0 = lr.lr_poisson3d_tucker(h, *d3, eps=1e-6, check=False)
-            b.record(stream)
-            stream.synchronize()
-            torch.cuda.nvtx.range_pop()
-            per.append(a.elapsed_time(b))
-        results["tucker"].append({"n": nt, "ms": round(statistics.median(per), 3), "status": r0.status,
-                                  "rhs_ranks": list(G3.shape), "solution_ranks": list(r0.G.shape),
-                                  "cross_steps": r0.steps, "probe_rounds": r0.probe_rounds})
+        row = {"n": nt, "rhs_ranks": list(G3.shape)}
+        for prec in ("fp64", "mixed"):
+            r0 = lr.lr_poisson3d_tucker(h, *d3, eps=1e-6, check=False, prec=prec)
+            per = []
+            for i in range(3):
+                flush.fill_(i & 0xFF)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.nvtx.range_push(f"tucker3d_{prec}_n{nt}")  # profiler range (ncu --nvtx-include)
+                a.record(stream)
+                r0 = lr.lr_poisson3d_tucker(h, *d3, eps=1e-6, check=False, prec=prec)
+                b.record(stream)
+                stream.synchronize()
+                torch.cuda.nvtx.range_pop()
+                per.append(a.elapsed_time(b))
+            row[prec] = {"ms": round(statistics.median(per), 3), "status": r0.status,
+                         "solution_ranks": list(r0.G.shape), "cross_steps": r0.steps,
+                         "probe_rounds": r0.probe_rounds}
+        results["tucker"].append(row)
     # ---- exponential-sum baseline against the cross (n = 1024, eps = 1e-7,
     # float64, the paper's comparison point)
     results["expsum"] = []
@@ -595,7 +598,7 @@ def main():
         "crossover_full_grid_vs_lowrank": res["crossover"],
         "stokes_uzawa_lowrank": res["stokes"],
         "expsum_vs_cross": res["expsum"],
-        "tucker3d_fp64": res["tucker"],
+        "tucker3d": res["tucker"],
         "uneven_batch": res["uneven"],
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),

@@ -268,9 +268,11 @@ typedef struct {
  * 0.1 aca_tol_factor eps.  Then the higher-order SVD of C, each mode
  * truncated with a tail <= eps ||C|| / sqrt(3), and the inverse DST of the
  * kept factors.  Output: sol->G, sol->U[k] (orthonormal columns), sol->r.
- * Requirements: opt->prec == LR_FP64, opt->op == LR_OP_5PT (its 3D
- * analogue), 1 <= n[k] <= 16384, 1 <= r[k] <= 64, opt->rmax <= 64 cross
- * steps.  LR_EINVAL for bad arguments, LR_ENOCONV if the cross did not
+ * Precision: LR_FP64 throughout; LR_MIXED runs the transforms and the
+ * Jacobi iterations of the rounding cores in float32 (the cross and the
+ * Cholesky QR in float64) and needs eps >= 1e-7.
+ * Requirements: opt->op == LR_OP_5PT (its 3D analogue), 1 <= n[k] <= 16384,
+ * 1 <= r[k] <= 64, opt->rmax <= 64 cross steps.  LR_EINVAL for bad arguments, LR_ENOCONV if the cross did not
  * converge within opt->rmax steps or a rank exceeded sol->rmax (result
  * truncated), LR_ENONFINITE for a non-finite value.  Synchronises. */
 lr_status lr_poisson3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options* opt);

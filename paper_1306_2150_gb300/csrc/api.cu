@@ -1197,6 +1197,9 @@ int q_cap(int p) { return p < 1 ? 1 : p; }
 
 lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options& o) {
   cudaStream_t stm = h->stream;
+  // LR_MIXED: float32 transforms and float32 Jacobi in the rounding cores of
+  // the higher-order SVD; the cross in float64
+  const bool mixed = o.prec == LR_MIXED;
   Plan* plan[3];
   int n[3], r[3], ldq[3];
   int nmax = 0;
@@ -1281,7 +1284,9 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
     cs.out[0] = const_cast<double*>(d.Uh[k]);
     cs.ld_out[0] = ldq[k];
     cs.ncol[0] = r[k];
-    LR_CUDA(h, launch_dst<double>(*plan[k], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm), "3D: forward");
+    LR_CUDA(h, mixed ? launch_dst<float>(*plan[k], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm)
+                     : launch_dst<double>(*plan[k], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm),
+            "3D: forward");
     ++launches;
   }
   // state
@@ -1445,14 +1450,27 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
         }
       }
       LR_CUDA(h, cudaMemsetAsync(b.st, 0, sizeof(SolveState), sm), "state reset");
-      CoreArgs<double> co;
-      co.GC = ident; co.GR = b.Ra0; co.ldg = KMAX; co.d = nullptr;
-      co.k_dev = nullptr; co.k_host = q;
-      co.eps = o.eps / std::sqrt(3.0); co.rmax_out = std::min(sol->rmax[m], KMAX);
-      co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = sig[m]; co.st = b.st;
-      co.tri_given = 1;
-      LR_CUDA(h, launch_core<double>(co, false, sm), "3D: core SVD");
-      LR_CUDA(h, cudaMemcpyAsync(W[m], b.Tc, sizeof(double) * KMAX * KMAX, cudaMemcpyDeviceToDevice, sm), "3D: W");
+      if (mixed) {
+        // float32 coefficient matrices in the (larger) float64 buffers, widened into W
+        CoreArgs<float> co;
+        co.GC = ident; co.GR = b.Ra0; co.ldg = KMAX; co.d = nullptr;
+        co.k_dev = nullptr; co.k_host = q;
+        co.eps = o.eps / std::sqrt(3.0); co.rmax_out = std::min(sol->rmax[m], KMAX);
+        co.Tc = reinterpret_cast<float*>(b.Tc); co.Tr = reinterpret_cast<float*>(b.Tr);
+        co.s_out = sig[m]; co.st = b.st;
+        co.tri_given = 1;
+        LR_CUDA(h, launch_core<float>(co, true, sm), "3D: core SVD");
+        LR_CUDA(h, launch_t3_widen(reinterpret_cast<const float*>(b.Tc), W[m], KMAX * KMAX, sm), "3D: W");
+      } else {
+        CoreArgs<double> co;
+        co.GC = ident; co.GR = b.Ra0; co.ldg = KMAX; co.d = nullptr;
+        co.k_dev = nullptr; co.k_host = q;
+        co.eps = o.eps / std::sqrt(3.0); co.rmax_out = std::min(sol->rmax[m], KMAX);
+        co.Tc = b.Tc; co.Tr = b.Tr; co.s_out = sig[m]; co.st = b.st;
+        co.tri_given = 1;
+        LR_CUDA(h, launch_core<double>(co, false, sm), "3D: core SVD");
+        LR_CUDA(h, cudaMemcpyAsync(W[m], b.Tc, sizeof(double) * KMAX * KMAX, cudaMemcpyDeviceToDevice, sm), "3D: W");
+      }
       // kept factor Q_m W_m (its rank read on the device)
       LR_CUDA(h, (launch_rotate<double, double>(d.Q[m], ldq[m], n[m], nullptr, q, W[m], false, &b.st->rank, XU[m], ldq[m], sm)), "3D: rot");
       launches += 3;
@@ -1469,7 +1487,9 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
       cs.ld_out[0] = sol->ld[m];
       cs.ncol[0] = std::min(sol->rmax[m], q_cap(p[m]));
       cs.dyn_count = &b3[m].st->rank;
-      LR_CUDA(h, launch_dst<double>(*plan[m], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm), "3D: inverse");
+      LR_CUDA(h, mixed ? launch_dst<float>(*plan[m], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm)
+                       : launch_dst<double>(*plan[m], cs, IoType::F64, IoType::F64, h->ws, h->num_sms, stm),
+              "3D: inverse");
       ++launches;
     }
     SolveState* hst = reinterpret_cast<SolveState*>(h->h_big + 512);
@@ -2078,7 +2098,9 @@ lr_status lr_poisson3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol,
   if (opt) o = *opt; else lr_options_default(&o);
   lr_status s = check_opts(h, o);
   if (s != LR_OK) return s;
-  if (o.prec != LR_FP64) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: LR_FP64 only");
+  if (o.prec != LR_FP64 && o.prec != LR_MIXED) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: unknown precision");
+  if (o.prec == LR_MIXED && !(o.eps >= 1e-7))
+    return fail(h, LR_EINVAL, "lr_poisson3d_tucker: LR_MIXED needs eps >= 1e-7 (float32 transforms and cores)");
   if (o.op != LR_OP_5PT) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: the 7-point operator (LR_OP_5PT kind) only");
   if (!rhs || !sol || !rhs->G || !sol->G) return fail(h, LR_EINVAL, "lr_poisson3d_tucker: null rhs, sol or core");
   for (int k = 0; k < 3; ++k) {

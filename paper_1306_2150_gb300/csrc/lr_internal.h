@@ -253,5 +253,6 @@ cudaError_t launch_t3_decide(const T3Dev& d, double tol, cudaStream_t st);
 cudaError_t launch_t3_probe_reduce(const T3Dev& d, const int* jobs, const double* nrm2, const int* amax,
                                    const T3ProbeCounts& c, double tol, cudaStream_t st);
 cudaError_t launch_t3_unfold(const T3Dev& d, int m, int total, double* A, int lda, cudaStream_t st);
+cudaError_t launch_t3_widen(const float* in, double* out, int n, cudaStream_t st);
 
 }  // namespace lrp

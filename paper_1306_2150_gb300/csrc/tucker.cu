@@ -594,7 +594,18 @@ __global__ void t3_unfold_kernel(T3Dev d, int m, double* __restrict__ A, int lda
 
 }  // namespace
 
+__global__ void t3_widen_kernel(const float* __restrict__ in, double* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+
 #define T3_LAUNCH_CHECK() return cudaGetLastError()
+
+cudaError_t launch_t3_widen(const float* in, double* out, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  t3_widen_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+  T3_LAUNCH_CHECK();
+}
 
 cudaError_t launch_t3_search(const T3Dev& d, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};

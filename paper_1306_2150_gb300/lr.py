@@ -540,9 +540,10 @@ class TuckerResult:
 
 def lr_poisson3d_tucker(h: Handle, G, U1, U2, U3, eps: float = 1e-6, rmax: int = 64, rmax_out: int = 64,
                         aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
-                        check: bool = True) -> TuckerResult:
-    """Low-rank 3D solve (float64): the right-hand side in Tucker format, core
-    G (r0, r1, r2) and factors U_k (n_k x r_k), device float64 tensors."""
+                        check: bool = True, prec="fp64") -> TuckerResult:
+    """Low-rank 3D solve: the right-hand side in Tucker format, core G
+    (r0, r1, r2) and factors U_k (n_k x r_k), device float64 tensors; prec
+    "mixed" runs the transforms and the rounding cores' Jacobi in float32."""
     import torch
     G = G.contiguous()
     Us = []
@@ -565,7 +566,7 @@ def lr_poisson3d_tucker(h: Handle, G, U1, U2, U3, eps: float = 1e-6, rmax: int =
         sol.n[k] = ns[k]; sol.r[k] = 0; sol.rmax[k] = rmax_out; sol.ld[k] = _ld(outs[k]); sol.U[k] = outs[k].data_ptr()
     rhs.G = G.data_ptr()
     sol.G = Go.data_ptr()
-    o = _options(eps, "fp64", "5pt", rmax, aca_tol_factor, probes, seed, 0, 0)
+    o = _options(eps, prec, "5pt", rmax, aca_tol_factor, probes, seed, 0, 0)
     st = load().lr_poisson3d_tucker(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o))
     if check and st not in (LR_OK,):
         raise LrError(st, h.last_error())

@@ -145,7 +145,8 @@ def test_invalid_arguments_are_rejected(lr, h):
         return lib.lr_poisson3d_tucker(h.ptr, ctypes.byref(rhs), ctypes.byref(sol), ctypes.byref(o))
 
     assert call() == lr.LR_OK
-    assert call(prec="mixed") == lr.LR_EINVAL
+    assert call(prec="mixed") == lr.LR_OK
+    assert call(prec=7) == lr.LR_EINVAL
     assert call(lambda r, s: r.r.__setitem__(0, 0)) == lr.LR_EINVAL
     assert call(lambda r, s: r.r.__setitem__(1, 65)) == lr.LR_EINVAL
     assert call(lambda r, s: r.n.__setitem__(2, 0)) == lr.LR_EINVAL
@@ -153,3 +154,32 @@ def test_invalid_arguments_are_rejected(lr, h):
     assert call(lambda r, s: r.ld.__setitem__(0, 15)) == lr.LR_EINVAL
     assert call(lambda r, s: s.rmax.__setitem__(2, 0)) == lr.LR_EINVAL
     assert call(lambda r, s: setattr(r, "G", None)) == lr.LR_EINVAL
+
+
+@pytest.mark.parametrize("case", ["smooth48", "random40", "uneven", "smooth128"])
+def test_tucker3d_mixed_matches_the_full_solve(lr, h, case):
+    # float32 transforms and float32 Jacobi in the HOSVD cores, eps = 1e-6
+    eps = 1e-6
+    if case == "smooth48":
+        rhs = inputs.smooth3d(48, eps)
+    elif case == "smooth128":
+        rhs = inputs.smooth3d(128, eps)
+    elif case == "random40":
+        rhs = inputs.tucker_random(40, 6, seed=5)
+    else:
+        rhs = inputs.tucker_random((47, 66, 75), (2, 5, 3), seed=6)
+    res = lr.lr_poisson3d_tucker(h, *to_dev(*rhs), eps=eps, prec="mixed")
+    assert res.status == lr.LR_OK, h.last_error()
+    G, Us = host(res)
+    for U in Us:
+        assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-5
+    F = T.tucker_full(*rhs)
+    Xs = T.solve_full3(F)
+    X = T.tucker_full(G, *Us)
+    err = np.linalg.norm(X - Xs) / np.linalg.norm(Xs)
+    assert err <= 10 * eps, err
+
+
+def test_tucker3d_mixed_rejects_tight_eps(lr, h):
+    with pytest.raises(lr.LrError):
+        lr.lr_poisson3d_tucker(h, *to_dev(*inputs.tucker_random(16, 2, seed=1)), eps=1e-9, prec="mixed")
