@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -109,7 +110,10 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples (the JSON line carries their summary); LR_BENCH_CLOCKS_DIR
+        # keeps them somewhere else than the system's temporary directory
+        self.path = os.path.join(os.environ.get("LR_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"lr_bench_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
