@@ -514,6 +514,27 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     return results
 
 
+# Timed quantities of a rank's results: the slowest rank sets the job's time.
+RANK_TIMES = (("mixed", "ms"), ("fp64", "ms"), ("batch_mixed", "ms_step"), ("batch_fp64", "ms_step"),
+              ("e2e_batch", "ms_step"))
+
+
+def combine_ranks(res: dict, world: int, device: str) -> dict:
+    """Replicas (one independent batch per rank, no collective on the data
+    path): the max over ranks of every timed quantity, and whole-job unit
+    counts, since every rank solved its own batch.  One all-reduce on the
+    initialised process group (NCCL on the GPU machine, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([res[a][b] for a, b in RANK_TIMES], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    for (a, b), v in zip(RANK_TIMES, t.tolist()):
+        res[a][b] = v
+    res["batch_mixed"]["batch"] *= world
+    res["e2e_batch"]["batch"] *= world
+    return res
+
+
 def main():
     args = parse()
     if args.cpu_worker:
@@ -542,17 +563,7 @@ def main():
         dist.init_process_group("nccl")
     res = gpu_arm(args, rank, world)
     if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([res["mixed"]["ms"], res["fp64"]["ms"], res["batch_mixed"]["ms_step"],
-                          res["batch_fp64"]["ms_step"], res["e2e_batch"]["ms_step"]],
-                         device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        (res["mixed"]["ms"], res["fp64"]["ms"], res["batch_mixed"]["ms_step"], res["batch_fp64"]["ms_step"],
-         res["e2e_batch"]["ms_step"]) = t.tolist()
-        # every rank solved its own batch: whole-job throughput counts all of them
-        res["batch_mixed"]["batch"] *= world
-        res["e2e_batch"]["batch"] *= world
+        combine_ranks(res, world, "cuda")
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
