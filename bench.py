@@ -107,15 +107,55 @@ def run_cpu_baseline(n: int, seconds: float, steps: int = 1) -> dict:
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
+    """SM clock and clock-event (throttle) reasons sampled while a timed region
+    runs: every 2 ms from NVML on a thread (read-only queries), else from
+    nvidia-smi (100 ms).  The JSON line carries the summary; LR_BENCH_CLOCKS_DIR
+    (default: the system's temporary directory) receives the raw nvidia-smi
+    samples."""
+    # NVML clock-event reason bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        # raw samples (the JSON line carries their summary); LR_BENCH_CLOCKS_DIR
-        # keeps them somewhere else than the system's temporary directory
+        self.thread = None
+        self.samples = []  # (sm MHz, max sm MHz, reason bits)
         self.path = os.path.join(os.environ.get("LR_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
                                  f"lr_bench_clocks_rank{index}.csv")
 
+    def _nvml_start(self) -> bool:
+        import ctypes
+        import threading
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            dev = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(dev)) != 0:
+                return False
+            reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        except Exception:
+            return False
+        self.stop = threading.Event()
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+
+        def run():
+            while not self.stop.is_set():
+                if (lib.nvmlDeviceGetClockInfo(dev, 1, ctypes.byref(clk)) == 0
+                        and lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0
+                        and reasons_fn(dev, ctypes.byref(rs)) == 0):
+                    self.samples.append((clk.value, mx.value, rs.value))
+                time.sleep(0.002)
+
+        self.thread = threading.Thread(target=run, daemon=True)
+        self.thread.start()
+        time.sleep(0.01)  # first sample before the region starts
+        return True
+
     def __enter__(self):
+        if self._nvml_start():
+            return self
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -131,6 +171,9 @@ class Clocks:
         return self
 
     def __exit__(self, *exc):
+        if self.thread:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -140,6 +183,13 @@ class Clocks:
             self.f.close()
 
     def summary(self) -> dict:
+        if self.thread:
+            if not self.samples:
+                return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            reasons = {nm for nm, bit in self.REASONS.items() if any(r & bit for _, _, r in self.samples)}
+            return {"sm_mhz": statistics.median(c for c, _, _ in self.samples),
+                    "sm_max_mhz": max(m for _, m, _ in self.samples), "reasons": sorted(reasons),
+                    "samples": len(self.samples), "source": "nvml, 2 ms"}
         try:
             rows = [l.split(",") for l in open(self.path).read().splitlines() if l.strip()]
         except Exception:
@@ -158,7 +208,7 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 100 ms"}
 
 
 # ---------------------------------------------------------------- ncu traffic
