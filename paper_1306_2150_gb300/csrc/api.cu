@@ -15,6 +15,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lr_internal.h"
 
 using namespace lrp;
@@ -65,6 +67,29 @@ struct lr_handle_s {
 };
 
 namespace {
+
+// NVTX range on the calling thread (profilers attribute the kernels launched
+// inside it; a no-op without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Consecutive phases of one call: to() closes the open phase and opens the
+// next; the last one closes on scope exit (early returns included).
+struct NvtxPhase {
+  bool open = false;
+  void to(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhase() {
+    if (open) nvtxRangePop();
+  }
+};
 
 lr_status fail(lr_handle h, lr_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -217,7 +242,9 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   cudaError_t e;
   if ((e = cudaMemsetAsync(st, 0, sizeof(SolveState), stm)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[0], stm)) != cudaSuccess) return e;
+  NvtxPhase phase;
   // Forward DST of both factors.
+  phase.to("lr:forward_dst");
   ColumnSet fw;
   fw.in[0] = rhs->U; fw.in[1] = rhs->V;
   fw.ld_in[0] = rhs->ld; fw.ld_in[1] = rhs->ld;
@@ -227,6 +254,7 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   if ((e = launch_dst<T>(plan, fw, IoType::F64, IoType::WORK, w.work, h->num_sms, stm)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], stm)) != cudaSuccess) return e;
   // Cross approximation in frequency space (symbol, pivots, skeleton).
+  phase.to("lr:cross");
   CrossArgs<T> ca;
   ca.m = g.m; ca.r = g.r; ca.kcap = g.kcap; ca.ld = g.ldw;
   ca.Uh = w.Uh; ca.Vh = w.Vh; ca.C = w.C; ca.R = w.R;
@@ -241,6 +269,7 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   if ((e = launch_cross<T>(ca, o.cluster_size, stm, used_cs)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], stm)) != cudaSuccess) return e;
   // Rounding core.
+  phase.to("lr:rounding");
   CoreArgs<T> co;
   co.GC = w.GC; co.GR = w.GR; co.ldg = g.kcap; co.d = w.d;
   co.k_dev = &st->k; co.k_host = 0;
@@ -249,6 +278,7 @@ cudaError_t enqueue_solve(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   if ((e = launch_core<T>(co, f32, stm)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], stm)) != cudaSuccess) return e;
   // Inverse DST of the kept columns into the caller's float64 factors;
+  phase.to("lr:inverse_dst");
   // the rotation of the skeleton by Tc, Tr (the last step of the rounding) is
   // applied as the transform loads its input.
   ColumnSet iv;
@@ -1997,6 +2027,7 @@ lr_status lr_dst1(lr_handle h, int m, int ncols, const double* in, int ld_in, do
 
 lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double* X, int ldx,
                             const lr_options* opt) {
+  NvtxRange nvtx_range("lr_poisson2d_full");
   if (!h) return LR_EINVAL;
   lr_options o;
   if (opt) o = *opt; else lr_options_default(&o);
@@ -2014,6 +2045,7 @@ lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double
 }
 
 lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt) {
+  NvtxRange nvtx_range("lr_poisson2d");
   if (!h) return LR_EINVAL;
   lr_options o;
   if (opt) o = *opt; else lr_options_default(&o);
@@ -2041,6 +2073,7 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
 
 lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options* opt,
                                lr_status* per_problem) {
+  NvtxRange nvtx_range("lr_poisson2d_batched");
   if (!h) return LR_EINVAL;
   lr_options o;
   if (opt) o = *opt; else lr_options_default(&o);
@@ -2070,6 +2103,7 @@ lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat
 lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p,
                           double tol_div, int maxit, const lr_options* opt, int* iters, double* resid,
                           double* history) {
+  NvtxRange nvtx_range("lr_stokes_uzawa");
   if (!h) return LR_EINVAL;
   lr_options o;
   if (opt) o = *opt; else lr_options_default(&o);
@@ -2093,6 +2127,7 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
 }
 
 lr_status lr_poisson3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options* opt) {
+  NvtxRange nvtx_range("lr_poisson3d_tucker");
   if (!h) return LR_EINVAL;
   lr_options o;
   if (opt) o = *opt; else lr_options_default(&o);
@@ -2118,6 +2153,7 @@ lr_status lr_poisson3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol,
 }
 
 lr_status lr_poisson2d_expsum(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_options* opt, int* nterms) {
+  NvtxRange nvtx_range("lr_poisson2d_expsum");
   if (!h) return LR_EINVAL;
   lr_options o;
   if (opt) o = *opt; else lr_options_default(&o);
@@ -2310,6 +2346,7 @@ lr_status lr_get_phase_times(lr_handle h, double* ms, int n) {
 }
 
 lr_status lr_truncate(lr_handle h, lr_mat* X, double eps, int rmax) {
+  NvtxRange nvtx_range("lr_truncate");
   if (!h) return LR_EINVAL;
   if (!X) return fail(h, LR_EINVAL, "null matrix");
   if (!(eps > 0.0) || eps >= 1.0) return fail(h, LR_EINVAL, "eps must be in (0, 1)");
