@@ -226,7 +226,9 @@ lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
  *   f     : 2 body-force components, (n-1) x (n-1), rank 1..64, s = NULL
  *   g     : must be NULL (divergence-free)
  *   u     : 2 velocity outputs (n-1) x (n-1), U, s, V capacity rmax
- *   p     : pressure output n x n (U, s, V capacity rmax)
+ *   p     : pressure output n x n (U, s, V capacity rmax).  On entry p->r = 0,
+ *           or the rank of an initial guess held in p (resume from a saved
+ *           pressure: CG restarts from r = rhs - S p, GMRES likewise)
  *   iters : CG iterations taken (may be NULL)
  *   resid : ||B^T u|| / ||B^T A^-1 f|| of the returned velocity (may be NULL)
  *   history: host array of maxit + 1 doubles (may be NULL): ||r_k|| / ||r_0||

@@ -1606,8 +1606,7 @@ lr_status stokes_gmres(StokesCtx& x, double tol, int maxit, double nr0, int* it_
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i + (size_t)j * (m + 1)]; };
   int it = 0;
   double res = nr0;
-  x.P.r = 0;
-  lr_status s;
+  lr_status s;  // x.P: the initial guess (empty, or a resumed pressure)
   // Only a cut of the pressure update counts (x.cut on return): a Krylov
   // vector or a product that needed more than 64 columns only changes the
   // space searched, and the result is certified by its true residual.
@@ -1783,6 +1782,36 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   const double nr0 = std::sqrt(rr);
   if (history) history[0] = nr0 > 0.0 ? 1.0 : 0.0;
   x.P.r = 0;
+  if (p->r > 0 && nr0 > 0.0) {
+    // Resume from the pressure given in p (a saved iterate): copied in with
+    // its kernel modes removed; CG restarts from r = rhs - S p (GMRES forms
+    // that residual itself).
+    LR_CUDA(h, cudaMemcpy2DAsync(x.T.U, sizeof(double) * x.ldp, p->U, sizeof(double) * p->ld, sizeof(double) * n,
+                                 p->r, cudaMemcpyDeviceToDevice, stm), "copy");
+    LR_CUDA(h, cudaMemcpy2DAsync(x.T.V, sizeof(double) * x.ldp, p->V, sizeof(double) * p->ld, sizeof(double) * n,
+                                 p->r, cudaMemcpyDeviceToDevice, stm), "copy");
+    LR_CUDA(h, cudaMemcpyAsync(x.T.s, p->s, sizeof(double) * p->r, cudaMemcpyDeviceToDevice, stm), "copy");
+    x.T.r = p->r;
+    double ka = 0.0, kb = 0.0;
+    if ((s = kernel_coeffs(x, x.T, 1.0, &ka, &kb)) != LR_OK) return s;
+    if ((s = sum_round(x, n, {{x.T.U, x.T.s, x.T.V, x.T.r, x.ldp, 1.0}, {x.E, nullptr, x.E, 1, x.ldp, -ka},
+                              {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -kb}}, x.P, x.ldp)) != LR_OK)
+      return s;
+    if (!x.gmres && x.P.r > 0) {
+      if ((s = schur_product(x, x.P, x.Q, 0.1 * x.eps)) != LR_OK) return s;
+      double qa = 0.0, qb = 0.0;
+      if ((s = kernel_coeffs(x, x.R, 1.0, &ka, &kb)) != LR_OK) return s;
+      if ((s = kernel_coeffs(x, x.Q, -1.0, &qa, &qb)) != LR_OK) return s;
+      if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.Q.U, x.Q.s, x.Q.V, x.Q.r, x.ldp, -1.0},
+                                {x.E, nullptr, x.E, 1, x.ldp, -(ka + qa)},
+                                {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, -(kb + qb)}},
+                         x.T, x.ldp, kCgFloor * x.eps * nr0)) != LR_OK)
+        return s;
+      std::swap(x.R, x.T);
+      if ((s = norm2_of(x, x.R, &rr)) != LR_OK) return s;
+      if (history) history[0] = std::sqrt(rr) / nr0;
+    }
+  }
   int it = 0;
   if (x.gmres && nr0 > 0.0) {
     double res = 0.0;
@@ -2123,6 +2152,8 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
   if (p->n1 != n || p->n2 != n || p->ld < n || p->rmax < 1 || !p->U || !p->V || !p->s ||
       !aligned16(p->U) || !aligned16(p->V) || !aligned16(p->s))
     return fail(h, LR_EINVAL, "lr_stokes_uzawa: p must be n x n with U, s, V set and aligned");
+  if (p->r < 0 || p->r > std::min(p->rmax, KMAX))
+    return fail(h, LR_EINVAL, "lr_stokes_uzawa: p->r (the initial guess's rank, 0 for none) must be in [0, min(p->rmax, 64)]");
   return stokes_uzawa(h, n, f, u, p, tol_div, maxit, o, iters, resid, history);
 }
 

@@ -466,7 +466,8 @@ class StokesResult:
 
 
 def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 200, eps: float = 1e-7,
-                    prec="mixed", rmax_out: int = 64, check: bool = True, gmres: bool = False) -> StokesResult:
+                    prec="mixed", rmax_out: int = 64, check: bool = True, gmres: bool = False,
+                    p0=None) -> StokesResult:
     """Low-rank Uzawa solve of the 2D Stokes problem on n x n cells; ``f`` is
     [(U1, V1), (U2, V2)], the body-force components at the (n-1)^2 interior
     vertices in factored form (device float64)."""
@@ -491,7 +492,14 @@ def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 20
     dev = keep[0].device
     Up, Vp = colmajor_empty(n, rmax_out, dev), colmajor_empty(n, rmax_out, dev)
     sp = torch.empty(rmax_out, dtype=torch.float64, device=dev)
-    c_p = LrMat(n, n, 0, rmax_out, _ld(Up), Up.data_ptr(), sp.data_ptr(), Vp.data_ptr())
+    r0 = 0
+    if p0 is not None:  # resume from a saved pressure (U, s, V)
+        U0, s0, V0 = p0
+        r0 = U0.shape[1]
+        Up[:, :r0].copy_(U0)
+        Vp[:, :r0].copy_(V0)
+        sp[:r0].copy_(s0)
+    c_p = LrMat(n, n, r0, rmax_out, _ld(Up), Up.data_ptr(), sp.data_ptr(), Vp.data_ptr())
     o = _options(eps, prec, "semi", 64, 1.0, 16, 0, LR_FLAG_GMRES if gmres else 0, 0)
     iters = ctypes.c_int(0)
     resid = ctypes.c_double(0.0)

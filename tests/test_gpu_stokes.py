@@ -100,3 +100,24 @@ def test_stokes_gmres_matches_oracle(lr, h, n, prec, eps, tol, acc):
         assert res.iters <= cg.iters + 3, (res.iters, cg.iters)
     else:
         assert res.iters <= 2 * cg.iters, (res.iters, cg.iters)
+
+
+@pytest.mark.parametrize("gmres", [False, True])
+def test_stokes_resumes_from_a_saved_pressure(lr, h, gmres):
+    # checkpoint / resume: a loose solve's pressure, passed back in, is the
+    # initial guess; the resumed solve reaches the tight tolerance in fewer
+    # iterations than a solve from zero and agrees with the oracle
+    n = 64
+    fdev, (f1, f2) = body_force_dev(n)
+    loose = lr.lr_stokes_uzawa(h, n, fdev, tol_div=1e-4, eps=1e-10, prec="fp64", gmres=gmres)
+    assert loose.status == lr.LR_OK, h.last_error()
+    saved = tuple(t.clone() for t in loose.p)
+    full = lr.lr_stokes_uzawa(h, n, fdev, tol_div=1e-9, eps=1e-10, prec="fp64", gmres=gmres)
+    res = lr.lr_stokes_uzawa(h, n, fdev, tol_div=1e-9, eps=1e-10, prec="fp64", gmres=gmres, p0=saved)
+    assert res.status == lr.LR_OK, h.last_error()
+    assert res.iters < full.iters, (res.iters, full.iters)
+    if not gmres:
+        assert res.history[0] < 1e-3  # CG starts from the saved iterate's residual
+    ref = S.uzawa_cg(f1, f2, n, tol=1e-13)
+    p = dense(res.p)
+    assert np.linalg.norm(p - ref.p) <= 1e-7 * np.linalg.norm(ref.p)
