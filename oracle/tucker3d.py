@@ -339,6 +339,9 @@ def hosvd_round(C: np.ndarray, Qs, eps: float):
     each unfolding of the core, each mode truncated with a tail <= eps ||C|| /
     sqrt(3) (so the error is <= eps ||C||), core projected on the kept
     singular vectors.  Returns (G, [U_k], [sigma_k])."""
+    if C.size == 0 or not np.any(C):
+        # the zero tensor: its rounding keeps nothing (ranks 0)
+        return np.zeros((0, 0, 0)), [q[:, :0] for q in Qs], [np.zeros(0)] * 3
     total = np.linalg.norm(C)
     W, sig = [], []
     for mode in range(3):

@@ -126,3 +126,18 @@ def test_smooth_rhs_generator_matches_its_function():
         D = inputs.smooth3d_dense(n)
         assert np.linalg.norm(F - D) <= 2e-6 * np.linalg.norm(D)
         assert max(G.shape) <= 24
+
+
+def test_zero_rhs_rounds_to_the_empty_tucker_tensor():
+    G, U1, U2, U3 = inputs.tucker_random(20, 2, seed=1)
+    res = T.lr_poisson3d(np.zeros_like(G), U1, U2, U3, 1e-6)
+    assert res.cross.converged and res.G.shape == (0, 0, 0)
+    assert all(U.shape == (20, 0) for U in res.U)
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 5), (7, 1, 4)])
+def test_tiny_grids_are_solved_to_rounding_error(n):
+    # grids smaller than the ranks: the cross spans the whole tensor
+    rhs = inputs.tucker_random(n, (1, 1, 1), seed=2)
+    res = T.lr_poisson3d(*rhs, 1e-10)
+    assert T.rel_error_full(res, T.tucker_full(*rhs)) <= 1e-13
