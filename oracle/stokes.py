@@ -136,7 +136,7 @@ def uzawa_cg(f1: np.ndarray, f2: np.ndarray, n: int, tol: float = 1e-10, maxit: 
     p = project_kernel(p, n)
     u = laplace_solve(f1 - bx(p, n), n)
     v = laplace_solve(f2 - by(p, n), n)
-    res = np.linalg.norm(bt(u, v, n)) / nr0
+    res = np.linalg.norm(bt(u, v, n)) / nr0 if nr0 > 0.0 else 0.0  # zero force: u = p = 0
     return UzawaResult(u, v, p, it, res, hist)
 
 

@@ -65,3 +65,9 @@ def test_cg_iterations_do_not_grow_with_the_grid():
         (a1, b1), (a2, b2) = S.body_force(n)
         its.append(S.uzawa_cg(a1 @ b1.T, a2 @ b2.T, n, tol=1e-8).iters)
     assert max(its) <= min(its) + 6, its
+
+
+def test_zero_force_gives_the_zero_solution():
+    res = S.uzawa_cg(np.zeros((7, 7)), np.zeros((7, 7)), 8)
+    assert res.iters == 0 and res.resid == 0.0
+    assert not np.any(res.u) and not np.any(res.v) and not np.any(res.p)
