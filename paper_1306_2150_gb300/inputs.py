@@ -20,6 +20,10 @@ x_i = i/(n+1)):
   factored form and compressed to a relative Frobenius tolerance.
 * ``batch_problems``    -- a list of (n, r) drawn with n log-uniform in
   [n_lo, n_hi] and r uniform in {1..r_hi}, each with separable_random factors.
+* ``smooth3d``          -- f(x,y,z) = exp(-(x+2y+3z)) + 1/sqrt(x^2+y^2+z^2+0.01) on
+  the n^3 interior grid, in Tucker format compressed to a relative tolerance.
+* ``tucker_random``     -- random Tucker tensors with separable factor columns
+  and normal core entries (3D parity cases).
 """
 from __future__ import annotations
 
