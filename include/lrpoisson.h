@@ -73,12 +73,13 @@ typedef enum {
 #define LR_FLAG_GRAPH 4u   /* capture the enqueued work once as a CUDA graph
                               (keyed by every pointer, size and option) and
                               replay it on later calls with the same key */
-#define LR_FLAG_CLUSTER_DST 8u
-#define LR_FLAG_GMRES 16u       /* lr_stokes_uzawa: restarted inexact GMRES with adaptive
-                                   accuracy (Section 5) instead of conjugate gradients */  /* lr_poisson2d: run both transforms with the
-                                   cluster variant (one thread-block cluster
-                                   per column, 8192 <= M <= 131072) for this
-                                   call, whatever the tuned choice */
+#define LR_FLAG_CLUSTER_DST 8u /* lr_poisson2d: run both transforms with the
+                                  cluster variant (one thread-block cluster
+                                  per column, 8192 <= M <= 131072) for this
+                                  call, whatever the tuned choice */
+#define LR_FLAG_GMRES 16u      /* lr_stokes_uzawa: restarted inexact GMRES with
+                                  adaptive accuracy (Section 5) instead of
+                                  conjugate gradients */
 
 /* Phases of lr_poisson2d timed under LR_FLAG_TIMING. */
 #define LR_PHASE_FORWARD_DST 0  /* DST of the right-hand side factors      */
@@ -341,7 +342,10 @@ lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat*
                               int reps, lr_tune* out);
 
 /* lr_truncate without any allocation (the paper has no counterpart; this is
- * a deployment variant of lr_truncate above, same arithmetic and results).
+ * a deployment variant of lr_truncate above).  The method is the same, but
+ * its Gram sums run over a fixed grid of 64 CTAs, so the summation order
+ * differs from lr_truncate's: results agree up to rounding, and the kept rank
+ * may differ by one where a singular value sits at the eps cutoff.
  *
  * For callers that cannot allocate device or pinned memory themselves: code
  * running inside another framework's memory pool, where a direct cudaMalloc

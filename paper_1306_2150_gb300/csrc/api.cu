@@ -2271,6 +2271,7 @@ lr_status lr_autotune(lr_handle h, const lr_mat* rhs, const lr_options* opt, int
   plan->log_tile[pi] = best_tile < 0 ? 0 : best_tile;
   h->tuned_cs[std::make_tuple(m, (int)o.prec, (int)o.op)] = best_cs;
   h->timed = false;
+  ++h->ws_gen;  // graphs captured before tuning bake in the untuned shapes
   if (out) {
     out->cluster_size = best_cs;
     out->log_tile = best_tile < 0 ? 0 : best_tile;
@@ -2326,6 +2327,7 @@ lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat*
   }
   h->batch_ipc[pi] = best_ipc;
   h->timed = false;
+  ++h->ws_gen;  // graphs captured before tuning bake in the untuned shapes
   if (out) {
     auto it = h->tuned_cs.find(std::make_tuple(rhs[0].n1, (int)o.prec, (int)o.op));
     out->cluster_size = it != h->tuned_cs.end() ? it->second : 0;

@@ -600,13 +600,12 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
     ++k;
     if (sh.small >= 2) {
       if (probe_rounds >= A.max_probe_rounds || A.probes <= 0) { converged = 1; break; }
-      // Residual probes at splitmix64-drawn entries; one warp per probe, the
-      // same arithmetic in every CTA.
-      int P = A.probes < 32 ? A.probes : 32;
-      if (P > (NT >> 5)) P = NT >> 5;
-      if (warp < P) {
+      // Residual probes at splitmix64-drawn entries; probe p on warp p mod
+      // (warps per CTA), the same arithmetic in every CTA.
+      const int P = A.probes < 32 ? A.probes : 32;
+      for (int p = warp; p < P; p += NT >> 5) {
         const unsigned long long z = splitmix64_at(A.seed + (unsigned long long)probe_rounds,
-                                                   (unsigned long long)(warp + 1));
+                                                   (unsigned long long)(p + 1));
         const int pi = (int)((z >> 32) % (unsigned long long)m);
         const int pj = (int)((z & 0xFFFFFFFFULL) % (unsigned long long)m);
         double num = 0.0, sk = 0.0;
@@ -618,7 +617,7 @@ __global__ void __launch_bounds__(512, 1) cross_kernel(CrossArgs<T> A, int KS, i
         num = warp_sum(num);
         sk = warp_sum(sk);
         const double den = (double)A.a[pi] * (double)A.b[pj] + (double)A.b[pi] * (double)A.a[pj];
-        if (lane == 0) { sh.probe[warp] = fabs(num / den - sk); sh.probe_row[warp] = pi; }
+        if (lane == 0) { sh.probe[p] = fabs(num / den - sk); sh.probe_row[p] = pi; }
       }
       __syncthreads();
       if (tid == 0) {

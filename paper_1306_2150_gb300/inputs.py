@@ -22,6 +22,8 @@ x_i = i/(n+1)):
   [n_lo, n_hi] and r uniform in {1..r_hi}, each with separable_random factors.
 * ``smooth3d``          -- f(x,y,z) = exp(-(x+2y+3z)) + 1/sqrt(x^2+y^2+z^2+0.01) on
   the n^3 interior grid, in Tucker format compressed to a relative tolerance.
+* ``block_diagonal_freq`` -- frequency-space factors with disjoint supports
+  (a block-diagonal frequency-space solution; residual-probe cases).
 * ``tucker_random``     -- random Tucker tensors with separable factor columns
   and normal core entries (3D parity cases).
 """
@@ -78,6 +80,19 @@ def separable_random(n: int, r: int, seed: int = 0):
     V = a * np.exp(np.outer(x, u[:, 2]))
     return np.asfortranarray(U), np.asfortranarray(V)
 
+
+
+def block_diagonal_freq(n: int, split: int, seed: int = 5):
+    """Two frequency-space factor columns (n x 2, Fortran order) with disjoint
+    supports: column 0 is standard normal on indices < split and zero after,
+    column 1 standard normal on indices >= split and zero before, in both Uh
+    and Vh.  Uh Vh^T (and any entrywise rescaling of it) is block diagonal.
+    The caller maps them to space with the sine transform."""
+    z = normal(seed, 4 * n).reshape(4, n)
+    Uh, Vh = np.zeros((n, 2), order="F"), np.zeros((n, 2), order="F")
+    Uh[:split, 0], Vh[:split, 0] = z[0, :split], z[1, :split]
+    Uh[split:, 1], Vh[split:, 1] = z[2, split:], z[3, split:]
+    return Uh, Vh
 
 def _compress(P: np.ndarray, Q: np.ndarray, tol: float):
     """Re-express P Q^T with the fewest columns that keep a relative Frobenius

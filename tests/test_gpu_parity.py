@@ -149,6 +149,39 @@ def test_semistaggered_operator(lr, h):
     assert np.linalg.norm(X - Xs) <= 10 * eps * np.linalg.norm(Xs)
 
 
+
+@pytest.mark.parametrize("kind", ["5pt", "semi"])
+@pytest.mark.parametrize("cs", [0, 1, 3])
+def test_probe_restart_fp64_bitexact(lr, h, kind, cs):
+    # Block-diagonal Xh (Section 4.2 cross, reading G7 of the stop rule): the
+    # cross converges on block A, a residual probe lands in block B and the
+    # loop restarts at its row.  Pivots, probe rounds, steps and rank of the
+    # float64 path equal the oracle's; the error is within 10 eps.
+    m, eps = 128, 1e-6
+    Uh, Vh = inputs.block_diagonal_freq(m, 32)
+    U, V = O.dst1(Uh), O.dst1(Vh)
+    res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="fp64", op=kind, cluster_size=cs)
+    assert res.status == lr.LR_OK
+    ou, os_, ov, info = O.lr_poisson2d(U, V, kind, eps)
+    assert info.cross.probe_rounds == 2
+    assert res.info.probe_rounds == info.cross.probe_rounds
+    assert res.info.aca_steps == info.cross.k
+    assert res.pivots_I == info.cross.I and res.pivots_J == info.cross.J
+    assert res.info.rank == info.rank
+    assert O.rel_error_freq(Uo, s, Vo, U, V, kind) <= 10 * eps
+
+
+def test_probe_restart_mixed(lr, h):
+    m, eps = 4096, 1e-6
+    Uh, Vh = inputs.block_diagonal_freq(m, 1024)
+    U, V = O.dst1(Uh), O.dst1(Vh)
+    res, Uo, s, Vo = solve(lr, h, U, V, eps=eps, prec="mixed")
+    assert res.status == lr.LR_OK
+    assert res.info.probe_rounds >= 2
+    assert max(res.pivots_I) >= 1024
+    assert O.rel_error_freq(Uo, s, Vo, U, V, "5pt") <= 10 * eps
+
+
 # ------------------------------------------------------------------ edges
 @pytest.mark.parametrize("m", [1, 2, 3, 5])
 def test_tiny_grids(lr, h, m):

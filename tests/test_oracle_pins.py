@@ -239,6 +239,78 @@ def test_cross_zero_first_row_moves_on():
     assert O.rel_error_freq(Uo, s, Vo, u, v, "5pt") < 1e-13
 
 
+
+@pytest.mark.parametrize("kind", O.KINDS)
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_cross_probe_restart_finds_untouched_block(kind, tol):
+    # Section 4.2's cross with the residual probes of the stop rule (reading
+    # G7) on a block-diagonal Xh: block A (rows and columns < split, the low
+    # frequencies where the cross starts) and block B.  Partial pivoting in A
+    # never sees B (its residual rows and columns are exactly zero there), so
+    # the first converged skeleton covers block A only; a probe lands in
+    # block B, whose residual is the full entry, and the loop restarts at that
+    # probe's row.  Pinned by brute force on the whole Xh: the result reaches
+    # the tolerance only because of the restart, and the restart row is the
+    # row of the largest probed residual of the first round.
+    m, split = 128, 32
+    a, b = O.symbol(m, kind)
+    Uh, Vh = inputs.block_diagonal_freq(m, split)
+    Xh = (Uh @ Vh.T) / O.symbol_matrix(a, b)
+    cr = O.aca_cross(Uh, Vh, a, b, tol, 64, probes=16, seed=0)
+    Xa = (cr.C * cr.d) @ cr.R.T
+    assert cr.converged and cr.probe_rounds == 2
+    assert np.linalg.norm(Xh - Xa) <= tol * np.linalg.norm(Xh)
+    # the steps before the restart stay in block A, the restart row is in B
+    k1 = next(l for l, i in enumerate(cr.I) if i >= split)
+    assert k1 >= 2 and all(i < split and j < split for i, j in zip(cr.I[:k1], cr.J[:k1]))
+    # brute force: residual of the first skeleton at the 16 probed entries
+    X1 = (cr.C[:, :k1] * cr.d[:k1]) @ cr.R[:, :k1].T
+    n1 = np.linalg.norm(X1)
+    best, best_row = -1.0, -1
+    for z in O.splitmix64_stream(0, 16):
+        pi, pj = (z >> 32) % m, (z & 0xFFFFFFFF) % m
+        res = abs(Xh[pi, pj] - X1[pi, pj])
+        if res > best:
+            best, best_row = res, pi
+    assert best > tol * n1            # the first round fails ...
+    assert cr.I[k1] == best_row       # ... and restarts at the worst probe's row
+    # without probes the cross stops after block A: the error is block B's size
+    cr0 = O.aca_cross(Uh, Vh, a, b, tol, 64, probes=0)
+    X0 = (cr0.C * cr0.d) @ cr0.R.T
+    eB = np.linalg.norm(Xh[split:, split:]) / np.linalg.norm(Xh)
+    assert max(cr0.I) < split and cr0.probe_rounds == 0
+    assert np.linalg.norm(Xh - X0) / np.linalg.norm(Xh) == pytest.approx(eB, rel=1e-6)
+    assert eB > 1e3 * tol
+
+
+
+@pytest.mark.parametrize("factor,restarts", [(2.0, True), (0.5, False)])
+def test_cross_probe_threshold_is_tol_times_skeleton_norm(factor, restarts):
+    # The probe test compares |residual| with tol ||S_k||_F (reading G7).
+    # Block A is scaled so that ||S_k||_F is far from 1 (a threshold on
+    # ||S_k||^2 or without the norm would move by orders of magnitude); block
+    # B is scaled so that its largest probed entry (restart expected) or its
+    # largest entry anywhere (no restart) is `factor` times the threshold.
+    m, split, tol = 128, 32, 1e-6
+    a, b = O.symbol(m, "5pt")
+    Uh, Vh = inputs.block_diagonal_freq(m, split)
+    Uh[:, 0] *= 1e4
+    lam = O.symbol_matrix(a, b)
+    XA = np.outer(Uh[:, 0], Vh[:, 0]) / lam
+    XB = np.outer(Uh[:, 1], Vh[:, 1]) / lam
+    nA = np.linalg.norm(XA)
+    assert nA > 1e2
+    probed = [((z >> 32) % m, (z & 0xFFFFFFFF) % m) for z in O.splitmix64_stream(0, 16)]
+    size = max(abs(XB[i, j]) for i, j in probed) if restarts else np.abs(XB).max()
+    Uh[:, 1] *= factor * tol * nA / size
+    cr = O.aca_cross(Uh, Vh, a, b, tol, 64, probes=16, seed=0)
+    assert cr.converged
+    if restarts:
+        assert cr.probe_rounds == 2 and max(cr.I) >= split
+    else:
+        assert cr.probe_rounds == 1 and max(cr.I) < split
+
+
 # ---------------------------------------------------------------- rounding
 def test_truncation_rank_hand_cases():
     assert O.truncation_rank(np.array([1.0, 0.0, 0.0]), 1e-12) == 1

@@ -73,6 +73,36 @@ def test_noalloc_truncate_matches_lr_truncate_twice(lr):
         h.close()
 
 
+def test_noalloc_truncate_matches_oracle(lr):
+    # Against the oracle's rounding (Section 3: QR of both factors, SVD of the
+    # core, truncation at eps): the kept rank may differ by one where a
+    # singular value sits at the cutoff; the singular values agree to 1e-10 of
+    # the largest and the rounded matrices to the truncation tolerance.
+    from oracle import poisson_lowrank as O
+    for seed, (n1, n2, k, eps) in enumerate([(700, 530, 14, 1e-7), (3000, 2900, 40, 1e-10), (129, 65, 64, 1e-6)]):
+        U, s, V = _problem(10 + seed, n1, n2, k)
+        st, Un, sn, Vn = _noalloc(lr, U, s, V, eps, 64)
+        Uo, so, Vo, ok = O.lr_truncate(U, s, V, eps, 64)
+        assert st == lr.LR_OK and ok
+        assert abs(len(sn) - len(so)) <= 1
+        q = min(len(sn), len(so))
+        assert np.abs(sn[:q] - so[:q]).max() <= 1e-10 * so[0]
+        Xn = (Un * sn) @ Vn.T
+        Xo = (Uo * so) @ Vo.T
+        assert np.linalg.norm(Xn - Xo) <= 10 * eps * np.linalg.norm(Xo)
+
+
+def test_noalloc_cut_to_rmax(lr):
+    # more columns needed than rmax: LR_ENOCONV with the leading rmax kept
+    from oracle import poisson_lowrank as O
+    U, s, V = _problem(3, 500, 400, 12)
+    st, Un, sn, Vn = _noalloc(lr, U, s, V, 1e-12, 5)
+    Uo, so, Vo, ok = O.lr_truncate(U, s, V, 1e-12, 5)
+    assert st == lr.LR_ENOCONV and not ok
+    assert len(sn) == 5
+    assert np.abs(sn - so).max() <= 1e-10 * so[0]
+
+
 def test_noalloc_rejects_rank_beyond_static_limit(lr):
     U, s, V = _problem(5, 200, 200, 65)
     st, *_ = _noalloc(lr, U, s, V, 1e-6, 64)
