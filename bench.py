@@ -105,6 +105,66 @@ def run_cpu_baseline(n: int, seconds: float, steps: int = 1) -> dict:
                       f"+ numpy QR/SVD), single thread, median"}
 
 
+def run_cpu_baseline_all_cores(n: int, seconds: float) -> dict:
+    """The oracle's low-rank solve on every host core at once: one
+    single-threaded worker process per core, each timing solves for about
+    `seconds`; ms per solve = the slowest worker's wall time / all solves."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")  # no fork after the GPU was touched
+        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx) as ex:
+            res = list(ex.map(_cpu_all_worker, [(n, seconds)] * cores))
+    except Exception as e:  # pragma: no cover
+        return {"error": str(e)[-200:]}
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    solves = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": round(1e3 * wall / solves, 3), "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"{solves} oracle low-rank solves at n={n} on {cores} worker processes "
+                      f"(one single-threaded solver per core), {wall:.1f} s wall"}
+
+
+def _cpu_all_worker(arg):
+    n, seconds = arg
+    sys.path.insert(0, ROOT)
+    from oracle import poisson_lowrank as O
+    from paper_1306_2150_gb300 import inputs
+    U, V = inputs.smooth_sum(n, EPS)
+    t0 = time.perf_counter()
+    count = 0
+    while count < 1 or time.perf_counter() - t0 < seconds:
+        O.lr_poisson2d(U, V, "5pt", EPS)
+        count += 1
+    return count, time.perf_counter() - t0
+
+
+def rel_error_sampled(res_U, res_s, res_V, U, V, rows: int = 256, kind: str = "5pt") -> float:
+    """Relative Frobenius error of a GPU result against the exact discrete
+    solution, from the oracle's Parseval evaluation on `rows` evenly spaced
+    frequency rows (all rows when the grid is smaller)."""
+    import numpy as np
+    from oracle import poisson_lowrank as O
+    Uo = res_U.detach().cpu().numpy() if hasattr(res_U, "cpu") else res_U
+    so = res_s.detach().cpu().numpy() if hasattr(res_s, "cpu") else res_s
+    Vo = res_V.detach().cpu().numpy() if hasattr(res_V, "cpu") else res_V
+    Un = U.numpy() if hasattr(U, "numpy") else U
+    Vn = V.numpy() if hasattr(V, "numpy") else V
+    m = Un.shape[0]
+    idx = None if m <= rows else np.unique(np.linspace(0, m - 1, rows).astype(int))
+    return float(O.rel_error_freq(Uo, so, Vo, Un, Vn, kind, rows=idx))
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     """SM clock and clock-event (throttle) reasons sampled while a timed region
@@ -214,7 +274,11 @@ class Clocks:
 # ---------------------------------------------------------------- ncu traffic
 # DRAM bytes per launch of each phase's kernel at this workload, from the
 # committed ncu summaries; null once the kernel source has changed since.
-TRAFFIC_FILES = {"cross": ("profiles/cross_kernel_f32_n16384.md", "paper_1306_2150_gb300/csrc/cross.cu")}
+TRAFFIC_FILES = {
+    "cross": ("profiles/batch_cross_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
+    "forward_dst": ("profiles/batch_dst_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
+    "inverse_dst": ("profiles/batch_dst_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
+}
 
 
 def committed_traffic(phase: str):
@@ -242,7 +306,7 @@ def algorithmic_bytes(n: int, r: int, k: int, R: int, w: int) -> dict:
     the cross reads Uh, Vh and writes the k-column skeleton C, R; the inverse
     DST reads the R kept columns of both factors (w) and writes float64."""
     return {"forward_dst": 2 * n * r * (8 + w), "cross": 2 * n * (r + k) * w,
-            "inverse_dst": 2 * n * R * (w + 8)}
+            "rounding": 2 * k * k * 8 + 2 * n * (k + R) * w, "inverse_dst": 2 * n * R * (w + 8)}
 
 
 def gpu_arm(args, rank: int, world: int) -> dict | None:
@@ -317,7 +381,11 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
             stream.synchronize()
             e2e.append(a.elapsed_time(b))
         R = info2.rank
+        # accuracy of the timed result (outside the timed region)
+        lr.lr_poisson2d(h, Ud, Vd, eps=EPS, prec=prec, out=out)
+        err = rel_error_sampled(out[0][:, :R], out[1][:R], out[2][:, :R], U, V)
         results[prec] = {
+            "rel_err": err,
             "ms": statistics.median(per), "ms_mean": statistics.mean(per), "per_step": per,
             "phases": {k: statistics.median([p[k] for p in ph]) for k in ph[0]},
             "rank": R, "aca_steps": info2.aca_steps, "launches": info2.launches,
@@ -344,7 +412,8 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
             stream.synchronize()
             per.append(a.elapsed_time(b))
         results["tight_" + prec] = {"ms": statistics.median(per), "rank": rr.info.rank, "r": U2.shape[1],
-                                    "refine_rounds": rr.info.refine_rounds, "status": rr.status}
+                                    "refine_rounds": rr.info.refine_rounds, "status": rr.status,
+                                    "rel_err": rel_error_sampled(rr.U, rr.s, rr.V, U2, V2)}
     # ---- crossover against the full-grid solver X = S((S F S)/Lambda)S on the
     # dense grid (same smooth right-hand side, single solves, 3 timed each)
     results["crossover"] = []
@@ -397,7 +466,9 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
             rs = lr.lr_stokes_uzawa(h, ns, fs, tol_div=1e-6, eps=1e-7, prec=prec, maxit=mi, check=False, gmres=gm)
             b.record(stream)
             stream.synchronize()
-            row[prec + ("_gmres" if gm else "")] = {"ms": round(a.elapsed_time(b), 3), "iters": rs.iters, "status": rs.status,
+            ok = rs.status == lr.LR_OK
+            row[prec + ("_gmres" if gm else "")] = {"ms": round(a.elapsed_time(b), 3) if ok else None,
+                         "converged": ok, "iters": rs.iters, "status": rs.status,
                          "cg_residual": rs.history[-1],
                          "velocity_divergence": rs.resid, "pressure_rank": int(rs.p[1].shape[0]),
                          "velocity_ranks": [int(c[1].shape[0]) for c in rs.u]}
@@ -472,20 +543,29 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                "r_min": min(x[1] for x in specs), "r_max": max(x[1] for x in specs),
                "unknowns_total": int(sum(x[0] * x[0] for x in specs))}
         for prec in ("mixed", "fp64"):
-            for _ in range(2):
-                lr.lr_poisson2d_batched(h, ub, eps=EPS, prec=prec, graph=True)
-            per = []
-            for i in range(3):
-                flush.fill_(i & 0xFF)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                lr.lr_poisson2d_batched(h, ub, eps=EPS, prec=prec, graph=True, async_=True)
-                b.record(stream)
-                stream.synchronize()
-                per.append(a.elapsed_time(b))
-            row["batched_" + prec + "_ms"] = round(statistics.median(per), 3)
-            row["status_" + prec] = sorted(set(int(ub.status[i]) for i in range(len(specs))))
+            for streams in (False, True):
+                tag = prec + ("_streams" if streams else "")
+                for _ in range(2):
+                    lr.lr_poisson2d_batched(h, ub, eps=EPS, prec=prec, graph=True, streams=streams)
+                per = []
+                for i in range(3):
+                    flush.fill_(i & 0xFF)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    lr.lr_poisson2d_batched(h, ub, eps=EPS, prec=prec, graph=True, async_=True, streams=streams)
+                    b.record(stream)
+                    stream.synchronize()
+                    per.append(a.elapsed_time(b))
+                info_u, _, _ = lr.lr_get_info(h)
+                row["batched_" + tag + "_ms"] = round(statistics.median(per), 3)
+                row["launches_" + tag] = info_u.launches
+                lr.lr_poisson2d_batched(h, ub, eps=EPS, prec=prec, graph=True, streams=streams, check=False)
+                row["status_" + tag] = sorted(set(int(ub.status[i]) for i in range(len(specs))))
+                # accuracy of every 16th problem, on sampled rows
+                errs = [rel_error_sampled(*ub.result(i), *uprobs[i], rows=128) for i in range(0, len(specs), 16)]
+                row["max_rel_err_" + tag] = max(errs)
+                row["checked_" + tag] = len(errs)
         flush.fill_(7)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -501,6 +581,7 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         results["uneven"] = row
         del ub, uprobs
     # ---- throughput: batches of independent solves, one CUDA graph per batch
+    # (phase-batched launches), the per-problem stream form beside it
     B = args.batch
     probs = [(torch.from_numpy(U) * (1.0 + p / B), torch.from_numpy(V)) for p in range(B)]
     for prec in ("mixed", "fp64"):
@@ -524,9 +605,35 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                 per.append(a.elapsed_time(b))
         info, _, _ = lr.lr_get_info(h)
         ranks = [batch.c_sol[i].r for i in range(B)]
+        # accuracy of the timed results (outside the timed region): the first,
+        # middle and last problem on sampled rows
+        errs = [rel_error_sampled(*batch.result(p), *probs[p]) for p in sorted({0, B // 2, B - 1})]
+        # per-phase device time of one batched step (events between the
+        # phases; not a graph replay)
+        ph = []
+        for i in range(max(3, args.steps // 4)):
+            flush.fill_(i & 0xFF)
+            lr.lr_poisson2d_batched(h, batch, eps=EPS, prec=prec, timing=True)
+            ph.append(lr.lr_get_phase_times(h))
+        # the per-problem stream form of the same batch
+        for _ in range(2):
+            lr.lr_poisson2d_batched(h, batch, eps=EPS, prec=prec, graph=True, streams=True)
+        per_s = []
+        for i in range(max(3, args.steps // 4)):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lr.lr_poisson2d_batched(h, batch, eps=EPS, prec=prec, graph=True, async_=True, streams=True)
+            b.record(stream)
+            stream.synchronize()
+            per_s.append(a.elapsed_time(b))
         results["batch_" + prec] = {"ms_step": statistics.median(per), "per_step": per, "batch": B,
                                     "launches": info.launches, "clocks": clocks.summary(),
-                                    "ranks": sorted(set(ranks))}
+                                    "ranks": sorted(set(ranks)), "max_rel_err": max(errs),
+                                    "checked": len(errs),
+                                    "phases": {k: statistics.median([p[k] for p in ph]) for k in ph[0]},
+                                    "streams_ms_step": statistics.median(per_s)}
         del batch
     # ---- end to end through the C ABI: host factors in, host factors out
     batch = lr.Batch(probs)
@@ -596,7 +703,7 @@ def main():
         # The reference arm is the CPU oracle: rank 0 alone runs it.
         if rank != 0:
             return
-        cb = run_cpu_baseline(args.n, max(5.0, args.cpu_seconds), steps=args.steps)
+        cb = run_cpu_baseline_all_cores(args.n, max(5.0, args.cpu_seconds))
         line = {"impl": "reference", "metric": METRIC, "value": cb.get("value"), "unit": "ms",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": cb.get("value"), "higher_is_better": False, "scaling": "weak",
@@ -630,14 +737,31 @@ def main():
     mx, f64 = res["mixed"], res["fp64"]
     bm, bf, eb = res["batch_mixed"], res["batch_fp64"], res["e2e_batch"]
     n = args.n
-    # dominant kernel of the mixed path: the phase with the largest time
     ph = mx["phases"]
-    dom = max(("forward_dst", "cross", "inverse_dst"), key=lambda k: ph[k])
-    byts = algorithmic_bytes(n, mx["r"], mx["aca_steps"], mx["rank"], 4)[dom]
-    achieved = byts / (ph[dom] * 1e-3) / 1e9
-    B = bm["batch"]
-    value = bm["ms_step"] / B  # whole-job throughput: ms per solve
-    alg_total = sum(algorithmic_bytes(n, mx["r"], mx["aca_steps"], mx["rank"], 4).values())
+    B = bm["batch"] // world
+    value = bm["ms_step"] / bm["batch"]  # whole-job throughput: ms per solve
+    alg = algorithmic_bytes(n, mx["r"], mx["aca_steps"], mx["rank"], 4)
+    alg_total = sum(alg.values())
+    # dominant phase of the timed batched step (each phase one or a few
+    # launches over all B problems of a rank): its algorithmic bytes over its
+    # CUDA-event time
+    bph = bm["phases"]
+    dom = max(("forward_dst", "cross", "rounding", "inverse_dst"), key=lambda k: bph[k])
+    byts = B * alg[dom]
+    achieved = byts / (bph[dom] * 1e-3) / 1e9
+    acc = {"single_mixed": mx["rel_err"], "single_fp64": f64["rel_err"],
+           "batch_mixed_max": bm["max_rel_err"], "batch_fp64_max": bf["max_rel_err"],
+           "tight_fp64": res["tight_fp64"]["rel_err"], "tight_mixed_refined": res["tight_mixed"]["rel_err"]}
+    un = res.get("uneven") or {}
+    for key in ("mixed", "fp64", "mixed_streams", "fp64_streams"):
+        if "max_rel_err_" + key in un:
+            acc["uneven_" + key + "_max"] = un["max_rel_err_" + key]
+    bound = {k: (EPS_TIGHT if k.startswith("tight") else EPS) for k in acc}
+    acc_line = {k: float(f"{v:.3e}") for k, v in acc.items()}
+    acc_line["within_10eps"] = all(acc[k] <= 10 * bound[k] for k in acc)
+    acc_line["note"] = ("relative Frobenius error against the exact discrete solution (oracle, Parseval, "
+                        "256 sampled frequency rows at n=16384); eps=1e-6 rows against 10*eps, eps=1e-10 rows "
+                        "against 10*1e-10")
     line = {
         "metric": METRIC, "value": round(value, 5), "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(bm["ms_step"], 4),
@@ -647,7 +771,13 @@ def main():
                    "rhs_rank": mx["r"], "solution_rank": mx["rank"], "cross_steps": mx["aca_steps"],
                    "l2": "flushed (512 MiB write) between timed steps",
                    "replicas_per_gpu": 1, "parallelism": "replicas" if world > 1 else "single"},
-        "batched_fp64": {"value": round(bf["ms_step"] / B, 5), "unit": "ms per solve"},
+        "batched_fp64": {"value": round(bf["ms_step"] / bm["batch"], 5), "unit": "ms per solve"},
+        "batched_phases_ms": {"mixed": {k: round(v, 4) for k, v in bph.items()},
+                              "fp64": {k: round(v, 4) for k, v in bf["phases"].items()}},
+        "batched_stream_form": {"mixed": round(bm["streams_ms_step"] / B, 5),
+                                "fp64": round(bf["streams_ms_step"] / B, 5), "unit": "ms per solve",
+                                "note": "one launch chain per problem over 32 streams (the previous form)"},
+        "accuracy": acc_line,
         "single_solve": {
             "mixed": {"value": round(mx["ms"], 4), "unit": "ms",
                       "phases_ms": {k: round(v, 4) for k, v in ph.items()}},
@@ -666,11 +796,13 @@ def main():
         "tucker3d": res["tucker"],
         "uneven_batch": res["uneven"],
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
+        "mixed_batched_over_fp64_batched": round(bf["ms_step"] / bm["ms_step"], 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2),
+        "roofline": {"bound": "hbm", "kernel": "batched " + dom, "achieved": round(achieved, 2),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 5),
                      "traffic": committed_traffic(dom), "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": byts, "launch_ms": round(ph[dom], 4)},
+                     "algorithmic_bytes_per_launch": byts, "launch_ms": round(bph[dom], 4),
+                     "problems_per_launch": B},
         "autotune": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                      for k, v in res["autotune"].items()},
         "e2e": {"value": round(eb["ms_step"] / eb["batch"], 5), "unit": "ms", "h2d_bytes_per_step": eb["h2d"],
@@ -679,7 +811,9 @@ def main():
         "clocks": bm["clocks"],
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = run_cpu_baseline(n, args.cpu_seconds)
+        cb = run_cpu_baseline_all_cores(n, args.cpu_seconds)
+        cb["single_core"] = run_cpu_baseline(n, args.cpu_seconds)
+        line["cpu_baseline"] = cb
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

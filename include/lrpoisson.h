@@ -68,8 +68,11 @@ typedef enum {
 /* Bits of lr_options.flags. */
 #define LR_FLAG_ASYNC 1u   /* do not wait for the stream; read rank/status with
                               lr_get_info() after synchronising the stream */
-#define LR_FLAG_TIMING 2u  /* record CUDA events between the phases of a solve;
-                              read them with lr_get_phase_times() */
+#define LR_FLAG_TIMING 2u  /* record CUDA events between the phases of a solve
+                              (lr_poisson2d, or a phase-batched
+                              lr_poisson2d_batched: each phase then covers
+                              every problem); read them with
+                              lr_get_phase_times() */
 #define LR_FLAG_GRAPH 4u   /* capture the enqueued work once as a CUDA graph
                               (keyed by every pointer, size and option) and
                               replay it on later calls with the same key */
@@ -80,6 +83,10 @@ typedef enum {
 #define LR_FLAG_GMRES 16u      /* lr_stokes_uzawa: restarted inexact GMRES with
                                   adaptive accuracy (Section 5) instead of
                                   conjugate gradients */
+#define LR_FLAG_BATCH_STREAMS 32u /* lr_poisson2d_batched: run each problem as
+                                     its own launch chain over internal
+                                     streams instead of the phase-batched
+                                     launches */
 
 /* Phases of lr_poisson2d timed under LR_FLAG_TIMING. */
 #define LR_PHASE_FORWARD_DST 0  /* DST of the right-hand side factors      */
@@ -180,13 +187,21 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
 
 /* Batched low-rank Poisson solves: `batch` independent problems (host arrays
  * rhs[batch], sol[batch] of lr_mat with device pointers, each as for
- * lr_poisson2d, sizes and ranks may differ) with shared options.  Problems
- * are enqueued in decreasing order of size over 32 internal streams that fork
- * from and join back into the handle's stream; with LR_FLAG_GRAPH the whole
- * batch is one replayed CUDA graph.  per_problem (host, may be NULL) receives
- * each problem's status; the return value is LR_OK or the first failure.
- * The paper solves one problem at a time; batching is the data-parallel form
- * of its Section 4.2 solve for many right-hand sides. */
+ * lr_poisson2d, sizes and ranks may differ) with shared options.
+ * Phase-batched form (default when every order m is at most 65536 in
+ * LR_MIXED, 32768 in LR_FP64): each step of the solve runs for all problems
+ * in one launch -- the forward DST of every factor column, the cross of
+ * every problem (one CTA, or a cluster of 2 or 4 CTAs, per problem, longest
+ * problems first; cluster sizes run concurrently), the rounding cores, the
+ * rotation of the skeletons and the inverse DST -- about ten launches per
+ * batch.  The problem descriptors are uploaded with the work.  With
+ * LR_FLAG_BATCH_STREAMS (or larger orders) each problem is instead its own
+ * launch chain, dealt in decreasing order of size over 32 internal streams.
+ * With LR_FLAG_GRAPH the whole batch is one replayed CUDA graph.
+ * per_problem (host, may be NULL) receives each problem's status; the return
+ * value is LR_OK or the first failure.  The paper solves one problem at a
+ * time; batching is the data-parallel form of its Section 4.2 solve for many
+ * right-hand sides. */
 lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol,
                                const lr_options* opt, lr_status* per_problem);
 
@@ -203,10 +218,12 @@ lr_status lr_truncate(lr_handle h, lr_mat* X, double eps, int rmax);
  * may be NULL) receive up to cap cross pivot indices (0-based). */
 lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, int cap);
 
-/* Milliseconds of each phase (LR_PHASE_*) of the last lr_poisson2d run with
- * LR_FLAG_TIMING, measured with CUDA events on the handle's stream.  Waits for
- * the last event.  n <= LR_NUM_PHASES entries are written.  LR_EINVAL if the
- * last solve was not timed. */
+/* Milliseconds of each phase (LR_PHASE_*) of the last lr_poisson2d or
+ * phase-batched lr_poisson2d_batched run with LR_FLAG_TIMING, measured with
+ * CUDA events on the handle's stream (in a batch, LR_PHASE_ROUNDING also
+ * covers the rotation of the skeletons).  Waits for the last event.
+ * n <= LR_NUM_PHASES entries are written.  LR_EINVAL if the last solve was
+ * not timed. */
 lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
 
 /* Low-rank Uzawa solve of the 2D Stokes problem on semi-staggered grids
@@ -322,9 +339,12 @@ lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double
  * while tuning.
  *
  * lr_autotune_batched times lr_poisson2d_batched on the given batch (its
- * sol buffers receive the trial results) for 1024, 2048, 4096 and 8192
- * indices per cross CTA and keeps the fastest for batched solves of that
- * precision on this handle (default 2048).
+ * sol buffers receive the trial results) for several numbers of indices per
+ * cross CTA and keeps the fastest for batched solves of that precision on
+ * this handle: 2048, 4096, 8192, 16384 (LR_FP64: up to 8192; default 4096)
+ * for the phase-batched form, which then takes 1, 2 or 4 CTAs per problem;
+ * 1024, 2048, 4096, 8192 (default 2048) for the stream form
+ * (LR_FLAG_BATCH_STREAMS in opt->flags).
  *
  * Both synchronise and return LR_EINVAL for bad arguments.  `out` (host, may
  * be NULL) receives the choice and the times. */

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrpoisson.so")
-SOURCES = ["dst.cu", "cross.cu", "core.cu", "api.cu", "noalloc.cu", "refine.cu", "stokes.cu", "tucker.cu"]
+SOURCES = ["dst.cu", "cross.cu", "core.cu", "api.cu", "noalloc.cu", "refine.cu", "stokes.cu", "tucker.cu",
+           "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

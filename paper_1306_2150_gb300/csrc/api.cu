@@ -64,6 +64,18 @@ struct lr_handle_s {
   // and indices per cross CTA of batched solves, per precision
   std::map<std::tuple<int, int, int>, int> tuned_cs;
   int batch_ipc[2] = {2048, 2048};
+  // phase-batched solves: twiddle tables of length 4096 (float64, float32),
+  // the device copy of the last batch's descriptors and its pinned staging
+  // buffer (reused once the event says the previous upload has run), and one
+  // device descriptor block per captured graph
+  void* tw4096[2] = {nullptr, nullptr};
+  char* bdesc = nullptr;
+  size_t bdesc_cap = 0;
+  char* h_bdesc = nullptr;
+  size_t h_bdesc_cap = 0;
+  cudaEvent_t bdesc_ev = nullptr;
+  std::map<std::string, char*> graph_desc;
+  int cross_rows[2] = {4096, 4096};  // indices per CTA of the batched cross (float64, float32)
 };
 
 namespace {
@@ -330,8 +342,11 @@ lr_status run_maybe_graph(lr_handle h, bool graph, const std::string& key, F&& b
     cudaGraphDestroy(gr);
     if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
     if (h->graphs.size() >= 32) {  // bounded cache
+      cudaStreamSynchronize(h->stream);
       for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
       h->graphs.clear();
+      for (auto& kv : h->graph_desc) cudaFree(kv.second);
+      h->graph_desc.clear();
     }
     it = h->graphs.emplace(k, ex).first;
   }
@@ -825,8 +840,8 @@ lr_status ensure_batch_streams(lr_handle h) {
 }
 
 template <typename T>
-lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options& o,
-                          const std::vector<Plan*>& plans, lr_status* per_problem) {
+lr_status solve2d_batched_streams(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options& o,
+                                  const std::vector<Plan*>& plans, lr_status* per_problem) {
   std::vector<SolveGeom> geo(batch);
   std::vector<size_t> off(batch);
   Carve c;
@@ -910,6 +925,357 @@ lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol
   }
   if (worst != LR_OK) fail(h, worst, "some problems did not converge or were cut (see per_problem)");
   return worst;
+}
+
+// Twiddles exp(-2 pi i q / 4096) of the batched transforms, per precision.
+lr_status ensure_tw4096(lr_handle h, bool f32) {
+  void*& t = h->tw4096[f32 ? 1 : 0];
+  if (t) return LR_OK;
+  std::vector<double> re(4096), im(4096);
+  for (int q = 0; q < 4096; ++q) {
+    // angle reduced to the first octant in integers (as the plan tables)
+    const int p = q / 1024, r = q % 1024;
+    double c, sn;
+    if (2 * r <= 1024) { const double th = 2.0 * M_PI * r / 4096.0; c = std::cos(th); sn = std::sin(th); }
+    else { const double th = 2.0 * M_PI * (1024 - r) / 4096.0; c = std::sin(th); sn = std::cos(th); }
+    double x, y;  // exp(+2 pi i q / 4096)
+    switch (p) { case 0: x = c; y = sn; break; case 1: x = -sn; y = c; break;
+                 case 2: x = -c; y = -sn; break; default: x = sn; y = -c; }
+    re[q] = x;
+    im[q] = -y;   // conjugate: exp(-2 pi i q / 4096)
+  }
+  const size_t w = f32 ? sizeof(float) : sizeof(double);
+  std::vector<char> buf(4096 * 2 * w);
+  for (int q = 0; q < 4096; ++q) {
+    if (f32) { float* f = reinterpret_cast<float*>(buf.data()); f[2 * q] = (float)re[q]; f[2 * q + 1] = (float)im[q]; }
+    else { double* d = reinterpret_cast<double*>(buf.data()); d[2 * q] = re[q]; d[2 * q + 1] = im[q]; }
+  }
+  if (cudaMalloc(&t, buf.size()) != cudaSuccess) {
+    cudaGetLastError();
+    t = nullptr;
+    return fail(h, LR_ENOMEM, "twiddle table");
+  }
+  LR_CUDA(h, cudaMemcpy(t, buf.data(), buf.size(), cudaMemcpyHostToDevice), "twiddle table");
+  return LR_OK;
+}
+
+// Host-built description of a phase-batched solve: the problem records and
+// the item lists of every launch, in one block uploaded to the device.
+struct BatchLayout {
+  std::vector<char> blob;  // [BatchProb x n][int lists]
+  size_t probs_off = 0;
+  struct ListRef { size_t list, start; int n, items; };
+  ListRef fwd_small{}, fwd_col{}, fwd_row{}, inv_small{}, inv_col{}, inv_row{}, rot{};
+  struct CrossGroup { size_t list; int n, cs, rows; };
+  std::vector<CrossGroup> cross;
+  BatchItems items(const ListRef& r, const char* dev) const {
+    BatchItems b;
+    b.list = reinterpret_cast<const int*>(dev + r.list);
+    b.start = reinterpret_cast<const int*>(dev + r.start);
+    b.n = r.n;
+    b.items = r.items;
+    return b;
+  }
+};
+
+// True if every problem fits the phase-batched kernels in this precision.
+bool batch_phased_fits(int batch, const lr_mat* rhs, bool f32) {
+  const int lim = 4 * batch_cross_max_rows(f32);
+  for (int i = 0; i < batch; ++i)
+    if (rhs[i].n1 > lim) return false;
+  return true;
+}
+
+template <typename T>
+lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options& o,
+                                 const std::vector<Plan*>& plans, lr_status* per_problem) {
+  const bool f32 = sizeof(T) == 4;
+  lr_status s;
+  if ((s = ensure_tw4096(h, f32)) != LR_OK) return s;
+  // ---- workspace: per problem the single-solve slice plus the rotated
+  // skeleton W (m x 2 ncap), then the solve states
+  std::vector<SolveGeom> geo(batch);
+  std::vector<size_t> off(batch), woff(batch);
+  Carve c;
+  for (int i = 0; i < batch; ++i) {
+    geo[i] = geom_of(rhs[i].n1, rhs[i].r, sol[i].rmax, o, *plans[i]);
+    off[i] = c.off;
+    carve_slice<T>(c, geo[i]);
+    woff[i] = c.off;
+    c.take<char>(sizeof(T) * (size_t)geo[i].ldw * 2 * geo[i].ncap_out);
+  }
+  const size_t st_off = c.off;
+  c.take<SolveState>(sizeof(SolveState) * batch);
+  const size_t live_off = c.off;  // device-written item tables of the inverse transforms
+  c.take<int>(sizeof(int) * 3 * ((size_t)batch + 1));
+  if ((s = ensure_ws(h, c.off)) != LR_OK) return s;
+  if (h->bstate_cap < batch) {
+    if (h->h_bstate) cudaFreeHost(h->h_bstate);
+    h->h_bstate = nullptr;
+    h->bstate_cap = 0;
+    if (cudaMallocHost(&h->h_bstate, sizeof(SolveState) * batch) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, LR_ENOMEM, "pinned status buffer");
+    }
+    h->bstate_cap = batch;
+    ++h->ws_gen;
+  }
+  if ((s = ensure_batch_streams(h)) != LR_OK) return s;
+  int* live_tab = reinterpret_cast<int*>(static_cast<char*>(h->ws) + live_off);
+  char* base = static_cast<char*>(h->ws);
+  SolveState* states = reinterpret_cast<SolveState*>(base + st_off);
+  // ---- problem records
+  BatchLayout L;
+  std::vector<BatchProb> P(batch);
+  const int pi = f32 ? 1 : 0;
+  for (int i = 0; i < batch; ++i) {
+    const SolveGeom& g = geo[i];
+    const Plan& pl = *plans[i];
+    Carve ci;
+    ci.base = base + off[i];
+    const Slice<T> w = carve_slice<T>(ci, g);
+    BatchProb& b = P[i];
+    b.m = g.m; b.r = g.r; b.kcap = g.kcap; b.ldw = g.ldw; b.ncap = g.ncap_out;
+    b.logM = pl.logM; b.logM1 = pl.logM1; b.logM2 = pl.logM2;
+    b.ld_in = rhs[i].ld; b.ld_out = sol[i].ld;
+    b.U = rhs[i].U; b.V = rhs[i].V;
+    b.Uo = sol[i].U; b.Vo = sol[i].V; b.so = sol[i].s;
+    b.Uh = w.Uh; b.Vh = w.Vh; b.C = w.C; b.R = w.R; b.Tc = w.Tc; b.Tr = w.Tr;
+    b.W = base + woff[i];
+    b.work = w.work;
+    b.GC = w.GC; b.GR = w.GR; b.d = w.d; b.I = w.I; b.J = w.J;
+    b.st = &states[i];
+    const TablesT& tb = f32 ? pl.t32 : pl.t64;
+    b.chirp = tb.chirp; b.tw = tb.tw; b.bhat = tb.bhat;
+    b.sa = f32 ? (const void*)pl.sym_a32[o.op] : (const void*)pl.sym_a64[o.op];
+    b.sb = f32 ? (const void*)pl.sym_b32[o.op] : (const void*)pl.sym_b64[o.op];
+  }
+  // ---- item lists.  Cost order (longest first) for every list.
+  std::vector<int> order(batch);
+  for (int i = 0; i < batch; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)geo[a].m * (geo[a].r + 16) > (double)geo[b].m * (geo[b].r + 16);
+  });
+  std::vector<int> ints;
+  auto add_list = [&](std::vector<int> lst, std::vector<int> cnt, BatchLayout::ListRef& ref) {
+    ref.n = (int)lst.size();
+    ref.list = ints.size() * sizeof(int);
+    ints.insert(ints.end(), lst.begin(), lst.end());
+    ref.start = ints.size() * sizeof(int);
+    int acc = 0;
+    for (int c2 : cnt) { ints.push_back(acc); acc += c2; }
+    ints.push_back(acc);
+    ref.items = acc;
+  };
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<int> ls, cs_, lf, cf, rf;
+    for (int i : order) {
+      const int ncols = dir == 0 ? 2 * geo[i].r : 2 * geo[i].ncap_out;
+      const int logM = plans[i]->logM;
+      if (logM <= 12) {
+        const int nf = 1 << (12 - logM);
+        ls.push_back(i);
+        cs_.push_back((ncols + nf - 1) / nf);
+      } else {
+        const int logM1 = plans[i]->logM1, logM2 = plans[i]->logM2;
+        lf.push_back(i);
+        cf.push_back(ncols * ((1 << logM1) >> (12 - logM2)));
+        rf.push_back(ncols * ((1 << logM2) >> (12 - logM1)));
+      }
+    }
+    add_list(ls, cs_, dir == 0 ? L.fwd_small : L.inv_small);
+    add_list(lf, cf, dir == 0 ? L.fwd_col : L.inv_col);
+    add_list(lf, rf, dir == 0 ? L.fwd_row : L.inv_row);
+    // the row-pass list shares problems with the column-pass list
+  }
+  {
+    std::vector<int> lr_, cr;
+    for (int i : order) { lr_.push_back(i); cr.push_back((geo[i].m + 255) / 256); }
+    add_list(lr_, cr, L.rot);
+  }
+  // cross groups: cluster size 1, 2 or 4 so that each CTA has at most
+  // rows_per_cta indices
+  const int rows = std::min(h->cross_rows[pi], batch_cross_max_rows(f32));
+  for (int cs : {4, 2, 1}) {
+    std::vector<int> lst;
+    int mx = 0;
+    for (int i : order) {
+      const int m = geo[i].m;
+      const int need = m <= rows ? 1 : (m <= 2 * rows ? 2 : 4);
+      if (need == cs) { lst.push_back(i); mx = std::max(mx, (m + cs - 1) / cs); }
+    }
+    if (lst.empty()) continue;
+    BatchLayout::CrossGroup g;
+    g.list = ints.size() * sizeof(int);
+    g.n = (int)lst.size();
+    g.cs = cs;
+    g.rows = mx;
+    ints.insert(ints.end(), lst.begin(), lst.end());
+    L.cross.push_back(g);
+  }
+  const size_t pbytes = align256(sizeof(BatchProb) * batch);
+  L.blob.assign(pbytes + ints.size() * sizeof(int), 0);
+  std::memcpy(L.blob.data(), P.data(), sizeof(BatchProb) * batch);
+  std::memcpy(L.blob.data() + pbytes, ints.data(), ints.size() * sizeof(int));
+  auto shift = [&](BatchLayout::ListRef& r) { r.list += pbytes; r.start += pbytes; };
+  shift(L.fwd_small); shift(L.fwd_col); shift(L.fwd_row);
+  shift(L.inv_small); shift(L.inv_col); shift(L.inv_row); shift(L.rot);
+  for (auto& g : L.cross) g.list += pbytes;
+  // ---- the enqueued steps, given the device copy of the block
+  BatchCrossParams cp;
+  cp.tol = o.aca_tol_factor * o.eps;
+  cp.probes = o.probes;
+  cp.seed = o.seed;
+  cp.max_probe_rounds = 4;
+  cp.max_zero_rows = 16;
+  const int nsm = h->num_sms;
+  const void* tw = h->tw4096[pi];
+  const int launches = (L.fwd_small.items > 0) + 3 * (L.fwd_col.items > 0) + (int)L.cross.size() + 3 +
+                       (L.inv_small.items > 0) + 3 * (L.inv_col.items > 0);
+  const bool timing = (o.flags & LR_FLAG_TIMING) != 0;
+  if (timing && (s = ensure_events(h)) != LR_OK) return s;
+  auto mark = [&](int i, cudaStream_t stm) -> cudaError_t {
+    return timing ? cudaEventRecord(h->ev[i], stm) : cudaSuccess;
+  };
+  auto body = [&](cudaStream_t main, const char* dev) -> cudaError_t {
+    cudaError_t e;
+    const BatchProb* dp = reinterpret_cast<const BatchProb*>(dev);
+    if ((e = cudaMemsetAsync(states, 0, sizeof(SolveState) * batch, main)) != cudaSuccess) return e;
+    if ((e = mark(0, main)) != cudaSuccess) return e;
+    {
+      NvtxRange r("lr:forward_dst");
+      if ((e = launch_batch_dst<T>(dp, 0, L.items(L.fwd_small, dev), L.items(L.fwd_col, dev),
+                                   L.items(L.fwd_row, dev), tw, nsm, main)) != cudaSuccess)
+        return e;
+      if ((e = mark(1, main)) != cudaSuccess) return e;
+    }
+    {
+      NvtxRange r("lr:cross");
+      // the cluster-size groups run concurrently on forked streams
+      const int ng = (int)L.cross.size();
+      if (ng > 1) {
+        if ((e = cudaEventRecord(h->bfork, main)) != cudaSuccess) return e;
+        for (int j = 0; j < ng; ++j)
+          if ((e = cudaStreamWaitEvent(h->bstreams[j], h->bfork, 0)) != cudaSuccess) return e;
+      }
+      for (int j = 0; j < ng; ++j) {
+        const auto& g = L.cross[j];
+        cudaStream_t sj = ng > 1 ? h->bstreams[j] : main;
+        if ((e = launch_batch_cross<T>(dp, reinterpret_cast<const int*>(dev + g.list), g.n, g.cs, g.rows, cp,
+                                       sj)) != cudaSuccess)
+          return e;
+      }
+      if (ng > 1)
+        for (int j = 0; j < ng; ++j) {
+          if ((e = cudaEventRecord(h->bjoin[j], h->bstreams[j])) != cudaSuccess) return e;
+          if ((e = cudaStreamWaitEvent(main, h->bjoin[j], 0)) != cudaSuccess) return e;
+        }
+      if ((e = mark(2, main)) != cudaSuccess) return e;
+    }
+    {
+      NvtxRange r("lr:rounding");
+      if ((e = launch_batch_core<T>(dp, batch, o.eps, f32, main)) != cudaSuccess) return e;
+      if ((e = launch_batch_rotate<T>(dp, L.items(L.rot, dev), nsm, main)) != cudaSuccess) return e;
+      if ((e = mark(3, main)) != cudaSuccess) return e;
+    }
+    {
+      NvtxRange r("lr:inverse_dst");
+      // only the kept columns (2 R per problem) are transformed: their item
+      // tables are counted on the device once the ranks are known
+      BatchItems ism = L.items(L.inv_small, dev), icol = L.items(L.inv_col, dev), irow = L.items(L.inv_row, dev);
+      ism.start = live_tab;
+      icol.start = live_tab + (batch + 1);
+      irow.start = live_tab + 2 * (batch + 1);
+      ism.live = icol.live = irow.live = 1;
+      if ((e = launch_batch_live_items(dp, ism, icol, irow, main)) != cudaSuccess) return e;
+      if ((e = launch_batch_dst<T>(dp, 1, ism, icol, irow, tw, nsm, main)) != cudaSuccess) return e;
+      if ((e = mark(4, main)) != cudaSuccess) return e;
+    }
+    return cudaMemcpyAsync(h->h_bstate, states, sizeof(SolveState) * batch, cudaMemcpyDeviceToHost, main);
+  };
+  const bool graph = (o.flags & LR_FLAG_GRAPH) != 0 && !timing;
+  h->timed = timing;
+  if (graph) {
+    // the graph bakes in the device copy of the block: one copy per graph
+    const std::string key = key_of("phased", rhs, batch, sol, o) + "|ipc" + std::to_string(rows) + "|ws" +
+                            std::to_string(h->ws_gen);
+    auto it = h->graph_desc.find(key);
+    char* dev = it != h->graph_desc.end() ? it->second : nullptr;
+    if (!dev) {
+      if (h->graphs.size() >= 32) {  // make room before allocating (bounded cache)
+        cudaStreamSynchronize(h->stream);
+        for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        h->graphs.clear();
+        for (auto& kv : h->graph_desc) cudaFree(kv.second);
+        h->graph_desc.clear();
+      }
+      if (cudaMalloc(&dev, L.blob.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LR_ENOMEM, "batch descriptor block");
+      }
+      cudaError_t e = cudaMemcpy(dev, L.blob.data(), L.blob.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) { cudaFree(dev); return cuda_fail(h, e, "batch descriptor upload"); }
+      h->graph_desc[key] = dev;
+    }
+    s = run_maybe_graph(h, true, key, [&](cudaStream_t stm) { return body(stm, dev); });
+  } else {
+    // stream-ordered upload through a pinned staging buffer
+    if (L.blob.size() > h->bdesc_cap) {
+      if (h->bdesc) { cudaStreamSynchronize(h->stream); cudaFree(h->bdesc); }
+      h->bdesc = nullptr;
+      h->bdesc_cap = 0;
+      if (cudaMalloc(&h->bdesc, L.blob.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LR_ENOMEM, "batch descriptor block");
+      }
+      h->bdesc_cap = L.blob.size();
+    }
+    if (!h->bdesc_ev) LR_CUDA(h, cudaEventCreateWithFlags(&h->bdesc_ev, cudaEventDisableTiming), "event create");
+    LR_CUDA(h, cudaEventSynchronize(h->bdesc_ev), "staging buffer");
+    if (L.blob.size() > h->h_bdesc_cap) {
+      if (h->h_bdesc) cudaFreeHost(h->h_bdesc);
+      h->h_bdesc = nullptr;
+      h->h_bdesc_cap = 0;
+      if (cudaMallocHost(&h->h_bdesc, L.blob.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LR_ENOMEM, "pinned descriptor buffer");
+      }
+      h->h_bdesc_cap = L.blob.size();
+    }
+    std::memcpy(h->h_bdesc, L.blob.data(), L.blob.size());
+    LR_CUDA(h, cudaMemcpyAsync(h->bdesc, h->h_bdesc, L.blob.size(), cudaMemcpyHostToDevice, h->stream), "upload");
+    LR_CUDA(h, cudaEventRecord(h->bdesc_ev, h->stream), "event record");
+    cudaError_t e = body(h->stream, h->bdesc);
+    s = e == cudaSuccess ? LR_OK : cuda_fail(h, e, "enqueue");
+  }
+  if (s != LR_OK) return s;
+  h->info.launches = launches;
+  if (o.flags & LR_FLAG_ASYNC) return LR_OK;
+  LR_CUDA(h, cudaStreamSynchronize(h->stream), "batched solve");
+  lr_status worst = LR_OK;
+  for (int i = 0; i < batch; ++i) {
+    const SolveState& hs = h->h_bstate[i];
+    sol[i].r = hs.rank;
+    const lr_status si = hs.status ? static_cast<lr_status>(hs.status)
+                                   : ((!hs.converged || hs.cut) ? LR_ENOCONV : LR_OK);
+    if (per_problem) per_problem[i] = si;
+    if (si != LR_OK && worst != LR_ENONFINITE) worst = si;
+  }
+  if (worst != LR_OK) fail(h, worst, "some problems did not converge or were cut (see per_problem)");
+  return worst;
+}
+
+// Batched solves: the phase-batched kernels when every problem fits them
+// (and the caller did not ask for the per-problem stream form), else one
+// launch chain per problem over the internal streams.
+template <typename T>
+lr_status solve2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options& o,
+                          const std::vector<Plan*>& plans, lr_status* per_problem, bool phased_ok = true) {
+  const bool f32 = sizeof(T) == 4;
+  if (phased_ok && !(o.flags & LR_FLAG_BATCH_STREAMS) &&
+      batch_phased_fits(batch, rhs, f32))
+    return solve2d_batched_phased<T>(h, batch, rhs, sol, o, plans, per_problem);
+  return solve2d_batched_streams<T>(h, batch, rhs, sol, o, plans, per_problem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1100,8 +1466,8 @@ lr_status velocity_solves(StokesCtx& x, const lr_mat* rhs, int* rx, int* ry) {
   for (int k = 0; k < 2; ++k) sol[k] = {m, m, 0, KMAX, x.ldv, x.WU[k], x.Ws[k], x.WV[k]};
   std::vector<Plan*> plans(2, x.plan);
   lr_status per[2] = {LR_OK, LR_OK};
-  lr_status s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, sol, x.oin, plans, per)
-                                       : solve2d_batched<double>(h, 2, rhs, sol, x.oin, plans, per);
+  lr_status s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, sol, x.oin, plans, per, false)
+                                       : solve2d_batched<double>(h, 2, rhs, sol, x.oin, plans, per, false);
   x.launches += h->info.launches;
   if (s == LR_ENONFINITE && x.oin.prec == LR_MIXED) {
     // A float32 solve broke down (noise-level pivots on a direction whose
@@ -1475,8 +1841,7 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
         if (step + 1 < kQrSteps) {
           double* Y = (step & 1) ? b.L : b.Lb;
           LR_CUDA(h, (launch_rotate<double, double>(X, lda, rows, nullptr, q, b.T0, false, &b.qout[0], Y, lda, sm)), "3D: qr");
-          ++launches;
-          X = Y;
+            X = Y;
         }
       }
       LR_CUDA(h, cudaMemsetAsync(b.st, 0, sizeof(SolveState), sm), "state reset");
@@ -1897,8 +2262,8 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   // the solutions go straight into the caller's buffers
   lr_options of = x.oin;
   std::vector<Plan*> plans(2, x.plan);
-  s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, u, of, plans, nullptr)
-                             : solve2d_batched<double>(h, 2, rhs, u, of, plans, nullptr);
+  s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, u, of, plans, nullptr, false)
+                             : solve2d_batched<double>(h, 2, rhs, u, of, plans, nullptr, false);
   if (s != LR_OK && s != LR_ENOCONV) return s;
   // divergence of the final velocity, relative to ||B^T A^-1 f||
   for (int k = 0; k < 2; ++k) {
@@ -2007,7 +2372,13 @@ lr_status lr_destroy(lr_handle h) {
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : h->graph_desc) cudaFree(kv.second);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (void* t : h->tw4096)
+    if (t) cudaFree(t);
+  if (h->bdesc) cudaFree(h->bdesc);
+  if (h->h_bdesc) cudaFreeHost(h->h_bdesc);
+  if (h->bdesc_ev) cudaEventDestroy(h->bdesc_ev);
   for (int i = 0; i < 32; ++i) {
     if (h->bstreams[i]) cudaStreamDestroy(h->bstreams[i]);
     if (h->bjoin[i]) cudaEventDestroy(h->bjoin[i]);
@@ -2110,7 +2481,9 @@ lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat
   if (s != LR_OK) return s;
   if (batch < 0 || (batch > 0 && (!rhs || !sol))) return fail(h, LR_EINVAL, "bad batch arguments");
   if (batch == 0) return LR_OK;
-  if (o.flags & LR_FLAG_TIMING) return fail(h, LR_EINVAL, "LR_FLAG_TIMING is for single solves");
+  if ((o.flags & LR_FLAG_TIMING) &&
+      ((o.flags & LR_FLAG_BATCH_STREAMS) || !batch_phased_fits(batch, rhs, o.prec == LR_MIXED)))
+    return fail(h, LR_EINVAL, "LR_FLAG_TIMING needs the phase-batched form");
   std::vector<Plan*> plans(batch);
   for (int i = 0; i < batch; ++i) {
     if ((s = check_problem(h, &rhs[i], &sol[i])) != LR_OK) {
@@ -2299,20 +2672,32 @@ lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat*
     if ((s = get_plan(h, rhs[i].n1, &plans[i])) != LR_OK) return s;
   }
   if ((s = ensure_events(h)) != LR_OK) return s;
-  o.flags = 0;
+  const bool streams = (o.flags & LR_FLAG_BATCH_STREAMS) != 0 ||
+                       !batch_phased_fits(batch, rhs, o.prec == LR_MIXED);
+  o.flags &= LR_FLAG_BATCH_STREAMS;
   o.cluster_size = 0;
   const int pi = o.prec == LR_MIXED ? 1 : 0;
-  const int before = h->batch_ipc[pi];
+  // the stream form tunes the indices per cross CTA of its per-problem
+  // clusters; the phase-batched form those of its batched cross (1, 2 or 4
+  // CTAs per problem)
+  int& knob = streams ? h->batch_ipc[pi] : h->cross_rows[pi];
+  const int before = knob;
+  std::vector<int> cands = streams ? std::vector<int>{2048, 1024, 4096, 8192}
+                                   : std::vector<int>{4096, 2048, 8192, 16384};
+  if (!streams)
+    cands.erase(std::remove_if(cands.begin(), cands.end(),
+                               [&](int c2) { return c2 > batch_cross_max_rows(o.prec == LR_MIXED); }),
+                cands.end());
   double best = 0.0, ms_def = 0.0;
   int best_ipc = before, ncand = 0;
-  for (int ipc : {2048, 1024, 4096, 8192}) {  // the default first
-    h->batch_ipc[pi] = ipc;
+  for (int ipc : cands) {  // the default first
+    knob = ipc;
     std::vector<double> t;
     for (int i = 0; i <= reps; ++i) {
       LR_CUDA(h, cudaEventRecord(h->ev[0], h->stream), "event");
       const lr_status st = o.prec == LR_MIXED ? solve2d_batched<float>(h, batch, rhs, sol, o, plans, nullptr)
                                               : solve2d_batched<double>(h, batch, rhs, sol, o, plans, nullptr);
-      if (st != LR_OK && st != LR_ENOCONV) { h->batch_ipc[pi] = before; return st; }
+      if (st != LR_OK && st != LR_ENOCONV) { knob = before; return st; }
       LR_CUDA(h, cudaEventRecord(h->ev[1], h->stream), "event");
       LR_CUDA(h, cudaEventSynchronize(h->ev[1]), "event");
       float e = 0.f;
@@ -2325,7 +2710,7 @@ lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat*
     ++ncand;
     if (ncand == 1 || ms < best) { best = ms; best_ipc = ipc; }
   }
-  h->batch_ipc[pi] = best_ipc;
+  knob = best_ipc;
   h->timed = false;
   ++h->ws_gen;  // graphs captured before tuning bake in the untuned shapes
   if (out) {

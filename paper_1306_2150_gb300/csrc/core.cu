@@ -208,7 +208,36 @@ __device__ void mixed_rebase_pass(CoreSmem<double>& S, int ke, const unsigned ch
 }
 
 template <typename T, typename JT>
+__device__ __forceinline__ void core_body(const CoreArgs<T>& A);
+
+template <typename T, typename JT>
 __global__ void __launch_bounds__(256, 1) core_kernel(CoreArgs<T> A) {
+  core_body<T, JT>(A);
+}
+
+// One rounding core per CTA for the problems of a batched solve: the skeleton
+// of problem blockIdx.x (Gram matrices, weights and k from its cross).
+template <typename T, typename JT>
+__global__ void __launch_bounds__(256, 1) batch_core_kernel(const BatchProb* __restrict__ P, double eps) {
+  const BatchProb& B = P[blockIdx.x];
+  CoreArgs<T> A;
+  A.GC = B.GC;
+  A.GR = B.GR;
+  A.ldg = B.kcap;
+  A.d = B.d;
+  A.k_dev = &B.st->k;
+  A.k_host = 0;
+  A.eps = eps;
+  A.rmax_out = B.ncap;
+  A.Tc = static_cast<T*>(B.Tc);
+  A.Tr = static_cast<T*>(B.Tr);
+  A.s_out = B.so;
+  A.st = B.st;
+  core_body<T, JT>(A);
+}
+
+template <typename T, typename JT>
+__device__ __forceinline__ void core_body(const CoreArgs<T>& A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CoreSmem<JT>& S = *reinterpret_cast<CoreSmem<JT>*>(smem_raw);
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
@@ -432,6 +461,27 @@ cudaError_t launch_core(const CoreArgs<T>& a, bool jacobi_fp32, cudaStream_t st)
 }
 template cudaError_t launch_core<double>(const CoreArgs<double>&, bool, cudaStream_t);
 template cudaError_t launch_core<float>(const CoreArgs<float>&, bool, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_batch_core(const BatchProb* probs, int n, double eps, bool jacobi_fp32, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (jacobi_fp32) {
+    auto kern = batch_core_kernel<T, float>;
+    const size_t sm = sizeof(CoreSmem<float>);
+    static cudaError_t set = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (set != cudaSuccess) return set;
+    kern<<<n, 256, sm, st>>>(probs, eps);
+  } else {
+    auto kern = batch_core_kernel<T, double>;
+    const size_t sm = sizeof(CoreSmem<double>);
+    static cudaError_t set = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (set != cudaSuccess) return set;
+    kern<<<n, 256, sm, st>>>(probs, eps);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_batch_core<double>(const BatchProb*, int, double, bool, cudaStream_t);
+template cudaError_t launch_batch_core<float>(const BatchProb*, int, double, bool, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Gram matrix G = X^T X of a tall float64 matrix: per-block partial sums in a

@@ -37,92 +37,12 @@
 
 #include <cooperative_groups.h>
 
+#include "fft_common.cuh"
 #include "lr_internal.h"
 
 namespace cg = cooperative_groups;
 
 namespace lrp {
-
-constexpr int EPT = 16;  // elements per thread in every FFT tile
-
-// ---------------------------------------------------------------------------
-// Shared-memory Stockham passes.  Element e of sequence f is buf[f*fs + e*es].
-// FMAJOR: consecutive threads take consecutive sequences (column tiles, fs=1);
-// otherwise consecutive threads take consecutive elements of one sequence.
-// tw[q] = exp(-2 pi i q / M) with M = 2^logM >= L.
-// ---------------------------------------------------------------------------
-template <typename T, int LOGR, bool FMAJOR>
-__device__ __forceinline__ void stockham_pass(cpx<T>* buf, int logL, int lognf, int es, int fs,
-                                              int logNs, const cpx<T>* __restrict__ tw, int logM,
-                                              bool inverse) {
-  constexpr int R = 1 << LOGR;
-  constexpr int NB = EPT / R;  // butterflies per thread
-  const int NT = blockDim.x;
-  const int logLR = logL - LOGR;
-  const int maskLR = (1 << logLR) - 1;
-  const int maskNs = (1 << logNs) - 1;
-  const int twshift = logM - LOGR - logNs;
-  cpx<T> v[EPT];
-#pragma unroll
-  for (int s = 0; s < NB; ++s) {
-    const int g = threadIdx.x + s * NT;
-    int f, j;
-    if (FMAJOR) { f = g & ((1 << lognf) - 1); j = g >> lognf; }
-    else { f = g >> logLR; j = g & maskLR; }
-    const int k = j & maskNs;
-    cpx<T> x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = buf[f * fs + (j + (r << logLR)) * es];
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      cpx<T> w = tw[(r * k) << twshift];
-      if (inverse) w.im = -w.im;
-      x[r] = cmul(x[r], w);
-    }
-    if (R == 2) {
-      v[s * R + 0] = cadd(x[0], x[1]);
-      v[s * R + 1] = csub(x[0], x[1]);
-    } else {
-      const cpx<T> s0 = cadd(x[0], x[2]), s1 = csub(x[0], x[2]);
-      const cpx<T> s2 = cadd(x[1], x[3]), s3 = csub(x[1], x[3]);
-      // forward: X1 = s1 - i s3, X3 = s1 + i s3; inverse swaps them
-      const cpx<T> mis3 = {s3.im, -s3.re};  // -i * s3
-      v[s * R + 0] = cadd(s0, s2);
-      v[s * R + 2] = csub(s0, s2);
-      v[s * R + 1] = inverse ? csub(s1, mis3) : cadd(s1, mis3);
-      v[s * R + 3] = inverse ? cadd(s1, mis3) : csub(s1, mis3);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < NB; ++s) {
-    const int g = threadIdx.x + s * NT;
-    int f, j;
-    if (FMAJOR) { f = g & ((1 << lognf) - 1); j = g >> lognf; }
-    else { f = g >> logLR; j = g & maskLR; }
-    const int k = j & maskNs;
-    const int base = ((j >> logNs) << (logNs + LOGR)) + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) buf[f * fs + (base + (r << logNs)) * es] = v[s * R + r];
-  }
-  __syncthreads();
-}
-
-// Full length-2^logL FFT of 2^lognf sequences; blockDim.x * EPT must equal
-// the number of elements 2^(logL + lognf).  Unnormalised.
-template <typename T, bool FMAJOR>
-__device__ void smem_fft(cpx<T>* buf, int logL, int lognf, int es, int fs,
-                         const cpx<T>* __restrict__ tw, int logM, bool inverse) {
-  int logNs = 0;
-  if (logL & 1) {
-    stockham_pass<T, 1, FMAJOR>(buf, logL, lognf, es, fs, logNs, tw, logM, inverse);
-    logNs += 1;
-  }
-  while (logNs < logL) {
-    stockham_pass<T, 2, FMAJOR>(buf, logL, lognf, es, fs, logNs, tw, logM, inverse);
-    logNs += 2;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Column addressing.
@@ -181,13 +101,6 @@ struct GeomArgs {
   int logTile;      // complex elements per four-step tile (2^logTile)
 };
 
-// Twiddles of a length-2^logL FFT, exp(-2 pi i j / L), copied into shared
-// memory from the length-M table (tw[j * M / L]).
-template <typename T>
-__device__ __forceinline__ void load_twiddles(cpx<T>* twS, const cpx<T>* __restrict__ tw, int logL, int logM) {
-  for (int j = threadIdx.x; j < (1 << logL); j += blockDim.x) twS[j] = tw[(size_t)j << (logM - logL)];
-}
-
 // ---------------------------------------------------------------------------
 // Small path: 2^lognf sequences of length M per CTA.
 // ---------------------------------------------------------------------------
@@ -201,8 +114,8 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
   const int nf = 1 << lognf;
   const int items = (g.ncols + nf - 1) >> lognf;
   const int nelem = nf << g.logM;
-  cpx<T>* twS = buf + nelem;
-  load_twiddles(twS, tw, g.logM, g.logM);
+  cpx<T>* stw = buf + nelem;
+  build_stage_twiddles(stw, tw, g.logM, g.logM - 2);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     // Every loop below covers exactly EPT elements per thread; it is unrolled
     // so that a thread's global loads are all in flight together.
@@ -225,7 +138,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM, lognf, 1, M, twS, g.logM, false);
+    smem_fft_st<T, false>(buf, g.logM, lognf, 1, M, stw, false);
     {
       cpx<T> b[EPT];
 #pragma unroll
@@ -237,7 +150,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
       }
     }
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM, lognf, 1, M, twS, g.logM, true);
+    smem_fft_st<T, false>(buf, g.logM, lognf, 1, M, stw, true);
 #pragma unroll
     for (int s = 0; s < EPT; ++s) {
       const int idx = threadIdx.x + s * blockDim.x;
@@ -268,8 +181,8 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
   const int logTX = g.logTile - g.logM2, TX = 1 << logTX;
   const int blocks_per_col = M1 >> logTX;
   const int items = g.ncols * blocks_per_col;
-  cpx<T>* twS = buf + tile;
-  load_twiddles(twS, tw, g.logM2, g.logM);
+  cpx<T>* stw = buf + tile;
+  build_stage_twiddles(stw, tw, g.logM, g.logM2 - 2);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int t1_0 = (item - col * blocks_per_col) << logTX;
@@ -293,7 +206,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
-    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, twS, g.logM2, false);
+    smem_fft_st<T, true>(buf, g.logM2, logTX, TX, 1, stw, false);
     cpx<T>* wc = work + ((size_t)col << g.logM);
     {
       cpx<T> w[EPT];
@@ -324,8 +237,8 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
   const int logTX = g.logTile - g.logM2, TX = 1 << logTX;
   const int blocks_per_col = M1 >> logTX;
   const int items = g.ncols * blocks_per_col;
-  cpx<T>* twS = buf + tile;
-  load_twiddles(twS, tw, g.logM2, g.logM);
+  cpx<T>* stw = buf + tile;
+  build_stage_twiddles(stw, tw, g.logM, g.logM2 - 2);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int t1_0 = (item - col * blocks_per_col) << logTX;
@@ -343,7 +256,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
-    smem_fft<T, true>(buf, g.logM2, logTX, TX, 1, twS, g.logM2, true);
+    smem_fft_st<T, true>(buf, g.logM2, logTX, TX, 1, stw, true);
 #pragma unroll
     for (int s = 0; s < EPT; ++s) {
       const int idx = threadIdx.x + s * blockDim.x;
@@ -370,8 +283,8 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
   const int logRY = g.logTile - g.logM1;
   const int blocks_per_col = M2 >> logRY;
   const int items = g.ncols * blocks_per_col;
-  cpx<T>* twS = buf + tile;
-  load_twiddles(twS, tw, g.logM1, g.logM);
+  cpx<T>* stw = buf + tile;
+  build_stage_twiddles(stw, tw, g.logM, g.logM1 - 2);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int k2_0 = (item - col * blocks_per_col) << logRY;
@@ -387,7 +300,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, twS, g.logM1, false);
+    smem_fft_st<T, false>(buf, g.logM1, logRY, 1, M1, stw, false);
     {
       cpx<T> b[EPT];
 #pragma unroll
@@ -399,7 +312,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
       }
     }
     __syncthreads();
-    smem_fft<T, false>(buf, g.logM1, logRY, 1, M1, twS, g.logM1, true);
+    smem_fft_st<T, false>(buf, g.logM1, logRY, 1, M1, stw, true);
     {
       cpx<T> w[EPT];
 #pragma unroll
@@ -551,13 +464,14 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
     while ((M << (lognf + 1)) <= kTileElems && (g.ncols >> (lognf + 1)) >= 2 * num_sms) ++lognf;
     const int nelem = M << lognf;
     const int threads = nelem / EPT;
-    const size_t smem = (size_t)(nelem + M) * sizeof(cpx<T>);
+    const size_t smem = (size_t)(nelem + stage_elems<T>()) * sizeof(cpx<T>);
     const int items = (g.ncols + (1 << lognf) - 1) >> lognf;
     const int grid = items < 8 * num_sms ? items : 8 * num_sms;
     auto kern = dst_small_kernel<T, INM, OUT64>;
-    static bool attr_set = false;  // once per instantiation: 128 KB covers every tile
+    static bool attr_set = false;  // once per instantiation: the largest tile plus the stage tables
     if (!attr_set) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTileElems * (int)sizeof(cpx<T>));
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (kTileElems + stage_elems<T>()) * (int)sizeof(cpx<T>));
       attr_set = true;
     }
     kern<<<grid, threads, smem, st>>>(c, g, chirp, tw, bhat, lognf);
@@ -610,7 +524,7 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
   }
   const int tile = 1 << g2.logTile;
   const int threads = tile / EPT;
-  const size_t smem = (size_t)(tile + (1 << g.logM1)) * sizeof(cpx<T>);
+  const size_t smem = (size_t)(tile + stage_elems<T>()) * sizeof(cpx<T>);
   const int items_col = g.ncols * ((1 << g.logM1) >> (g2.logTile - g.logM2));
   const int items_row = g.ncols * ((1 << g.logM2) >> (g2.logTile - g.logM1));
   const int cap = 8 * num_sms;
@@ -618,9 +532,9 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
   auto k1 = dst_col_fwd_kernel<T, INM>;
   auto k2 = dst_row_mid_kernel<T>;
   auto k3 = dst_col_inv_kernel<T, OUT64>;
-  static bool attr_set = false;  // once per instantiation: tile + twiddles <= 2 tiles
+  static bool attr_set = false;  // once per instantiation: the largest tile plus the stage tables
   if (!attr_set) {
-    const int mx = 2 * kTileElems * (int)sizeof(cpx<T>);
+    const int mx = (kTileElems + stage_elems<T>()) * (int)sizeof(cpx<T>);
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

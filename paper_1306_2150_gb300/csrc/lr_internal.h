@@ -187,6 +187,94 @@ cudaError_t launch_expsum_cols(int m, int r, int nterms, const double* Uh, const
                                const double* mu, const double* t, const double* w, double* L, double* R, int ldo,
                                int off, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Phase-batched solves (batch.cu): every step of the Section 4.2 solve for all
+// problems of a batch in one launch per step.  Each problem is described on
+// the device by a BatchProb; the working-precision buffers are T* of the
+// launch's precision.
+// ---------------------------------------------------------------------------
+struct BatchProb {
+  int m, r, kcap, ldw;       // order, RHS rank, cross step cap, ld of working buffers
+  int ncap;                  // output columns (min(kcap, sol->rmax))
+  int logM, logM1, logM2;    // transform length M = 2^logM = M1 * M2
+  int ld_in, ld_out;
+  const double* U;           // right-hand side factors (caller, float64)
+  const double* V;
+  double* Uo;                // solution factors and singular values (caller)
+  double* Vo;
+  double* so;
+  void* Uh;                  // m x r transformed factors
+  void* Vh;
+  void* C;                   // m x kcap skeleton factors
+  void* R;
+  void* Tc;                  // KMAX x KMAX rotations of the rounding core
+  void* Tr;
+  void* W;                   // m x 2 ncap rotated skeleton (inverse transform input)
+  void* work;                // four-step scratch, M complex per column
+  double* GC;                // kcap x kcap Gram matrices
+  double* GR;
+  double* d;                 // pivot values
+  int* I;
+  int* J;
+  SolveState* st;
+  const void* chirp;         // plan tables of the working precision
+  const void* tw;
+  const void* bhat;
+  const void* sa;            // symbol of the operator kind
+  const void* sb;
+};
+
+// Item lists of one batched launch: the problems taking part (list[q]) and
+// the first item of each (start[q], start[n] = total items).
+struct BatchItems {
+  const int* list = nullptr;
+  const int* start = nullptr;
+  int n = 0;
+  int items = 0;     // items, or (live lists) the capacity the grid is sized for
+  int live = 0;      // 1: start[] is written on the device by launch_batch_live_items
+                     // and counts only the live (rank < R) columns, start[n] = items
+};
+
+// Item tables of the inverse transforms over live columns only: for each of
+// the lists (small, column pass, row pass) start[q] = sum over earlier
+// problems of their live items (2 R columns, R the kept rank).
+cudaError_t launch_batch_live_items(const BatchProb* probs, const BatchItems& small, const BatchItems& col,
+                                    const BatchItems& row, cudaStream_t st);
+
+// Batched sine transforms of all problems' columns (dir 0: U, V -> Uh, Vh;
+// dir 1: the rotated skeleton W -> the caller's solution factors, live
+// columns < rank).  small: problems with M <= 4096 (items of 4096 / M
+// columns); col, row: four-step problems (col: column-pass items, row:
+// row-pass items, same list).  tw4096: twiddles exp(-2 pi i q / 4096).
+template <typename T>
+cudaError_t launch_batch_dst(const BatchProb* probs, int dir, const BatchItems& small, const BatchItems& col,
+                             const BatchItems& row, const void* tw4096, int num_sms, cudaStream_t st);
+
+// Batched rotation W = [C Tc, R Tr] (rows < m, columns < rank) of every
+// problem; items: row blocks of 256.
+template <typename T>
+cudaError_t launch_batch_rotate(const BatchProb* probs, const BatchItems& rows, int num_sms, cudaStream_t st);
+
+struct BatchCrossParams {
+  double tol;
+  int probes;
+  unsigned long long seed;
+  int max_probe_rounds;
+  int max_zero_rows;
+};
+
+// Batched cross: problems list[0..n) (LPT order), each on a cluster of cs
+// CTAs (1, 2 or 4) with rows_per_cta >= ceil(m / cs) indices per CTA.
+template <typename T>
+cudaError_t launch_batch_cross(const BatchProb* probs, const int* list, int n, int cs, int rows_per_cta,
+                               const BatchCrossParams& cp, cudaStream_t st);
+// Largest indices per CTA the batched cross supports in this precision.
+int batch_cross_max_rows(bool f32);
+
+// Batched rounding cores, one CTA per problem (core.cu).
+template <typename T>
+cudaError_t launch_batch_core(const BatchProb* probs, int n, double eps, bool jacobi_fp32, cudaStream_t st);
+
 // ---- 3D Tucker solve (tucker.cu) -------------------------------------------
 constexpr int T3P = KMAX;  // largest basis size per mode; stride of core-sized tensors
 

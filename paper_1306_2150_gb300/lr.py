@@ -25,6 +25,7 @@ LR_FLAG_TIMING = 2
 LR_FLAG_GRAPH = 4
 LR_FLAG_CLUSTER_DST = 8
 LR_FLAG_GMRES = 16
+LR_FLAG_BATCH_STREAMS = 32
 PHASES = ("forward_dst", "cross", "rounding", "inverse_dst")
 
 PRECISIONS = {"fp64": LR_FP64, "mixed": LR_MIXED}
@@ -395,10 +396,13 @@ class Batch:
 def lr_poisson2d_batched(h: Handle, batch: Batch, eps: float = 1e-6, prec="mixed", op="5pt",
                          rmax: int = 64, aca_tol_factor: float = 1.0, probes: int = 16, seed: int = 0,
                          cluster_size: int = 0, async_: bool = False, graph: bool = False,
-                         check: bool = True) -> int:
+                         check: bool = True, streams: bool = False, timing: bool = False) -> int:
     """Solve every problem of ``batch``; returns the lr_status of the call
-    (per-problem statuses in ``batch.status``, results via ``batch.result``)."""
-    flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_GRAPH if graph else 0)
+    (per-problem statuses in ``batch.status``, results via ``batch.result``).
+    ``streams`` selects the per-problem launch chains over internal streams
+    instead of the phase-batched launches."""
+    flags = (LR_FLAG_ASYNC if async_ else 0) | (LR_FLAG_GRAPH if graph else 0) | \
+        (LR_FLAG_BATCH_STREAMS if streams else 0) | (LR_FLAG_TIMING if timing else 0)
     o = _options(eps, prec, op, rmax, aca_tol_factor, probes, seed, flags, cluster_size)
     st = load().lr_poisson2d_batched(h.ptr, len(batch), batch.c_rhs, batch.c_sol, ctypes.byref(o),
                                      batch.status)
@@ -428,10 +432,11 @@ def lr_autotune(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rmax
 
 
 def lr_autotune_batched(h: Handle, batch: Batch, eps: float = 1e-6, prec="mixed", op="5pt", rmax: int = 64,
-                        reps: int = 3) -> dict:
+                        reps: int = 3, streams: bool = False) -> dict:
     """Time the indices-per-CTA candidates of lr_poisson2d_batched on ``batch``
-    and keep the fastest in the handle for this precision."""
-    o = _options(eps, prec, op, rmax, 1.0, 16, 0, 0, 0)
+    and keep the fastest in the handle for this precision (``streams``: tune
+    the per-problem stream form instead of the phase-batched form)."""
+    o = _options(eps, prec, op, rmax, 1.0, 16, 0, LR_FLAG_BATCH_STREAMS if streams else 0, 0)
     t = LrTune()
     st = load().lr_autotune_batched(h.ptr, len(batch), batch.c_rhs, batch.c_sol, ctypes.byref(o), int(reps),
                                     ctypes.byref(t))

@@ -40,9 +40,10 @@ def _problems(count, n_lo, n_hi, r_hi, seed):
 
 @pytest.mark.parametrize("prec,eps", [("mixed", 1e-6), ("fp64", 1e-9)])
 def test_batched_equals_single_solves_and_oracle(lr, h, prec, eps):
+    # the stream form: each problem is the single-solve launch chain
     probs = _problems(20, 300, 3000, 32, seed=3)
     batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
-    st = lr.lr_poisson2d_batched(h, batch, eps=eps, prec=prec)
+    st = lr.lr_poisson2d_batched(h, batch, eps=eps, prec=prec, streams=True)
     torch.cuda.synchronize()
     assert st == lr.LR_OK and all(s == lr.LR_OK for s in batch.status)
     for i, (U, V) in enumerate(probs):
@@ -56,6 +57,80 @@ def test_batched_equals_single_solves_and_oracle(lr, h, prec, eps):
         torch.cuda.synchronize()
         assert np.array_equal(Ub, npy(single.U)) and np.array_equal(sb, npy(single.s))
         assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt") <= 10 * eps
+
+
+@pytest.mark.parametrize("prec,eps", [("mixed", 1e-6), ("fp64", 1e-9), ("fp64", 1e-6)])
+def test_phased_batch_matches_oracle(lr, h, prec, eps):
+    # the phase-batched form on uneven problems: small-path (M <= 4096) and
+    # four-step transforms, single-CTA and clustered crosses (4096 indices per
+    # CTA by default: m > 4096 takes 2 CTAs).  Mixed: every problem within
+    # 10 eps of the exact solution.  Float64: the oracle's rank and singular
+    # values, and its error (the cross stop rule at tol = eps leaves some of
+    # these random problems slightly above 10 eps at eps = 1e-9, in the
+    # oracle as on the GPU)
+    probs = _problems(24, 300, 12000, 32, seed=13)
+    batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
+    st = lr.lr_poisson2d_batched(h, batch, eps=eps, prec=prec)
+    torch.cuda.synchronize()
+    assert st == lr.LR_OK and all(s == lr.LR_OK for s in batch.status)
+    info, _, _ = lr.lr_get_info(h)
+    assert info.launches <= 14
+    for i, (U, V) in enumerate(probs):
+        Ub, sb, Vb = (npy(t) for t in batch.result(i))
+        rows = None if U.shape[0] <= 4096 else np.unique(np.linspace(0, U.shape[0] - 1, 256).astype(int))
+        err = O.rel_error_freq(Ub, sb, Vb, U, V, "5pt", rows=rows)
+        if prec == "mixed":
+            assert err <= 10 * eps, i
+            continue
+        ou, os_, ov, inf = O.lr_poisson2d(U, V, "5pt", eps)
+        assert len(sb) == inf.rank, i
+        assert np.allclose(sb, os_, rtol=1e-8, atol=1e-11 * os_[0]), i
+        assert err <= max(10 * eps, 1.1 * O.rel_error_freq(ou, os_, ov, U, V, "5pt", rows=rows)), i
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_phased_batch_probe_restart_and_edge_problems(lr, h, prec):
+    # a block-diagonal problem whose second block only a residual probe finds
+    # (Section 4.2, reading G7), an eigenfunction (zero rows), tiny grids and
+    # a zero right-hand side, in one batch; float64 ranks equal the oracle's
+    eps = 1e-6
+    Uh, Vh = inputs.block_diagonal_freq(128, 32)
+    x = np.arange(1, 31) / 31
+    probs = [(O.dst1(Uh), O.dst1(Vh)),
+             (np.sin(3 * np.pi * x)[:, None], (np.sin(np.pi * x) + 0.3 * np.sin(2 * np.pi * x))[:, None]),
+             inputs.separable_random(1, 1, seed=1), inputs.separable_random(2, 2, seed=2),
+             inputs.separable_random(5, 3, seed=5), (np.zeros((64, 2)), np.ones((64, 2))),
+             inputs.separable_random(4097, 7, seed=9)]
+    probs = [(np.asfortranarray(a), np.asfortranarray(b)) for a, b in probs]
+    batch = lr.Batch([(torch.from_numpy(a), torch.from_numpy(b)) for a, b in probs])
+    lr.lr_poisson2d_batched(h, batch, eps=eps, prec=prec, check=False)
+    torch.cuda.synchronize()
+    for i, (U, V) in enumerate(probs):
+        Ub, sb, Vb = (npy(t) for t in batch.result(i))
+        if not U.any():
+            assert len(sb) == 0 and batch.status[i] == lr.LR_OK
+            continue
+        assert batch.status[i] == lr.LR_OK, i
+        assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt") <= 10 * eps, i
+        if prec == "fp64":
+            assert len(sb) == O.lr_poisson2d(U, V, "5pt", eps)[3].rank, i
+
+
+def test_phased_batch_headline_shape(lr, h):
+    # the benchmark's shape: m = 16384 smooth right-hand sides (4 CTAs per
+    # problem at the default 4096 indices per CTA), mixed precision, graph
+    m, eps = 16384, 1e-6
+    U, V = inputs.smooth_sum(m, eps)
+    probs = [(U * (1.0 + p / 8), V) for p in range(8)]
+    batch = lr.Batch([(torch.from_numpy(np.asfortranarray(a)), torch.from_numpy(b)) for a, b in probs])
+    for _ in range(2):
+        st = lr.lr_poisson2d_batched(h, batch, eps=eps, prec="mixed", graph=True)
+        torch.cuda.synchronize()
+        assert st == lr.LR_OK
+    rows = np.unique(np.linspace(0, m - 1, 192).astype(int))
+    for i, (a, b) in enumerate(probs):
+        Ub, sb, Vb = (npy(t) for t in batch.result(i))
+        assert O.rel_error_freq(Ub, sb, Vb, a, b, "5pt", rows=rows) <= 10 * eps, i
 
 
 def test_batched_graph_replay_tracks_new_data(lr, h):
@@ -87,12 +162,13 @@ def test_single_solve_graph_replay(lr, h):
         assert np.array_equal(npy(res.U), npy(ref.U)) and np.array_equal(npy(res.s), npy(ref.s))
 
 
-def test_batch_of_uneven_log_uniform_problems_converges(lr, h):
+@pytest.mark.parametrize("streams", [False, True])
+def test_batch_of_uneven_log_uniform_problems_converges(lr, h, streams):
     # the 512-problem batch recipe, scaled to 64 problems for test time:
     # n log-uniform in [512, 16384], r uniform in {1..32}, eps = 1e-6
     probs = _problems(64, 512, 16384, 32, seed=3)
     batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
-    st = lr.lr_poisson2d_batched(h, batch, eps=1e-6, prec="mixed", graph=True)
+    st = lr.lr_poisson2d_batched(h, batch, eps=1e-6, prec="mixed", graph=True, streams=streams)
     torch.cuda.synchronize()
     assert st == lr.LR_OK
     assert all(s == lr.LR_OK for s in batch.status)
@@ -121,12 +197,14 @@ def test_autotune_single_then_lookup(lr, h):
     assert O.rel_error_freq(npy(a.U), npy(a.s), npy(a.V), U, V, "5pt", rows=rows) <= 10 * eps
 
 
-def test_autotune_batched(lr, h):
+@pytest.mark.parametrize("streams", [False, True])
+def test_autotune_batched(lr, h, streams):
     probs = _problems(16, 512, 4096, 16, seed=5)
     batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
-    t = lr.lr_autotune_batched(h, batch, eps=1e-6, prec="mixed", reps=2)
-    assert t["batch_indices_per_cta"] in (1024, 2048, 4096, 8192) and t["candidates"] == 4
-    st = lr.lr_poisson2d_batched(h, batch, eps=1e-6, prec="mixed")
+    t = lr.lr_autotune_batched(h, batch, eps=1e-6, prec="mixed", reps=2, streams=streams)
+    allowed = (1024, 2048, 4096, 8192) if streams else (2048, 4096, 8192, 16384)
+    assert t["batch_indices_per_cta"] in allowed and t["candidates"] == 4
+    st = lr.lr_poisson2d_batched(h, batch, eps=1e-6, prec="mixed", streams=streams)
     torch.cuda.synchronize()
     assert st == lr.LR_OK
     for i, (U, V) in enumerate(probs):
