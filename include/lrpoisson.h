@@ -188,10 +188,10 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
 /* Batched low-rank Poisson solves: `batch` independent problems (host arrays
  * rhs[batch], sol[batch] of lr_mat with device pointers, each as for
  * lr_poisson2d, sizes and ranks may differ) with shared options.
- * Phase-batched form (default when every order m is at most 65536 in
- * LR_MIXED, 32768 in LR_FP64): each step of the solve runs for all problems
+ * Phase-batched form (default when every order m is at most 65536): each
+ * step of the solve runs for all problems
  * in one launch -- the forward DST of every factor column, the cross of
- * every problem (one CTA, or a cluster of 2 or 4 CTAs, per problem, longest
+ * every problem (one CTA, or a cluster of 2 to 16 CTAs, per problem, longest
  * problems first; cluster sizes run concurrently), the rounding cores, the
  * rotation of the skeletons and the inverse DST -- about ten launches per
  * batch.  The problem descriptors are uploaded with the work.  With
@@ -341,8 +341,9 @@ lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double
  * lr_autotune_batched times lr_poisson2d_batched on the given batch (its
  * sol buffers receive the trial results) for several numbers of indices per
  * cross CTA and keeps the fastest for batched solves of that precision on
- * this handle: 2048, 4096, 8192, 16384 (LR_FP64: up to 8192; default 4096)
- * for the phase-batched form, which then takes 1, 2 or 4 CTAs per problem;
+ * this handle: 2048, 4096, 8192, 16384 (LR_FP64 up to 8192; default 4096)
+ * for the phase-batched form, which then takes 1 to 16 CTAs per problem
+ * (slices of 2048 indices keep the factors in shared memory);
  * 1024, 2048, 4096, 8192 (default 2048) for the stream form
  * (LR_FLAG_BATCH_STREAMS in opt->flags).
  *

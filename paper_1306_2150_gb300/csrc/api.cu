@@ -964,7 +964,7 @@ lr_status ensure_tw4096(lr_handle h, bool f32) {
 struct BatchLayout {
   std::vector<char> blob;  // [BatchProb x n][int lists]
   size_t probs_off = 0;
-  struct ListRef { size_t list, start; int n, items; };
+  struct ListRef { size_t list, start; int n, items, slog; };
   ListRef fwd_small{}, fwd_col{}, fwd_row{}, inv_small{}, inv_col{}, inv_row{}, rot{};
   struct CrossGroup { size_t list; int n, cs, rows; };
   std::vector<CrossGroup> cross;
@@ -974,13 +974,15 @@ struct BatchLayout {
     b.start = reinterpret_cast<const int*>(dev + r.start);
     b.n = r.n;
     b.items = r.items;
+    b.slog = r.slog;
     return b;
   }
 };
 
 // True if every problem fits the phase-batched kernels in this precision.
 bool batch_phased_fits(int batch, const lr_mat* rhs, bool f32) {
-  const int lim = 4 * batch_cross_max_rows(f32);
+  // transform length M <= 2^17 (the batched four-step twiddle tables)
+  const int lim = std::min(65536, 16 * batch_cross_max_rows(f32));
   for (int i = 0; i < batch; ++i)
     if (rhs[i].n1 > lim) return false;
   return true;
@@ -1069,6 +1071,7 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
   };
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<int> ls, cs_, lf, cf, rf;
+    int slog_s = 0, slog_c = 0, slog_r = 0;  // largest FFT stage each launch needs
     for (int i : order) {
       const int ncols = dir == 0 ? 2 * geo[i].r : 2 * geo[i].ncap_out;
       const int logM = plans[i]->logM;
@@ -1076,16 +1079,25 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
         const int nf = 1 << (12 - logM);
         ls.push_back(i);
         cs_.push_back((ncols + nf - 1) / nf);
+        slog_s = std::max(slog_s, logM - 2);
       } else {
         const int logM1 = plans[i]->logM1, logM2 = plans[i]->logM2;
         lf.push_back(i);
         cf.push_back(ncols * ((1 << logM1) >> (12 - logM2)));
         rf.push_back(ncols * ((1 << logM2) >> (12 - logM1)));
+        slog_c = std::max(slog_c, logM2 - 2);
+        slog_r = std::max(slog_r, logM1 - 2);
       }
     }
-    add_list(ls, cs_, dir == 0 ? L.fwd_small : L.inv_small);
-    add_list(lf, cf, dir == 0 ? L.fwd_col : L.inv_col);
-    add_list(lf, rf, dir == 0 ? L.fwd_row : L.inv_row);
+    BatchLayout::ListRef& rs_ = dir == 0 ? L.fwd_small : L.inv_small;
+    BatchLayout::ListRef& rc_ = dir == 0 ? L.fwd_col : L.inv_col;
+    BatchLayout::ListRef& rr_ = dir == 0 ? L.fwd_row : L.inv_row;
+    add_list(ls, cs_, rs_);
+    add_list(lf, cf, rc_);
+    add_list(lf, rf, rr_);
+    rs_.slog = slog_s;
+    rc_.slog = slog_c;
+    rr_.slog = slog_r;
     // the row-pass list shares problems with the column-pass list
   }
   {
@@ -1093,15 +1105,22 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
     for (int i : order) { lr_.push_back(i); cr.push_back((geo[i].m + 255) / 256); }
     add_list(lr_, cr, L.rot);
   }
-  // cross groups: cluster size 1, 2 or 4 so that each CTA has at most
-  // rows_per_cta indices
+  // cross groups: cluster sizes 1, 2, 4, 8, 16 so that each CTA has at most
+  // rows_per_cta indices (more only at 16 CTAs)
   const int rows = std::min(h->cross_rows[pi], batch_cross_max_rows(f32));
-  for (int cs : {4, 2, 1}) {
+  for (int cs : {16, 8, 4, 2, 1}) {
     std::vector<int> lst;
     int mx = 0;
     for (int i : order) {
       const int m = geo[i].m;
-      const int need = m <= rows ? 1 : (m <= 2 * rows ? 2 : 4);
+      int need = 1;
+      while (need < 16 && (long long)need * rows < m) need *= 2;
+      if (o.cluster_size > 0) {  // the caller's cluster size (a power of two), enough for the rows
+        int want = 1;
+        while (want < o.cluster_size && want < 16) want *= 2;
+        need = std::max(want, need);
+        while (need > 1 && (long long)(need / 2) * batch_cross_max_rows(f32) >= m && need > want) need /= 2;
+      }
       if (need == cs) { lst.push_back(i); mx = std::max(mx, (m + cs - 1) / cs); }
     }
     if (lst.empty()) continue;
@@ -1128,6 +1147,10 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
   cp.seed = o.seed;
   cp.max_probe_rounds = 4;
   cp.max_zero_rows = 16;
+  // slices of at most 2048 indices: keep the factors and the first skeleton
+  // columns in shared memory (larger slices: everything from L2, which keeps
+  // the CTA's shared memory small)
+  cp.cache = rows <= 2048 ? 1 : 0;
   const int nsm = h->num_sms;
   const void* tw = h->tw4096[pi];
   const int launches = (L.fwd_small.items > 0) + 3 * (L.fwd_col.items > 0) + (int)L.cross.size() + 3 +

@@ -115,9 +115,10 @@ template <typename T, int DIR>
 __global__ void __launch_bounds__(kBThreads, 2) bdst_small_kernel(const BatchProb* __restrict__ P, BatchItems it,
                                                                const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* stw = buf + kBTile;
-  build_stage_twiddles(stw, tw4096, 12, kStageLog);
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);  // padded tile (smem_ix<true>)
+  cpx<T>* stw = buf + kBTile + (kBTile >> 4);
+  build_stage_twiddles(stw, tw4096, 12, it.slog);
+  const int stride = stage_stride(it.slog);
   const int items = item_count(it);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
@@ -143,22 +144,22 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_small_kernel(const BatchPro
       }
       __syncthreads();  // the previous item's stores read buf
 #pragma unroll
-      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * kBThreads] = v[s];
+      for (int s = 0; s < EPT; ++s) buf[smem_ix<true>(threadIdx.x + s * kBThreads)] = v[s];
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, logM, lognf, 1, M, stw, false);
+    smem_fft_st<T, false, true>(buf, logM, lognf, 1, M, stw, stride, false);
     {
       cpx<T> b[EPT];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) b[s] = bhat[(threadIdx.x + s * kBThreads) & (M - 1)];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
-        const int idx = threadIdx.x + s * kBThreads;
+        const int idx = smem_ix<true>(threadIdx.x + s * kBThreads);
         buf[idx] = cmul(buf[idx], b[s]);
       }
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, logM, lognf, 1, M, stw, true);
+    smem_fft_st<T, false, true>(buf, logM, lognf, 1, M, stw, stride, true);
 #pragma unroll
     for (int s = 0; s < EPT; ++s) {
       const int idx = threadIdx.x + s * kBThreads;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_small_kernel(const BatchPro
       const int cl = it.live ? live_col(B, col0 + (idx >> logM)) : col0 + (idx >> logM);
       const BCol<T, DIR> c(B, cl < 0 ? 2 * B.ncap : cl);
       if (c.live && t < B.m) {
-        const cpx<T> w = chirp[t], z = buf[idx];
+        const cpx<T> w = chirp[t], z = buf[smem_ix<true>(idx)];
         c.store(t, w.re * z.im + w.im * z.re);  // Im(w z)
       }
     }
@@ -181,8 +182,12 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_fwd_kernel(const BatchP
                                                                  const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* stw = buf + kBTile;
-  build_stage_twiddles(stw, tw4096, 12, kStageLog);
+  cpx<T>* stw = buf + kBTile + 512;  // after the (row pass: padded) tile
+  build_stage_twiddles(stw, tw4096, 12, it.slog);
+  const int stride = stage_stride(it.slog);
+  cpx<T>* th = stw + stage_elems<T>(it.slog);  // inter-pass twiddles of the current M
+  cpx<T>* tl = th + kTwHi;
+  int curM = 0;
   const int items = item_count(it);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
@@ -197,7 +202,6 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_fwd_kernel(const BatchP
     const BCol<T, DIR> c(B, col < 0 ? 2 * B.ncap : col);
     if (!c.live) continue;  // uniform across the CTA
     const cpx<T>* chirp = static_cast<const cpx<T>*>(B.chirp);
-    const cpx<T>* tw = static_cast<const cpx<T>*>(B.tw);
     {
       cpx<T> v[EPT];
 #pragma unroll
@@ -214,16 +218,20 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_fwd_kernel(const BatchP
       __syncthreads();
 #pragma unroll
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * kBThreads] = v[s];
+      if (B.logM != curM) {  // uniform across the CTA
+        load_twiddles2(th, tl, static_cast<const cpx<T>*>(B.tw), B.logM);
+        curM = B.logM;
+      }
     }
     __syncthreads();
-    smem_fft_st<T, true>(buf, logM2, logTX, TX, 1, stw, false);
+    smem_fft_st<T, true>(buf, logM2, logTX, TX, 1, stw, stride, false);
     cpx<T>* wc = static_cast<cpx<T>*>(B.work) + ((size_t)col << B.logM);
     {
       cpx<T> w[EPT];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * kBThreads;
-        w[s] = tw[(t1_0 + (idx & (TX - 1))) * (idx >> logTX)];
+        w[s] = twiddle2(th, tl, (t1_0 + (idx & (TX - 1))) * (idx >> logTX));
       }
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
@@ -240,8 +248,12 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_row_mid_kernel(const BatchP
                                                                  const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* stw = buf + kBTile;
-  build_stage_twiddles(stw, tw4096, 12, kStageLog);
+  cpx<T>* stw = buf + kBTile + 512;  // after the (row pass: padded) tile
+  build_stage_twiddles(stw, tw4096, 12, it.slog);
+  const int stride = stage_stride(it.slog);
+  cpx<T>* th = stw + stage_elems<T>(it.slog);  // inter-pass twiddles of the current M
+  cpx<T>* tl = th + kTwHi;
+  int curM = 0;
   const int items = item_count(it);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
@@ -255,19 +267,28 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_row_mid_kernel(const BatchP
     const int k2_0 = (local - lc * bpc) << logRY;
     const BCol<T, DIR> c(B, col < 0 ? 2 * B.ncap : col);
     if (!c.live) continue;
-    const cpx<T>* tw = static_cast<const cpx<T>*>(B.tw);
     cpx<T>* wc = static_cast<cpx<T>*>(B.work) + ((size_t)col << B.logM) + ((size_t)k2_0 << logM1);
     const cpx<T>* bh = static_cast<const cpx<T>*>(B.bhat) + ((size_t)k2_0 << logM1);
+    // rows interleaved in shared memory (element e of row f at e (RY + 1) + f):
+    // the FFT passes then run with consecutive lanes on consecutive rows
+    const int ES = (1 << logRY) + 1;
     {
       cpx<T> v[EPT];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) v[s] = wc[threadIdx.x + s * kBThreads];
       __syncthreads();
 #pragma unroll
-      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * kBThreads] = v[s];
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * kBThreads;
+        buf[(idx & (M1 - 1)) * ES + (idx >> logM1)] = v[s];
+      }
+      if (B.logM != curM) {  // uniform across the CTA
+        load_twiddles2(th, tl, static_cast<const cpx<T>*>(B.tw), B.logM);
+        curM = B.logM;
+      }
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, logM1, logRY, 1, M1, stw, false);
+    smem_fft_st<T, true>(buf, logM1, logRY, ES, 1, stw, stride, false);
     {
       cpx<T> b[EPT];
 #pragma unroll
@@ -275,22 +296,23 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_row_mid_kernel(const BatchP
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * kBThreads;
-        buf[idx] = cmul(buf[idx], b[s]);
+        const int bi = (idx & (M1 - 1)) * ES + (idx >> logM1);
+        buf[bi] = cmul(buf[bi], b[s]);
       }
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, logM1, logRY, 1, M1, stw, true);
+    smem_fft_st<T, true>(buf, logM1, logRY, ES, 1, stw, stride, true);
     {
       cpx<T> w[EPT];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * kBThreads;
-        w[s] = tw[(idx & (M1 - 1)) * (k2_0 + (idx >> logM1))];
+        w[s] = twiddle2(th, tl, (idx & (M1 - 1)) * (k2_0 + (idx >> logM1)));
       }
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * kBThreads;
-        wc[idx] = cmulc(buf[idx], w[s]);  // times exp(+2 pi i t1 k2 / M)
+        wc[idx] = cmulc(buf[(idx & (M1 - 1)) * ES + (idx >> logM1)], w[s]);  // times exp(+2 pi i t1 k2 / M)
       }
     }
   }
@@ -301,8 +323,9 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_inv_kernel(const BatchP
                                                                  const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* stw = buf + kBTile;
-  build_stage_twiddles(stw, tw4096, 12, kStageLog);
+  cpx<T>* stw = buf + kBTile + 512;  // after the (row pass: padded) tile
+  build_stage_twiddles(stw, tw4096, 12, it.slog);
+  const int stride = stage_stride(it.slog);
   const int items = item_count(it);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
@@ -330,7 +353,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_inv_kernel(const BatchP
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * kBThreads] = v[s];
     }
     __syncthreads();
-    smem_fft_st<T, true>(buf, logM2, logTX, TX, 1, stw, true);
+    smem_fft_st<T, true>(buf, logM2, logTX, TX, 1, stw, stride, true);
 #pragma unroll
     for (int s = 0; s < EPT; ++s) {
       const int idx = threadIdx.x + s * kBThreads;
@@ -346,7 +369,13 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_inv_kernel(const BatchP
 template <typename T, int DIR>
 cudaError_t launch_bdst_dir(const BatchProb* probs, const BatchItems& small, const BatchItems& col,
                             const BatchItems& row, const cpx<T>* tw, int num_sms, cudaStream_t st) {
-  const size_t smem = ((size_t)kBTile + stage_elems<T>()) * sizeof(cpx<T>);
+  // tile (padded by 1/16, or by up to 512 for the row pass) + stage tables
+  // tile (padded by 1/16, or by up to 512 for the row pass), stage tables,
+  // inter-pass twiddles
+  const size_t smax = ((size_t)kBTile + 512 + stage_elems<T>(kStageLog) + kTwHi + kTwLo) * sizeof(cpx<T>);
+  auto bytes = [](const BatchItems& b) {
+    return ((size_t)kBTile + 512 + stage_elems<T>(b.slog) + kTwHi + kTwLo) * sizeof(cpx<T>);
+  };
   auto k0 = bdst_small_kernel<T, DIR>;
   auto k1 = bdst_col_fwd_kernel<T, DIR>;
   auto k2 = bdst_row_mid_kernel<T, DIR>;
@@ -354,7 +383,9 @@ cudaError_t launch_bdst_dir(const BatchProb* probs, const BatchItems& small, con
   static cudaError_t attr = [&] {
     cudaError_t e = cudaSuccess;
     for (const void* k : {(const void*)k0, (const void*)k1, (const void*)k2, (const void*)k3}) {
-      const cudaError_t ek = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t ek = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+      if (ek == cudaSuccess)  // let several CTAs share an SM's shared memory
+        ek = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       if (ek != cudaSuccess) e = ek;
     }
     return e;
@@ -362,11 +393,11 @@ cudaError_t launch_bdst_dir(const BatchProb* probs, const BatchItems& small, con
   if (attr != cudaSuccess) return attr;
   // grid: enough CTAs for every item, at most 4 per SM (grid-stride beyond)
   const int cap = 4 * num_sms;
-  if (small.items > 0) k0<<<small.items < cap ? small.items : cap, kBThreads, smem, st>>>(probs, small, tw);
+  if (small.items > 0) k0<<<small.items < cap ? small.items : cap, kBThreads, bytes(small), st>>>(probs, small, tw);
   if (col.items > 0) {
-    k1<<<col.items < cap ? col.items : cap, kBThreads, smem, st>>>(probs, col, tw);
-    k2<<<row.items < cap ? row.items : cap, kBThreads, smem, st>>>(probs, row, tw);
-    k3<<<col.items < cap ? col.items : cap, kBThreads, smem, st>>>(probs, col, tw);
+    k1<<<col.items < cap ? col.items : cap, kBThreads, bytes(col), st>>>(probs, col, tw);
+    k2<<<row.items < cap ? row.items : cap, kBThreads, bytes(row), st>>>(probs, row, tw);
+    k3<<<col.items < cap ? col.items : cap, kBThreads, bytes(col), st>>>(probs, col, tw);
   }
   return cudaGetLastError();
 }
@@ -478,17 +509,18 @@ __global__ void __launch_bounds__(256) brotate_kernel(const BatchProb* __restric
     for (int side = 0; side < 2; ++side) {
       const T* X = static_cast<const T*>(side ? B.R : B.C) + row;
       T* out = static_cast<T*>(B.W) + (size_t)side * B.ncap * B.ldw + row;
-      for (int q0 = 0; q0 < R; q0 += 8) {
-        T acc[8];
+      for (int q0 = 0; q0 < R; q0 += 16) {  // one pass over X for ranks up to 16
+        T acc[16];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = T(0);
+        for (int c = 0; c < 16; ++c) acc[c] = T(0);
+#pragma unroll 4
         for (int l = 0; l < k; ++l) {
           const T x = X[(size_t)l * B.ldw];
 #pragma unroll
-          for (int c = 0; c < 8; ++c) acc[c] += x * tm[side][l + (q0 + c) * KMAX];
+          for (int c = 0; c < 16; ++c) acc[c] += x * tm[side][l + (q0 + c) * KMAX];
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+        for (int c = 0; c < 16; ++c)
           if (q0 + c < R) out[(size_t)(q0 + c) * B.ldw] = acc[c];
       }
     }
@@ -518,7 +550,6 @@ namespace {
 constexpr int BX_NT = 512;            // threads per CTA
 constexpr int BX_NW = BX_NT / 32;
 constexpr int BX_CAND = 2 * KMAX + 3; // candidate pivot data: F row, X row (KMAX + 1), a, b
-constexpr int BX_CSMAX = 4;
 
 __device__ __forceinline__ unsigned long long bx_splitmix64_at(unsigned long long state, unsigned long long t) {
   unsigned long long z = state + t * 0x9E3779B97F4A7C15ULL;
@@ -585,7 +616,6 @@ struct BxShared {
   int widx[BX_NW];
   T wdots[KMAX][BX_NW];
   T wcand[BX_NW][BX_CAND];          // per warp: its candidate's F row, X row, a, b
-  T inbox[2][BX_CSMAX][BxMsg<T>::WORDS];
   T d[KMAX + 1];                    // pivot values
   T dots[KMAX];                     // reduced dot products of the last reduction
   T gr[KMAX];                       // R_l . r of the current step
@@ -599,7 +629,10 @@ struct BxShared {
   int idx, win, flag, small;
 };
 
-// Problem-level constants of one CTA.
+// Problem-level constants of one CTA.  The CTA's slices (local index li =
+// j - row0 < SP) of the symbol, of Uh and Vh (if uv) and of the first KS
+// skeleton columns live in dynamic shared memory, column-major with leading
+// dimension SP; the rest is read from global memory (L2).
 template <typename T>
 struct BxProb {
   int m, r, ld, kcap, row0, row1;
@@ -609,58 +642,100 @@ struct BxProb {
   T* R;
   const T* a;
   const T* b;
+  int SP, KS, uv;
+  const T* as;   // symbol slices
+  const T* bs;
+  const T* Us;   // Uh, Vh slices (uv)
+  const T* Vs;
+  T* Cs;         // skeleton columns < KS
+  T* Rs;
+  T* inbox;      // [2][cs][BxMsg::WORDS] cluster partials (dynamic shared memory)
 };
+
+// A tall factor as seen by the CTA: global copy, shared copy of columns < ns.
+template <typename T>
+struct BxSrc {
+  const T* g;
+  const T* s;
+  int ns;
+};
+template <typename T>
+__device__ __forceinline__ T bx_at(const BxProb<T>& p, const BxSrc<T>& S, int l, int li) {
+  return l < S.ns ? S.s[(size_t)l * p.SP + li] : __ldcg(&S.g[p.row0 + li + (size_t)l * p.ld]);
+}
 
 // out[s] = (vec . F[j]) / (pa b_j + pb a_j) - sum_{l<k} cd[l] X[j, l] for the
 // owned indices j = row0 + tid + s NT (0 elsewhere).
 template <typename T, int RPT>
-__device__ __forceinline__ void bx_eval(const BxProb<T>& p, const T* __restrict__ F, const T* __restrict__ X,
-                                        int k, const BxShared<T>& sh, T (&out)[RPT]) {
-  const int base = p.row0 + threadIdx.x;
+__device__ __forceinline__ void bx_eval(const BxProb<T>& p, const BxSrc<T>& F, const BxSrc<T>& X, int k,
+                                        const BxShared<T>& sh, T (&out)[RPT]) {
+  const int S = p.row1 - p.row0;
+  const int tid = threadIdx.x;
 #pragma unroll
   for (int s = 0; s < RPT; ++s) out[s] = T(0);
+  // F . vec: shared columns, then global ones (uniform loop bounds)
+  const int nF = F.ns < p.r ? F.ns : p.r;
 #pragma unroll 4
-  for (int al = 0; al < p.r; ++al) {
+  for (int al = 0; al < nF; ++al) {
     const T w = sh.vec[al];
-    const T* Fc = F + (size_t)al * p.ld + base;
+    const T* Fc = F.s + (size_t)al * p.SP + tid;
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if (base + s * BX_NT < p.row1) out[s] += w * Fc[s * BX_NT];
+      if (tid + s * BX_NT < S) out[s] += w * Fc[s * BX_NT];
+  }
+#pragma unroll 4
+  for (int al = nF; al < p.r; ++al) {
+    const T w = sh.vec[al];
+    const T* Fc = F.g + (size_t)al * p.ld + p.row0 + tid;
+#pragma unroll
+    for (int s = 0; s < RPT; ++s)
+      if (tid + s * BX_NT < S) out[s] += w * Fc[s * BX_NT];
   }
   const T pa = sh.piv_a, pb = sh.piv_b;
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    const int j = base + s * BX_NT;
-    out[s] = j < p.row1 ? bx_ratio<T>(out[s], pa * p.b[j] + pb * p.a[j]) : T(0);
+    const int li = tid + s * BX_NT;
+    out[s] = li < S ? bx_ratio<T>(out[s], pa * p.bs[li] + pb * p.as[li]) : T(0);
   }
+  const int nX = X.ns < k ? X.ns : k;
 #pragma unroll 4
-  for (int l = 0; l < k; ++l) {
+  for (int l = 0; l < nX; ++l) {
     const T c = sh.cd[l];
-    const T* Xc = X + (size_t)l * p.ld + base;
+    const T* Xc = X.s + (size_t)l * p.SP + tid;
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if (base + s * BX_NT < p.row1) out[s] -= c * __ldcg(&Xc[s * BX_NT]);
+      if (tid + s * BX_NT < S) out[s] -= c * Xc[s * BX_NT];
+  }
+#pragma unroll 4
+  for (int l = nX; l < k; ++l) {
+    const T c = sh.cd[l];
+    const T* Xc = X.g + (size_t)l * p.ld + p.row0 + tid;
+#pragma unroll
+    for (int s = 0; s < RPT; ++s)
+      if (tid + s * BX_NT < S) out[s] -= c * __ldcg(&Xc[s * BX_NT]);
   }
 }
 
 // Start score ||Uh[j]||^2 / Lambda[j, 0]^2 of the owned indices.
 template <typename T, int RPT>
 __device__ __forceinline__ void bx_scores(const BxProb<T>& p, T a0, T b0, T (&out)[RPT]) {
-  const int base = p.row0 + threadIdx.x;
+  const int S = p.row1 - p.row0;
+  const BxSrc<T> U{p.Uh, p.Us, p.uv ? p.r : 0};
 #pragma unroll
   for (int s = 0; s < RPT; ++s) out[s] = T(0);
 #pragma unroll 4
   for (int al = 0; al < p.r; ++al) {
-    const T* Fc = p.Uh + (size_t)al * p.ld + base;
 #pragma unroll
-    for (int s = 0; s < RPT; ++s)
-      if (base + s * BX_NT < p.row1) { const T u = Fc[s * BX_NT]; out[s] += u * u; }
+    for (int s = 0; s < RPT; ++s) {
+      const int li = threadIdx.x + s * BX_NT;
+      if (li < S) { const T u = bx_at(p, U, al, li); out[s] += u * u; }
+    }
   }
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    const int j = base + s * BX_NT;
-    if (j < p.row1) {
-      const T lam0 = p.a[j] * b0 + p.b[j] * a0;
+    const int li = threadIdx.x + s * BX_NT;
+    if (li < S) {
+      const T lam0 = p.as[li] * b0 + p.bs[li] * a0;
       out[s] = out[s] / (lam0 * lam0);
     }
   }
@@ -674,8 +749,8 @@ __device__ __forceinline__ void bx_scores(const BxProb<T>& p, T a0, T b0, T (&ou
 // sh.vec, sh.craw[0..kx), sh.piv_a, sh.piv_b.
 template <typename T, int RPT>
 __device__ __forceinline__ void bx_reduce(const BxProb<T>& p, const T (&v)[RPT], unsigned cand,
-                                          const T* __restrict__ Xd, int kd, const T* __restrict__ F,
-                                          const T* __restrict__ X, int kx, int cs, int& par, BxShared<T>& sh) {
+                                          const BxSrc<T>& Xd, int kd, const BxSrc<T>& F, const BxSrc<T>& X,
+                                          int kx, int cs, int& par, BxShared<T>& sh) {
   using Mg = BxMsg<T>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int base = p.row0 + tid;
@@ -692,14 +767,20 @@ __device__ __forceinline__ void bx_reduce(const BxProb<T>& p, const T (&v)[RPT],
   }
   bx_warp_argmax(babs, bidx, bval);
   ssq = bx_warp_sum(ssq);
-  // the warp's candidate pivot data (the loads overlap the reductions below)
-  if (bidx != INT_MAX) {
-    for (int w = lane; w < p.r + kx + 2; w += 32) {
-      T x;
-      if (w < p.r) x = F[bidx + (size_t)w * p.ld];
-      else if (w < p.r + kx) x = __ldcg(&X[bidx + (size_t)(w - p.r) * p.ld]);
-      else x = (w == p.r + kx) ? p.a[bidx] : p.b[bidx];
-      sh.wcand[warp][w] = x;
+  // the warp's candidate pivot data: loads issued now, stored after the dot
+  // products below, so that their latency overlaps the reductions
+  constexpr int CV = (BX_CAND + 31) / 32;
+  const int ncand = p.r + kx + 2;
+  T cv[CV];
+#pragma unroll
+  for (int u = 0; u < CV; ++u) {
+    const int w = lane + 32 * u;
+    cv[u] = T(0);
+    if (bidx != INT_MAX && w < ncand) {
+      const int li = bidx - p.row0;  // the warp's candidate is one of the CTA's indices
+      if (w < p.r) cv[u] = bx_at(p, F, w, li);
+      else if (w < p.r + kx) cv[u] = bx_at(p, X, w - p.r, li);
+      else cv[u] = (w == p.r + kx) ? p.as[li] : p.bs[li];
     }
   }
   // dot products with the columns of Xd, 16 at a time
@@ -707,23 +788,42 @@ __device__ __forceinline__ void bx_reduce(const BxProb<T>& p, const T (&v)[RPT],
     T acc[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) acc[i] = T(0);
+    if (l0 + 16 <= Xd.ns || l0 >= Xd.ns) {  // the chunk is all shared or all global
+      const bool shd = l0 < Xd.ns;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int l = l0 + i;
-      if (l < kd) {
-        const T* Xc = Xd + (size_t)l * p.ld + base;
+      for (int i = 0; i < 16; ++i) {
+        const int l = l0 + i;
+        if (l < kd) {
+          const T* Xc = shd ? Xd.s + (size_t)l * p.SP + tid : Xd.g + (size_t)l * p.ld + base;
 #pragma unroll
-        for (int s = 0; s < RPT; ++s)
-          if (base + s * BX_NT < p.row1) acc[i] += __ldcg(&Xc[s * BX_NT]) * v[s];
+          for (int s = 0; s < RPT; ++s)
+            if (base + s * BX_NT < p.row1) acc[i] += (shd ? Xc[s * BX_NT] : __ldcg(&Xc[s * BX_NT])) * v[s];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int l = l0 + i;
+        if (l < kd) {
+#pragma unroll
+          for (int s = 0; s < RPT; ++s) {
+            const int li = tid + s * BX_NT;
+            if (base + s * BX_NT < p.row1) acc[i] += bx_at(p, Xd, l, li) * v[s];
+          }
+        }
       }
     }
     const T x = bx_transpose_sum16(acc, lane);
     if (lane < 16 && l0 + lane < kd) sh.wdots[l0 + lane][warp] = x;
   }
+#pragma unroll
+  for (int u = 0; u < CV; ++u)
+    if (bidx != INT_MAX && lane + 32 * u < ncand) sh.wcand[warp][lane + 32 * u] = cv[u];
   if (lane == 0) { sh.wabs[warp] = babs; sh.widx[warp] = bidx; sh.wval[warp] = bval; sh.wsum[warp] = ssq; }
   __syncthreads();
   // CTA reduction (warps in order) into the CTA's partial.
-  T* msg = sh.inbox[par][cs > 1 ? (int)cg::this_cluster().block_rank() : 0];
+  constexpr int WD = Mg::WORDS;
+  T* msg = p.inbox + ((size_t)par * cs + (cs > 1 ? (int)cg::this_cluster().block_rank() : 0)) * WD;
   if (warp == 0) {
     T a = lane < BX_NW ? sh.wabs[lane] : T(-1);
     int i = lane < BX_NW ? sh.widx[lane] : INT_MAX;
@@ -775,7 +875,7 @@ __device__ __forceinline__ void bx_reduce(const BxProb<T>& p, const T (&v)[RPT],
       T a = T(-1), vv = T(0), ss = T(0);
       int i = INT_MAX, src = -1;
       for (int qq = 0; qq < cs; ++qq) {
-        const T* mq = sh.inbox[par][qq];
+        const T* mq = p.inbox + ((size_t)par * cs + qq) * WD;
         ss += mq[Mg::SSQ];
         const int iq = (int)mq[Mg::IDX];
         if (iq >= 0 && bx_better(mq[Mg::ABS], iq, a, i)) { a = mq[Mg::ABS]; i = iq; vv = mq[Mg::VAL]; src = qq; }
@@ -787,13 +887,13 @@ __device__ __forceinline__ void bx_reduce(const BxProb<T>& p, const T (&v)[RPT],
     }
     for (int l = tid; l < kd; l += BX_NT) {
       T x = T(0);
-      for (int qq = 0; qq < cs; ++qq) x += sh.inbox[par][qq][Mg::DOTS + l];
+      for (int qq = 0; qq < cs; ++qq) x += p.inbox[((size_t)par * cs + qq) * WD + Mg::DOTS + l];
       sh.dots[l] = x;
     }
     __syncthreads();
     const int src = sh.win;
     if (src >= 0) {
-      const T* mq = sh.inbox[par][src];
+      const T* mq = p.inbox + ((size_t)par * cs + src) * WD;
       for (int w = tid; w < p.r + kx + 2; w += BX_NT) {
         const T x = mq[Mg::CAND + w];
         if (w < p.r) sh.vec[w] = x;
@@ -852,6 +952,48 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
   p.a = static_cast<const T*>(B.sa);
   p.b = static_cast<const T*>(B.sb);
   SolveState* st = B.st;
+  // shared-memory copies of the CTA's slices: the symbol always, Uh and Vh if
+  // they fit in half of what is left, then as many skeleton columns as fit
+  // (the same choice in every CTA of the cluster)
+  extern __shared__ __align__(16) unsigned char bx_dyn[];
+  {
+    const int SP = BX_NT * RPT;
+    const long long w = (long long)sizeof(T);
+    const long long inbox = 2LL * cs * BxMsg<T>::WORDS * w;
+    const long long budget = cp.smem_bytes;
+    const long long fixed = inbox + 2LL * SP * w;
+    const long long uvb = 2LL * SP * p.r * w;
+    p.uv = cp.cache && uvb <= (budget - fixed) / 2;
+    const long long left = budget - fixed - (p.uv ? uvb : 0);
+    long long KS = cp.cache ? left / (2LL * SP * w) : 0;
+    if (KS > p.kcap) KS = p.kcap;
+    if (KS < 0) KS = 0;
+    p.SP = SP;
+    p.KS = (int)KS;
+    T* q0 = reinterpret_cast<T*>(bx_dyn);
+    p.inbox = q0; q0 += 2 * cs * BxMsg<T>::WORDS;
+    T* as = q0; q0 += SP;
+    T* bs = q0; q0 += SP;
+    T* Us = q0; q0 += p.uv ? (size_t)SP * p.r : 0;
+    T* Vs = q0; q0 += p.uv ? (size_t)SP * p.r : 0;
+    p.Cs = q0; q0 += (size_t)SP * KS;
+    p.Rs = q0;
+    p.as = as; p.bs = bs; p.Us = Us; p.Vs = Vs;
+    const int S = p.row1 - p.row0;
+    for (int li = tid; li < S; li += BX_NT) {
+      as[li] = p.a[p.row0 + li];
+      bs[li] = p.b[p.row0 + li];
+    }
+    if (p.uv)
+      for (int al = 0; al < p.r; ++al)
+        for (int li = tid; li < S; li += BX_NT) {
+          Us[(size_t)al * SP + li] = p.Uh[p.row0 + li + (size_t)al * p.ld];
+          Vs[(size_t)al * SP + li] = p.Vh[p.row0 + li + (size_t)al * p.ld];
+        }
+  }
+  __syncthreads();
+  const BxSrc<T> srcU{p.Uh, p.Us, p.uv ? p.r : 0}, srcV{p.Vh, p.Vs, p.uv ? p.r : 0};
+  const BxSrc<T> srcC{p.C, p.Cs, p.KS}, srcR{p.R, p.Rs, p.KS};
   const T tol2 = (T)(cp.tol * cp.tol);
   const int base = p.row0 + tid;
   unsigned own = 0;  // owned indices
@@ -865,7 +1007,7 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
   int par = 0;
   T v[RPT];
   bx_scores<T, RPT>(p, a0, b0, v);
-  bx_reduce<T, RPT>(p, v, own, p.C, 0, p.Uh, p.C, 0, cs, par, sh);
+  bx_reduce<T, RPT>(p, v, own, srcC, 0, srcU, srcC, 0, cs, par, sh);
   int istar = sh.idx;
   int k = 0, probe_rounds = 0, zero_rows = 0, converged = 0;
   // index s of an owned index j (or -1)
@@ -877,12 +1019,12 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
     // ---------------- row half-step at istar (pivot data in sh.vec, sh.craw)
     for (int l = tid; l < k; l += BX_NT) sh.cd[l] = sh.craw[l] * sh.d[l];
     __syncthreads();
-    bx_eval<T, RPT>(p, p.Vh, p.R, k, sh, v);
+    bx_eval<T, RPT>(p, srcV, srcR, k, sh, v);
     {
       const int s = slot(istar);
       if (s >= 0) used_r |= 1u << s;
     }
-    bx_reduce<T, RPT>(p, v, own & ~used_c, p.R, k, p.Vh, p.R, k, cs, par, sh);
+    bx_reduce<T, RPT>(p, v, own & ~used_c, srcR, k, srcV, srcR, k, cs, par, sh);
     const int jstar = sh.idx;
     {
       const int s = jstar >= 0 ? slot(jstar) : -1;
@@ -901,7 +1043,7 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
       // the row is represented exactly: move to the best-scored unused row
       ++zero_rows;
       bx_scores<T, RPT>(p, a0, b0, v);
-      bx_reduce<T, RPT>(p, v, own & ~used_r, p.C, 0, p.Uh, p.C, k, cs, par, sh);
+      bx_reduce<T, RPT>(p, v, own & ~used_r, srcC, 0, srcU, srcC, k, cs, par, sh);
       if (zero_rows > cp.max_zero_rows || sh.idx < 0) { converged = 1; break; }
       istar = sh.idx;
       continue;
@@ -914,17 +1056,24 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
     }
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if ((own >> s) & 1u) p.R[base + s * BX_NT + (size_t)k * p.ld] = v[s] / tdelta;
+      if ((own >> s) & 1u) {
+        const T rv = v[s] / tdelta;
+        p.R[base + s * BX_NT + (size_t)k * p.ld] = rv;
+        if (k < p.KS) p.Rs[(size_t)k * p.SP + tid + s * BX_NT] = rv;
+      }
     __syncthreads();
-    bx_eval<T, RPT>(p, p.Uh, p.C, k, sh, v);
+    bx_eval<T, RPT>(p, srcU, srcC, k, sh, v);
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
       v[s] = v[s] / tdelta;
-      if ((own >> s) & 1u) p.C[base + s * BX_NT + (size_t)k * p.ld] = v[s];
+      if ((own >> s) & 1u) {
+        p.C[base + s * BX_NT + (size_t)k * p.ld] = v[s];
+        if (k < p.KS) p.Cs[(size_t)k * p.SP + tid + s * BX_NT] = v[s];
+      }
     }
     if (tid == 0) sh.d[k] = tdelta;
     // the next row step needs column k of C: the winner's own value
-    bx_reduce<T, RPT>(p, v, own & ~used_r, p.C, k, p.Uh, p.C, k, cs, par, sh);
+    bx_reduce<T, RPT>(p, v, own & ~used_r, srcC, k, srcU, srcC, k, cs, par, sh);
     const int inext = sh.idx;
     // ---------------- bookkeeping (thread 0 of every CTA, same arithmetic)
     if (tid == 0) {
@@ -1001,7 +1150,7 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
             if (ss == s) v[ss] = T(INFINITY);
         }
       }
-      bx_reduce<T, RPT>(p, v, own & ~used_r, p.C, 0, p.Uh, p.C, k, cs, par, sh);
+      bx_reduce<T, RPT>(p, v, own & ~used_r, srcC, 0, srcU, srcC, k, cs, par, sh);
       istar = sh.idx;
       if (istar < 0) { converged = 1; break; }
       continue;
@@ -1024,12 +1173,31 @@ template <typename T, int RPT>
 cudaError_t launch_bcross_rpt(const BatchProb* probs, const int* list, int n, int cs,
                               const BatchCrossParams& cp, cudaStream_t st) {
   auto kern = bcross_kernel<T, RPT>;
-  static cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // dynamic shared memory: what the SM has left beside the static part
+  static int dyn = 0;
+  static cudaError_t attr = [&] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess) {
+      dyn = optin - (int)fa.sharedSizeBytes - 1024;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+  }();
   if (attr != cudaSuccess) return attr;
+  BatchCrossParams c2 = cp;
+  c2.smem_bytes = dyn;
+  // without the factor cache only the inbox and the symbol slices are needed
+  const size_t need = c2.cache ? (size_t)dyn
+                               : ((size_t)2 * cs * BxMsg<T>::WORDS + 2 * (size_t)BX_NT * RPT) * sizeof(T);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * cs), 1, 1);
   cfg.blockDim = dim3(BX_NT, 1, 1);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = need;
   cfg.stream = st;
   cudaLaunchAttribute attr_[1];
   attr_[0].id = cudaLaunchAttributeClusterDimension;
@@ -1038,7 +1206,7 @@ cudaError_t launch_bcross_rpt(const BatchProb* probs, const int* list, int n, in
   attr_[0].val.clusterDim.z = 1;
   cfg.attrs = attr_;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, probs, list, cp);
+  return cudaLaunchKernelEx(&cfg, kern, probs, list, c2);
 }
 
 }  // namespace
@@ -1049,7 +1217,7 @@ template <typename T>
 cudaError_t launch_batch_cross(const BatchProb* probs, const int* list, int n, int cs, int rows_per_cta,
                                const BatchCrossParams& cp, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (cs != 1 && cs != 2 && cs != 4) return cudaErrorInvalidValue;
+  if (cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16) return cudaErrorInvalidValue;
   const int rpt = (rows_per_cta + BX_NT - 1) / BX_NT;
   if (rpt <= 4) return launch_bcross_rpt<T, 4>(probs, list, n, cs, cp, st);
   if (rpt <= 8) return launch_bcross_rpt<T, 8>(probs, list, n, cs, cp, st);

@@ -30,6 +30,7 @@
 // Shared-memory FFTs are in-place Stockham radix-4 (one radix-2 pass when
 // log2 L is odd): every thread keeps its 16 elements in registers between the
 // read and the write phase of a pass.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -105,7 +106,7 @@ struct GeomArgs {
 // Small path: 2^lognf sequences of length M per CTA.
 // ---------------------------------------------------------------------------
 template <typename T, int INM, bool OUT64>
-__global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
+__global__ void __launch_bounds__(kFftThreads, 2) dst_small_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     const cpx<T>* __restrict__ bhat, int lognf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -114,8 +115,9 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
   const int nf = 1 << lognf;
   const int items = (g.ncols + nf - 1) >> lognf;
   const int nelem = nf << g.logM;
-  cpx<T>* stw = buf + nelem;
+  cpx<T>* stw = buf + nelem + (nelem >> 4);  // after the padded tile
   build_stage_twiddles(stw, tw, g.logM, g.logM - 2);
+  const int stride = stage_stride(g.logM - 2);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     // Every loop below covers exactly EPT elements per thread; it is unrolled
     // so that a thread's global loads are all in flight together.
@@ -135,22 +137,22 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
         }
       }
 #pragma unroll
-      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
+      for (int s = 0; s < EPT; ++s) buf[smem_ix<true>(threadIdx.x + s * blockDim.x)] = v[s];
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, g.logM, lognf, 1, M, stw, false);
+    smem_fft_st<T, false, true>(buf, g.logM, lognf, 1, M, stw, stride, false);
     {
       cpx<T> b[EPT];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) b[s] = bhat[(threadIdx.x + s * blockDim.x) & (M - 1)];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
-        const int idx = threadIdx.x + s * blockDim.x;
+        const int idx = smem_ix<true>(threadIdx.x + s * blockDim.x);
         buf[idx] = cmul(buf[idx], b[s]);
       }
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, g.logM, lognf, 1, M, stw, true);
+    smem_fft_st<T, false, true>(buf, g.logM, lognf, 1, M, stw, stride, true);
 #pragma unroll
     for (int s = 0; s < EPT; ++s) {
       const int idx = threadIdx.x + s * blockDim.x;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
       const int col = (item << lognf) + row;
       int seg, cc;
       if (col < g.ncols && t < g.m && col_live(c, col, seg, cc)) {
-        const cpx<T> w = chirp[t], z = buf[idx];
+        const cpx<T> w = chirp[t], z = buf[smem_ix<true>(idx)];
         store_out<T, OUT64>(c, seg, cc, t, w.re * z.im + w.im * z.re);  // Im(w z)
       }
     }
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_small_kernel(
 // values and all M2 values of t2 (or k2): tile[t2 * TX + dt1].
 // ---------------------------------------------------------------------------
 template <typename T, int INM>
-__global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
+__global__ void __launch_bounds__(kFftThreads, 2) dst_col_fwd_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     cpx<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -183,6 +185,10 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
   const int items = g.ncols * blocks_per_col;
   cpx<T>* stw = buf + tile;
   build_stage_twiddles(stw, tw, g.logM, g.logM2 - 2);
+  const int stride = stage_stride(g.logM2 - 2);
+  cpx<T>* th = stw + stage_elems<T>(std::max(g.logM1, g.logM2) - 2);  // inter-pass twiddles
+  cpx<T>* tl = th + kTwHi;
+  load_twiddles2(th, tl, tw, g.logM);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int t1_0 = (item - col * blocks_per_col) << logTX;
@@ -206,14 +212,14 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
-    smem_fft_st<T, true>(buf, g.logM2, logTX, TX, 1, stw, false);
+    smem_fft_st<T, true>(buf, g.logM2, logTX, TX, 1, stw, stride, false);
     cpx<T>* wc = work + ((size_t)col << g.logM);
     {
       cpx<T> w[EPT];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * blockDim.x;
-        w[s] = tw[(t1_0 + (idx & (TX - 1))) * (idx >> logTX)];
+        w[s] = twiddle2(th, tl, (t1_0 + (idx & (TX - 1))) * (idx >> logTX));
       }
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_fwd_kernel(
 }
 
 template <typename T, bool OUT64>
-__global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
+__global__ void __launch_bounds__(kFftThreads, 2) dst_col_inv_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     const cpx<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
   const int items = g.ncols * blocks_per_col;
   cpx<T>* stw = buf + tile;
   build_stage_twiddles(stw, tw, g.logM, g.logM2 - 2);
+  const int stride = stage_stride(g.logM2 - 2);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int t1_0 = (item - col * blocks_per_col) << logTX;
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
       for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
     }
     __syncthreads();
-    smem_fft_st<T, true>(buf, g.logM2, logTX, TX, 1, stw, true);
+    smem_fft_st<T, true>(buf, g.logM2, logTX, TX, 1, stw, stride, true);
 #pragma unroll
     for (int s = 0; s < EPT; ++s) {
       const int idx = threadIdx.x + s * blockDim.x;
@@ -271,9 +278,13 @@ __global__ void __launch_bounds__(kFftThreads) dst_col_inv_kernel(
   }
 }
 
-// Row pass: RY = 4096 / M1 rows k2 per tile, each of M1 contiguous elements.
+// Row pass: RY = 4096 / M1 rows k2 per tile, each of M1 contiguous elements
+// in global memory.  In shared memory the rows are interleaved, element e of
+// row f at buf[e (RY + 1) + f], so that the FFT passes run with consecutive
+// lanes on consecutive rows (no bank conflicts; the padding keeps the
+// transposing loads and stores at two-way conflicts).
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
+__global__ void __launch_bounds__(kFftThreads, 2) dst_row_mid_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ tw, const cpx<T>* __restrict__ bhat,
     cpx<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -283,8 +294,13 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
   const int logRY = g.logTile - g.logM1;
   const int blocks_per_col = M2 >> logRY;
   const int items = g.ncols * blocks_per_col;
-  cpx<T>* stw = buf + tile;
+  const int RY = 1 << logRY, ES = RY + 1;
+  cpx<T>* stw = buf + tile + M1;  // after the padded tile (M1 x (RY + 1))
   build_stage_twiddles(stw, tw, g.logM, g.logM1 - 2);
+  const int stride = stage_stride(g.logM1 - 2);
+  cpx<T>* th = stw + stage_elems<T>(std::max(g.logM1, g.logM2) - 2);  // inter-pass twiddles
+  cpx<T>* tl = th + kTwHi;
+  load_twiddles2(th, tl, tw, g.logM);
   for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = item / blocks_per_col;
     const int k2_0 = (item - col * blocks_per_col) << logRY;
@@ -297,10 +313,13 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
 #pragma unroll
       for (int s = 0; s < EPT; ++s) v[s] = wc[threadIdx.x + s * blockDim.x];
 #pragma unroll
-      for (int s = 0; s < EPT; ++s) buf[threadIdx.x + s * blockDim.x] = v[s];
+      for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * blockDim.x;
+        buf[(idx & (M1 - 1)) * ES + (idx >> g.logM1)] = v[s];
+      }
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, g.logM1, logRY, 1, M1, stw, false);
+    smem_fft_st<T, true>(buf, g.logM1, logRY, ES, 1, stw, stride, false);
     {
       cpx<T> b[EPT];
 #pragma unroll
@@ -308,22 +327,23 @@ __global__ void __launch_bounds__(kFftThreads) dst_row_mid_kernel(
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * blockDim.x;
-        buf[idx] = cmul(buf[idx], b[s]);
+        const int bi = (idx & (M1 - 1)) * ES + (idx >> g.logM1);
+        buf[bi] = cmul(buf[bi], b[s]);
       }
     }
     __syncthreads();
-    smem_fft_st<T, false>(buf, g.logM1, logRY, 1, M1, stw, true);
+    smem_fft_st<T, true>(buf, g.logM1, logRY, ES, 1, stw, stride, true);
     {
       cpx<T> w[EPT];
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * blockDim.x;
-        w[s] = tw[(idx & (M1 - 1)) * (k2_0 + (idx >> g.logM1))];
+        w[s] = twiddle2(th, tl, (idx & (M1 - 1)) * (k2_0 + (idx >> g.logM1)));
       }
 #pragma unroll
       for (int s = 0; s < EPT; ++s) {
         const int idx = threadIdx.x + s * blockDim.x;
-        wc[idx] = cmulc(buf[idx], w[s]);  // times exp(+2 pi i t1 k2 / M)
+        wc[idx] = cmulc(buf[(idx & (M1 - 1)) * ES + (idx >> g.logM1)], w[s]);  // times exp(+2 pi i t1 k2 / M)
       }
     }
     __syncthreads();
@@ -464,14 +484,14 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
     while ((M << (lognf + 1)) <= kTileElems && (g.ncols >> (lognf + 1)) >= 2 * num_sms) ++lognf;
     const int nelem = M << lognf;
     const int threads = nelem / EPT;
-    const size_t smem = (size_t)(nelem + stage_elems<T>()) * sizeof(cpx<T>);
+    const size_t smem = (size_t)(nelem + (nelem >> 4) + stage_elems<T>(g.logM - 2)) * sizeof(cpx<T>);
     const int items = (g.ncols + (1 << lognf) - 1) >> lognf;
     const int grid = items < 8 * num_sms ? items : 8 * num_sms;
     auto kern = dst_small_kernel<T, INM, OUT64>;
     static bool attr_set = false;  // once per instantiation: the largest tile plus the stage tables
     if (!attr_set) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (kTileElems + stage_elems<T>()) * (int)sizeof(cpx<T>));
+                           (kTileElems + (kTileElems >> 4) + stage_elems<T>(kStageLog)) * (int)sizeof(cpx<T>));
       attr_set = true;
     }
     kern<<<grid, threads, smem, st>>>(c, g, chirp, tw, bhat, lognf);
@@ -524,7 +544,8 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
   }
   const int tile = 1 << g2.logTile;
   const int threads = tile / EPT;
-  const size_t smem = (size_t)(tile + stage_elems<T>()) * sizeof(cpx<T>);
+  const int slog = std::max(g.logM1, g.logM2) - 2;
+  const size_t smem = (size_t)(tile + (1 << g.logM1) + stage_elems<T>(slog) + kTwHi + kTwLo) * sizeof(cpx<T>);
   const int items_col = g.ncols * ((1 << g.logM1) >> (g2.logTile - g.logM2));
   const int items_row = g.ncols * ((1 << g.logM2) >> (g2.logTile - g.logM1));
   const int cap = 8 * num_sms;
@@ -534,7 +555,7 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
   auto k3 = dst_col_inv_kernel<T, OUT64>;
   static bool attr_set = false;  // once per instantiation: the largest tile plus the stage tables
   if (!attr_set) {
-    const int mx = (kTileElems + stage_elems<T>()) * (int)sizeof(cpx<T>);
+    const int mx = (kTileElems + 4096 + stage_elems<T>(kStageLog) + kTwHi + kTwLo) * (int)sizeof(cpx<T>);
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

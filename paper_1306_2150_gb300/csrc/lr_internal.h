@@ -233,6 +233,7 @@ struct BatchItems {
   int items = 0;     // items, or (live lists) the capacity the grid is sized for
   int live = 0;      // 1: start[] is written on the device by launch_batch_live_items
                      // and counts only the live (rank < R) columns, start[n] = items
+  int slog = 0;      // largest log2 sub-length of the launch's FFT stages (log2 L - 2)
 };
 
 // Item tables of the inverse transforms over live columns only: for each of
@@ -261,10 +262,12 @@ struct BatchCrossParams {
   unsigned long long seed;
   int max_probe_rounds;
   int max_zero_rows;
+  int smem_bytes;  // dynamic shared memory of the launch (set by the launcher)
+  int cache = 0;   // 1: keep Uh, Vh and the first skeleton columns in shared memory
 };
 
 // Batched cross: problems list[0..n) (LPT order), each on a cluster of cs
-// CTAs (1, 2 or 4) with rows_per_cta >= ceil(m / cs) indices per CTA.
+// CTAs (1, 2, 4, 8 or 16) with rows_per_cta >= ceil(m / cs) indices per CTA.
 template <typename T>
 cudaError_t launch_batch_cross(const BatchProb* probs, const int* list, int n, int cs, int rows_per_cta,
                                const BatchCrossParams& cp, cudaStream_t st);

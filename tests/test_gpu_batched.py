@@ -63,7 +63,7 @@ def test_batched_equals_single_solves_and_oracle(lr, h, prec, eps):
 def test_phased_batch_matches_oracle(lr, h, prec, eps):
     # the phase-batched form on uneven problems: small-path (M <= 4096) and
     # four-step transforms, single-CTA and clustered crosses (4096 indices per
-    # CTA by default: m > 4096 takes 2 CTAs).  Mixed: every problem within
+    # CTA by default: m > 4096 takes 2 or more CTAs).  Mixed: every problem within
     # 10 eps of the exact solution.  Float64: the oracle's rank and singular
     # values, and its error (the cross stop rule at tol = eps leaves some of
     # these random problems slightly above 10 eps at eps = 1e-9, in the
@@ -74,7 +74,7 @@ def test_phased_batch_matches_oracle(lr, h, prec, eps):
     torch.cuda.synchronize()
     assert st == lr.LR_OK and all(s == lr.LR_OK for s in batch.status)
     info, _, _ = lr.lr_get_info(h)
-    assert info.launches <= 14
+    assert info.launches <= 16  # 4 + 4 transform launches, <= 5 cluster-size groups, 3 rounding
     for i, (U, V) in enumerate(probs):
         Ub, sb, Vb = (npy(t) for t in batch.result(i))
         rows = None if U.shape[0] <= 4096 else np.unique(np.linspace(0, U.shape[0] - 1, 256).astype(int))

@@ -52,9 +52,10 @@ def test_stokes_matches_oracle(lr, h, n, prec, eps, tol, acc):
     div = np.linalg.norm(S.bt(u, v, n)) / np.linalg.norm(S.bt(S.laplace_solve(f1, n), S.laplace_solve(f2, n), n))
     bound = 5 * tol + 2 * n * (max(eps, 1e-6) if prec == "mixed" else eps)  # mixed inner solves run at >= 1e-6
     assert div <= bound and res.resid <= bound, (div, res.resid)
-    # the pressure has no kernel component
+    # the pressure has no kernel component beyond the rounding that follows
+    # the projection (relative eps; the modes have unit norm)
     for K in S.kernel_modes(n):
-        assert abs(np.sum(p * K)) <= 1e-8 * np.linalg.norm(p)
+        assert abs(np.sum(p * K)) <= max(1e-8, 2 * eps) * np.linalg.norm(p)
 
 
 def test_stokes_iterations_independent_of_h(lr, h):
