@@ -64,6 +64,8 @@ def parse():
                    help="problems in the uneven batch (n log-uniform in [512, 16384], r in 1..32; 0: skip)")
     p.add_argument("--tucker", type=int, nargs="*", default=[128, 256, 512, 1024],
                    help="grid sizes of the 3D Tucker solves (eps = 1e-6, float64)")
+    p.add_argument("--sweep", type=int, nargs="*", default=[1024, 4096, 16384, 65536],
+                   help="grid sizes of the single-solve sweep (eps 1e-6 and 1e-10, float64 and mixed)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -414,6 +416,33 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         results["tight_" + prec] = {"ms": statistics.median(per), "rank": rr.info.rank, "r": U2.shape[1],
                                     "refine_rounds": rr.info.refine_rounds, "status": rr.status,
                                     "rel_err": rel_error_sampled(rr.U, rr.s, rr.V, U2, V2)}
+    # ---- the n-sweep of single solves: eps 1e-6 and 1e-10, float64 and mixed
+    # (mixed at 1e-10 with float64 refinement), each with its error
+    results["sweep"] = []
+    for ns in args.sweep:
+        for eps_s in (EPS, EPS_TIGHT):
+            Us, Vs = inputs.smooth_sum(ns, eps_s)
+            Usd, Vsd = torch.from_numpy(Us).cuda(), torch.from_numpy(Vs).cuda()
+            outs = (lr.colmajor_empty(ns, 64), torch.empty(64, dtype=torch.float64, device="cuda"),
+                    lr.colmajor_empty(ns, 64))
+            row = {"n": ns, "eps": eps_s, "rhs_rank": Us.shape[1]}
+            for prec in ("fp64", "mixed"):
+                rr = lr.lr_poisson2d(h, Usd, Vsd, eps=eps_s, prec=prec, out=outs)
+                per = []
+                for i in range(3):
+                    flush.fill_(i & 0xFF)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    rr = lr.lr_poisson2d(h, Usd, Vsd, eps=eps_s, prec=prec, out=outs)
+                    b.record(stream)
+                    stream.synchronize()
+                    per.append(a.elapsed_time(b))
+                row[prec] = {"ms": round(statistics.median(per), 4), "rank": rr.info.rank, "status": rr.status,
+                             "refine_rounds": rr.info.refine_rounds,
+                             "rel_err": float(f"{rel_error_sampled(rr.U, rr.s, rr.V, Us, Vs):.3e}")}
+            results["sweep"].append(row)
+            del Usd, Vsd, outs
     # ---- crossover against the full-grid solver X = S((S F S)/Lambda)S on the
     # dense grid (same smooth right-hand side, single solves, 3 timed each)
     results["crossover"] = []
@@ -790,6 +819,7 @@ def main():
             "refine_rounds": res["tight_mixed"]["refine_rounds"],
             "rank": {"fp64": res["tight_fp64"]["rank"], "mixed": res["tight_mixed"]["rank"]},
             "rhs_rank": res["tight_fp64"]["r"]},
+        "single_solve_sweep": res["sweep"],
         "crossover_full_grid_vs_lowrank": res["crossover"],
         "stokes_uzawa_lowrank": res["stokes"],
         "expsum_vs_cross": res["expsum"],

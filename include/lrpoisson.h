@@ -29,6 +29,8 @@
 #ifndef LRPOISSON_H
 #define LRPOISSON_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -163,6 +165,13 @@ void lr_options_default(lr_options* opt);
  * stream) on the current device.  Returns LR_ECUDA if no device is usable. */
 lr_status lr_create(lr_handle* h, void* cuda_stream);
 lr_status lr_set_stream(lr_handle h, void* cuda_stream);
+/* Cap the total device workspace the handle may hold (the paper has no
+ * counterpart; memory budgeting for processes that share a GPU).  bytes = 0
+ * removes the cap (default).  A call whose workspace would exceed the cap
+ * returns LR_ENOMEM before launching anything and leaves the handle usable;
+ * workspace already held is kept.  Plan tables, captured graphs and their
+ * descriptor blocks are not counted. */
+lr_status lr_set_workspace_limit(lr_handle h, size_t bytes);
 lr_status lr_destroy(lr_handle h);
 const char* lr_last_error(lr_handle h);
 const char* lr_status_string(lr_status s);
@@ -230,25 +239,30 @@ lr_status lr_get_phase_times(lr_handle h, double* ms, int n);
  * (Section 2: Eq. flr:stprob with A = I_2 (x) Delta, B = [B_x; B_y],
  * B_x = G (x) H / (4h), B_y = H (x) G / (4h), h = 1/n; Section 5: the Uzawa
  * iteration in low-rank format).  Conjugate gradients on the Schur equation
- * (B^T A^-1 B) p = B^T A^-1 f (Eq. flr:schur) with every iterate in low-rank
+ * (B^T A^-1 B) p = B^T A^-1 f - g (Eq. flr:schur; the paper prints it without
+ * the divergence right-hand side g, elimination of u gives the -g) with every iterate in low-rank
  * format: each Schur product applies B to the factors (bidiagonal maps, rank
  * kept), runs the two velocity Poisson solves (semi-staggered kind, m = n - 1,
  * batched, opt->prec) and rounds B^T of the result; every CG update is
  * rounded in float64 at opt->eps; the CG scalars are float64.  The
  * pressure's two kernel modes (constant, checkerboard) are projected out of
- * p.  Stops when ||r|| <= tol_div ||B^T A^-1 f|| (r the Schur residual) or
+ * p.  Stops when ||r|| <= tol_div ||B^T A^-1 f - g|| (r the Schur residual) or
  * after maxit iterations (LR_ENOCONV, best iterate written).
  *   d     : 2 (the only dimension built)
  *   n     : cells per direction; velocity on the (n-1) x (n-1) interior
  *           vertices, pressure on the n x n cell centres (first index x)
  *   f     : 2 body-force components, (n-1) x (n-1), rank 1..64, s = NULL
- *   g     : must be NULL (divergence-free)
+ *   g     : NULL (divergence-free, B^T u = 0) or the divergence right-hand
+ *           side B^T u = g: n x n, rank 0..64, s may be NULL; rounded at
+ *           eps on entry; its components along the pressure's two kernel
+ *           modes cannot be met (B annihilates them) and are dropped
  *   u     : 2 velocity outputs (n-1) x (n-1), U, s, V capacity rmax
  *   p     : pressure output n x n (U, s, V capacity rmax).  On entry p->r = 0,
  *           or the rank of an initial guess held in p (resume from a saved
  *           pressure: CG restarts from r = rhs - S p, GMRES likewise)
  *   iters : CG iterations taken (may be NULL)
- *   resid : ||B^T u|| / ||B^T A^-1 f|| of the returned velocity (may be NULL)
+ *   resid : ||B^T u - g'|| / ||B^T A^-1 f - g'|| of the returned velocity,
+ *           g' = g without its kernel components (may be NULL)
  *   history: host array of maxit + 1 doubles (may be NULL): ||r_k|| / ||r_0||
  *           of the CG residual for k = 0..iters (the rest untouched)
  * LR_EINVAL for bad arguments, LR_ENOCONV if tol_div was not reached or a
@@ -342,8 +356,7 @@ lr_status lr_poisson2d_full(lr_handle h, int m, const double* F, int ldf, double
  * sol buffers receive the trial results) for several numbers of indices per
  * cross CTA and keeps the fastest for batched solves of that precision on
  * this handle: 2048, 4096, 8192, 16384 (LR_FP64 up to 8192; default 4096)
- * for the phase-batched form, which then takes 1 to 16 CTAs per problem
- * (slices of 2048 indices keep the factors in shared memory);
+ * for the phase-batched form, which then takes 1 to 16 CTAs per problem;
  * 1024, 2048, 4096, 8192 (default 2048) for the stream form
  * (LR_FLAG_BATCH_STREAMS in opt->flags).
  *

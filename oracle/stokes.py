@@ -112,9 +112,16 @@ class UzawaResult:
     history: list
 
 
-def uzawa_cg(f1: np.ndarray, f2: np.ndarray, n: int, tol: float = 1e-10, maxit: int = 500) -> UzawaResult:
-    """Conjugate gradients on (B^T A^-1 B) p = B^T A^-1 f, p0 = 0, full format."""
+def uzawa_cg(f1: np.ndarray, f2: np.ndarray, n: int, tol: float = 1e-10, maxit: int = 500,
+             g: np.ndarray | None = None) -> UzawaResult:
+    """Conjugate gradients on (B^T A^-1 B) p = B^T A^-1 f - g, p0 = 0, full
+    format.  g (n x n, default 0) is the right-hand side of the divergence
+    equation B^T u = g; the Schur equation of Eq. flr:schur is printed
+    without it, and elimination of u = A^-1 (f - B p) gives the -g (reading
+    G5).  Only the part of g orthogonal to the kernel modes can be met."""
     rhs = bt(laplace_solve(f1, n), laplace_solve(f2, n), n)
+    if g is not None:
+        rhs = rhs - g
     rhs = project_kernel(rhs, n)
     nr0 = np.linalg.norm(rhs)
     p = np.zeros((n, n))
@@ -136,14 +143,16 @@ def uzawa_cg(f1: np.ndarray, f2: np.ndarray, n: int, tol: float = 1e-10, maxit: 
     p = project_kernel(p, n)
     u = laplace_solve(f1 - bx(p, n), n)
     v = laplace_solve(f2 - by(p, n), n)
-    res = np.linalg.norm(bt(u, v, n)) / nr0 if nr0 > 0.0 else 0.0  # zero force: u = p = 0
+    div = bt(u, v, n) if g is None else bt(u, v, n) - project_kernel(g, n)
+    res = np.linalg.norm(div) / nr0 if nr0 > 0.0 else 0.0  # zero force: u = p = 0
     return UzawaResult(u, v, p, it, res, hist)
 
 
-def saddle_dense(f1: np.ndarray, f2: np.ndarray, n: int):
-    """The assembled saddle system of Eq. flr:stprob (small n), solved by least
-    squares with the minimum-norm pressure (independent of the DST and of
-    the Uzawa reduction)."""
+def saddle_dense(f1: np.ndarray, f2: np.ndarray, n: int, g: np.ndarray | None = None):
+    """The assembled saddle system of Eq. flr:stprob (small n), divergence
+    equation B^T u = g (default 0), solved by least squares with the
+    minimum-norm pressure (independent of the DST and of the Uzawa
+    reduction)."""
     m = n - 1
     G, H = gh(n)
     # vec with the first index fastest: vec(G P H^T) = (H (x) G) vec(P)
@@ -158,7 +167,8 @@ def saddle_dense(f1: np.ndarray, f2: np.ndarray, n: int):
     K[nv:2 * nv, 2 * nv:] = By
     K[2 * nv:, :nv] = Bx.T
     K[2 * nv:, nv:2 * nv] = By.T
-    rhs = np.concatenate([f1.reshape(-1, order="F"), f2.reshape(-1, order="F"), np.zeros(n * n)])
+    gv = np.zeros(n * n) if g is None else g.reshape(-1, order="F")
+    rhs = np.concatenate([f1.reshape(-1, order="F"), f2.reshape(-1, order="F"), gv])
     sol = np.linalg.lstsq(K, rhs, rcond=None)[0]
     u = sol[:nv].reshape(m, m, order="F")
     v = sol[nv:2 * nv].reshape(m, m, order="F")

@@ -76,6 +76,7 @@ struct lr_handle_s {
   cudaEvent_t bdesc_ev = nullptr;
   std::map<std::string, char*> graph_desc;
   int cross_rows[2] = {4096, 4096};  // indices per CTA of the batched cross (float64, float32)
+  size_t ws_limit = 0;               // cap on the workspaces' total bytes (0: none)
 };
 
 namespace {
@@ -136,8 +137,35 @@ lr_status get_plan(lr_handle h, int m, Plan** out) {
   return LR_OK;
 }
 
+// Grow one of the handle's workspaces to `need` bytes (freeing the old one
+// after the stream has finished with it), within the handle's limit.
+lr_status grow_ws(lr_handle h, void** slot, size_t* slot_bytes, size_t need, const char* what) {
+  if (need <= *slot_bytes) return LR_OK;
+  const size_t total = h->ws_bytes + h->ws2_bytes + h->ws3_bytes + h->ws4_bytes + h->ws5_bytes;
+  if (h->ws_limit && total - *slot_bytes + need > h->ws_limit)
+    return fail(h, LR_ENOMEM, std::string(what) + ": " + std::to_string(need) +
+                                  " bytes would exceed the handle's workspace limit of " + std::to_string(h->ws_limit));
+  if (*slot) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(*slot);
+    *slot = nullptr;
+    *slot_bytes = 0;
+  }
+  if (cudaMalloc(slot, need) != cudaSuccess) {
+    cudaGetLastError();
+    *slot = nullptr;
+    return fail(h, LR_ENOMEM, std::string(what) + ": cudaMalloc of " + std::to_string(need) + " bytes failed");
+  }
+  *slot_bytes = need;
+  return LR_OK;
+}
+
 lr_status ensure_ws(lr_handle h, size_t bytes) {
   if (bytes <= h->ws_bytes) return LR_OK;
+  const size_t total = h->ws_bytes + h->ws2_bytes + h->ws3_bytes + h->ws4_bytes + h->ws5_bytes;
+  if (h->ws_limit && total - h->ws_bytes + bytes > h->ws_limit)
+    return fail(h, LR_ENOMEM, "workspace: " + std::to_string(bytes) +
+                                  " bytes would exceed the handle's workspace limit of " + std::to_string(h->ws_limit));
   if (h->ws) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->ws);
@@ -541,9 +569,8 @@ lr_status solve2d_refined(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_
   Carve sizing;
   carve_refine(sizing, b, ld, m);
   if (sizing.off > h->ws2_bytes) {
-    if (h->ws2) { cudaStreamSynchronize(h->stream); cudaFree(h->ws2); h->ws2 = nullptr; h->ws2_bytes = 0; }
-    if (cudaMalloc(&h->ws2, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "refinement buffers"); }
-    h->ws2_bytes = sizing.off;
+    const lr_status sg = grow_ws(h, &h->ws2, &h->ws2_bytes, sizing.off, "refinement buffers");
+    if (sg != LR_OK) return sg;
   }
   Carve cv;
   cv.base = static_cast<char*>(h->ws2);
@@ -697,9 +724,8 @@ lr_status solve2d_full(lr_handle h, int m, const double* F, int ldf, double* X, 
   const size_t sbytes = M > (size_t)kSmallM ? align256(sizeof(cpx<T>) * M * (size_t)m) : 256;
   const size_t need = 2 * wbytes + sbytes;
   if (need > h->ws3_bytes) {
-    if (h->ws3) { cudaStreamSynchronize(h->stream); cudaFree(h->ws3); h->ws3 = nullptr; h->ws3_bytes = 0; }
-    if (cudaMalloc(&h->ws3, need) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "full-grid workspace"); }
-    h->ws3_bytes = need;
+    const lr_status sg = grow_ws(h, &h->ws3, &h->ws3_bytes, need, "full-grid workspace");
+    if (sg != LR_OK) return sg;
   }
   char* base = static_cast<char*>(h->ws3);
   T* W1 = reinterpret_cast<T*>(base);
@@ -743,9 +769,8 @@ lr_status solve2d_expsum(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_o
   Carve sizing;
   carve_refine(sizing, b, ld, m);
   if (sizing.off > h->ws2_bytes) {
-    if (h->ws2) { cudaStreamSynchronize(h->stream); cudaFree(h->ws2); h->ws2 = nullptr; h->ws2_bytes = 0; }
-    if (cudaMalloc(&h->ws2, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "exp-sum buffers"); }
-    h->ws2_bytes = sizing.off;
+    const lr_status sg = grow_ws(h, &h->ws2, &h->ws2_bytes, sizing.off, "exp-sum buffers");
+    if (sg != LR_OK) return sg;
   }
   Carve cv;
   cv.base = static_cast<char*>(h->ws2);
@@ -1147,10 +1172,6 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
   cp.seed = o.seed;
   cp.max_probe_rounds = 4;
   cp.max_zero_rows = 16;
-  // slices of at most 2048 indices: keep the factors and the first skeleton
-  // columns in shared memory (larger slices: everything from L2, which keeps
-  // the CTA's shared memory small)
-  cp.cache = rows <= 2048 ? 1 : 0;
   const int nsm = h->num_sms;
   const void* tw = h->tw4096[pi];
   const int launches = (L.fwd_small.items > 0) + 3 * (L.fwd_col.items > 0) + (int)L.cross.size() + 3 +
@@ -1318,6 +1339,8 @@ struct StokesCtx {
   int n, ldp, ldv;
   RefineBufs b;
   LrDev P, R, D, Q, T;               // pressure-sized (n x KMAX), T: scratch result
+  LrDev G;                           // the divergence right-hand side g (rounded copy)
+  bool has_g = false;
   double *RU[2], *RV[2];             // velocity right-hand sides ((n-1) x KMAX, weights folded)
   double *WU[2], *Ws[2], *WV[2];     // velocity solutions
   double *wts, *gm0, *gm1, *cs, *E;  // weights, cross Gram matrices, column sums, kernel modes
@@ -1341,7 +1364,7 @@ constexpr double kGmresMaxDelta = 1e-4;
 void carve_stokes(Carve& c, StokesCtx& x) {
   carve_refine(c, x.b, x.ldp, x.n);
   const size_t cp = sizeof(double) * (size_t)x.ldp * KMAX, cv = sizeof(double) * (size_t)x.ldv * KMAX;
-  for (LrDev* d : {&x.P, &x.R, &x.D, &x.Q, &x.T}) {
+  for (LrDev* d : {&x.P, &x.R, &x.D, &x.Q, &x.T, &x.G}) {
     d->U = c.take<double>(cp);
     d->V = c.take<double>(cp);
     d->s = c.take<double>(sizeof(double) * KMAX);
@@ -1672,9 +1695,8 @@ lr_status solve3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, cons
   Carve sizing;
   layout(sizing);
   if (sizing.off > h->ws5_bytes) {
-    if (h->ws5) { cudaStreamSynchronize(stm); cudaFree(h->ws5); h->ws5 = nullptr; h->ws5_bytes = 0; }
-    if (cudaMalloc(&h->ws5, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "3D workspace"); }
-    h->ws5_bytes = sizing.off;
+    const lr_status sg = grow_ws(h, &h->ws5, &h->ws5_bytes, sizing.off, "3D workspace");
+    if (sg != LR_OK) return sg;
   }
   if (!h->h_big && cudaMallocHost(&h->h_big, sizeof(double) * (2 * KMAX * KMAX + 4 * KMAX)) != cudaSuccess) {
     cudaGetLastError();
@@ -2121,8 +2143,8 @@ lr_status stokes_gmres(StokesCtx& x, double tol, int maxit, double nr0, int* it_
 // eps ||r0|| (the Schur product q: a tenth of it).
 constexpr double kCgFloor = 0.3;
 
-lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p, double tol, int maxit,
-                       const lr_options& o, int* iters, double* resid, double* history) {
+lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p, double tol,
+                       int maxit, const lr_options& o, int* iters, double* resid, double* history) {
   StokesCtx x;
   x.h = h;
   x.n = n;
@@ -2146,9 +2168,7 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   Carve sizing;
   carve_stokes(sizing, x);
   if (sizing.off > h->ws4_bytes) {
-    if (h->ws4) { cudaStreamSynchronize(h->stream); cudaFree(h->ws4); h->ws4 = nullptr; h->ws4_bytes = 0; }
-    if (cudaMalloc(&h->ws4, sizing.off) != cudaSuccess) { cudaGetLastError(); return fail(h, LR_ENOMEM, "Stokes workspace"); }
-    h->ws4_bytes = sizing.off;
+    if ((s = grow_ws(h, &h->ws4, &h->ws4_bytes, sizing.off, "Stokes workspace")) != LR_OK) return s;
   }
   if (!h->h_big && cudaMallocHost(&h->h_big, sizeof(double) * (2 * KMAX * KMAX + 4 * KMAX)) != cudaSuccess) {
     cudaGetLastError();
@@ -2165,6 +2185,24 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
   int rx = 0, ry = 0;
   if ((s = velocity_solves(x, f, &rx, &ry)) != LR_OK) return s;
   if ((s = div_round(x, rx, ry, x.R)) != LR_OK) return s;
+  // divergence right-hand side (B^T u = g): the Schur right-hand side is
+  // B^T A^-1 f - g (Eq. flr:schur with -g); g's components along the kernel
+  // modes cannot be met and are dropped
+  double ga = 0.0, gb = 0.0;
+  if (g && g->r > 0) {
+    if ((s = sum_round(x, n, {{g->U, g->s, g->V, g->r, g->ld, 1.0}}, x.G, x.ldp)) != LR_OK) return s;
+    x.has_g = x.G.r > 0;
+  }
+  if (x.has_g) {
+    double ra = 0.0, rb = 0.0;
+    if ((s = kernel_coeffs(x, x.R, 1.0, &ra, &rb)) != LR_OK) return s;
+    if ((s = kernel_coeffs(x, x.G, 1.0, &ga, &gb)) != LR_OK) return s;
+    if ((s = sum_round(x, n, {{x.R.U, x.R.s, x.R.V, x.R.r, x.ldp, 1.0}, {x.G.U, x.G.s, x.G.V, x.G.r, x.ldp, -1.0},
+                              {x.E, nullptr, x.E, 1, x.ldp, ga - ra}, {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, gb - rb}},
+                       x.T, x.ldp)) != LR_OK)
+      return s;
+    std::swap(x.R, x.T);
+  }
   double rr = 0.0;
   if ((s = norm2_of(x, x.R, &rr)) != LR_OK) return s;
   const double nr0 = std::sqrt(rr);
@@ -2297,6 +2335,13 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, lr_mat* u, lr_mat* p
     LR_CUDA(h, cudaMemcpyAsync(x.Ws[k], u[k].s, sizeof(double) * u[k].r, cudaMemcpyDeviceToDevice, stm), "copy");
   }
   if ((s = div_round(x, u[0].r, u[1].r, x.T)) != LR_OK) return s;
+  if (x.has_g) {  // B^T u - (g without its kernel components)
+    if ((s = sum_round(x, n, {{x.T.U, x.T.s, x.T.V, x.T.r, x.ldp, 1.0}, {x.G.U, x.G.s, x.G.V, x.G.r, x.ldp, -1.0},
+                              {x.E, nullptr, x.E, 1, x.ldp, ga}, {x.E + x.ldp, nullptr, x.E + x.ldp, 1, x.ldp, gb}},
+                       x.Q, x.ldp)) != LR_OK)
+      return s;
+    std::swap(x.T, x.Q);
+  }
   double dv = 0.0;
   if ((s = norm2_of(x, x.T, &dv)) != LR_OK) return s;
   // pressure out
@@ -2380,6 +2425,12 @@ lr_status lr_create(lr_handle* out, void* stream) {
   std::memset(h->h_state, 0, sizeof(SolveState));
   std::memset(h->h_piv, 0, sizeof(int) * 2 * KMAX);
   *out = h;
+  return LR_OK;
+}
+
+lr_status lr_set_workspace_limit(lr_handle h, size_t bytes) {
+  if (!h) return LR_EINVAL;
+  h->ws_limit = bytes;
   return LR_OK;
 }
 
@@ -2535,7 +2586,9 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
   lr_status s = check_opts(h, o);
   if (s != LR_OK) return s;
   if (d != 2) return fail(h, LR_EINVAL, "lr_stokes_uzawa: only d = 2 is built");
-  if (g) return fail(h, LR_EINVAL, "lr_stokes_uzawa: g must be NULL (divergence-free constraint)");
+  if (g && (g->n1 != n || g->n2 != n || g->r < 0 || g->r > KMAX || g->ld < n || !g->U || !g->V ||
+            !aligned16(g->U) || !aligned16(g->V) || (g->s && !aligned16(g->s))))
+    return fail(h, LR_EINVAL, "lr_stokes_uzawa: g must be NULL or n x n of rank 0..64 with aligned U, V");
   if (n < 3 || n > 32768) return fail(h, LR_EINVAL, "lr_stokes_uzawa: n must be in [3, 32768]");
   if (!f || !u || !p) return fail(h, LR_EINVAL, "lr_stokes_uzawa: null f, u or p");
   if (!(tol_div > 0.0) || tol_div >= 1.0 || maxit < 1) return fail(h, LR_EINVAL, "lr_stokes_uzawa: bad tol_div or maxit");
@@ -2550,7 +2603,7 @@ lr_status lr_stokes_uzawa(lr_handle h, int d, int n, const lr_mat* f, const lr_m
     return fail(h, LR_EINVAL, "lr_stokes_uzawa: p must be n x n with U, s, V set and aligned");
   if (p->r < 0 || p->r > std::min(p->rmax, KMAX))
     return fail(h, LR_EINVAL, "lr_stokes_uzawa: p->r (the initial guess's rank, 0 for none) must be in [0, min(p->rmax, 64)]");
-  return stokes_uzawa(h, n, f, u, p, tol_div, maxit, o, iters, resid, history);
+  return stokes_uzawa(h, n, f, g, u, p, tol_div, maxit, o, iters, resid, history);
 }
 
 lr_status lr_poisson3d_tucker(lr_handle h, const lr_tucker* rhs, lr_tucker* sol, const lr_options* opt) {

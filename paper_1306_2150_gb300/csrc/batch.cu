@@ -106,6 +106,33 @@ __device__ __forceinline__ int find_live_item(const BatchItems& it, int item) {
   return lo;
 }
 
+// The contiguous range of items of this CTA (items of one problem are
+// contiguous, so a CTA looks its problem up once and then steps through the
+// prefix table instead of searching it for every item).
+struct ItemRange {
+  int begin, end, q, qbeg, qend;  // qbeg, qend: the items of problem q
+  __device__ __forceinline__ ItemRange(const BatchItems& it, int items) {
+    const int per = (items + (int)gridDim.x - 1) / (int)gridDim.x;
+    begin = min(items, (int)blockIdx.x * per);
+    end = min(items, begin + per);
+    q = -1;
+    qbeg = qend = 0;
+  }
+  __device__ __forceinline__ int problem(const BatchItems& it, int item) {
+    if (q < 0) {
+      q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
+      qbeg = __ldcg(&it.start[q]);
+      qend = __ldcg(&it.start[q + 1]);
+    }
+    while (item >= qend) {  // uniform across the CTA
+      ++q;
+      qbeg = qend;
+      qend = __ldcg(&it.start[q + 1]);
+    }
+    return q;
+  }
+};
+
 constexpr int kBTile = 4096;          // complex elements per tile
 constexpr int kBThreads = kBTile / EPT;
 
@@ -120,11 +147,12 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_small_kernel(const BatchPro
   build_stage_twiddles(stw, tw4096, 12, it.slog);
   const int stride = stage_stride(it.slog);
   const int items = item_count(it);
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
+  ItemRange rg(it, items);
+  for (int item = rg.begin; item < rg.end; ++item) {
+    const int q = rg.problem(it, item);
     const BatchProb& B = P[it.list[q]];
     const int logM = B.logM, M = 1 << logM, lognf = 12 - logM;
-    const int col0 = (item - __ldcg(&it.start[q])) << lognf;
+    const int col0 = (item - rg.qbeg) << lognf;
     const cpx<T>* chirp = static_cast<const cpx<T>*>(B.chirp);
     const cpx<T>* bhat = static_cast<const cpx<T>*>(B.bhat);
     {
@@ -189,13 +217,14 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_fwd_kernel(const BatchP
   cpx<T>* tl = th + kTwHi;
   int curM = 0;
   const int items = item_count(it);
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
+  ItemRange rg(it, items);
+  for (int item = rg.begin; item < rg.end; ++item) {
+    const int q = rg.problem(it, item);
     const BatchProb& B = P[it.list[q]];
     const int logM1 = B.logM1, logM2 = B.logM2;
     const int logTX = 12 - logM2, TX = 1 << logTX;
     const int bpc = (1 << logM1) >> logTX;
-    const int local = item - __ldcg(&it.start[q]);
+    const int local = item - rg.qbeg;
     const int lc = local / bpc;
     const int col = it.live ? live_col(B, lc) : lc;
     const int t1_0 = (local - lc * bpc) << logTX;
@@ -255,13 +284,14 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_row_mid_kernel(const BatchP
   cpx<T>* tl = th + kTwHi;
   int curM = 0;
   const int items = item_count(it);
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
+  ItemRange rg(it, items);
+  for (int item = rg.begin; item < rg.end; ++item) {
+    const int q = rg.problem(it, item);
     const BatchProb& B = P[it.list[q]];
     const int logM1 = B.logM1, logM2 = B.logM2, M1 = 1 << logM1;
     const int logRY = 12 - logM1;
     const int bpc = (1 << logM2) >> logRY;
-    const int local = item - __ldcg(&it.start[q]);
+    const int local = item - rg.qbeg;
     const int lc = local / bpc;
     const int col = it.live ? live_col(B, lc) : lc;
     const int k2_0 = (local - lc * bpc) << logRY;
@@ -327,13 +357,14 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_inv_kernel(const BatchP
   build_stage_twiddles(stw, tw4096, 12, it.slog);
   const int stride = stage_stride(it.slog);
   const int items = item_count(it);
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
+  ItemRange rg(it, items);
+  for (int item = rg.begin; item < rg.end; ++item) {
+    const int q = rg.problem(it, item);
     const BatchProb& B = P[it.list[q]];
     const int logM1 = B.logM1, logM2 = B.logM2;
     const int logTX = 12 - logM2, TX = 1 << logTX;
     const int bpc = (1 << logM1) >> logTX;
-    const int local = item - __ldcg(&it.start[q]);
+    const int local = item - rg.qbeg;
     const int lc = local / bpc;
     const int col = it.live ? live_col(B, lc) : lc;
     const int t1_0 = (local - lc * bpc) << logTX;
@@ -492,8 +523,9 @@ __global__ void __launch_bounds__(256) brotate_kernel(const BatchProb* __restric
   extern __shared__ __align__(16) unsigned char rot_raw[];
   T (*tm)[KMAX * KMAX] = reinterpret_cast<T (*)[KMAX * KMAX]>(rot_raw);  // [2][KMAX * KMAX]
   const int items = item_count(it);
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int q = it.live ? find_live_item(it, item) : find_item(it.start, it.n, item);
+  ItemRange rg(it, items);
+  for (int item = rg.begin; item < rg.end; ++item) {
+    const int q = rg.problem(it, item);
     const BatchProb& B = P[it.list[q]];
     const int k = B.st->k, R = B.st->rank;
     __syncthreads();  // the previous item's rows read tm
@@ -504,7 +536,7 @@ __global__ void __launch_bounds__(256) brotate_kernel(const BatchProb* __restric
       tm[1][l + qq * KMAX] = static_cast<const T*>(B.Tr)[l + (size_t)qq * KMAX];
     }
     __syncthreads();
-    const int row = ((item - it.start[q]) << 8) + threadIdx.x;
+    const int row = ((item - rg.qbeg) << 8) + threadIdx.x;
     if (row >= B.m) continue;
     for (int side = 0; side < 2; ++side) {
       const T* X = static_cast<const T*>(side ? B.R : B.C) + row;
@@ -543,13 +575,30 @@ template cudaError_t launch_batch_rotate<float>(const BatchProb*, const BatchIte
 template cudaError_t launch_batch_rotate<double>(const BatchProb*, const BatchItems&, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Batched cross.
+// Batched cross.  Every thread of the cluster holds the state of the cross
+// (step, pivots, norm estimate, stop counters) in registers and takes every
+// decision itself from reductions whose results are identical in every warp
+// and every CTA, so a half-step needs one CTA barrier (and, in a cluster,
+// one cluster barrier) and no broadcast of decisions:
+//   1. residual entries of the owned indices (F = Uh or Vh, X = C or R);
+//   2. warp partials -- argmax (lowest index on ties), sum of squares, dot
+//      products with the columns of X, and the pivot data of the warp's own
+//      candidate (its rows of F and X and its symbol) -- into a slot per warp;
+//   3. CTA barrier; every warp combines the slots in warp order;
+//   4. cluster: warp 0 pushes the CTA result into a slot per CTA in every
+//      CTA's inbox (distributed shared memory); cluster barrier; every warp
+//      combines the inbox in rank order.
+// Slots and inboxes alternate between two buffers, so a buffer is rewritten
+// only after a barrier that every reader of its previous contents has passed.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int BX_NT = 512;            // threads per CTA
 constexpr int BX_NW = BX_NT / 32;
-constexpr int BX_CAND = 2 * KMAX + 3; // candidate pivot data: F row, X row (KMAX + 1), a, b
+constexpr int BX_CAND = 2 * KMAX + 3; // pivot data: a, b, F row (<= KMAX), X row (<= KMAX)
+// words of a slot: header, dot products, pivot data
+constexpr int BX_ABS = 0, BX_VAL = 1, BX_SSQ = 2, BX_IDX = 3, BX_DOTS = 4, BX_CND = BX_DOTS + KMAX;
+constexpr int BX_WORDS = BX_CND + BX_CAND;
 
 __device__ __forceinline__ unsigned long long bx_splitmix64_at(unsigned long long state, unsigned long long t) {
   unsigned long long z = state + t * 0x9E3779B97F4A7C15ULL;
@@ -570,14 +619,16 @@ __device__ __forceinline__ T bx_warp_sum(T v) {
   return v;
 }
 
+// argmax over the warp carrying the value and a source tag
 template <typename T>
-__device__ __forceinline__ void bx_warp_argmax(T& a, int& i, T& v) {
+__device__ __forceinline__ void bx_warp_argmax(T& a, int& i, T& v, int& src) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const T oa = __shfl_xor_sync(0xffffffffu, a, o);
     const int oi = __shfl_xor_sync(0xffffffffu, i, o);
     const T ov = __shfl_xor_sync(0xffffffffu, v, o);
-    if (bx_better(oa, oi, a, i)) { a = oa; i = oi; v = ov; }
+    const int os = __shfl_xor_sync(0xffffffffu, src, o);
+    if (bx_better(oa, oi, a, i)) { a = oa; i = oi; v = ov; src = os; }
   }
 }
 
@@ -585,8 +636,8 @@ template <typename T> __device__ __forceinline__ T bx_ratio(T a, T b) { return a
 template <> __device__ __forceinline__ float bx_ratio<float>(float a, float b) { return __fdividef(a, b); }
 
 // Sum over the warp of a[i], i < 16, for every i at once (recursive halving);
-// afterwards lane L holds the sum for index L mod 16.  The addition pattern is
-// fixed, so every CTA gets the same bits.
+// afterwards lane L holds the sum for index L mod 16.  Fixed pattern: every
+// warp and CTA gets the same bits.
 template <typename T>
 __device__ __forceinline__ T bx_transpose_sum16(T (&a)[16], int lane) {
 #pragma unroll
@@ -602,160 +653,108 @@ __device__ __forceinline__ T bx_transpose_sum16(T (&a)[16], int lane) {
   return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 16);
 }
 
-// Message of one CTA in a cluster reduction (values of type T): header
-// (abs, val, ssq, idx), dot products, candidate pivot data.
-template <typename T>
-struct BxMsg {
-  static constexpr int ABS = 0, VAL = 1, SSQ = 2, IDX = 3, DOTS = 4, CAND = DOTS + KMAX;
-  static constexpr int WORDS = CAND + BX_CAND;
-};
-
-template <typename T>
-struct BxShared {
-  T wabs[BX_NW], wval[BX_NW], wsum[BX_NW];
-  int widx[BX_NW];
-  T wdots[KMAX][BX_NW];
-  T wcand[BX_NW][BX_CAND];          // per warp: its candidate's F row, X row, a, b
-  T d[KMAX + 1];                    // pivot values
-  T dots[KMAX];                     // reduced dot products of the last reduction
-  T gr[KMAX];                       // R_l . r of the current step
-  T vec[KMAX];                      // pivot row of F for the next half-step
-  T cd[KMAX + 1];                   // pivot row of X times d for the next half-step
-  T craw[KMAX + 1];                 // pivot row of X
-  T piv_a, piv_b;
-  double probe[32];
-  int probe_row[32];
-  T val, sumsq, norm2, rsq, delta, pfloor;
-  int idx, win, flag, small;
-};
-
-// Problem-level constants of one CTA.  The CTA's slices (local index li =
-// j - row0 < SP) of the symbol, of Uh and Vh (if uv) and of the first KS
-// skeleton columns live in dynamic shared memory, column-major with leading
-// dimension SP; the rest is read from global memory (L2).
+// Problem-level constants of one CTA: owned indices j = row0 + tid + s NT.
 template <typename T>
 struct BxProb {
-  int m, r, ld, kcap, row0, row1;
+  int m, r, ld, kcap, row0, row1, cs, rank;
   const T* Uh;
   const T* Vh;
   T* C;
   T* R;
   const T* a;
   const T* b;
-  int SP, KS, uv;
-  const T* as;   // symbol slices
-  const T* bs;
-  const T* Us;   // Uh, Vh slices (uv)
-  const T* Vs;
-  T* Cs;         // skeleton columns < KS
-  T* Rs;
-  T* inbox;      // [2][cs][BxMsg::WORDS] cluster partials (dynamic shared memory)
+  T* slots;   // [2][NW][BX_WORDS]
+  T* inbox;   // [2][cs][BX_WORDS]
 };
 
-// A tall factor as seen by the CTA: global copy, shared copy of columns < ns.
+// Result of a reduction, identical in every thread of the cluster.
 template <typename T>
-struct BxSrc {
-  const T* g;
-  const T* s;
-  int ns;
+struct BxRed {
+  int idx;          // winning index (-1: no candidate)
+  T val, ssq;
+  T dlo, dhi;       // dot products l = lane and l = lane + 32 (this lane's)
+  const T* cand;    // pivot data of the winner: a, b, F row, X row
 };
-template <typename T>
-__device__ __forceinline__ T bx_at(const BxProb<T>& p, const BxSrc<T>& S, int l, int li) {
-  return l < S.ns ? S.s[(size_t)l * p.SP + li] : __ldcg(&S.g[p.row0 + li + (size_t)l * p.ld]);
-}
 
-// out[s] = (vec . F[j]) / (pa b_j + pb a_j) - sum_{l<k} cd[l] X[j, l] for the
-// owned indices j = row0 + tid + s NT (0 elsewhere).
+// Pivot data of the next half-step: cand (a, b, F row, X row of kx entries)
+// and, if ext, one more X entry xv (the column the step just built).
+template <typename T>
+struct BxPivot {
+  const T* cand;
+  int kx;
+  int ext;
+  T xv;
+};
+
+// out[s] = (vec . F[j]) / (pa b_j + pb a_j) - sum_{l<k} craw[l] d[l] X[j, l]
+// for the owned indices (0 elsewhere); vec, craw, pa, pb from the pivot data.
 template <typename T, int RPT>
-__device__ __forceinline__ void bx_eval(const BxProb<T>& p, const BxSrc<T>& F, const BxSrc<T>& X, int k,
-                                        const BxShared<T>& sh, T (&out)[RPT]) {
-  const int S = p.row1 - p.row0;
-  const int tid = threadIdx.x;
+__device__ __forceinline__ void bx_eval(const BxProb<T>& p, const T* __restrict__ F, const T* __restrict__ X, int k,
+                                        const BxPivot<T>& pv, const T* d, T (&out)[RPT]) {
+  const int base = p.row0 + threadIdx.x;
+  const T* vec = pv.cand + 2;
 #pragma unroll
   for (int s = 0; s < RPT; ++s) out[s] = T(0);
-  // F . vec: shared columns, then global ones (uniform loop bounds)
-  const int nF = F.ns < p.r ? F.ns : p.r;
-#pragma unroll 4
-  for (int al = 0; al < nF; ++al) {
-    const T w = sh.vec[al];
-    const T* Fc = F.s + (size_t)al * p.SP + tid;
+#pragma unroll 8
+  for (int al = 0; al < p.r; ++al) {
+    const T w = vec[al];
+    const T* Fc = F + (size_t)al * p.ld + base;
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if (tid + s * BX_NT < S) out[s] += w * Fc[s * BX_NT];
+      if (base + s * BX_NT < p.row1) out[s] += w * __ldg(&Fc[s * BX_NT]);
   }
-#pragma unroll 4
-  for (int al = nF; al < p.r; ++al) {
-    const T w = sh.vec[al];
-    const T* Fc = F.g + (size_t)al * p.ld + p.row0 + tid;
-#pragma unroll
-    for (int s = 0; s < RPT; ++s)
-      if (tid + s * BX_NT < S) out[s] += w * Fc[s * BX_NT];
-  }
-  const T pa = sh.piv_a, pb = sh.piv_b;
+  const T pa = pv.cand[0], pb = pv.cand[1];
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    const int li = tid + s * BX_NT;
-    out[s] = li < S ? bx_ratio<T>(out[s], pa * p.bs[li] + pb * p.as[li]) : T(0);
+    const int j = base + s * BX_NT;
+    out[s] = j < p.row1 ? bx_ratio<T>(out[s], pa * __ldg(&p.b[j]) + pb * __ldg(&p.a[j])) : T(0);
   }
-  const int nX = X.ns < k ? X.ns : k;
-#pragma unroll 4
-  for (int l = 0; l < nX; ++l) {
-    const T c = sh.cd[l];
-    const T* Xc = X.s + (size_t)l * p.SP + tid;
+  const T* craw = pv.cand + 2 + p.r;
+#pragma unroll 8
+  for (int l = 0; l < k; ++l) {
+    const T c = (l < pv.kx ? craw[l] : pv.xv) * d[l];
+    const T* Xc = X + (size_t)l * p.ld + base;
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if (tid + s * BX_NT < S) out[s] -= c * Xc[s * BX_NT];
-  }
-#pragma unroll 4
-  for (int l = nX; l < k; ++l) {
-    const T c = sh.cd[l];
-    const T* Xc = X.g + (size_t)l * p.ld + p.row0 + tid;
-#pragma unroll
-    for (int s = 0; s < RPT; ++s)
-      if (tid + s * BX_NT < S) out[s] -= c * __ldcg(&Xc[s * BX_NT]);
+      if (base + s * BX_NT < p.row1) out[s] -= c * Xc[s * BX_NT];
   }
 }
 
 // Start score ||Uh[j]||^2 / Lambda[j, 0]^2 of the owned indices.
 template <typename T, int RPT>
 __device__ __forceinline__ void bx_scores(const BxProb<T>& p, T a0, T b0, T (&out)[RPT]) {
-  const int S = p.row1 - p.row0;
-  const BxSrc<T> U{p.Uh, p.Us, p.uv ? p.r : 0};
+  const int base = p.row0 + threadIdx.x;
 #pragma unroll
   for (int s = 0; s < RPT; ++s) out[s] = T(0);
-#pragma unroll 4
+#pragma unroll 8
   for (int al = 0; al < p.r; ++al) {
+    const T* Fc = p.Uh + (size_t)al * p.ld + base;
 #pragma unroll
-    for (int s = 0; s < RPT; ++s) {
-      const int li = threadIdx.x + s * BX_NT;
-      if (li < S) { const T u = bx_at(p, U, al, li); out[s] += u * u; }
-    }
+    for (int s = 0; s < RPT; ++s)
+      if (base + s * BX_NT < p.row1) { const T u = __ldg(&Fc[s * BX_NT]); out[s] += u * u; }
   }
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
-    const int li = threadIdx.x + s * BX_NT;
-    if (li < S) {
-      const T lam0 = p.as[li] * b0 + p.bs[li] * a0;
+    const int j = base + s * BX_NT;
+    if (j < p.row1) {
+      const T lam0 = __ldg(&p.a[j]) * b0 + __ldg(&p.b[j]) * a0;
       out[s] = out[s] / (lam0 * lam0);
     }
   }
 }
 
-// Reduction over the cluster of a half-step's values v (see the file
+// Reduction of a half-step's values v over the cluster (see the section
 // comment).  cand: bit s set if owned index s may be chosen.  kd dot
-// products with the columns of Xd (kd = 0: none); the candidate pivot data
-// come from row idx of F (r values) and of X (kx values) and the symbol.
-// Results: sh.idx (-1 if no candidate), sh.val, sh.sumsq, sh.dots[0..kd),
-// sh.vec, sh.craw[0..kx), sh.piv_a, sh.piv_b.
+// products with the columns of Xd; pivot data from row idx of F (r values)
+// and of X (kx values).
 template <typename T, int RPT>
-__device__ __forceinline__ void bx_reduce(const BxProb<T>& p, const T (&v)[RPT], unsigned cand,
-                                          const BxSrc<T>& Xd, int kd, const BxSrc<T>& F, const BxSrc<T>& X,
-                                          int kx, int cs, int& par, BxShared<T>& sh) {
-  using Mg = BxMsg<T>;
+__device__ __forceinline__ BxRed<T> bx_reduce(const BxProb<T>& p, const T (&v)[RPT], unsigned cand,
+                                              const T* __restrict__ Xd, int kd, const T* __restrict__ F,
+                                              const T* __restrict__ X, int kx, int& par) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int base = p.row0 + tid;
   T babs = T(-1), bval = T(0), ssq = T(0);
-  int bidx = INT_MAX;
+  int bidx = INT_MAX, src = 0;
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
     ssq += v[s] * v[s];
@@ -765,181 +764,147 @@ __device__ __forceinline__ void bx_reduce(const BxProb<T>& p, const T (&v)[RPT],
       if (bx_better(av, j, babs, bidx)) { babs = av; bidx = j; bval = v[s]; }
     }
   }
-  bx_warp_argmax(babs, bidx, bval);
+  bx_warp_argmax(babs, bidx, bval, src);
   ssq = bx_warp_sum(ssq);
-  // the warp's candidate pivot data: loads issued now, stored after the dot
-  // products below, so that their latency overlaps the reductions
+  // the warp candidate's pivot data: loads issued now, stored after the dot
+  // products so that their latency overlaps them
   constexpr int CV = (BX_CAND + 31) / 32;
-  const int ncand = p.r + kx + 2;
+  const int ncand = 2 + p.r + kx;
   T cv[CV];
 #pragma unroll
   for (int u = 0; u < CV; ++u) {
     const int w = lane + 32 * u;
     cv[u] = T(0);
     if (bidx != INT_MAX && w < ncand) {
-      const int li = bidx - p.row0;  // the warp's candidate is one of the CTA's indices
-      if (w < p.r) cv[u] = bx_at(p, F, w, li);
-      else if (w < p.r + kx) cv[u] = bx_at(p, X, w - p.r, li);
-      else cv[u] = (w == p.r + kx) ? p.as[li] : p.bs[li];
+      if (w == 0) cv[u] = __ldg(&p.a[bidx]);
+      else if (w == 1) cv[u] = __ldg(&p.b[bidx]);
+      else if (w < 2 + p.r) cv[u] = __ldg(&F[bidx + (size_t)(w - 2) * p.ld]);
+      else cv[u] = X[bidx + (size_t)(w - 2 - p.r) * p.ld];
     }
   }
-  // dot products with the columns of Xd, 16 at a time
+  T* slot = p.slots + ((size_t)par * BX_NW + warp) * BX_WORDS;
   for (int l0 = 0; l0 < kd; l0 += 16) {
     T acc[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i] = T(0);
-    if (l0 + 16 <= Xd.ns || l0 >= Xd.ns) {  // the chunk is all shared or all global
-      const bool shd = l0 < Xd.ns;
+    for (int i = 0; i < 16; ++i) {
+      acc[i] = T(0);
+      const int l = l0 + i;
+      if (l < kd) {
+        const T* Xc = Xd + (size_t)l * p.ld + base;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int l = l0 + i;
-        if (l < kd) {
-          const T* Xc = shd ? Xd.s + (size_t)l * p.SP + tid : Xd.g + (size_t)l * p.ld + base;
-#pragma unroll
-          for (int s = 0; s < RPT; ++s)
-            if (base + s * BX_NT < p.row1) acc[i] += (shd ? Xc[s * BX_NT] : __ldcg(&Xc[s * BX_NT])) * v[s];
-        }
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int l = l0 + i;
-        if (l < kd) {
-#pragma unroll
-          for (int s = 0; s < RPT; ++s) {
-            const int li = tid + s * BX_NT;
-            if (base + s * BX_NT < p.row1) acc[i] += bx_at(p, Xd, l, li) * v[s];
-          }
-        }
+        for (int s = 0; s < RPT; ++s)
+          if (base + s * BX_NT < p.row1) acc[i] += Xc[s * BX_NT] * v[s];
       }
     }
     const T x = bx_transpose_sum16(acc, lane);
-    if (lane < 16 && l0 + lane < kd) sh.wdots[l0 + lane][warp] = x;
+    if (lane < 16 && l0 + lane < kd) slot[BX_DOTS + l0 + lane] = x;
   }
 #pragma unroll
   for (int u = 0; u < CV; ++u)
-    if (bidx != INT_MAX && lane + 32 * u < ncand) sh.wcand[warp][lane + 32 * u] = cv[u];
-  if (lane == 0) { sh.wabs[warp] = babs; sh.widx[warp] = bidx; sh.wval[warp] = bval; sh.wsum[warp] = ssq; }
+    if (lane + 32 * u < ncand) slot[BX_CND + lane + 32 * u] = cv[u];
+  if (lane == 0) {
+    slot[BX_ABS] = babs;
+    slot[BX_VAL] = bval;
+    slot[BX_SSQ] = ssq;
+    slot[BX_IDX] = (T)(bidx == INT_MAX ? -1 : bidx);
+  }
   __syncthreads();
-  // CTA reduction (warps in order) into the CTA's partial.
-  constexpr int WD = Mg::WORDS;
-  T* msg = p.inbox + ((size_t)par * cs + (cs > 1 ? (int)cg::this_cluster().block_rank() : 0)) * WD;
+  // every warp: combine the warp slots in warp order
+  const T* sl = p.slots + (size_t)par * BX_NW * BX_WORDS;
+  T a = T(-1), vv = T(0), ss = T(0);
+  int i = INT_MAX, sw = 0;
+  if (lane < BX_NW) {
+    const T* q = sl + (size_t)lane * BX_WORDS;
+    const int qi = (int)q[BX_IDX];
+    ss = q[BX_SSQ];
+    if (qi >= 0) { a = q[BX_ABS]; i = qi; vv = q[BX_VAL]; }
+    sw = lane;
+  }
+  bx_warp_argmax(a, i, vv, sw);
+  ss = bx_warp_sum(ss);
+  T dlo = T(0), dhi = T(0);
+  for (int w = 0; w < BX_NW; ++w) {
+    if (lane < kd) dlo += sl[(size_t)w * BX_WORDS + BX_DOTS + lane];
+    if (lane + 32 < kd) dhi += sl[(size_t)w * BX_WORDS + BX_DOTS + lane + 32];
+  }
+  BxRed<T> res;
+  if (p.cs == 1) {
+    res.idx = i == INT_MAX ? -1 : i;
+    res.val = vv;
+    res.ssq = ss;
+    res.dlo = dlo;
+    res.dhi = dhi;
+    res.cand = sl + (size_t)sw * BX_WORDS + BX_CND;
+    par ^= 1;
+    return res;
+  }
+  // cluster: warp 0 pushes this CTA's result into slot `rank` of every
+  // CTA's inbox, then every warp combines the inbox in rank order
+  cg::cluster_group cl = cg::this_cluster();
   if (warp == 0) {
-    T a = lane < BX_NW ? sh.wabs[lane] : T(-1);
-    int i = lane < BX_NW ? sh.widx[lane] : INT_MAX;
-    T vv = lane < BX_NW ? sh.wval[lane] : T(0);
-    T ss = lane < BX_NW ? sh.wsum[lane] : T(0);
-    int src = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T oa = __shfl_xor_sync(0xffffffffu, a, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, i, o);
-      const T ov = __shfl_xor_sync(0xffffffffu, vv, o);
-      const int os = __shfl_xor_sync(0xffffffffu, src, o);
-      if (bx_better(oa, oi, a, i)) { a = oa; i = oi; vv = ov; src = os; }
-    }
-    ss = bx_warp_sum(ss);
-    if (lane == 0) {
-      msg[Mg::ABS] = a;
-      msg[Mg::VAL] = vv;
-      msg[Mg::SSQ] = ss;
-      msg[Mg::IDX] = (T)(i == INT_MAX ? -1 : i);
-      sh.win = (i == INT_MAX) ? -1 : src;
-    }
-  }
-  for (int l = tid; l < kd; l += BX_NT) {
-    T x = T(0);
-#pragma unroll
-    for (int w = 0; w < BX_NW; ++w) x += sh.wdots[l][w];
-    msg[Mg::DOTS + l] = x;
-  }
-  __syncthreads();
-  {
-    const int wsrc = sh.win;
-    if (wsrc >= 0)
-      for (int w = tid; w < p.r + kx + 2; w += BX_NT) msg[Mg::CAND + w] = sh.wcand[wsrc][w];
-  }
-  if (cs > 1) {
-    // push the partial into every CTA's inbox (slot = this rank), then reduce
-    // the cs partials in rank order
-    cg::cluster_group cl = cg::this_cluster();
-    const int me = (int)cl.block_rank();
-    const int live = Mg::CAND + p.r + kx + 2;
-    __syncthreads();
-    for (int i = tid; i < cs * live; i += BX_NT) {
-      const int dst = i / live, w = i - dst * live;
-      if (dst != me && (w < Mg::DOTS + kd || w >= Mg::CAND)) *cl.map_shared_rank(&msg[w], dst) = msg[w];
-    }
-    cl.sync();
-    if (tid == 0) {
-      T a = T(-1), vv = T(0), ss = T(0);
-      int i = INT_MAX, src = -1;
-      for (int qq = 0; qq < cs; ++qq) {
-        const T* mq = p.inbox + ((size_t)par * cs + qq) * WD;
-        ss += mq[Mg::SSQ];
-        const int iq = (int)mq[Mg::IDX];
-        if (iq >= 0 && bx_better(mq[Mg::ABS], iq, a, i)) { a = mq[Mg::ABS]; i = iq; vv = mq[Mg::VAL]; src = qq; }
+    T* dst0 = p.inbox + ((size_t)par * p.cs + p.rank) * BX_WORDS;
+    const T* wc = sl + (size_t)sw * BX_WORDS + BX_CND;
+    for (int qd = 0; qd < p.cs; ++qd) {
+      T* dq = cl.map_shared_rank(dst0, qd);
+      if (lane == 0) {
+        dq[BX_ABS] = a;
+        dq[BX_VAL] = vv;
+        dq[BX_SSQ] = ss;
+        dq[BX_IDX] = (T)(i == INT_MAX ? -1 : i);
       }
-      sh.idx = src < 0 ? -1 : i;
-      sh.val = vv;
-      sh.sumsq = ss;
-      sh.win = src;
+      if (lane < kd) dq[BX_DOTS + lane] = dlo;
+      if (lane + 32 < kd) dq[BX_DOTS + lane + 32] = dhi;
+      if (i != INT_MAX)
+        for (int w = lane; w < ncand; w += 32) dq[BX_CND + w] = wc[w];
     }
-    for (int l = tid; l < kd; l += BX_NT) {
-      T x = T(0);
-      for (int qq = 0; qq < cs; ++qq) x += p.inbox[((size_t)par * cs + qq) * WD + Mg::DOTS + l];
-      sh.dots[l] = x;
-    }
-    __syncthreads();
-    const int src = sh.win;
-    if (src >= 0) {
-      const T* mq = p.inbox + ((size_t)par * cs + src) * WD;
-      for (int w = tid; w < p.r + kx + 2; w += BX_NT) {
-        const T x = mq[Mg::CAND + w];
-        if (w < p.r) sh.vec[w] = x;
-        else if (w < p.r + kx) sh.craw[w - p.r] = x;
-        else if (w == p.r + kx) sh.piv_a = x;
-        else sh.piv_b = x;
-      }
-    }
-  } else {
-    __syncthreads();
-    if (tid == 0) {
-      const int i = (int)msg[Mg::IDX];
-      sh.idx = i;
-      sh.val = msg[Mg::VAL];
-      sh.sumsq = msg[Mg::SSQ];
-    }
-    for (int l = tid; l < kd; l += BX_NT) sh.dots[l] = msg[Mg::DOTS + l];
-    if (sh.win >= 0)
-      for (int w = tid; w < p.r + kx + 2; w += BX_NT) {
-        const T x = msg[Mg::CAND + w];
-        if (w < p.r) sh.vec[w] = x;
-        else if (w < p.r + kx) sh.craw[w - p.r] = x;
-        else if (w == p.r + kx) sh.piv_a = x;
-        else sh.piv_b = x;
-      }
   }
-  __syncthreads();
+  cl.sync();
+  const T* ib = p.inbox + (size_t)par * p.cs * BX_WORDS;
+  a = T(-1); vv = T(0); ss = T(0); i = INT_MAX; sw = 0;
+  if (lane < p.cs) {
+    const T* q = ib + (size_t)lane * BX_WORDS;
+    const int qi = (int)q[BX_IDX];
+    ss = q[BX_SSQ];
+    if (qi >= 0) { a = q[BX_ABS]; i = qi; vv = q[BX_VAL]; }
+    sw = lane;
+  }
+  bx_warp_argmax(a, i, vv, sw);
+  ss = bx_warp_sum(ss);
+  dlo = T(0);
+  dhi = T(0);
+  for (int q = 0; q < p.cs; ++q) {
+    if (lane < kd) dlo += ib[(size_t)q * BX_WORDS + BX_DOTS + lane];
+    if (lane + 32 < kd) dhi += ib[(size_t)q * BX_WORDS + BX_DOTS + lane + 32];
+  }
+  res.idx = i == INT_MAX ? -1 : i;
+  res.val = vv;
+  res.ssq = ss;
+  res.dlo = dlo;
+  res.dhi = dhi;
+  res.cand = ib + (size_t)sw * BX_WORDS + BX_CND;
   par ^= 1;
+  return res;
 }
 
 template <typename T, int RPT>
 __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __restrict__ P,
                                                           const int* __restrict__ list, BatchCrossParams cp) {
-  __shared__ BxShared<T> sh;
+  extern __shared__ __align__(16) unsigned char bx_dyn[];
+  __shared__ T sd[KMAX + 1];  // pivot values
+  __shared__ double sprobe[32];
+  __shared__ int sprow[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int cs = 1, q = 0;
-  if (gridDim.x > 1 && cg::this_cluster().num_blocks() > 1) {
-    cs = (int)cg::this_cluster().num_blocks();
-    q = (int)cg::this_cluster().block_rank();
-  }
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks();
+  const int q = (int)cl.block_rank();
   const BatchProb& B = P[list[blockIdx.x / cs]];
   BxProb<T> p;
   p.m = B.m;
   p.r = B.r;
   p.ld = B.ldw;
   p.kcap = B.kcap;
+  p.cs = cs;
+  p.rank = q;
   {
     const int S = (p.m + cs - 1) / cs;
     p.row0 = min(p.m, q * S);
@@ -951,164 +916,111 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
   p.R = static_cast<T*>(B.R);
   p.a = static_cast<const T*>(B.sa);
   p.b = static_cast<const T*>(B.sb);
+  p.slots = reinterpret_cast<T*>(bx_dyn);
+  p.inbox = p.slots + 2 * BX_NW * BX_WORDS;
   SolveState* st = B.st;
-  // shared-memory copies of the CTA's slices: the symbol always, Uh and Vh if
-  // they fit in half of what is left, then as many skeleton columns as fit
-  // (the same choice in every CTA of the cluster)
-  extern __shared__ __align__(16) unsigned char bx_dyn[];
-  {
-    const int SP = BX_NT * RPT;
-    const long long w = (long long)sizeof(T);
-    const long long inbox = 2LL * cs * BxMsg<T>::WORDS * w;
-    const long long budget = cp.smem_bytes;
-    const long long fixed = inbox + 2LL * SP * w;
-    const long long uvb = 2LL * SP * p.r * w;
-    p.uv = cp.cache && uvb <= (budget - fixed) / 2;
-    const long long left = budget - fixed - (p.uv ? uvb : 0);
-    long long KS = cp.cache ? left / (2LL * SP * w) : 0;
-    if (KS > p.kcap) KS = p.kcap;
-    if (KS < 0) KS = 0;
-    p.SP = SP;
-    p.KS = (int)KS;
-    T* q0 = reinterpret_cast<T*>(bx_dyn);
-    p.inbox = q0; q0 += 2 * cs * BxMsg<T>::WORDS;
-    T* as = q0; q0 += SP;
-    T* bs = q0; q0 += SP;
-    T* Us = q0; q0 += p.uv ? (size_t)SP * p.r : 0;
-    T* Vs = q0; q0 += p.uv ? (size_t)SP * p.r : 0;
-    p.Cs = q0; q0 += (size_t)SP * KS;
-    p.Rs = q0;
-    p.as = as; p.bs = bs; p.Us = Us; p.Vs = Vs;
-    const int S = p.row1 - p.row0;
-    for (int li = tid; li < S; li += BX_NT) {
-      as[li] = p.a[p.row0 + li];
-      bs[li] = p.b[p.row0 + li];
-    }
-    if (p.uv)
-      for (int al = 0; al < p.r; ++al)
-        for (int li = tid; li < S; li += BX_NT) {
-          Us[(size_t)al * SP + li] = p.Uh[p.row0 + li + (size_t)al * p.ld];
-          Vs[(size_t)al * SP + li] = p.Vh[p.row0 + li + (size_t)al * p.ld];
-        }
-  }
-  __syncthreads();
-  const BxSrc<T> srcU{p.Uh, p.Us, p.uv ? p.r : 0}, srcV{p.Vh, p.Vs, p.uv ? p.r : 0};
-  const BxSrc<T> srcC{p.C, p.Cs, p.KS}, srcR{p.R, p.Rs, p.KS};
   const T tol2 = (T)(cp.tol * cp.tol);
   const int base = p.row0 + tid;
-  unsigned own = 0;  // owned indices
+  unsigned own = 0;
 #pragma unroll
   for (int s = 0; s < RPT; ++s)
     if (base + s * BX_NT < p.row1) own |= 1u << s;
   unsigned used_r = 0, used_c = 0;
-  if (tid == 0) { sh.norm2 = T(0); sh.small = 0; sh.pfloor = T(0); }
-  if (cs > 1) cg::this_cluster().sync();  // every CTA runs before anyone pushes into its inbox
-  const T a0 = p.a[0], b0 = p.b[0];
-  int par = 0;
-  T v[RPT];
-  bx_scores<T, RPT>(p, a0, b0, v);
-  bx_reduce<T, RPT>(p, v, own, srcC, 0, srcU, srcC, 0, cs, par, sh);
-  int istar = sh.idx;
-  int k = 0, probe_rounds = 0, zero_rows = 0, converged = 0;
-  // index s of an owned index j (or -1)
-  auto slot = [&](int j) -> int {
+  auto slot = [&](int j) -> int {  // owned index slot of j, or -1
     const int o = j - base;
     return (j >= p.row0 && j < p.row1 && o >= 0 && o % BX_NT == 0) ? o / BX_NT : -1;
   };
+  if (cs > 1) cl.sync();  // every CTA runs before anyone pushes into its inbox
+  const T a0 = __ldg(&p.a[0]), b0 = __ldg(&p.b[0]);
+  int par = 0;
+  T v[RPT];
+  bx_scores<T, RPT>(p, a0, b0, v);
+  BxRed<T> red = bx_reduce<T, RPT>(p, v, own, p.C, 0, p.Uh, p.C, 0, par);
+  int istar = red.idx;
+  BxPivot<T> pv{red.cand, 0, 0, T(0)};
+  int k = 0, probe_rounds = 0, zero_rows = 0, converged = 0, small = 0;
+  T norm2 = T(0), pfloor = T(0);
   while (k < p.kcap && istar >= 0) {
-    // ---------------- row half-step at istar (pivot data in sh.vec, sh.craw)
-    for (int l = tid; l < k; l += BX_NT) sh.cd[l] = sh.craw[l] * sh.d[l];
-    __syncthreads();
-    bx_eval<T, RPT>(p, srcV, srcR, k, sh, v);
+    // ---------------- row half-step at istar
+    bx_eval<T, RPT>(p, p.Vh, p.R, k, pv, sd, v);
     {
       const int s = slot(istar);
       if (s >= 0) used_r |= 1u << s;
     }
-    bx_reduce<T, RPT>(p, v, own & ~used_c, srcR, k, srcV, srcR, k, cs, par, sh);
-    const int jstar = sh.idx;
+    red = bx_reduce<T, RPT>(p, v, own & ~used_c, p.R, k, p.Vh, p.R, k, par);
+    const int jstar = red.idx;
     {
       const int s = jstar >= 0 ? slot(jstar) : -1;
       if (s >= 0) used_c |= 1u << s;
     }
-    if (tid == 0) {
-      const T dv = jstar >= 0 ? sh.val : T(0);
-      // a pivot far below the working precision's rounding noise (relative
-      // to the first pivot) is a zero row
-      sh.flag = !(fabs(dv) > sh.pfloor);
-      sh.delta = dv;
-      sh.rsq = sh.sumsq;
-    }
-    __syncthreads();
-    if (sh.flag) {
-      // the row is represented exactly: move to the best-scored unused row
+    const T delta = jstar >= 0 ? red.val : T(0);
+    // a pivot far below the working precision's rounding noise (relative to
+    // the first pivot) is a zero row
+    if (!(fabs(delta) > pfloor)) {
       ++zero_rows;
       bx_scores<T, RPT>(p, a0, b0, v);
-      bx_reduce<T, RPT>(p, v, own & ~used_r, srcC, 0, srcU, srcC, k, cs, par, sh);
-      if (zero_rows > cp.max_zero_rows || sh.idx < 0) { converged = 1; break; }
-      istar = sh.idx;
+      red = bx_reduce<T, RPT>(p, v, own & ~used_r, p.C, 0, p.Uh, p.C, k, par);
+      if (zero_rows > cp.max_zero_rows || red.idx < 0) { converged = 1; break; }
+      istar = red.idx;
+      pv = {red.cand, k, 0, T(0)};
       continue;
     }
+    const T rsq = red.ssq;
+    const T grlo = red.dlo / delta, grhi = red.dhi / delta;  // R_l . r
+    pv = {red.cand, k, 0, T(0)};
     // ---------------- column half-step at jstar
-    const T tdelta = sh.delta;
-    for (int l = tid; l < k; l += BX_NT) {
-      sh.gr[l] = sh.dots[l] / tdelta;
-      sh.cd[l] = sh.craw[l] * sh.d[l];
-    }
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if ((own >> s) & 1u) {
-        const T rv = v[s] / tdelta;
-        p.R[base + s * BX_NT + (size_t)k * p.ld] = rv;
-        if (k < p.KS) p.Rs[(size_t)k * p.SP + tid + s * BX_NT] = rv;
-      }
-    __syncthreads();
-    bx_eval<T, RPT>(p, srcU, srcC, k, sh, v);
+      if ((own >> s) & 1u) p.R[base + s * BX_NT + (size_t)k * p.ld] = v[s] / delta;
+    bx_eval<T, RPT>(p, p.Uh, p.C, k, pv, sd, v);
 #pragma unroll
     for (int s = 0; s < RPT; ++s) {
-      v[s] = v[s] / tdelta;
-      if ((own >> s) & 1u) {
-        p.C[base + s * BX_NT + (size_t)k * p.ld] = v[s];
-        if (k < p.KS) p.Cs[(size_t)k * p.SP + tid + s * BX_NT] = v[s];
+      v[s] = v[s] / delta;
+      if ((own >> s) & 1u) p.C[base + s * BX_NT + (size_t)k * p.ld] = v[s];
+    }
+    if (tid == 0) sd[k] = delta;  // read after the next barrier
+    red = bx_reduce<T, RPT>(p, v, own & ~used_r, p.C, k, p.Uh, p.C, k, par);
+    const int inext = red.idx;
+    // ---------------- bookkeeping (every thread, the same arithmetic)
+    {
+      const T csq = red.ssq;
+      const T rr = (rsq / delta) / delta;
+      T part = T(0);
+      if (lane < k) part += sd[lane] * red.dlo * grlo;
+      if (lane + 32 < k) part += sd[lane + 32] * red.dhi * grhi;
+      const T csum = bx_warp_sum(part);
+      const T term2 = csq * rsq;  // |d|^2 |c|^2 |r|^2
+      norm2 += T(2) * delta * csum + term2;
+      small = (term2 <= tol2 * norm2) ? small + 1 : 0;
+      if (k == 0) pfloor = fabs(delta) * (T)(sizeof(T) == 4 ? 1e-9 : 1e-20);
+      if (q == 0 && warp == 0) {
+        if (lane == 0) {
+          B.GC[k + (size_t)k * p.kcap] = (double)csq;
+          B.GR[k + (size_t)k * p.kcap] = (double)rr;
+          B.d[k] = (double)delta;
+          B.I[k] = istar;
+          B.J[k] = jstar;
+        }
+        for (int h = 0; h < 2; ++h) {
+          const int l = lane + 32 * h;
+          if (l < k) {
+            const double gc = (double)(h ? red.dhi : red.dlo), gr = (double)(h ? grhi : grlo);
+            B.GC[l + (size_t)k * p.kcap] = gc;
+            B.GC[k + (size_t)l * p.kcap] = gc;
+            B.GR[l + (size_t)k * p.kcap] = gr;
+            B.GR[k + (size_t)l * p.kcap] = gr;
+          }
+        }
       }
     }
-    if (tid == 0) sh.d[k] = tdelta;
-    // the next row step needs column k of C: the winner's own value
-    bx_reduce<T, RPT>(p, v, own & ~used_r, srcC, k, srcU, srcC, k, cs, par, sh);
-    const int inext = sh.idx;
-    // ---------------- bookkeeping (thread 0 of every CTA, same arithmetic)
-    if (tid == 0) {
-      if (inext >= 0) sh.craw[k] = sh.val;
-      const T delta = sh.delta;
-      const T csq = sh.sumsq;
-      const T rr = (sh.rsq / delta) / delta;
-      T csum = T(0);
-      for (int l = 0; l < k; ++l) csum += sh.d[l] * sh.dots[l] * sh.gr[l];
-      const T term2 = csq * sh.rsq;  // |d|^2 |c|^2 |r|^2
-      sh.norm2 += T(2) * delta * csum + term2;
-      sh.small = (term2 <= tol2 * sh.norm2) ? sh.small + 1 : 0;
-      if (k == 0) sh.pfloor = fabs(delta) * (T)(sizeof(T) == 4 ? 1e-9 : 1e-20);
-      if (q == 0) {
-        B.GC[k + (size_t)k * p.kcap] = (double)csq;
-        B.GR[k + (size_t)k * p.kcap] = (double)rr;
-        B.d[k] = (double)delta;
-        B.I[k] = istar;
-        B.J[k] = jstar;
-      }
-    }
-    if (q == 0)
-      for (int l = tid; l < k; l += BX_NT) {
-        const double gc = (double)sh.dots[l], gr = (double)sh.gr[l];
-        B.GC[l + (size_t)k * p.kcap] = gc;
-        B.GC[k + (size_t)l * p.kcap] = gc;
-        B.GR[l + (size_t)k * p.kcap] = gr;
-        B.GR[k + (size_t)l * p.kcap] = gr;
-      }
-    __syncthreads();
+    // the next row half-step needs column k of C: the winner's own value
+    pv = {red.cand, k, inext >= 0 ? 1 : 0, red.val};
     ++k;
-    if (sh.small >= 2) {
+    if (small >= 2) {
       if (probe_rounds >= cp.max_probe_rounds || cp.probes <= 0) { converged = 1; break; }
       // residual probes at splitmix64-drawn entries; probe pr on warp pr mod
       // (warps per CTA), the same arithmetic in every CTA
+      __syncthreads();  // sd[k - 1]
       const int Pn = cp.probes < 32 ? cp.probes : 32;
       for (int pr = warp; pr < Pn; pr += BX_NW) {
         const unsigned long long z = bx_splitmix64_at(cp.seed + (unsigned long long)probe_rounds,
@@ -1119,53 +1031,50 @@ __global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __res
         for (int al = lane; al < p.r; al += 32)
           num += (double)p.Uh[pi + (size_t)al * p.ld] * (double)p.Vh[pj + (size_t)al * p.ld];
         for (int l = lane; l < k; l += 32)
-          sk += (double)__ldcg(&p.C[pi + (size_t)l * p.ld]) * (double)sh.d[l] *
+          sk += (double)__ldcg(&p.C[pi + (size_t)l * p.ld]) * (double)sd[l] *
                 (double)__ldcg(&p.R[pj + (size_t)l * p.ld]);
         num = bx_warp_sum(num);
         sk = bx_warp_sum(sk);
         const double den = (double)p.a[pi] * (double)p.b[pj] + (double)p.b[pi] * (double)p.a[pj];
-        if (lane == 0) { sh.probe[pr] = fabs(num / den - sk); sh.probe_row[pr] = pi; }
+        if (lane == 0) { sprobe[pr] = fabs(num / den - sk); sprow[pr] = pi; }
       }
-      __syncthreads();
-      if (tid == 0) {
-        double worst = -1.0;
-        int wrow = -1;
-        for (int pr = 0; pr < Pn; ++pr)
-          if (sh.probe[pr] > worst) { worst = sh.probe[pr]; wrow = sh.probe_row[pr]; }
-        const double n2 = (double)sh.norm2;
-        sh.flag = worst <= cp.tol * sqrt(n2 > 0.0 ? n2 : 0.0) ? -1 : wrow;
-        if (sh.flag >= 0) sh.small = 0;
-      }
-      __syncthreads();
+      // the probes read skeleton entries other CTAs wrote in this step
+      if (cs > 1) cl.sync(); else __syncthreads();
+      double worst = -1.0;
+      int wrow = -1;
+      for (int pr = 0; pr < Pn; ++pr)
+        if (sprobe[pr] > worst) { worst = sprobe[pr]; wrow = sprow[pr]; }
+      const double n2 = (double)norm2;
       ++probe_rounds;
-      const int bad_row = sh.flag;
-      if (bad_row < 0) { converged = 1; break; }
+      if (worst <= cp.tol * sqrt(n2 > 0.0 ? n2 : 0.0)) { converged = 1; break; }
+      small = 0;
       // restart at the bad probe's row if unused, else at the best unused score
       bx_scores<T, RPT>(p, a0, b0, v);
       {
-        const int s = slot(bad_row);
+        const int s = slot(wrow);
         if (s >= 0 && !((used_r >> s) & 1u)) {
 #pragma unroll
           for (int ss = 0; ss < RPT; ++ss)
             if (ss == s) v[ss] = T(INFINITY);
         }
       }
-      bx_reduce<T, RPT>(p, v, own & ~used_r, srcC, 0, srcU, srcC, k, cs, par, sh);
-      istar = sh.idx;
+      red = bx_reduce<T, RPT>(p, v, own & ~used_r, p.C, 0, p.Uh, p.C, k, par);
+      istar = red.idx;
       if (istar < 0) { converged = 1; break; }
+      pv = {red.cand, k, 0, T(0)};
       continue;
     }
     istar = inext;
     if (istar < 0) { converged = 1; break; }
   }
   // no CTA may exit while another can still write into its shared memory
-  if (cs > 1) cg::this_cluster().sync();
+  if (cs > 1) cl.sync();
   if (q == 0 && tid == 0) {
     st->k = k;
     st->converged = converged;
     st->probe_rounds = probe_rounds;
     st->zero_rows = zero_rows;
-    st->norm2 = (double)sh.norm2;
+    st->norm2 = (double)norm2;
   }
 }
 
@@ -1173,31 +1082,17 @@ template <typename T, int RPT>
 cudaError_t launch_bcross_rpt(const BatchProb* probs, const int* list, int n, int cs,
                               const BatchCrossParams& cp, cudaStream_t st) {
   auto kern = bcross_kernel<T, RPT>;
-  // dynamic shared memory: what the SM has left beside the static part
-  static int dyn = 0;
+  const size_t smax = (size_t)(2 * BX_NW + 2 * 16) * BX_WORDS * sizeof(T);
   static cudaError_t attr = [&] {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
-    if (e == cudaSuccess) {
-      dyn = optin - (int)fa.sharedSizeBytes - 1024;
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
   }();
   if (attr != cudaSuccess) return attr;
-  BatchCrossParams c2 = cp;
-  c2.smem_bytes = dyn;
-  // without the factor cache only the inbox and the symbol slices are needed
-  const size_t need = c2.cache ? (size_t)dyn
-                               : ((size_t)2 * cs * BxMsg<T>::WORDS + 2 * (size_t)BX_NT * RPT) * sizeof(T);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * cs), 1, 1);
   cfg.blockDim = dim3(BX_NT, 1, 1);
-  cfg.dynamicSmemBytes = need;
+  cfg.dynamicSmemBytes = (size_t)(2 * BX_NW + 2 * cs) * BX_WORDS * sizeof(T);
   cfg.stream = st;
   cudaLaunchAttribute attr_[1];
   attr_[0].id = cudaLaunchAttributeClusterDimension;
@@ -1206,7 +1101,7 @@ cudaError_t launch_bcross_rpt(const BatchProb* probs, const int* list, int n, in
   attr_[0].val.clusterDim.z = 1;
   cfg.attrs = attr_;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, probs, list, c2);
+  return cudaLaunchKernelEx(&cfg, kern, probs, list, cp);
 }
 
 }  // namespace

@@ -262,8 +262,6 @@ struct BatchCrossParams {
   unsigned long long seed;
   int max_probe_rounds;
   int max_zero_rows;
-  int smem_bytes;  // dynamic shared memory of the launch (set by the launcher)
-  int cache = 0;   // 1: keep Uh, Vh and the first skeleton columns in shared memory
 };
 
 // Batched cross: problems list[0..n) (LPT order), each on a cluster of cs

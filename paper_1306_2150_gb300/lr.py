@@ -36,7 +36,7 @@ EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
            "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full",
-           "lr_stokes_uzawa", "lr_poisson2d_expsum", "lr_poisson3d_tucker")
+           "lr_stokes_uzawa", "lr_poisson2d_expsum", "lr_poisson3d_tucker", "lr_set_workspace_limit")
 
 
 class LrMat(ctypes.Structure):
@@ -101,6 +101,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_create.restype = c_int
     lib.lr_set_stream.argtypes = [c_void_p, c_void_p]
     lib.lr_set_stream.restype = c_int
+    lib.lr_set_workspace_limit.argtypes = [c_void_p, ctypes.c_size_t]
+    lib.lr_set_workspace_limit.restype = c_int
     lib.lr_destroy.argtypes = [c_void_p]
     lib.lr_destroy.restype = c_int
     lib.lr_last_error.argtypes = [c_void_p]
@@ -300,6 +302,13 @@ def lr_poisson2d(h: Handle, U, V, eps: float = 1e-6, prec="mixed", op="5pt", rma
     return SolveResult(Uo[:, :R], s[:R], Vo[:, :R], info, st, pi, pj)
 
 
+def lr_set_workspace_limit(h: Handle, nbytes: int) -> None:
+    """Cap the handle's device workspace (0: no cap); larger needs give LR_ENOMEM."""
+    st = load().lr_set_workspace_limit(h.ptr, int(nbytes))
+    if st != LR_OK:
+        raise LrError(st, "lr_set_workspace_limit failed")
+
+
 def lr_get_info(h: Handle, cap: int = 64):
     info = LrInfo()
     pi = (ctypes.c_int * cap)()
@@ -472,10 +481,11 @@ class StokesResult:
 
 def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 200, eps: float = 1e-7,
                     prec="mixed", rmax_out: int = 64, check: bool = True, gmres: bool = False,
-                    p0=None) -> StokesResult:
+                    p0=None, g=None) -> StokesResult:
     """Low-rank Uzawa solve of the 2D Stokes problem on n x n cells; ``f`` is
     [(U1, V1), (U2, V2)], the body-force components at the (n-1)^2 interior
-    vertices in factored form (device float64)."""
+    vertices in factored form (device float64); ``g`` (optional) the
+    divergence right-hand side (Ug, Vg) on the n x n cell centres."""
     import torch
     m = n - 1
     c_f = (LrMat * 2)()
@@ -506,10 +516,20 @@ def lr_stokes_uzawa(h: Handle, n: int, f, tol_div: float = 1e-6, maxit: int = 20
         sp[:r0].copy_(s0)
     c_p = LrMat(n, n, r0, rmax_out, _ld(Up), Up.data_ptr(), sp.data_ptr(), Vp.data_ptr())
     o = _options(eps, prec, "semi", 64, 1.0, 16, 0, LR_FLAG_GMRES if gmres else 0, 0)
+    c_g = None
+    if g is not None:
+        Ug, Vg = as_colmajor(g[0]), as_colmajor(g[1])
+        if Ug.stride(1) != Vg.stride(1):
+            V2 = colmajor_empty(Vg.shape[0], Vg.shape[1], Vg.device)
+            V2.copy_(Vg)
+            Vg = V2
+        keep += [Ug, Vg]
+        c_g = LrMat(n, n, Ug.shape[1], Ug.shape[1], _ld(Ug), Ug.data_ptr(), None, Vg.data_ptr())
     iters = ctypes.c_int(0)
     resid = ctypes.c_double(0.0)
     hist = (ctypes.c_double * (int(maxit) + 1))()
-    st = load().lr_stokes_uzawa(h.ptr, 2, n, c_f, None, c_u, ctypes.byref(c_p), float(tol_div), int(maxit),
+    st = load().lr_stokes_uzawa(h.ptr, 2, n, c_f, ctypes.byref(c_g) if c_g is not None else None, c_u,
+                                ctypes.byref(c_p), float(tol_div), int(maxit),
                                 ctypes.byref(o), ctypes.byref(iters), ctypes.byref(resid), hist)
     if check and st not in (LR_OK, LR_ENOCONV):
         raise LrError(st, h.last_error())

@@ -264,6 +264,31 @@ def test_async_mode_then_info(lr, h):
     assert err <= 1e-8
 
 
+def test_workspace_limit_gives_enomem_and_handle_recovers(lr):
+    # allocation failure on the host side: a workspace request above the
+    # handle's cap returns LR_ENOMEM before any launch; lifting the cap, the
+    # same handle solves the problem
+    m = 16384
+    U, V = inputs.smooth_sum(m, 1e-6)
+    Ut, Vt = cuda(U), cuda(V)
+    with lr.Handle() as h2:
+        lr.lr_set_workspace_limit(h2, 1 << 20)
+        res = lr.lr_poisson2d(h2, Ut, Vt, eps=1e-6, prec="mixed", check=False)
+        assert res.status == lr.LR_ENOMEM
+        assert "limit" in h2.last_error()
+        b = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V))] * 2)
+        assert lr.lr_poisson2d_batched(h2, b, eps=1e-6, check=False) == lr.LR_ENOMEM
+        x = np.arange(1, 1024) / 1024
+        fdev = [(cuda(np.sin(np.pi * x)[:, None]), cuda(np.cos(np.pi * x)[:, None]))] * 2
+        assert lr.lr_stokes_uzawa(h2, 1024, fdev, check=False).status == lr.LR_ENOMEM
+        lr.lr_set_workspace_limit(h2, 0)
+        res = lr.lr_poisson2d(h2, Ut, Vt, eps=1e-6, prec="mixed")
+        torch.cuda.synchronize()
+        assert res.status == lr.LR_OK
+        rows = np.unique(np.linspace(0, m - 1, 64).astype(int))
+        assert O.rel_error_freq(npy(res.U), npy(res.s), npy(res.V), U, V, "5pt", rows=rows) <= 1e-5
+
+
 def test_invalid_arguments(lr, h):
     import ctypes
     U = lr.colmajor_empty(100, 2)

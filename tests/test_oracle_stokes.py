@@ -45,6 +45,35 @@ def test_uzawa_matches_the_assembled_saddle_system(n):
     assert np.allclose(res.p, p, atol=1e-9 * max(1.0, np.abs(p).max()))
 
 
+def compatible_g(n, seed):
+    """A low-rank divergence right-hand side orthogonal to the pressure's
+    kernel modes (the part B^T u can meet)."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(np.stack([np.ones(n), (-1.0) ** np.arange(n)], axis=1))
+    gu, gv = rng.standard_normal((n, 2)), rng.standard_normal((n, 2))
+    gu -= Q @ (Q.T @ gu)
+    return gu @ gv.T
+
+
+@pytest.mark.parametrize("n", [6, 8, 16])
+def test_uzawa_with_divergence_rhs_matches_the_assembled_saddle_system(n):
+    # B^T u = g (Eq. flr:stprob with a second right-hand side; Schur
+    # right-hand side B^T A^-1 f - g, reading G5), against the dense saddle
+    # solve; the velocity's divergence is g and the momentum equation holds
+    rng = np.random.default_rng(100 + n)
+    f1 = rng.standard_normal((n - 1, n - 1))
+    f2 = rng.standard_normal((n - 1, n - 1))
+    g = compatible_g(n, n)
+    res = S.uzawa_cg(f1, f2, n, tol=1e-13, g=g)
+    u, v, p = S.saddle_dense(f1, f2, n, g=g)
+    assert np.allclose(res.u, u, atol=1e-10) and np.allclose(res.v, v, atol=1e-10)
+    assert np.allclose(res.p, p, atol=1e-9 * max(1.0, np.abs(p).max()))
+    assert np.linalg.norm(S.bt(res.u, res.v, n) - g) <= 1e-10 * np.linalg.norm(g)
+    m1 = S.laplace(res.u, n) + S.bx(res.p, n) - f1
+    assert np.linalg.norm(m1) <= 1e-9 * np.linalg.norm(f1)
+    assert res.resid <= 1e-12
+
+
 def test_uzawa_solution_satisfies_momentum_and_divergence():
     n = 24
     (a1, b1), (a2, b2) = S.body_force(n)
