@@ -76,6 +76,9 @@ struct lr_handle_s {
   cudaEvent_t bdesc_ev = nullptr;
   std::map<std::string, char*> graph_desc;
   int cross_rows[2] = {4096, 4096};  // indices per CTA of the batched cross (float64, float32)
+  int dst_fused[2] = {0, 1};         // batched transforms of M > 4096: one pass per column (1) or
+                                     // the four-step passes through scratch (0); float64 keeps
+                                     // the four-step passes (FP64-bound either way, and faster)
   size_t ws_limit = 0;               // cap on the workspaces' total bytes (0: none)
 };
 
@@ -989,7 +992,7 @@ lr_status ensure_tw4096(lr_handle h, bool f32) {
 struct BatchLayout {
   std::vector<char> blob;  // [BatchProb x n][int lists]
   size_t probs_off = 0;
-  struct ListRef { size_t list, start; int n, items, slog; };
+  struct ListRef { size_t list, start; int n, items, slog, fused_logh; };
   ListRef fwd_small{}, fwd_col{}, fwd_row{}, inv_small{}, inv_col{}, inv_row{}, rot{};
   struct CrossGroup { size_t list; int n, cs, rows; };
   std::vector<CrossGroup> cross;
@@ -1000,6 +1003,7 @@ struct BatchLayout {
     b.n = r.n;
     b.items = r.items;
     b.slog = r.slog;
+    b.fused_logh = r.fused_logh;
     return b;
   }
 };
@@ -1073,7 +1077,7 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
     b.GC = w.GC; b.GR = w.GR; b.d = w.d; b.I = w.I; b.J = w.J;
     b.st = &states[i];
     const TablesT& tb = f32 ? pl.t32 : pl.t64;
-    b.chirp = tb.chirp; b.tw = tb.tw; b.bhat = tb.bhat;
+    b.chirp = tb.chirp; b.tw = tb.tw; b.bhat = tb.bhat; b.bres = tb.bhat_rs;
     b.sa = f32 ? (const void*)pl.sym_a32[o.op] : (const void*)pl.sym_a64[o.op];
     b.sb = f32 ? (const void*)pl.sym_b32[o.op] : (const void*)pl.sym_b64[o.op];
   }
@@ -1094,6 +1098,12 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
     ints.push_back(acc);
     ref.items = acc;
   };
+  // the one-pass transform runs one CTA per column: only batches with enough
+  // columns to fill the GPU take it
+  int fwd_cols = 0;
+  for (int i = 0; i < batch; ++i) fwd_cols += 2 * geo[i].r;
+  const int fused_lh =
+      h->dst_fused[pi] && fwd_cols >= h->num_sms / 2 ? (f32 ? kFusedLogH32 : kFusedLogH64) : 0;
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<int> ls, cs_, lf, cf, rf;
     int slog_s = 0, slog_c = 0, slog_r = 0;  // largest FFT stage each launch needs
@@ -1105,6 +1115,10 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
         ls.push_back(i);
         cs_.push_back((ncols + nf - 1) / nf);
         slog_s = std::max(slog_s, logM - 2);
+      } else if (fused_lh) {  // one pass per column (an item: 2^(LH - min(logM, LH)) columns)
+        const int nf = 1 << (fused_lh - std::min(logM, fused_lh));
+        lf.push_back(i);
+        cf.push_back((ncols + nf - 1) / nf);
       } else {
         const int logM1 = plans[i]->logM1, logM2 = plans[i]->logM2;
         lf.push_back(i);
@@ -1119,7 +1133,9 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
     BatchLayout::ListRef& rr_ = dir == 0 ? L.fwd_row : L.inv_row;
     add_list(ls, cs_, rs_);
     add_list(lf, cf, rc_);
-    add_list(lf, rf, rr_);
+    if (fused_lh) add_list({}, {}, rr_);
+    else add_list(lf, rf, rr_);
+    rc_.fused_logh = fused_lh;
     rs_.slog = slog_s;
     rc_.slog = slog_c;
     rr_.slog = slog_r;
@@ -1174,8 +1190,9 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
   cp.max_zero_rows = 16;
   const int nsm = h->num_sms;
   const void* tw = h->tw4096[pi];
-  const int launches = (L.fwd_small.items > 0) + 3 * (L.fwd_col.items > 0) + (int)L.cross.size() + 3 +
-                       (L.inv_small.items > 0) + 3 * (L.inv_col.items > 0);
+  const int col_launches = fused_lh ? 1 : 3;
+  const int launches = (L.fwd_small.items > 0) + col_launches * (L.fwd_col.items > 0) + (int)L.cross.size() + 3 +
+                       (L.inv_small.items > 0) + col_launches * (L.inv_col.items > 0);
   const bool timing = (o.flags & LR_FLAG_TIMING) != 0;
   if (timing && (s = ensure_events(h)) != LR_OK) return s;
   auto mark = [&](int i, cudaStream_t stm) -> cudaError_t {

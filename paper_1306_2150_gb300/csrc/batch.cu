@@ -36,6 +36,7 @@
 #include <climits>
 
 #include "fft_common.cuh"
+#include "fft_inplace.cuh"
 #include "lr_internal.h"
 
 namespace cg = cooperative_groups;
@@ -54,14 +55,35 @@ __device__ __forceinline__ int find_item(const int* __restrict__ start, int n, i
   return lo;
 }
 
+// The fields of a problem that column addressing reads, loaded once (a
+// kernel that addresses many columns of one problem keeps them in registers
+// instead of reading the problem record again for every column).
+struct ColGeom {
+  int r, ncap, rank, ld_in, ldw, ld_out;
+  const double* U;
+  const double* V;
+  double* Uo;
+  double* Vo;
+  void* Uh;
+  void* Vh;
+  const void* W;
+  ColGeom() = default;
+  __device__ __forceinline__ ColGeom(const BatchProb& B, bool with_rank) {
+    r = B.r; ncap = B.ncap; ld_in = B.ld_in; ldw = B.ldw; ld_out = B.ld_out;
+    U = B.U; V = B.V; Uo = B.Uo; Vo = B.Vo; Uh = B.Uh; Vh = B.Vh; W = B.W;
+    rank = with_rank ? B.st->rank : 0;
+  }
+};
+
 // Column addressing of a batched transform.  dir 0: column c < 2r of
 // [U V] -> [Uh Vh]; dir 1: column c < 2 ncap of W -> [Uo Vo], live while its
 // index within its factor is below the kept rank.
 template <typename T, int DIR>
 struct BCol {
-  const void* in;
-  void* out;
-  bool live;
+  const void* in = nullptr;
+  void* out = nullptr;
+  bool live = false;
+  BCol() = default;
   __device__ __forceinline__ BCol(const BatchProb& B, int col) {
     if (DIR == 0) {
       const int seg = col < B.r ? 0 : 1, cc = col - seg * B.r;
@@ -75,6 +97,19 @@ struct BCol {
       out = (seg ? B.Vo : B.Uo) + (size_t)cc * B.ld_out;
     }
   }
+  __device__ __forceinline__ BCol(const ColGeom& G, int col) {
+    if (DIR == 0) {
+      const int seg = col < G.r ? 0 : 1, cc = col - seg * G.r;
+      live = col < 2 * G.r;
+      in = (seg ? G.V : G.U) + (size_t)cc * G.ld_in;
+      out = static_cast<T*>(seg ? G.Vh : G.Uh) + (size_t)cc * G.ldw;
+    } else {
+      const int seg = col < G.ncap ? 0 : 1, cc = col - seg * G.ncap;
+      live = col < 2 * G.ncap && cc < G.rank;
+      in = static_cast<const T*>(G.W) + (size_t)col * G.ldw;
+      out = (seg ? G.Vo : G.Uo) + (size_t)cc * G.ld_out;
+    }
+  }
   __device__ __forceinline__ T load(int t) const {
     if (DIR == 0) return (T)static_cast<const double*>(in)[t];
     return static_cast<const T*>(in)[t];
@@ -83,6 +118,11 @@ struct BCol {
     if (DIR == 0) static_cast<T*>(out)[t] = v;
     else static_cast<double*>(out)[t] = (double)v;
   }
+  // out[t] as stored (read back by the thread that stored it)
+  __device__ __forceinline__ T loadout(int t) const {
+    if (DIR == 0) return static_cast<const T*>(out)[t];
+    return (T)static_cast<const double*>(out)[t];
+  }
 };
 
 // Column of the inverse transform for dense live index c (0 <= c < 2R:
@@ -90,6 +130,11 @@ struct BCol {
 __device__ __forceinline__ int live_col(const BatchProb& B, int c) {
   const int R = B.st->rank;
   return c < R ? c : (c < 2 * R ? B.ncap + (c - R) : -1);
+}
+
+__device__ __forceinline__ int live_col(const ColGeom& G, int c) {
+  const int R = G.rank;
+  return c < R ? c : (c < 2 * R ? G.ncap + (c - R) : -1);
 }
 
 // Items of a launch: fixed, or counted on the device (live columns).
@@ -139,7 +184,7 @@ constexpr int kBThreads = kBTile / EPT;
 
 // ---- M <= 4096: whole sequences in shared memory ---------------------------
 template <typename T, int DIR>
-__global__ void __launch_bounds__(kBThreads, 2) bdst_small_kernel(const BatchProb* __restrict__ P, BatchItems it,
+__global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bdst_small_kernel(const BatchProb* __restrict__ P, BatchItems it,
                                                                const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);  // padded tile (smem_ix<true>)
@@ -206,7 +251,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_small_kernel(const BatchPro
 // scratch of each column stored as [k2][t1] (see dst.cu).  Column passes:
 // a tile holds TX = 4096 / M2 consecutive t1 and all M2 values of t2 (k2).
 template <typename T, int DIR>
-__global__ void __launch_bounds__(kBThreads, 2) bdst_col_fwd_kernel(const BatchProb* __restrict__ P, BatchItems it,
+__global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bdst_col_fwd_kernel(const BatchProb* __restrict__ P, BatchItems it,
                                                                  const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -273,7 +318,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_fwd_kernel(const BatchP
 
 // Row pass: RY = 4096 / M1 rows k2 per tile, each of M1 contiguous elements.
 template <typename T, int DIR>
-__global__ void __launch_bounds__(kBThreads, 2) bdst_row_mid_kernel(const BatchProb* __restrict__ P, BatchItems it,
+__global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bdst_row_mid_kernel(const BatchProb* __restrict__ P, BatchItems it,
                                                                  const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -349,7 +394,7 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_row_mid_kernel(const BatchP
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(kBThreads, 2) bdst_col_inv_kernel(const BatchProb* __restrict__ P, BatchItems it,
+__global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bdst_col_inv_kernel(const BatchProb* __restrict__ P, BatchItems it,
                                                                  const cpx<T>* __restrict__ tw4096) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -397,6 +442,164 @@ __global__ void __launch_bounds__(kBThreads, 2) bdst_col_inv_kernel(const BatchP
   }
 }
 
+// ---- M > 4096, one pass per column: Bluestein's convolution of length M
+// split into R = M / H residue classes of the frequency index, H = min(M,
+// 2^LH), each a length-H FFT held whole in shared memory (fft_inplace.cuh).
+// With a_j = x_j chirp_j (j < m <= M / 2) and w_M = exp(-2 pi i / M):
+//   A[R k + t] = FFT_H( sum_q a_(j + qH) w_M^((j + qH) t) )[k]       (fold)
+//   z_j = sum_t w_M^(-j t) IFFT_H( A[R k + t] bhat[R k + t] )[j mod H]
+// (IFFT unnormalised), out_j = Im(chirp_j z_j) accumulated over t in the
+// output column itself.  The fold is the first forward stage's load, the
+// spectrum product sits between the last forward and the first inverse
+// stage in registers, and the last inverse stage writes the output: the
+// column is read R times (from L2) and no M-length scratch passes through
+// memory.  R = 1 for M <= 2^LH, where an item holds 2^LH / M columns.
+template <typename T> __host__ __device__ constexpr int fused_logh() { return sizeof(T) == 4 ? kFusedLogH32 : kFusedLogH64; }
+// 512 threads: two radix-16 butterflies per thread and stage in float32, one
+// in float64 (up to 128 registers per thread)
+template <typename T> __host__ __device__ constexpr int fused_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+
+template <typename T>
+__host__ __device__ constexpr size_t fused_smem_elems() {
+  return (size_t)(1 << fused_logh<T>()) + (1 << (fused_logh<T>() - 4)) + inplace_tab_elems(fused_logh<T>()) +
+         kTwHi + kTwLo;
+}
+
+template <typename T, int DIR, int NT>
+__device__ __forceinline__ void fused_last(cpx<T>* buf, int logH, const cpx<T>* spec) {
+  constexpr int N = 1 << fused_logh<T>();
+  const int rem = logH & 3;
+  if (rem == 2) inplace_last<T, 4, NT, N>(buf, logH, spec);
+  else if (rem == 1) inplace_last<T, 2, NT, N>(buf, logH, spec);
+  else inplace_last<T, 16, NT, N>(buf, logH, spec);
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(fused_threads<T>(), 1) bdst_fused_kernel(const BatchProb* __restrict__ P,
+                                                                          BatchItems it) {
+  constexpr int LH = fused_logh<T>(), HX = 1 << LH, NT = fused_threads<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);  // padded (smem_ix<true>)
+  cpx<T>* tab = buf + HX + (HX >> 4);                  // radix-16 stage twiddles
+  cpx<T>* th = tab + inplace_tab_elems(LH);            // w_M two-level tables
+  cpx<T>* tl = th + kTwHi;
+  __shared__ ColGeom sg[2];  // column geometry of the current item (by item parity)
+  int curM = 0;
+  const int items = item_count(it);
+  ItemRange rg(it, items);
+  for (int item = rg.begin; item < rg.end; ++item) {
+    const int q = rg.problem(it, item);
+    const BatchProb& B = P[it.list[q]];
+    const int logM = B.logM, M = 1 << logM;
+    const int logH = logM < LH ? logM : LH, H = 1 << logH;
+    const int R = M >> logH, lognf = LH - logH;
+    const int logS0 = logH - 4, s0 = 1 << logS0;  // span of the first stage
+    const int n16 = logH >> 2, rem = logH & 3;
+    const int col0 = (item - rg.qbeg) << lognf;
+    if (threadIdx.x == 0) sg[item & 1] = ColGeom(B, DIR == 1);  // read after the next barrier
+    const ColGeom& G = sg[item & 1];
+    if (logM != curM) {  // uniform across the CTA
+      __syncthreads();   // the previous item read the tables
+      const cpx<T>* tw = static_cast<const cpx<T>*>(B.tw);
+      load_twiddles2(th, tl, tw, logM);
+      build_inplace_tables(tab, tw, logM, logH);
+      curM = logM;
+    }
+    const cpx<T>* chirp = static_cast<const cpx<T>*>(B.chirp);
+    const cpx<T>* bres = static_cast<const cpx<T>*>(B.bres);
+    const int m = B.m;
+    for (int t = 0; t < R; ++t) {
+      __syncthreads();  // tables and G written; the previous residue read buf
+      // first forward stage, its elements folded from the input columns
+      for (int g = threadIdx.x; g < (HX >> 4); g += NT) {
+        const int f = g >> logS0, j = g & (s0 - 1);
+        const int lc = col0 + f;
+        const int cl = it.live ? live_col(G, lc) : lc;
+        const BCol<T, DIR> c(G, cl < 0 ? 2 * G.ncap : cl);
+        cpx<T> x[16], a[3], b[3];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = {T(0), T(0)};
+        if (c.live)
+          for (int e0 = 0; e0 < m; e0 += H) {  // uniform; once unless m > H
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int e = e0 + j + (u << logS0);
+              if (e < m) {
+                const T xv = c.load(e);
+                const cpx<T> w = chirp[e];
+                cpx<T> av = {xv * w.re, xv * w.im};
+                if (t > 0) av = cmul(av, twiddle2(th, tl, (t * e) & (M - 1)));
+                x[u] = cadd(x[u], av);
+              }
+            }
+          }
+        stage_twiddles(tab, s0, j, a, b);
+        dif16(x, a, b);
+        const int base = (f << logH) + j;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) buf[smem_ix<true>(base + (u << logS0))] = x[u];
+      }
+      const int nmid = rem ? n16 : n16 - 1;  // radix-16 stages before the last stage
+      for (int i = 1; i < nmid; ++i) {
+        __syncthreads();
+        inplace_stage16<T, false, NT>(buf, LH, logH - 4 * i - 4, tab + inplace_tab_offset(logH, i));
+      }
+      __syncthreads();
+      fused_last<T, DIR, NT>(buf, logH, bres + (size_t)t * H);
+      for (int i = nmid - 1; i >= 1; --i) {
+        __syncthreads();
+        inplace_stage16<T, true, NT>(buf, LH, logH - 4 * i - 4, tab + inplace_tab_offset(logH, i));
+      }
+      __syncthreads();
+      // last inverse stage, its elements written to the output columns
+      for (int g = threadIdx.x; g < (HX >> 4); g += NT) {
+        const int f = g >> logS0, j = g & (s0 - 1);
+        const int lc = col0 + f;
+        const int cl = it.live ? live_col(G, lc) : lc;
+        const BCol<T, DIR> c(G, cl < 0 ? 2 * G.ncap : cl);
+        const int base = (f << logH) + j;
+        cpx<T> x[16], a[3], b[3];
+        // the earlier residues' sums: loaded before the butterfly (float32;
+        // float64 has no registers to spare for them there)
+        constexpr bool early = sizeof(T) == 4;
+        T old[16];
+        if (early && t > 0) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int k = j + (u << logS0);
+            old[u] = c.live && k < m ? c.loadout(k) : T(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = buf[smem_ix<true>(base + (u << logS0))];
+        stage_twiddles(tab, s0, j, a, b);
+        dit16(x, a, b);
+        if (!c.live) continue;
+        for (int e0 = 0; e0 < m; e0 += H) {  // uniform; once unless m > H
+          if (t > 0 && (e0 > 0 || !early)) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int k = e0 + j + (u << logS0);
+              old[u] = k < m ? c.loadout(k) : T(0);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int k = e0 + j + (u << logS0);
+            if (k < m) {
+              cpx<T> z = x[u];
+              if (t > 0) z = cmulc(z, twiddle2(th, tl, (t * k) & (M - 1)));  // times w_M^(-k t)
+              const cpx<T> w = chirp[k];
+              const T val = w.re * z.im + w.im * z.re;  // Im(chirp z)
+              c.store(k, t > 0 ? old[u] + val : val);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename T, int DIR>
 cudaError_t launch_bdst_dir(const BatchProb* probs, const BatchItems& small, const BatchItems& col,
                             const BatchItems& row, const cpx<T>* tw, int num_sms, cudaStream_t st) {
@@ -425,6 +628,16 @@ cudaError_t launch_bdst_dir(const BatchProb* probs, const BatchItems& small, con
   // grid: enough CTAs for every item, at most 4 per SM (grid-stride beyond)
   const int cap = 4 * num_sms;
   if (small.items > 0) k0<<<small.items < cap ? small.items : cap, kBThreads, bytes(small), st>>>(probs, small, tw);
+  if (col.items > 0 && col.fused_logh) {
+    if (col.fused_logh != fused_logh<T>()) return cudaErrorInvalidValue;
+    auto kf = bdst_fused_kernel<T, DIR>;
+    const size_t fbytes = fused_smem_elems<T>() * sizeof(cpx<T>);
+    static cudaError_t fattr = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fbytes);
+    if (fattr != cudaSuccess) return fattr;
+    // one CTA per SM (the whole sequence in shared memory)
+    kf<<<col.items < num_sms ? col.items : num_sms, fused_threads<T>(), fbytes, st>>>(probs, col);
+    return cudaGetLastError();
+  }
   if (col.items > 0) {
     k1<<<col.items < cap ? col.items : cap, kBThreads, bytes(col), st>>>(probs, col, tw);
     k2<<<row.items < cap ? row.items : cap, kBThreads, bytes(row), st>>>(probs, row, tw);
@@ -449,6 +662,9 @@ __device__ void live_scan(const BatchProb* __restrict__ P, const BatchItems& it,
       const int cols = 2 * B.st->rank;
       if (kind == 0) {
         const int nf = 1 << (12 - B.logM);
+        cnt = (cols + nf - 1) / nf;
+      } else if (kind == 1 && it.fused_logh) {
+        const int nf = 1 << (it.fused_logh - min(B.logM, it.fused_logh));
         cnt = (cols + nf - 1) / nf;
       } else if (kind == 1) {
         cnt = cols * ((1 << B.logM1) >> (12 - B.logM2));
@@ -515,7 +731,8 @@ template cudaError_t launch_batch_dst<double>(const BatchProb*, int, const Batch
 // ---------------------------------------------------------------------------
 // Rotation W[:, q] = C Tc[:, q], W[:, ncap + q] = R Tr[:, q] (q < rank): the
 // last step of the rounding (Section 3), before the inverse transform.  One
-// thread per row, both factors; Tc and Tr staged in shared memory per item.
+// thread per row, both factors; Tc and Tr staged in shared memory once per
+// problem of the CTA's item range.
 // ---------------------------------------------------------------------------
 namespace {
 template <typename T>
@@ -524,18 +741,22 @@ __global__ void __launch_bounds__(256) brotate_kernel(const BatchProb* __restric
   T (*tm)[KMAX * KMAX] = reinterpret_cast<T (*)[KMAX * KMAX]>(rot_raw);  // [2][KMAX * KMAX]
   const int items = item_count(it);
   ItemRange rg(it, items);
+  int lastq = -1;
   for (int item = rg.begin; item < rg.end; ++item) {
     const int q = rg.problem(it, item);
     const BatchProb& B = P[it.list[q]];
     const int k = B.st->k, R = B.st->rank;
-    __syncthreads();  // the previous item's rows read tm
     if (R <= 0 || k <= 0) continue;  // uniform across the CTA
-    for (int idx = threadIdx.x; idx < k * R; idx += blockDim.x) {
-      const int l = idx % k, qq = idx / k;
-      tm[0][l + qq * KMAX] = static_cast<const T*>(B.Tc)[l + (size_t)qq * KMAX];
-      tm[1][l + qq * KMAX] = static_cast<const T*>(B.Tr)[l + (size_t)qq * KMAX];
+    if (q != lastq) {  // a new problem: stage its rotations
+      __syncthreads();  // the previous problem's rows read tm
+      for (int idx = threadIdx.x; idx < k * R; idx += blockDim.x) {
+        const int l = idx % k, qq = idx / k;
+        tm[0][l + qq * KMAX] = static_cast<const T*>(B.Tc)[l + (size_t)qq * KMAX];
+        tm[1][l + qq * KMAX] = static_cast<const T*>(B.Tr)[l + (size_t)qq * KMAX];
+      }
+      __syncthreads();
+      lastq = q;
     }
-    __syncthreads();
     const int row = ((item - rg.qbeg) << 8) + threadIdx.x;
     if (row >= B.m) continue;
     for (int side = 0; side < 2; ++side) {

@@ -39,6 +39,7 @@
 #include <cooperative_groups.h>
 
 #include "fft_common.cuh"
+#include "fft_inplace.cuh"
 #include "lr_internal.h"
 
 namespace cg = cooperative_groups;
@@ -106,7 +107,7 @@ struct GeomArgs {
 // Small path: 2^lognf sequences of length M per CTA.
 // ---------------------------------------------------------------------------
 template <typename T, int INM, bool OUT64>
-__global__ void __launch_bounds__(kFftThreads, 2) dst_small_kernel(
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) dst_small_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     const cpx<T>* __restrict__ bhat, int lognf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) dst_small_kernel(
 // values and all M2 values of t2 (or k2): tile[t2 * TX + dt1].
 // ---------------------------------------------------------------------------
 template <typename T, int INM>
-__global__ void __launch_bounds__(kFftThreads, 2) dst_col_fwd_kernel(
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) dst_col_fwd_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     cpx<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) dst_col_fwd_kernel(
 }
 
 template <typename T, bool OUT64>
-__global__ void __launch_bounds__(kFftThreads, 2) dst_col_inv_kernel(
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) dst_col_inv_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ chirp, const cpx<T>* __restrict__ tw,
     const cpx<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) dst_col_inv_kernel(
 // lanes on consecutive rows (no bank conflicts; the padding keeps the
 // transposing loads and stores at two-way conflicts).
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 2) dst_row_mid_kernel(
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) dst_row_mid_kernel(
     ColArgs c, GeomArgs g, const cpx<T>* __restrict__ tw, const cpx<T>* __restrict__ bhat,
     cpx<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -555,7 +556,8 @@ static cudaError_t launch_dst_t(const Plan& p, const ColArgs& c, const GeomArgs&
   auto k3 = dst_col_inv_kernel<T, OUT64>;
   static bool attr_set = false;  // once per instantiation: the largest tile plus the stage tables
   if (!attr_set) {
-    const int mx = (kTileElems + 4096 + stage_elems<T>(kStageLog) + kTwHi + kTwLo) * (int)sizeof(cpx<T>);
+    // m <= 131072: M1, M2 <= 512 (row padding <= 512, stages up to Ns = 128)
+    const int mx = (kTileElems + 512 + stage_elems<T>(7) + kTwHi + kTwLo) * (int)sizeof(cpx<T>);
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -757,6 +759,16 @@ std::string build_plan(int m, Plan& p) {
   if (!(e = upload<float>(p, chirp, &p.t32.chirp)).empty()) return e;
   if (!(e = upload<float>(p, tw, &p.t32.tw)).empty()) return e;
   if (!(e = upload<float>(p, bh, &p.t32.bhat)).empty()) return e;
+  // one-pass batched transform: residue order per precision
+  for (int prec = 0; prec < 2; ++prec) {
+    const int logH = std::min(logM, prec ? kFusedLogH32 : kFusedLogH64);
+    const size_t H = (size_t)1 << logH, R = M >> logH;
+    std::vector<std::complex<double>> br(M);
+    for (size_t t = 0; t < R; ++t)
+      for (size_t pos = 0; pos < H; ++pos) br[t * H + pos] = b[R * (size_t)inplace_freq((long long)pos, logH) + t];
+    if (!(e = prec ? upload<float>(p, br, &p.t32.bhat_rs) : upload<double>(p, br, &p.t64.bhat_rs)).empty())
+      return e;
+  }
   // cluster path: chunks of N2 = 4096 (8192 at M = 131072), spectrum stored
   // per CTA as [k1][k2] = b[k1 + CS k2]
   if (logM >= 13 && logM <= 17) {

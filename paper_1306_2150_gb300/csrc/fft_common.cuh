@@ -103,15 +103,16 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* twS, const cpx<T>* __restr
 // Stored stage by stage, k contiguous, consecutive lanes (consecutive k) read
 // consecutive words: no shared-memory bank conflicts, where indexing one
 // full-length table with a stage-dependent stride made up to 32 lanes hit one
-// bank.  Planes r = 1, 2, 3 in float32 (each value rounded once); float64
-// keeps the r = 1 plane and forms w_2 = w_1^2, w_3 = w_1 w_2.
+// bank.  Planes r = 1, 2, 3, each value rounded once (forming w_2, w_3 from
+// w_1 would cost float32 accuracy, and float64 multiplies, which GB300 runs
+// at a small fraction of its float32 rate).
 //   stw[(r - 1) stride + 2^logNs - 1 + k],  logNs <= maxLogNs,
 //   stride = stage_stride(maxLogNs) = 2^(maxLogNs + 1) - 1.
 // An FFT of length 2^logL needs maxLogNs = logL - 2.
 // ---------------------------------------------------------------------------
 constexpr int kStageLog = 10;  // up to Ns = 1024: FFT lengths <= 4096
 __host__ __device__ constexpr int stage_stride(int maxLogNs) { return maxLogNs < 0 ? 0 : (2 << maxLogNs) - 1; }
-template <typename T> __host__ __device__ constexpr int stage_planes() { return sizeof(T) == 4 ? 3 : 1; }
+template <typename T> __host__ __device__ constexpr int stage_planes() { return 3; }
 template <typename T> __host__ __device__ constexpr int stage_elems(int maxLogNs) {
   return stage_planes<T>() * stage_stride(maxLogNs);
 }

@@ -23,6 +23,9 @@ namespace lrp {
 // Symbol tables: Lambda[i,j] = a_i b_j + b_i a_j (both operator kinds).
 // ---------------------------------------------------------------------------
 constexpr int kSmallM = 4096;      // one CTA holds a whole length-M sequence
+// One-pass batched transform: FFT length H <= 2^kFusedLogH (per precision)
+// held whole in one CTA's shared memory; longer M split into M / H residues.
+constexpr int kFusedLogH32 = 14, kFusedLogH64 = 13;
 constexpr int kTileElems = 4096;   // complex elements per CTA tile
 constexpr int kFftThreads = 256;   // 16 elements per thread
 
@@ -31,6 +34,10 @@ struct TablesT {
   void* tw = nullptr;     // cpx<T>[M]
   void* bhat = nullptr;   // cpx<T>[M]
   void* bhat_cl = nullptr;  // cpx<T>[M], cluster order [k1][k2] (cluster path only)
+  void* bhat_rs = nullptr;  // cpx<T>[M], order of the one-pass transform: residue t
+                            // of R = M / H (H = min(M, 2^kFusedLogH..)), then the
+                            // digit-reversed position p of its length-H FFT:
+                            // [t][p] = b[R inplace_freq(p) + t]
   void* a = nullptr;      // T[m] per operator kind (index by op)
   void* b = nullptr;
 };
@@ -220,6 +227,7 @@ struct BatchProb {
   const void* chirp;         // plan tables of the working precision
   const void* tw;
   const void* bhat;
+  const void* bres;          // kernel spectrum in residue order (one-pass transform)
   const void* sa;            // symbol of the operator kind
   const void* sb;
 };
@@ -234,6 +242,9 @@ struct BatchItems {
   int live = 0;      // 1: start[] is written on the device by launch_batch_live_items
                      // and counts only the live (rank < R) columns, start[n] = items
   int slog = 0;      // largest log2 sub-length of the launch's FFT stages (log2 L - 2)
+  int fused_logh = 0;  // column list of the one-pass transform (FFT length cap
+                       // 2^fused_logh, one item per 2^(fused_logh - min(logM,
+                       // fused_logh)) columns); 0: four-step passes
 };
 
 // Item tables of the inverse transforms over live columns only: for each of
