@@ -1115,7 +1115,8 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
         ls.push_back(i);
         cs_.push_back((ncols + nf - 1) / nf);
         slog_s = std::max(slog_s, logM - 2);
-      } else if (fused_lh) {  // one pass per column (an item: 2^(LH - min(logM, LH)) columns)
+      } else if (fused_lh && logM >= fused_lh - 1) {  // one pass per column (an item:
+                                                      // 2^(LH - min(logM, LH)) columns)
         const int nf = 1 << (fused_lh - std::min(logM, fused_lh));
         lf.push_back(i);
         cf.push_back((ncols + nf - 1) / nf);

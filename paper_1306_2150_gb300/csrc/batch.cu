@@ -34,6 +34,7 @@
 #include <cooperative_groups.h>
 
 #include <climits>
+#include <type_traits>
 
 #include "fft_common.cuh"
 #include "fft_inplace.cuh"
@@ -457,7 +458,12 @@ __global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bdst_col_in
 template <typename T> __host__ __device__ constexpr int fused_logh() { return sizeof(T) == 4 ? kFusedLogH32 : kFusedLogH64; }
 // 512 threads: two radix-16 butterflies per thread and stage in float32, one
 // in float64 (up to 128 registers per thread)
-template <typename T> __host__ __device__ constexpr int fused_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+template <typename T> __host__ __device__ constexpr int fused_threads() { return (1 << fused_logh<T>()) / 16; }
+// CTAs per SM: two when a CTA's shared memory allows (one CTA's global-memory
+// waits between its barrier-separated stages then overlap the other's work)
+template <typename T> __host__ __device__ constexpr int fused_ctas_per_sm() {
+  return fused_logh<T>() <= (sizeof(T) == 4 ? 13 : 12) ? 2 : 1;
+}
 
 template <typename T>
 __host__ __device__ constexpr size_t fused_smem_elems() {
@@ -465,19 +471,122 @@ __host__ __device__ constexpr size_t fused_smem_elems() {
          kTwHi + kTwLo;
 }
 
-template <typename T, int DIR, int NT>
-__device__ __forceinline__ void fused_last(cpx<T>* buf, int logH, const cpx<T>* spec) {
-  constexpr int N = 1 << fused_logh<T>();
-  const int rem = logH & 3;
-  if (rem == 2) inplace_last<T, 4, NT, N>(buf, logH, spec);
-  else if (rem == 1) inplace_last<T, 2, NT, N>(buf, logH, spec);
-  else inplace_last<T, 16, NT, N>(buf, logH, spec);
+// The stages of one residue t of one item, sequences of length 2^LOGH.
+template <typename T, int DIR, int LOGH>
+__device__ __forceinline__ void fused_residue(cpx<T>* buf, const cpx<T>* tab, const cpx<T>* th, const cpx<T>* tl,
+                                              const ColGeom& G, const BatchItems& it, int col0, int m, int logM,
+                                              int t, const cpx<T>* __restrict__ chirp,
+                                              const cpx<T>* __restrict__ spec) {
+  constexpr int LH = fused_logh<T>(), HX = 1 << LH, NT = fused_threads<T>();
+  constexpr int H = 1 << LOGH, LOGS0 = LOGH - 4, S0 = 1 << LOGS0;
+  constexpr int N16 = LOGH >> 2, REM = LOGH & 3;
+  constexpr int NMID = REM ? N16 : N16 - 1;  // radix-16 stages before the last stage
+  const int M = 1 << logM;
+  __syncthreads();  // tables and G written; the previous residue read buf
+  // first forward stage, its elements folded from the input columns
+#pragma unroll
+  for (int g0 = 0; g0 < (HX >> 4); g0 += NT) {
+    const int g = g0 + (int)threadIdx.x;
+    const int f = g >> LOGS0, j = g & (S0 - 1);
+    const int lc = col0 + f;
+    const int cl = it.live ? live_col(G, lc) : lc;
+    const BCol<T, DIR> c(G, cl < 0 ? 2 * G.ncap : cl);
+    cpx<T> x[16], a[3], b[3];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = {T(0), T(0)};
+    if (c.live)
+      for (int e0 = 0; e0 < m; e0 += H) {  // uniform; once unless m > H
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int e = e0 + j + u * S0;
+          if (e < m) {
+            const T xv = c.load(e);
+            const cpx<T> w = chirp[e];
+            cpx<T> av = {xv * w.re, xv * w.im};
+            if (t > 0) av = cmul(av, twiddle2(th, tl, (t * e) & (M - 1)));
+            x[u] = cadd(x[u], av);
+          }
+        }
+      }
+    stage_twiddles(tab, S0, j, a, b);
+    dif16(x, a, b);
+    cpx<T>* bp = buf + smem_ix<true>((f << LOGH) + j);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) bp[pad_off(u * S0)] = x[u];
+  }
+  if constexpr (NMID > 1) {
+    __syncthreads();
+    inplace_stage16c<T, false, NT, LH, LOGH - 8>(buf, tab + inplace_tab_offset(LOGH, 1));
+  }
+  if constexpr (NMID > 2) {
+    __syncthreads();
+    inplace_stage16c<T, false, NT, LH, LOGH - 12>(buf, tab + inplace_tab_offset(LOGH, 2));
+  }
+  static_assert(NMID <= 3, "at most four radix-16 stages");
+  __syncthreads();
+  inplace_last<T, REM == 2 ? 4 : (REM == 1 ? 2 : 16), NT, HX>(buf, LOGH, spec);
+  if constexpr (NMID > 2) {
+    __syncthreads();
+    inplace_stage16c<T, true, NT, LH, LOGH - 12>(buf, tab + inplace_tab_offset(LOGH, 2));
+  }
+  if constexpr (NMID > 1) {
+    __syncthreads();
+    inplace_stage16c<T, true, NT, LH, LOGH - 8>(buf, tab + inplace_tab_offset(LOGH, 1));
+  }
+  __syncthreads();
+  // last inverse stage, its elements written to the output columns
+#pragma unroll
+  for (int g0 = 0; g0 < (HX >> 4); g0 += NT) {
+    const int g = g0 + (int)threadIdx.x;
+    const int f = g >> LOGS0, j = g & (S0 - 1);
+    const int lc = col0 + f;
+    const int cl = it.live ? live_col(G, lc) : lc;
+    const BCol<T, DIR> c(G, cl < 0 ? 2 * G.ncap : cl);
+    const cpx<T>* bp = buf + smem_ix<true>((f << LOGH) + j);
+    cpx<T> x[16], a[3], b[3];
+    // the earlier residues' sums: loaded before the butterfly (float32;
+    // float64 has no registers to spare for them there)
+    constexpr bool early = sizeof(T) == 4;
+    T old[16];
+    if (early && t > 0) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int k = j + u * S0;
+        old[u] = c.live && k < m ? c.loadout(k) : T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = bp[pad_off(u * S0)];
+    stage_twiddles(tab, S0, j, a, b);
+    dit16(x, a, b);
+    if (!c.live) continue;
+    for (int e0 = 0; e0 < m; e0 += H) {  // uniform; once unless m > H
+      if (t > 0 && (e0 > 0 || !early)) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int k = e0 + j + u * S0;
+          old[u] = k < m ? c.loadout(k) : T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int k = e0 + j + u * S0;
+        if (k < m) {
+          cpx<T> z = x[u];
+          if (t > 0) z = cmulc(z, twiddle2(th, tl, (t * k) & (M - 1)));  // times w_M^(-k t)
+          const cpx<T> w = chirp[k];
+          const T val = w.re * z.im + w.im * z.re;  // Im(chirp z)
+          c.store(k, t > 0 ? old[u] + val : val);
+        }
+      }
+    }
+  }
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(fused_threads<T>(), 1) bdst_fused_kernel(const BatchProb* __restrict__ P,
+__global__ void __launch_bounds__(fused_threads<T>(), fused_ctas_per_sm<T>()) bdst_fused_kernel(const BatchProb* __restrict__ P,
                                                                           BatchItems it) {
-  constexpr int LH = fused_logh<T>(), HX = 1 << LH, NT = fused_threads<T>();
+  constexpr int LH = fused_logh<T>(), HX = 1 << LH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);  // padded (smem_ix<true>)
   cpx<T>* tab = buf + HX + (HX >> 4);                  // radix-16 stage twiddles
@@ -490,11 +599,9 @@ __global__ void __launch_bounds__(fused_threads<T>(), 1) bdst_fused_kernel(const
   for (int item = rg.begin; item < rg.end; ++item) {
     const int q = rg.problem(it, item);
     const BatchProb& B = P[it.list[q]];
-    const int logM = B.logM, M = 1 << logM;
-    const int logH = logM < LH ? logM : LH, H = 1 << logH;
-    const int R = M >> logH, lognf = LH - logH;
-    const int logS0 = logH - 4, s0 = 1 << logS0;  // span of the first stage
-    const int n16 = logH >> 2, rem = logH & 3;
+    const int logM = B.logM;
+    const int logH = logM < LH ? logM : LH;
+    const int R = 1 << (logM - logH), lognf = LH - logH;
     const int col0 = (item - rg.qbeg) << lognf;
     if (threadIdx.x == 0) sg[item & 1] = ColGeom(B, DIR == 1);  // read after the next barrier
     const ColGeom& G = sg[item & 1];
@@ -508,94 +615,10 @@ __global__ void __launch_bounds__(fused_threads<T>(), 1) bdst_fused_kernel(const
     const cpx<T>* chirp = static_cast<const cpx<T>*>(B.chirp);
     const cpx<T>* bres = static_cast<const cpx<T>*>(B.bres);
     const int m = B.m;
-    for (int t = 0; t < R; ++t) {
-      __syncthreads();  // tables and G written; the previous residue read buf
-      // first forward stage, its elements folded from the input columns
-      for (int g = threadIdx.x; g < (HX >> 4); g += NT) {
-        const int f = g >> logS0, j = g & (s0 - 1);
-        const int lc = col0 + f;
-        const int cl = it.live ? live_col(G, lc) : lc;
-        const BCol<T, DIR> c(G, cl < 0 ? 2 * G.ncap : cl);
-        cpx<T> x[16], a[3], b[3];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) x[u] = {T(0), T(0)};
-        if (c.live)
-          for (int e0 = 0; e0 < m; e0 += H) {  // uniform; once unless m > H
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              const int e = e0 + j + (u << logS0);
-              if (e < m) {
-                const T xv = c.load(e);
-                const cpx<T> w = chirp[e];
-                cpx<T> av = {xv * w.re, xv * w.im};
-                if (t > 0) av = cmul(av, twiddle2(th, tl, (t * e) & (M - 1)));
-                x[u] = cadd(x[u], av);
-              }
-            }
-          }
-        stage_twiddles(tab, s0, j, a, b);
-        dif16(x, a, b);
-        const int base = (f << logH) + j;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) buf[smem_ix<true>(base + (u << logS0))] = x[u];
-      }
-      const int nmid = rem ? n16 : n16 - 1;  // radix-16 stages before the last stage
-      for (int i = 1; i < nmid; ++i) {
-        __syncthreads();
-        inplace_stage16<T, false, NT>(buf, LH, logH - 4 * i - 4, tab + inplace_tab_offset(logH, i));
-      }
-      __syncthreads();
-      fused_last<T, DIR, NT>(buf, logH, bres + (size_t)t * H);
-      for (int i = nmid - 1; i >= 1; --i) {
-        __syncthreads();
-        inplace_stage16<T, true, NT>(buf, LH, logH - 4 * i - 4, tab + inplace_tab_offset(logH, i));
-      }
-      __syncthreads();
-      // last inverse stage, its elements written to the output columns
-      for (int g = threadIdx.x; g < (HX >> 4); g += NT) {
-        const int f = g >> logS0, j = g & (s0 - 1);
-        const int lc = col0 + f;
-        const int cl = it.live ? live_col(G, lc) : lc;
-        const BCol<T, DIR> c(G, cl < 0 ? 2 * G.ncap : cl);
-        const int base = (f << logH) + j;
-        cpx<T> x[16], a[3], b[3];
-        // the earlier residues' sums: loaded before the butterfly (float32;
-        // float64 has no registers to spare for them there)
-        constexpr bool early = sizeof(T) == 4;
-        T old[16];
-        if (early && t > 0) {
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int k = j + (u << logS0);
-            old[u] = c.live && k < m ? c.loadout(k) : T(0);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 16; ++u) x[u] = buf[smem_ix<true>(base + (u << logS0))];
-        stage_twiddles(tab, s0, j, a, b);
-        dit16(x, a, b);
-        if (!c.live) continue;
-        for (int e0 = 0; e0 < m; e0 += H) {  // uniform; once unless m > H
-          if (t > 0 && (e0 > 0 || !early)) {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              const int k = e0 + j + (u << logS0);
-              old[u] = k < m ? c.loadout(k) : T(0);
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int k = e0 + j + (u << logS0);
-            if (k < m) {
-              cpx<T> z = x[u];
-              if (t > 0) z = cmulc(z, twiddle2(th, tl, (t * k) & (M - 1)));  // times w_M^(-k t)
-              const cpx<T> w = chirp[k];
-              const T val = w.re * z.im + w.im * z.re;  // Im(chirp z)
-              c.store(k, t > 0 ? old[u] + val : val);
-            }
-          }
-        }
-      }
+    for (int t = 0; t < R; ++t) {  // uniform
+      const cpx<T>* spec = bres + ((size_t)t << logH);
+      if (logH == LH) fused_residue<T, DIR, LH>(buf, tab, th, tl, G, it, col0, m, logM, t, chirp, spec);
+      else fused_residue<T, DIR, LH - 1>(buf, tab, th, tl, G, it, col0, m, logM, t, chirp, spec);
     }
   }
 }
@@ -634,8 +657,9 @@ cudaError_t launch_bdst_dir(const BatchProb* probs, const BatchItems& small, con
     const size_t fbytes = fused_smem_elems<T>() * sizeof(cpx<T>);
     static cudaError_t fattr = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fbytes);
     if (fattr != cudaSuccess) return fattr;
-    // one CTA per SM (the whole sequence in shared memory)
-    kf<<<col.items < num_sms ? col.items : num_sms, fused_threads<T>(), fbytes, st>>>(probs, col);
+    // one or two CTAs per SM (the whole sequence in shared memory)
+    const int cap = fused_ctas_per_sm<T>() * num_sms;
+    kf<<<col.items < cap ? col.items : cap, fused_threads<T>(), fbytes, st>>>(probs, col);
     return cudaGetLastError();
   }
   if (col.items > 0) {
@@ -738,43 +762,74 @@ namespace {
 template <typename T>
 __global__ void __launch_bounds__(256) brotate_kernel(const BatchProb* __restrict__ P, BatchItems it) {
   extern __shared__ __align__(16) unsigned char rot_raw[];
-  T (*tm)[KMAX * KMAX] = reinterpret_cast<T (*)[KMAX * KMAX]>(rot_raw);  // [2][KMAX * KMAX]
+  // rotations transposed, [side][l][q] (q contiguous, zero past the rank), so
+  // that the 16 coefficients of a row l are four (float32) or eight (float64)
+  // vector loads that every thread of the CTA shares
+  T* tm = reinterpret_cast<T*>(rot_raw);
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int VW = (int)(sizeof(V) / sizeof(T));
   const int items = item_count(it);
   ItemRange rg(it, items);
-  int lastq = -1;
+  int lastq = -1, k = 0, R = 0, m = 0, ldw = 0;
+  const T* Xs[2] = {nullptr, nullptr};
+  T* W = nullptr;
+  size_t side_off = 0;
   for (int item = rg.begin; item < rg.end; ++item) {
     const int q = rg.problem(it, item);
-    const BatchProb& B = P[it.list[q]];
-    const int k = B.st->k, R = B.st->rank;
-    if (R <= 0 || k <= 0) continue;  // uniform across the CTA
-    if (q != lastq) {  // a new problem: stage its rotations
+    if (q != lastq) {  // a new problem: its sizes, and its rotations staged
+      const BatchProb& B = P[it.list[q]];
+      k = B.st->k;
+      R = B.st->rank;
+      m = B.m;
+      ldw = B.ldw;
+      Xs[0] = static_cast<const T*>(B.C);
+      Xs[1] = static_cast<const T*>(B.R);
+      W = static_cast<T*>(B.W);
+      side_off = (size_t)B.ncap * B.ldw;
       __syncthreads();  // the previous problem's rows read tm
-      for (int idx = threadIdx.x; idx < k * R; idx += blockDim.x) {
-        const int l = idx % k, qq = idx / k;
-        tm[0][l + qq * KMAX] = static_cast<const T*>(B.Tc)[l + (size_t)qq * KMAX];
-        tm[1][l + qq * KMAX] = static_cast<const T*>(B.Tr)[l + (size_t)qq * KMAX];
-      }
+      const int R16 = (R + 15) & ~15;
+      if (R > 0 && k > 0)
+        for (int idx = threadIdx.x; idx < k * R16; idx += blockDim.x) {
+          const int qq = idx % R16, l = idx / R16;
+          const bool in = qq < R;
+          tm[l * KMAX + qq] = in ? static_cast<const T*>(B.Tc)[l + (size_t)qq * KMAX] : T(0);
+          tm[KMAX * KMAX + l * KMAX + qq] = in ? static_cast<const T*>(B.Tr)[l + (size_t)qq * KMAX] : T(0);
+        }
       __syncthreads();
       lastq = q;
     }
+    if (R <= 0 || k <= 0) continue;
     const int row = ((item - rg.qbeg) << 8) + threadIdx.x;
-    if (row >= B.m) continue;
+    if (row >= m) continue;
     for (int side = 0; side < 2; ++side) {
-      const T* X = static_cast<const T*>(side ? B.R : B.C) + row;
-      T* out = static_cast<T*>(B.W) + (size_t)side * B.ncap * B.ldw + row;
+      const T* X = Xs[side] + row;
+      const T* ts = tm + side * KMAX * KMAX;
+      T* out = W + side * side_off + row;
       for (int q0 = 0; q0 < R; q0 += 16) {  // one pass over X for ranks up to 16
         T acc[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = T(0);
 #pragma unroll 4
         for (int l = 0; l < k; ++l) {
-          const T x = X[(size_t)l * B.ldw];
+          const T x = X[(size_t)l * ldw];
+          const V* tv = reinterpret_cast<const V*>(ts + l * KMAX + q0);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc[c] += x * tm[side][l + (q0 + c) * KMAX];
+          for (int v = 0; v < 16 / VW; ++v) {
+            const V c4 = tv[v];
+            if constexpr (VW == 4) {
+              acc[4 * v] += x * c4.x;
+              acc[4 * v + 1] += x * c4.y;
+              acc[4 * v + 2] += x * c4.z;
+              acc[4 * v + 3] += x * c4.w;
+            } else {
+              acc[2 * v] += x * c4.x;
+              acc[2 * v + 1] += x * c4.y;
+            }
+          }
         }
 #pragma unroll
         for (int c = 0; c < 16; ++c)
-          if (q0 + c < R) out[(size_t)(q0 + c) * B.ldw] = acc[c];
+          if (q0 + c < R) out[(size_t)(q0 + c) * ldw] = acc[c];
       }
     }
   }
@@ -1108,7 +1163,7 @@ __device__ __forceinline__ BxRed<T> bx_reduce(const BxProb<T>& p, const T (&v)[R
 }
 
 template <typename T, int RPT>
-__global__ void __launch_bounds__(BX_NT, 1) bcross_kernel(const BatchProb* __restrict__ P,
+__global__ void __launch_bounds__(BX_NT, (sizeof(T) == 4 && RPT <= 8) ? 2 : 1) bcross_kernel(const BatchProb* __restrict__ P,
                                                           const int* __restrict__ list, BatchCrossParams cp) {
   extern __shared__ __align__(16) unsigned char bx_dyn[];
   __shared__ T sd[KMAX + 1];  // pivot values

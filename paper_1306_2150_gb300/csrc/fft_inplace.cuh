@@ -127,6 +127,35 @@ __device__ __forceinline__ void stage_twiddles(const cpx<T>* tabi, int s, int j,
   }
 }
 
+// Padded-index offset of element q s of a butterfly from its first element
+// b (smem_ix<true>): q s + (q s) / 16 whenever b mod 16 < s or s is a
+// multiple of 16, which holds for every butterfly of the stages below (b =
+// B 16 s + j, j < s).  Constant per q and s, so every access of a butterfly
+// is one shared-memory instruction with an immediate offset.
+__host__ __device__ constexpr int pad_off(int qs) { return qs + (qs >> 4); }
+
+// One radix-16 stage with compile-time sizes: 2^LOGN padded elements,
+// span 2^LOGS, NT threads.
+template <typename T, bool INV, int NT, int LOGN, int LOGS>
+__device__ __forceinline__ void inplace_stage16c(cpx<T>* buf, const cpx<T>* tabi) {
+  constexpr int nb = 1 << (LOGN - 4), s = 1 << LOGS;
+#pragma unroll
+  for (int g0 = 0; g0 < nb; g0 += NT) {
+    const int g = g0 + (int)threadIdx.x;
+    if (nb % NT != 0 && g >= nb) break;
+    const int j = g & (s - 1);
+    cpx<T>* bp = buf + smem_ix<true>(((g >> LOGS) << (LOGS + 4)) + j);
+    cpx<T> x[16], a[3], b[3];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = bp[pad_off(q << LOGS)];
+    stage_twiddles(tabi, s, j, a, b);
+    if (INV) dit16(x, a, b);
+    else dif16(x, a, b);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) bp[pad_off(q << LOGS)] = x[q];
+  }
+}
+
 // One radix-16 stage over a buffer of 2^logN padded elements (several
 // sequences of length >= 16 s back to back), span s = 2^logS, NT threads.
 template <typename T, bool INV, int NT>
@@ -158,10 +187,11 @@ __device__ __forceinline__ void inplace_last(cpx<T>* buf, int logH, const cpx<T>
     const int g = g0 + (int)threadIdx.x;
     if (NB % NT != 0 && g >= NB) break;
     const int base = g * RL;
+    cpx<T>* bp = buf + smem_ix<true>(base);  // RL contiguous elements, no pad inside
     cpx<T> x[RL], sp[RL];
 #pragma unroll
     for (int q = 0; q < RL; ++q) {
-      x[q] = buf[smem_ix<true>(base + q)];
+      x[q] = bp[q];
       sp[q] = spec[(base + q) & hmask];
     }
     if constexpr (RL == 16) {
@@ -183,7 +213,7 @@ __device__ __forceinline__ void inplace_last(cpx<T>* buf, int logH, const cpx<T>
       x[1] = csub(y0, y1);
     }
 #pragma unroll
-    for (int q = 0; q < RL; ++q) buf[smem_ix<true>(base + q)] = x[q];
+    for (int q = 0; q < RL; ++q) bp[q] = x[q];
   }
 }
 
