@@ -911,13 +911,19 @@ __device__ __forceinline__ void bx_warp_argmax(T& a, int& i, T& v, int& src) {
 template <typename T> __device__ __forceinline__ T bx_ratio(T a, T b) { return a / b; }
 template <> __device__ __forceinline__ float bx_ratio<float>(float a, float b) { return __fdividef(a, b); }
 
-// Sum over the warp of a[i], i < 16, for every i at once (recursive halving);
-// afterwards lane L holds the sum for index L mod 16.  Fixed pattern: every
+// Two CTAs per SM (64 registers per thread) for float32 slices of up to 8
+// indices per thread, so that a batch of many problems on a few CTAs each
+// runs in one wave; one CTA per SM (128 registers) otherwise.
+template <typename T, int RPT>
+__host__ __device__ constexpr bool bx_two_per_sm() { return sizeof(T) == 4 && RPT <= 8; }
+
+// Sum over the warp of a[i], i < DC, for every i at once (recursive halving);
+// afterwards lane L holds the sum for index L mod DC.  Fixed pattern: every
 // warp and CTA gets the same bits.
-template <typename T>
-__device__ __forceinline__ T bx_transpose_sum16(T (&a)[16], int lane) {
+template <int DC, typename T>
+__device__ __forceinline__ T bx_transpose_sum(T (&a)[DC], int lane) {
 #pragma unroll
-  for (int h = 8; h >= 1; h >>= 1) {
+  for (int h = DC / 2; h >= 1; h >>= 1) {
     const bool up = (lane & h) != 0;
 #pragma unroll
     for (int i = 0; i < h; ++i) {
@@ -926,7 +932,10 @@ __device__ __forceinline__ T bx_transpose_sum16(T (&a)[16], int lane) {
       a[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
     }
   }
-  return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 16);
+  T x = a[0];
+#pragma unroll
+  for (int h = DC; h < 32; h <<= 1) x += __shfl_xor_sync(0xffffffffu, x, h);
+  return x;  // sum of value (lane mod DC) over the warp
 }
 
 // Problem-level constants of one CTA: owned indices j = row0 + tid + s NT.
@@ -1059,10 +1068,13 @@ __device__ __forceinline__ BxRed<T> bx_reduce(const BxProb<T>& p, const T (&v)[R
     }
   }
   T* slot = p.slots + ((size_t)par * BX_NW + warp) * BX_WORDS;
-  for (int l0 = 0; l0 < kd; l0 += 16) {
-    T acc[16];
+  // dot products DC columns at a time (8 where two CTAs share an SM's
+  // registers, 16 otherwise)
+  constexpr int DC = bx_two_per_sm<T, RPT>() ? 8 : 16;
+  for (int l0 = 0; l0 < kd; l0 += DC) {
+    T acc[DC];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < DC; ++i) {
       acc[i] = T(0);
       const int l = l0 + i;
       if (l < kd) {
@@ -1072,8 +1084,8 @@ __device__ __forceinline__ BxRed<T> bx_reduce(const BxProb<T>& p, const T (&v)[R
           if (base + s * BX_NT < p.row1) acc[i] += Xc[s * BX_NT] * v[s];
       }
     }
-    const T x = bx_transpose_sum16(acc, lane);
-    if (lane < 16 && l0 + lane < kd) slot[BX_DOTS + l0 + lane] = x;
+    const T x = bx_transpose_sum<DC>(acc, lane);
+    if (lane < DC && l0 + lane < kd) slot[BX_DOTS + l0 + lane] = x;
   }
 #pragma unroll
   for (int u = 0; u < CV; ++u)
@@ -1163,7 +1175,7 @@ __device__ __forceinline__ BxRed<T> bx_reduce(const BxProb<T>& p, const T (&v)[R
 }
 
 template <typename T, int RPT>
-__global__ void __launch_bounds__(BX_NT, (sizeof(T) == 4 && RPT <= 8) ? 2 : 1) bcross_kernel(const BatchProb* __restrict__ P,
+__global__ void __launch_bounds__(BX_NT, bx_two_per_sm<T, RPT>() ? 2 : 1) bcross_kernel(const BatchProb* __restrict__ P,
                                                           const int* __restrict__ list, BatchCrossParams cp) {
   extern __shared__ __align__(16) unsigned char bx_dyn[];
   __shared__ T sd[KMAX + 1];  // pivot values
