@@ -476,7 +476,7 @@ template <typename T, int DIR, int LOGH>
 __device__ __forceinline__ void fused_residue(cpx<T>* buf, const cpx<T>* tab, const cpx<T>* th, const cpx<T>* tl,
                                               const ColGeom& G, const BatchItems& it, int col0, int m, int logM,
                                               int t, const cpx<T>* __restrict__ chirp,
-                                              const cpx<T>* __restrict__ spec) {
+                                              const cpx<T>* __restrict__ spec, int pf_col0) {
   constexpr int LH = fused_logh<T>(), HX = 1 << LH, NT = fused_threads<T>();
   constexpr int H = 1 << LOGH, LOGS0 = LOGH - 4, S0 = 1 << LOGS0;
   constexpr int N16 = LOGH >> 2, REM = LOGH & 3;
@@ -491,6 +491,18 @@ __device__ __forceinline__ void fused_residue(cpx<T>* buf, const cpx<T>* tab, co
     const int lc = col0 + f;
     const int cl = it.live ? live_col(G, lc) : lc;
     const BCol<T, DIR> c(G, cl < 0 ? 2 * G.ncap : cl);
+    if (DIR == 0 && pf_col0 >= 0) {
+      // the CTA's next column (same problem) into L2 while this one runs:
+      // the forward input is read from HBM, the inverse one is already in L2
+      const BCol<T, DIR> cn(G, pf_col0 + f);
+      if (cn.live)
+        for (int e0 = 0; e0 < m; e0 += H)
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int e = e0 + j + u * S0;
+            if (e < m) asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const double*>(cn.in) + e));
+          }
+    }
     cpx<T> x[16], a[3], b[3];
 #pragma unroll
     for (int u = 0; u < 16; ++u) x[u] = {T(0), T(0)};
@@ -615,10 +627,13 @@ __global__ void __launch_bounds__(fused_threads<T>(), fused_ctas_per_sm<T>()) bd
     const cpx<T>* chirp = static_cast<const cpx<T>*>(B.chirp);
     const cpx<T>* bres = static_cast<const cpx<T>*>(B.bres);
     const int m = B.m;
+    // next column of the same problem in this CTA's range: prefetched in the first residue
+    const int pf = item + 1 < rg.end && item + 1 < rg.qend ? col0 + (1 << lognf) : -1;
     for (int t = 0; t < R; ++t) {  // uniform
       const cpx<T>* spec = bres + ((size_t)t << logH);
-      if (logH == LH) fused_residue<T, DIR, LH>(buf, tab, th, tl, G, it, col0, m, logM, t, chirp, spec);
-      else fused_residue<T, DIR, LH - 1>(buf, tab, th, tl, G, it, col0, m, logM, t, chirp, spec);
+      const int pft = t == 0 ? pf : -1;
+      if (logH == LH) fused_residue<T, DIR, LH>(buf, tab, th, tl, G, it, col0, m, logM, t, chirp, spec, pft);
+      else fused_residue<T, DIR, LH - 1>(buf, tab, th, tl, G, it, col0, m, logM, t, chirp, spec, pft);
     }
   }
 }

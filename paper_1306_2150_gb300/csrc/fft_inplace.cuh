@@ -180,35 +180,40 @@ __device__ __forceinline__ void inplace_stage16(cpx<T>* buf, int logN, int logS,
 // every sequence of the buffer), and the first inverse stage, in registers.
 template <typename T, int RL, int NT, int N>
 __device__ __forceinline__ void inplace_last(cpx<T>* buf, int logH, const cpx<T>* __restrict__ spec) {
-  constexpr int NB = N / RL;
+  constexpr int NB = N / RL, NI = (NB + NT - 1) / NT;
   const int hmask = (1 << logH) - 1;
+  // every spectrum value of the thread first: one global-memory wait
+  cpx<T> sp[NI][RL];
 #pragma unroll
-  for (int g0 = 0; g0 < NB; g0 += NT) {
-    const int g = g0 + (int)threadIdx.x;
+  for (int i = 0; i < NI; ++i) {
+    const int g = i * NT + (int)threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < RL; ++q) sp[i][q] = g < NB ? spec[(g * RL + q) & hmask] : cpx<T>{T(0), T(0)};
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int g = i * NT + (int)threadIdx.x;
     if (NB % NT != 0 && g >= NB) break;
     const int base = g * RL;
     cpx<T>* bp = buf + smem_ix<true>(base);  // RL contiguous elements, no pad inside
-    cpx<T> x[RL], sp[RL];
+    cpx<T> x[RL];
 #pragma unroll
-    for (int q = 0; q < RL; ++q) {
-      x[q] = bp[q];
-      sp[q] = spec[(base + q) & hmask];
-    }
+    for (int q = 0; q < RL; ++q) x[q] = bp[q];
     if constexpr (RL == 16) {
       cpx<T> one[3] = {{T(1), T(0)}, {T(1), T(0)}, {T(1), T(0)}};
       dif16(x, one, one);
 #pragma unroll
-      for (int q = 0; q < RL; ++q) x[q] = cmul(x[q], sp[q]);
+      for (int q = 0; q < RL; ++q) x[q] = cmul(x[q], sp[i][q]);
       dit16(x, one, one);
     } else if constexpr (RL == 4) {
       dft4(x[0], x[1], x[2], x[3], false);
 #pragma unroll
-      for (int q = 0; q < RL; ++q) x[q] = cmul(x[q], sp[q]);
+      for (int q = 0; q < RL; ++q) x[q] = cmul(x[q], sp[i][q]);
       dft4(x[0], x[1], x[2], x[3], true);
     } else {
       cpx<T> y0 = cadd(x[0], x[1]), y1 = csub(x[0], x[1]);
-      y0 = cmul(y0, sp[0]);
-      y1 = cmul(y1, sp[1]);
+      y0 = cmul(y0, sp[i][0]);
+      y1 = cmul(y1, sp[i][1]);
       x[0] = cadd(y0, y1);
       x[1] = csub(y0, y1);
     }
