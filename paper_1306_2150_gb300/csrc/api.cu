@@ -76,9 +76,9 @@ struct lr_handle_s {
   cudaEvent_t bdesc_ev = nullptr;
   std::map<std::string, char*> graph_desc;
   int cross_rows[2] = {4096, 4096};  // indices per CTA of the batched cross (float64, float32)
-  int dst_fused[2] = {0, 1};         // batched transforms of M > 4096: one pass per column (1) or
-                                     // the four-step passes through scratch (0); float64 keeps
-                                     // the four-step passes (FP64-bound either way, and faster)
+  int dst_fused[2] = {0, 1};         // batched transforms of M > 4096: one pass per column (1, float32
+                                     // only) or the four-step passes through scratch (0); float64
+                                     // keeps the four-step passes (FP64-bound either way, and faster)
   size_t ws_limit = 0;               // cap on the workspaces' total bytes (0: none)
 };
 
@@ -1103,7 +1103,7 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
   int fwd_cols = 0;
   for (int i = 0; i < batch; ++i) fwd_cols += 2 * geo[i].r;
   const int fused_lh =
-      h->dst_fused[pi] && fwd_cols >= h->num_sms / 2 ? (f32 ? kFusedLogH32 : kFusedLogH64) : 0;
+      f32 && h->dst_fused[pi] && fwd_cols >= h->num_sms / 2 ? kFusedLogH32 : 0;
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<int> ls, cs_, lf, cf, rf;
     int slog_s = 0, slog_c = 0, slog_r = 0;  // largest FFT stage each launch needs

@@ -9,15 +9,17 @@
 //
 // Transforms (Section 4.1, Eq. flr:diag): the Bluestein evaluation of dst.cu
 // (chirp, power-of-two FFT of length M >= 2m - 1, kernel spectrum, inverse
-// FFT, chirp), with tiles of 4096 complex elements:
+// FFT, chirp):
 //   M <= 4096 : one item = 4096 / M columns of one problem, whole sequences in
-//               shared memory;
-//   M >  4096 : four-step split M = M1 M2 through the problem's global scratch
-//               (column pass, row pass with the spectrum product, column pass).
-// All shared-memory FFT lengths are at most 4096, so every CTA builds the
-// stage twiddle tables (fft_common.cuh) once, from one table of length 4096.
+//               shared memory (Stockham passes, tiles of 4096 elements);
+//   M >  4096 : float32 batches with enough columns: the one-pass transform,
+//               one CTA per column, the length-M convolution split into
+//               residue classes of FFTs held whole in shared memory (in-place
+//               stages, fft_inplace.cuh), no scratch; otherwise the four-step
+//               split M = M1 M2 through the problem's global scratch (column
+//               pass, row pass with the spectrum product, column pass).
 //
-// Cross (Section 4.2, Eq. flr:div): one CTA, or a cluster of 2 or 4 CTAs, per
+// Cross (Section 4.2, Eq. flr:div): one CTA, or a cluster of 2 to 16 CTAs, per
 // problem.  A CTA owns a contiguous slice of indices; thread t owns indices
 // row0 + t + s NT (s < RPT), so every column access of a warp is one
 // coalesced 128-byte line.  Factors and skeleton are read from global memory
@@ -455,14 +457,14 @@ __global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) bdst_col_in
 // stage in registers, and the last inverse stage writes the output: the
 // column is read R times (from L2) and no M-length scratch passes through
 // memory.  R = 1 for M <= 2^LH, where an item holds 2^LH / M columns.
-template <typename T> __host__ __device__ constexpr int fused_logh() { return sizeof(T) == 4 ? kFusedLogH32 : kFusedLogH64; }
+template <typename T> __host__ __device__ constexpr int fused_logh() { return kFusedLogH32; }
 // 512 threads: two radix-16 butterflies per thread and stage in float32, one
 // in float64 (up to 128 registers per thread)
 template <typename T> __host__ __device__ constexpr int fused_threads() { return (1 << fused_logh<T>()) / 16; }
 // CTAs per SM: two when a CTA's shared memory allows (one CTA's global-memory
 // waits between its barrier-separated stages then overlap the other's work)
 template <typename T> __host__ __device__ constexpr int fused_ctas_per_sm() {
-  return fused_logh<T>() <= (sizeof(T) == 4 ? 13 : 12) ? 2 : 1;
+  return fused_logh<T>() <= 13 ? 2 : 1;
 }
 
 template <typename T>
@@ -667,15 +669,20 @@ cudaError_t launch_bdst_dir(const BatchProb* probs, const BatchItems& small, con
   const int cap = 4 * num_sms;
   if (small.items > 0) k0<<<small.items < cap ? small.items : cap, kBThreads, bytes(small), st>>>(probs, small, tw);
   if (col.items > 0 && col.fused_logh) {
-    if (col.fused_logh != fused_logh<T>()) return cudaErrorInvalidValue;
-    auto kf = bdst_fused_kernel<T, DIR>;
-    const size_t fbytes = fused_smem_elems<T>() * sizeof(cpx<T>);
-    static cudaError_t fattr = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fbytes);
-    if (fattr != cudaSuccess) return fattr;
-    // one or two CTAs per SM (the whole sequence in shared memory)
-    const int cap = fused_ctas_per_sm<T>() * num_sms;
-    kf<<<col.items < cap ? col.items : cap, fused_threads<T>(), fbytes, st>>>(probs, col);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) != 4) {
+      return cudaErrorInvalidValue;  // float32 only
+    } else {
+      if (col.fused_logh != fused_logh<T>()) return cudaErrorInvalidValue;
+      auto kf = bdst_fused_kernel<T, DIR>;
+      const size_t fbytes = fused_smem_elems<T>() * sizeof(cpx<T>);
+      static cudaError_t fattr =
+          cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fbytes);
+      if (fattr != cudaSuccess) return fattr;
+      // one or two CTAs per SM (the whole sequence in shared memory)
+      const int cap = fused_ctas_per_sm<T>() * num_sms;
+      kf<<<col.items < cap ? col.items : cap, fused_threads<T>(), fbytes, st>>>(probs, col);
+      return cudaGetLastError();
+    }
   }
   if (col.items > 0) {
     k1<<<col.items < cap ? col.items : cap, kBThreads, bytes(col), st>>>(probs, col, tw);

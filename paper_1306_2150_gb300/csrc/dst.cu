@@ -759,15 +759,14 @@ std::string build_plan(int m, Plan& p) {
   if (!(e = upload<float>(p, chirp, &p.t32.chirp)).empty()) return e;
   if (!(e = upload<float>(p, tw, &p.t32.tw)).empty()) return e;
   if (!(e = upload<float>(p, bh, &p.t32.bhat)).empty()) return e;
-  // one-pass batched transform: residue order per precision
-  for (int prec = 0; prec < 2; ++prec) {
-    const int logH = std::min(logM, prec ? kFusedLogH32 : kFusedLogH64);
+  // one-pass batched transform (float32): residue order
+  if (logM > 12) {
+    const int logH = std::min(logM, kFusedLogH32);
     const size_t H = (size_t)1 << logH, R = M >> logH;
     std::vector<std::complex<double>> br(M);
     for (size_t t = 0; t < R; ++t)
       for (size_t pos = 0; pos < H; ++pos) br[t * H + pos] = b[R * (size_t)inplace_freq((long long)pos, logH) + t];
-    if (!(e = prec ? upload<float>(p, br, &p.t32.bhat_rs) : upload<double>(p, br, &p.t64.bhat_rs)).empty())
-      return e;
+    if (!(e = upload<float>(p, br, &p.t32.bhat_rs)).empty()) return e;
   }
   // cluster path: chunks of N2 = 4096 (8192 at M = 131072), spectrum stored
   // per CTA as [k1][k2] = b[k1 + CS k2]

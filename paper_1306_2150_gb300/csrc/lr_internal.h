@@ -23,9 +23,9 @@ namespace lrp {
 // Symbol tables: Lambda[i,j] = a_i b_j + b_i a_j (both operator kinds).
 // ---------------------------------------------------------------------------
 constexpr int kSmallM = 4096;      // one CTA holds a whole length-M sequence
-// One-pass batched transform: FFT length H <= 2^kFusedLogH (per precision)
-// held whole in one CTA's shared memory; longer M split into M / H residues.
-constexpr int kFusedLogH32 = 14, kFusedLogH64 = 13;
+// One-pass batched transform (float32): FFT length H <= 2^kFusedLogH32 held
+// whole in one CTA's shared memory; longer M split into M / H residues.
+constexpr int kFusedLogH32 = 14;
 constexpr int kTileElems = 4096;   // complex elements per CTA tile
 constexpr int kFftThreads = 256;   // 16 elements per thread
 
@@ -34,9 +34,9 @@ struct TablesT {
   void* tw = nullptr;     // cpx<T>[M]
   void* bhat = nullptr;   // cpx<T>[M]
   void* bhat_cl = nullptr;  // cpx<T>[M], cluster order [k1][k2] (cluster path only)
-  void* bhat_rs = nullptr;  // cpx<T>[M], order of the one-pass transform: residue t
-                            // of R = M / H (H = min(M, 2^kFusedLogH..)), then the
-                            // digit-reversed position p of its length-H FFT:
+  void* bhat_rs = nullptr;  // cpx<T>[M], float32 only, order of the one-pass transform:
+                            // residue t of R = M / H (H = min(M, 2^kFusedLogH32)), then
+                            // the digit-reversed position p of its length-H FFT:
                             // [t][p] = b[R inplace_freq(p) + t]
   void* a = nullptr;      // T[m] per operator kind (index by op)
   void* b = nullptr;

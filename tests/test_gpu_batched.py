@@ -116,6 +116,24 @@ def test_phased_batch_probe_restart_and_edge_problems(lr, h, prec):
             assert len(sb) == O.lr_poisson2d(U, V, "5pt", eps)[3].rank, i
 
 
+def test_phased_batch_one_pass_transform_long_orders(lr, h):
+    # float32 batches with enough columns take the one-pass transform: orders
+    # with M = 2^13 (two columns per CTA), 2^14 and 2^15 (one and two residue
+    # classes) and M = 2^16, 2^17 (four and eight residues, inputs folded);
+    # every problem within 10 eps on sampled rows
+    eps = 1e-6
+    ms = [2500, 4097, 9000, 16385, 20000, 40000, 65536]
+    probs = [inputs.separable_random(m, 6, seed=40 + i) for i, m in enumerate(ms)]
+    batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
+    st = lr.lr_poisson2d_batched(h, batch, eps=eps, prec="mixed")
+    torch.cuda.synchronize()
+    assert st == lr.LR_OK and all(s == lr.LR_OK for s in batch.status)
+    for i, (U, V) in enumerate(probs):
+        Ub, sb, Vb = (npy(t) for t in batch.result(i))
+        rows = np.unique(np.linspace(0, U.shape[0] - 1, 128).astype(int))
+        assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt", rows=rows) <= 10 * eps, (i, ms[i])
+
+
 def test_phased_batch_headline_shape(lr, h):
     # the benchmark's shape: m = 16384 smooth right-hand sides (4 CTAs per
     # problem at the default 4096 indices per CTA), mixed precision, graph
