@@ -2161,6 +2161,28 @@ lr_status stokes_gmres(StokesCtx& x, double tol, int maxit, double nr0, int* it_
 // eps ||r0|| (the Schur product q: a tenth of it).
 constexpr double kCgFloor = 0.3;
 
+// The velocity solves of a Schur product, of the right-hand side B^T A^-1 f
+// and of the final velocity carry their error through B^T, a difference over
+// h, into the divergence: float32 solves (1e-6 at best) cannot deliver a
+// product asked at a tenth of eps below 1e-6.  Those solves run in float64
+// (the CG recursion and the final divergence then reach tol_div), the rest
+// stay float32.  Restores the options on destruction.
+struct VelocityPrecision {
+  StokesCtx& x;
+  lr_precision prec;
+  double eps;
+  VelocityPrecision(StokesCtx& xx, double eps_user) : x(xx), prec(xx.oin.prec), eps(xx.oin.eps) {
+    if (x.oin.prec == LR_MIXED && 0.1 * eps_user < 1e-6) {
+      x.oin.prec = LR_FP64;
+      x.oin.eps = 0.1 * eps_user;
+    }
+  }
+  ~VelocityPrecision() {
+    x.oin.prec = prec;
+    x.oin.eps = eps;
+  }
+};
+
 lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, const lr_mat* g, lr_mat* u, lr_mat* p, double tol,
                        int maxit, const lr_options& o, int* iters, double* resid, double* history) {
   StokesCtx x;
@@ -2201,7 +2223,10 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, const lr_mat* g, lr_
   LR_CUDA(h, launch_kernel_modes(n, x.E, x.ldp, stm), "modes");
   // r0 = B^T A^-1 f
   int rx = 0, ry = 0;
-  if ((s = velocity_solves(x, f, &rx, &ry)) != LR_OK) return s;
+  {
+    VelocityPrecision vp(x, o.eps);
+    if ((s = velocity_solves(x, f, &rx, &ry)) != LR_OK) return s;
+  }
   if ((s = div_round(x, rx, ry, x.R)) != LR_OK) return s;
   // divergence right-hand side (B^T u = g): the Schur right-hand side is
   // B^T A^-1 f - g (Eq. flr:schur with -g); g's components along the kernel
@@ -2265,7 +2290,10 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, const lr_mat* g, lr_
   if (!x.gmres && (s = copy_lr(x, n, x.R, x.D)) != LR_OK) return s;
   while (!x.gmres && it < maxit && nr0 > 0.0 && std::sqrt(rr) > tol * nr0 && x.D.r > 0) {
     // q = (B^T A^-1 B) d
-    if ((s = grad_solve(x, x.D, &rx, &ry)) != LR_OK) return s;
+    {
+      VelocityPrecision vp(x, o.eps);
+      if ((s = grad_solve(x, x.D, &rx, &ry)) != LR_OK) return s;
+    }
     // q enters r - alpha q with alpha = O(1) (the Schur spectrum lies in
     // (0, 1]): rounded to a tenth of the residual's absolute level
     if ((s = div_round(x, rx, ry, x.Q, 0.1 * kCgFloor * x.eps * nr0)) != LR_OK) return s;
@@ -2339,10 +2367,13 @@ lr_status stokes_uzawa(lr_handle h, int n, const lr_mat* f, const lr_mat* g, lr_
     }
   }
   // the solutions go straight into the caller's buffers
-  lr_options of = x.oin;
   std::vector<Plan*> plans(2, x.plan);
-  s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, u, of, plans, nullptr, false)
-                             : solve2d_batched<double>(h, 2, rhs, u, of, plans, nullptr, false);
+  {
+    VelocityPrecision vp(x, o.eps);
+    lr_options of = x.oin;
+    s = x.oin.prec == LR_MIXED ? solve2d_batched<float>(h, 2, rhs, u, of, plans, nullptr, false)
+                               : solve2d_batched<double>(h, 2, rhs, u, of, plans, nullptr, false);
+  }
   if (s != LR_OK && s != LR_ENOCONV) return s;
   // divergence of the final velocity, relative to ||B^T A^-1 f||
   for (int k = 0; k < 2; ++k) {

@@ -150,3 +150,17 @@ def test_stokes_resumes_from_a_saved_pressure(lr, h, gmres):
     ref = S.uzawa_cg(f1, f2, n, tol=1e-13)
     p = dense(res.p)
     assert np.linalg.norm(p - ref.p) <= 1e-7 * np.linalg.norm(ref.p)
+
+
+def test_stokes_mixed_reaches_the_tolerance_at_larger_n(lr, h):
+    # config 4's tolerance at n = 1024: the mixed path runs the velocity solves
+    # of the Schur products in float64 when the accuracy they need (a tenth of
+    # eps) is below what float32 solves resolve, so CG reaches tol_div in about
+    # as many iterations as the float64 path
+    n, eps, tol = 1024, 1e-7, 1e-6
+    fdev, _ = body_force_dev(n)
+    mixed = lr.lr_stokes_uzawa(h, n, fdev, tol_div=tol, eps=eps, prec="mixed", maxit=60)
+    assert mixed.status == lr.LR_OK, h.last_error()
+    fp64 = lr.lr_stokes_uzawa(h, n, fdev, tol_div=tol, eps=eps, prec="fp64", maxit=60)
+    assert fp64.status == lr.LR_OK
+    assert mixed.history[-1] <= tol and abs(mixed.iters - fp64.iters) <= 2, (mixed.iters, fp64.iters)
