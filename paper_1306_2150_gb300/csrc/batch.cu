@@ -964,6 +964,7 @@ __device__ __forceinline__ T bx_transpose_sum(T (&a)[DC], int lane) {
 template <typename T>
 struct BxProb {
   int m, r, ld, kcap, row0, row1, cs, rank;
+  bool full;  // all RPT indices of this thread are in its CTA's slice
   const T* Uh;
   const T* Vh;
   T* C;
@@ -995,9 +996,15 @@ struct BxPivot {
 
 // out[s] = (vec . F[j]) / (pa b_j + pb a_j) - sum_{l<k} craw[l] d[l] X[j, l]
 // for the owned indices (0 elsewhere); vec, craw, pa, pb from the pivot data.
-template <typename T, int RPT>
-__device__ __forceinline__ void bx_eval(const BxProb<T>& p, const T* __restrict__ F, const T* __restrict__ X, int k,
-                                        const BxPivot<T>& pv, const T* d, T (&out)[RPT]) {
+// Index s of the thread is in its CTA's slice (always, for FULL threads).
+template <bool FULL, typename T>
+__device__ __forceinline__ bool bx_in(const BxProb<T>& p, int base, int s) {
+  return FULL || base + s * BX_NT < p.row1;
+}
+
+template <typename T, int RPT, bool FULL>
+__device__ __forceinline__ void bx_eval_t(const BxProb<T>& p, const T* __restrict__ F, const T* __restrict__ X, int k,
+                                          const BxPivot<T>& pv, const T* d, T (&out)[RPT]) {
   const int base = p.row0 + threadIdx.x;
   const T* vec = pv.cand + 2;
 #pragma unroll
@@ -1008,13 +1015,13 @@ __device__ __forceinline__ void bx_eval(const BxProb<T>& p, const T* __restrict_
     const T* Fc = F + (size_t)al * p.ld + base;
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if (base + s * BX_NT < p.row1) out[s] += w * __ldg(&Fc[s * BX_NT]);
+      if (bx_in<FULL>(p, base, s)) out[s] += w * __ldg(&Fc[s * BX_NT]);
   }
   const T pa = pv.cand[0], pb = pv.cand[1];
 #pragma unroll
   for (int s = 0; s < RPT; ++s) {
     const int j = base + s * BX_NT;
-    out[s] = j < p.row1 ? bx_ratio<T>(out[s], pa * __ldg(&p.b[j]) + pb * __ldg(&p.a[j])) : T(0);
+    out[s] = bx_in<FULL>(p, base, s) ? bx_ratio<T>(out[s], pa * __ldg(&p.b[j]) + pb * __ldg(&p.a[j])) : T(0);
   }
   const T* craw = pv.cand + 2 + p.r;
 #pragma unroll 8
@@ -1023,8 +1030,17 @@ __device__ __forceinline__ void bx_eval(const BxProb<T>& p, const T* __restrict_
     const T* Xc = X + (size_t)l * p.ld + base;
 #pragma unroll
     for (int s = 0; s < RPT; ++s)
-      if (base + s * BX_NT < p.row1) out[s] -= c * Xc[s * BX_NT];
+      if (bx_in<FULL>(p, base, s)) out[s] -= c * Xc[s * BX_NT];
   }
+}
+
+// Threads whose indices all lie in the slice (every thread but the last few
+// of a problem's last CTA) run the loops without per-index tests.
+template <typename T, int RPT>
+__device__ __forceinline__ void bx_eval(const BxProb<T>& p, const T* __restrict__ F, const T* __restrict__ X, int k,
+                                        const BxPivot<T>& pv, const T* d, T (&out)[RPT]) {
+  if (p.full) bx_eval_t<T, RPT, true>(p, F, X, k, pv, d, out);
+  else bx_eval_t<T, RPT, false>(p, F, X, k, pv, d, out);
 }
 
 // Start score ||Uh[j]||^2 / Lambda[j, 0]^2 of the owned indices.
@@ -1093,22 +1109,29 @@ __device__ __forceinline__ BxRed<T> bx_reduce(const BxProb<T>& p, const T (&v)[R
   // dot products DC columns at a time (8 where two CTAs share an SM's
   // registers, 16 otherwise)
   constexpr int DC = bx_two_per_sm<T, RPT>() ? 8 : 16;
-  for (int l0 = 0; l0 < kd; l0 += DC) {
-    T acc[DC];
+  auto dots = [&](auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    for (int l0 = 0; l0 < kd; l0 += DC) {
+      T acc[DC];
 #pragma unroll
-    for (int i = 0; i < DC; ++i) {
-      acc[i] = T(0);
-      const int l = l0 + i;
-      if (l < kd) {
-        const T* Xc = Xd + (size_t)l * p.ld + base;
+      for (int i = 0; i < DC; ++i) {
+        acc[i] = T(0);
+        const int l = l0 + i;
+        if (l < kd) {
+          const T* Xc = Xd + (size_t)l * p.ld + base;
 #pragma unroll
-        for (int s = 0; s < RPT; ++s)
-          if (base + s * BX_NT < p.row1) acc[i] += Xc[s * BX_NT] * v[s];
+          for (int s = 0; s < RPT; ++s)
+            if (bx_in<FULL>(p, base, s)) acc[i] += Xc[s * BX_NT] * v[s];
+        }
       }
+      const T x = bx_transpose_sum<DC>(acc, lane);
+      if (lane < DC && l0 + lane < kd) slot[BX_DOTS + l0 + lane] = x;
     }
-    const T x = bx_transpose_sum<DC>(acc, lane);
-    if (lane < DC && l0 + lane < kd) slot[BX_DOTS + l0 + lane] = x;
-  }
+  };
+  // the transpose sums are warp-collective: a warp with both kinds of
+  // threads runs the tested loop in all of them
+  if (__all_sync(0xffffffffu, p.full)) dots(std::true_type{});
+  else dots(std::false_type{});
 #pragma unroll
   for (int u = 0; u < CV; ++u)
     if (lane + 32 * u < ncand) slot[BX_CND + lane + 32 * u] = cv[u];
@@ -1231,6 +1254,7 @@ __global__ void __launch_bounds__(BX_NT, bx_two_per_sm<T, RPT>() ? 2 : 1) bcross
   SolveState* st = B.st;
   const T tol2 = (T)(cp.tol * cp.tol);
   const int base = p.row0 + tid;
+  p.full = base + (RPT - 1) * BX_NT < p.row1;
   unsigned own = 0;
 #pragma unroll
   for (int s = 0; s < RPT; ++s)
