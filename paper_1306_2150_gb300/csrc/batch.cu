@@ -876,18 +876,20 @@ template cudaError_t launch_batch_rotate<double>(const BatchProb*, const BatchIt
 // Batched cross.  Every thread of the cluster holds the state of the cross
 // (step, pivots, norm estimate, stop counters) in registers and takes every
 // decision itself from reductions whose results are identical in every warp
-// and every CTA, so a half-step needs one CTA barrier (and, in a cluster,
-// one cluster barrier) and no broadcast of decisions:
+// and every CTA, so no decision is broadcast:
 //   1. residual entries of the owned indices (F = Uh or Vh, X = C or R);
 //   2. warp partials -- argmax (lowest index on ties), sum of squares, dot
 //      products with the columns of X, and the pivot data of the warp's own
 //      candidate (its rows of F and X and its symbol) -- into a slot per warp;
-//   3. CTA barrier; every warp combines the slots in warp order;
+//   3. CTA barrier; warp 0 combines the slots in warp order;
 //   4. cluster: warp 0 pushes the CTA result into a slot per CTA in every
-//      CTA's inbox (distributed shared memory); cluster barrier; every warp
-//      combines the inbox in rank order.
-// Slots and inboxes alternate between two buffers, so a buffer is rewritten
-// only after a barrier that every reader of its previous contents has passed.
+//      CTA's inbox (distributed shared memory); cluster barrier; warp 0
+//      combines the inbox in rank order;
+//   5. warp 0 writes the combined result to shared memory; CTA barrier;
+//      every warp reads it.
+// Slots, inboxes and results alternate between two buffers, so a buffer is
+// rewritten only after a barrier that every reader of its previous contents
+// has passed.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -897,6 +899,7 @@ constexpr int BX_CAND = 2 * KMAX + 3; // pivot data: a, b, F row (<= KMAX), X ro
 // words of a slot: header, dot products, pivot data
 constexpr int BX_ABS = 0, BX_VAL = 1, BX_SSQ = 2, BX_IDX = 3, BX_DOTS = 4, BX_CND = BX_DOTS + KMAX;
 constexpr int BX_WORDS = BX_CND + BX_CAND;
+constexpr int BX_RES = 4 + KMAX;  // result words: index, value, sum of squares, winner slot, dots
 
 __device__ __forceinline__ unsigned long long bx_splitmix64_at(unsigned long long state, unsigned long long t) {
   unsigned long long z = state + t * 0x9E3779B97F4A7C15ULL;
@@ -973,6 +976,7 @@ struct BxProb {
   const T* b;
   T* slots;   // [2][NW][BX_WORDS]
   T* inbox;   // [2][cs][BX_WORDS]
+  T* res;     // [2][BX_RES]: the CTA's combined result
 };
 
 // Result of a reduction, identical in every thread of the cluster.
@@ -1142,79 +1146,83 @@ __device__ __forceinline__ BxRed<T> bx_reduce(const BxProb<T>& p, const T (&v)[R
     slot[BX_IDX] = (T)(bidx == INT_MAX ? -1 : bidx);
   }
   __syncthreads();
-  // every warp: combine the warp slots in warp order
+  // warp 0 combines the warp slots in warp order (and, in a cluster, pushes
+  // the CTA result into every CTA's inbox and combines the inbox in rank
+  // order) and writes the result for every warp of the CTA
   const T* sl = p.slots + (size_t)par * BX_NW * BX_WORDS;
-  T a = T(-1), vv = T(0), ss = T(0);
-  int i = INT_MAX, sw = 0;
-  if (lane < BX_NW) {
-    const T* q = sl + (size_t)lane * BX_WORDS;
-    const int qi = (int)q[BX_IDX];
-    ss = q[BX_SSQ];
-    if (qi >= 0) { a = q[BX_ABS]; i = qi; vv = q[BX_VAL]; }
-    sw = lane;
-  }
-  bx_warp_argmax(a, i, vv, sw);
-  ss = bx_warp_sum(ss);
-  T dlo = T(0), dhi = T(0);
-  for (int w = 0; w < BX_NW; ++w) {
-    if (lane < kd) dlo += sl[(size_t)w * BX_WORDS + BX_DOTS + lane];
-    if (lane + 32 < kd) dhi += sl[(size_t)w * BX_WORDS + BX_DOTS + lane + 32];
-  }
-  BxRed<T> res;
-  if (p.cs == 1) {
-    res.idx = i == INT_MAX ? -1 : i;
-    res.val = vv;
-    res.ssq = ss;
-    res.dlo = dlo;
-    res.dhi = dhi;
-    res.cand = sl + (size_t)sw * BX_WORDS + BX_CND;
-    par ^= 1;
-    return res;
-  }
-  // cluster: warp 0 pushes this CTA's result into slot `rank` of every
-  // CTA's inbox, then every warp combines the inbox in rank order
-  cg::cluster_group cl = cg::this_cluster();
+  const T* ib = p.inbox + (size_t)par * p.cs * BX_WORDS;
+  T* rs = p.res + (size_t)par * BX_RES;
+  auto combine = [&](const T* base, int nq, int& i, T& a, T& vv, T& ss, int& sw, T& dlo, T& dhi) {
+    a = T(-1); vv = T(0); ss = T(0); i = INT_MAX; sw = 0;
+    if (lane < nq) {
+      const T* q = base + (size_t)lane * BX_WORDS;
+      const int qi = (int)q[BX_IDX];
+      ss = q[BX_SSQ];
+      if (qi >= 0) { a = q[BX_ABS]; i = qi; vv = q[BX_VAL]; }
+      sw = lane;
+    }
+    bx_warp_argmax(a, i, vv, sw);
+    ss = bx_warp_sum(ss);
+    dlo = T(0);
+    dhi = T(0);
+    for (int w = 0; w < nq; ++w) {
+      if (lane < kd) dlo += base[(size_t)w * BX_WORDS + BX_DOTS + lane];
+      if (lane + 32 < kd) dhi += base[(size_t)w * BX_WORDS + BX_DOTS + lane + 32];
+    }
+  };
+  auto publish = [&](int i, T vv, T ss, int sw, T dlo, T dhi) {
+    if (lane == 0) {
+      rs[0] = (T)(i == INT_MAX ? -1 : i);
+      rs[1] = vv;
+      rs[2] = ss;
+      rs[3] = (T)sw;
+    }
+    if (lane < kd) rs[4 + lane] = dlo;
+    if (lane + 32 < kd) rs[4 + lane + 32] = dhi;
+  };
   if (warp == 0) {
-    T* dst0 = p.inbox + ((size_t)par * p.cs + p.rank) * BX_WORDS;
-    const T* wc = sl + (size_t)sw * BX_WORDS + BX_CND;
-    for (int qd = 0; qd < p.cs; ++qd) {
-      T* dq = cl.map_shared_rank(dst0, qd);
-      if (lane == 0) {
-        dq[BX_ABS] = a;
-        dq[BX_VAL] = vv;
-        dq[BX_SSQ] = ss;
-        dq[BX_IDX] = (T)(i == INT_MAX ? -1 : i);
+    int i, sw;
+    T a, vv, ss, dlo, dhi;
+    combine(sl, BX_NW, i, a, vv, ss, sw, dlo, dhi);
+    if (p.cs == 1) {
+      publish(i, vv, ss, sw, dlo, dhi);
+    } else {
+      // push this CTA's result into slot `rank` of every CTA's inbox
+      cg::cluster_group cl = cg::this_cluster();
+      T* dst0 = p.inbox + ((size_t)par * p.cs + p.rank) * BX_WORDS;
+      const T* wc = sl + (size_t)sw * BX_WORDS + BX_CND;
+      for (int qd = 0; qd < p.cs; ++qd) {
+        T* dq = cl.map_shared_rank(dst0, qd);
+        if (lane == 0) {
+          dq[BX_ABS] = a;
+          dq[BX_VAL] = vv;
+          dq[BX_SSQ] = ss;
+          dq[BX_IDX] = (T)(i == INT_MAX ? -1 : i);
+        }
+        if (lane < kd) dq[BX_DOTS + lane] = dlo;
+        if (lane + 32 < kd) dq[BX_DOTS + lane + 32] = dhi;
+        if (i != INT_MAX)
+          for (int w = lane; w < ncand; w += 32) dq[BX_CND + w] = wc[w];
       }
-      if (lane < kd) dq[BX_DOTS + lane] = dlo;
-      if (lane + 32 < kd) dq[BX_DOTS + lane + 32] = dhi;
-      if (i != INT_MAX)
-        for (int w = lane; w < ncand; w += 32) dq[BX_CND + w] = wc[w];
     }
   }
-  cl.sync();
-  const T* ib = p.inbox + (size_t)par * p.cs * BX_WORDS;
-  a = T(-1); vv = T(0); ss = T(0); i = INT_MAX; sw = 0;
-  if (lane < p.cs) {
-    const T* q = ib + (size_t)lane * BX_WORDS;
-    const int qi = (int)q[BX_IDX];
-    ss = q[BX_SSQ];
-    if (qi >= 0) { a = q[BX_ABS]; i = qi; vv = q[BX_VAL]; }
-    sw = lane;
+  if (p.cs > 1) {
+    cg::this_cluster().sync();
+    if (warp == 0) {
+      int i, sw;
+      T a, vv, ss, dlo, dhi;
+      combine(ib, p.cs, i, a, vv, ss, sw, dlo, dhi);
+      publish(i, vv, ss, sw, dlo, dhi);
+    }
   }
-  bx_warp_argmax(a, i, vv, sw);
-  ss = bx_warp_sum(ss);
-  dlo = T(0);
-  dhi = T(0);
-  for (int q = 0; q < p.cs; ++q) {
-    if (lane < kd) dlo += ib[(size_t)q * BX_WORDS + BX_DOTS + lane];
-    if (lane + 32 < kd) dhi += ib[(size_t)q * BX_WORDS + BX_DOTS + lane + 32];
-  }
-  res.idx = i == INT_MAX ? -1 : i;
-  res.val = vv;
-  res.ssq = ss;
-  res.dlo = dlo;
-  res.dhi = dhi;
-  res.cand = ib + (size_t)sw * BX_WORDS + BX_CND;
+  __syncthreads();
+  BxRed<T> res;
+  res.idx = (int)rs[0];
+  res.val = rs[1];
+  res.ssq = rs[2];
+  res.dlo = lane < kd ? rs[4 + lane] : T(0);
+  res.dhi = lane + 32 < kd ? rs[4 + lane + 32] : T(0);
+  res.cand = (p.cs == 1 ? sl : ib) + (size_t)(int)rs[3] * BX_WORDS + BX_CND;
   par ^= 1;
   return res;
 }
@@ -1251,6 +1259,7 @@ __global__ void __launch_bounds__(BX_NT, bx_two_per_sm<T, RPT>() ? 2 : 1) bcross
   p.b = static_cast<const T*>(B.sb);
   p.slots = reinterpret_cast<T*>(bx_dyn);
   p.inbox = p.slots + 2 * BX_NW * BX_WORDS;
+  p.res = p.inbox + 2 * cs * BX_WORDS;
   SolveState* st = B.st;
   const T tol2 = (T)(cp.tol * cp.tol);
   const int base = p.row0 + tid;
@@ -1416,7 +1425,7 @@ template <typename T, int RPT>
 cudaError_t launch_bcross_rpt(const BatchProb* probs, const int* list, int n, int cs,
                               const BatchCrossParams& cp, cudaStream_t st) {
   auto kern = bcross_kernel<T, RPT>;
-  const size_t smax = (size_t)(2 * BX_NW + 2 * 16) * BX_WORDS * sizeof(T);
+  const size_t smax = ((size_t)(2 * BX_NW + 2 * 16) * BX_WORDS + 2 * BX_RES) * sizeof(T);
   static cudaError_t attr = [&] {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1426,7 +1435,7 @@ cudaError_t launch_bcross_rpt(const BatchProb* probs, const int* list, int n, in
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n * cs), 1, 1);
   cfg.blockDim = dim3(BX_NT, 1, 1);
-  cfg.dynamicSmemBytes = (size_t)(2 * BX_NW + 2 * cs) * BX_WORDS * sizeof(T);
+  cfg.dynamicSmemBytes = ((size_t)(2 * BX_NW + 2 * cs) * BX_WORDS + 2 * BX_RES) * sizeof(T);
   cfg.stream = st;
   cudaLaunchAttribute attr_[1];
   attr_[0].id = cudaLaunchAttributeClusterDimension;
