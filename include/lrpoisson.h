@@ -41,7 +41,9 @@ typedef enum {
   LR_ENOMEM = 2,     /* device or pinned allocation failed */
   LR_ENOCONV = 3,    /* cross hit its step cap or the rank was cut to capacity;
                         the best partial result is written */
-  LR_ETIMEOUT = 4,   /* a bounded device wait ran out */
+  LR_ETIMEOUT = 4,   /* reserved for a bounded device wait that ran out; no
+                        kernel of this library waits on a flag (every loop
+                        and barrier is bounded), so it is not returned */
   LR_ECUDA = 5,      /* a CUDA runtime call failed */
   LR_ENONFINITE = 6  /* a non-finite value reached the rounding core (in
                         LR_MIXED: entries of the frequency-space solution
