@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_GRID)
     p.add_argument("--batch", type=int, default=64)
+    p.add_argument("--batch-sweep", type=int, nargs="*", default=[16, 72, 152],
+                   help="other batch sizes of the mixed batched step (ms per solve, context)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--crossover", type=int, nargs="*", default=[256, 1024, 4096, 16384],
@@ -280,6 +282,7 @@ TRAFFIC_FILES = {
     "cross": ("profiles/batch_cross_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
     "forward_dst": ("profiles/batch_dst_forward_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
     "inverse_dst": ("profiles/batch_dst_inverse_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
+    "rounding": ("profiles/batch_rounding_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
 }
 
 
@@ -664,6 +667,31 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                                     "phases": {k: statistics.median([p[k] for p in ph]) for k in ph[0]},
                                     "streams_ms_step": statistics.median(per_s)}
         del batch
+    # ---- the same step at other batch sizes (mixed, graph replay; context for
+    # the choice of 64: at two CTAs per SM and four per problem 72 clusters
+    # fit one wave of the cross, and the transforms fill the SMs in whole
+    # columns)
+    results["batch_sweep"] = []
+    for Bs in args.batch_sweep:
+        sp = [(torch.from_numpy(U) * (1.0 + p / Bs), torch.from_numpy(V)) for p in range(Bs)]
+        sb = lr.Batch(sp)
+        for _ in range(3):
+            lr.lr_poisson2d_batched(h, sb, eps=EPS, prec="mixed", graph=True)
+        per = []
+        for i in range(5):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lr.lr_poisson2d_batched(h, sb, eps=EPS, prec="mixed", graph=True, async_=True)
+            b.record(stream)
+            stream.synchronize()
+            per.append(a.elapsed_time(b))
+        err = rel_error_sampled(*sb.result(Bs - 1), *sp[Bs - 1])
+        results["batch_sweep"].append({"batch": Bs, "ms_step": round(statistics.median(per), 4),
+                                       "ms_per_solve": round(statistics.median(per) / Bs, 5),
+                                       "rel_err_last": float(f"{err:.3e}")})
+        del sb
     # ---- end to end through the C ABI: host factors in, host factors out.
     # The batch's input factors are views into one device buffer filled by one
     # copy from one pinned host buffer; the kept factors and singular values
@@ -683,6 +711,7 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         off += sz
     batch = lr.Batch(views)
     host_out = torch.empty(B * (2 * n * 64 + 64), dtype=torch.float64).pin_memory()
+    din.copy_(hin)
     for _ in range(max(2, args.warmup)):
         lr.lr_poisson2d_batched(h, batch, eps=EPS, prec="mixed", graph=True)
     e2e = []
@@ -788,6 +817,24 @@ def main():
     dom = max(("forward_dst", "cross", "rounding", "inverse_dst"), key=lambda k: bph[k])
     byts = B * alg[dom]
     achieved = byts / (bph[dom] * 1e-3) / 1e9
+    # every phase against HBM; the transforms also against the FP32 FMA peak
+    # (152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s): 5 H log2 H
+    # flops per H-point FFT, two per residue class, M / H classes per column
+    M = 1 << max(6, (2 * n - 1 - 1).bit_length())
+    H = min(M, 16384)
+    fft_flops_col = (M // H) * 2 * 5 * H * (H.bit_length() - 1)
+    fp32_peak = 152 * 128 * 2 * 2.07e9
+    cols = {"forward_dst": 2 * mx["r"], "inverse_dst": 2 * mx["rank"]}
+    phase_roof = {}
+    for k in ("forward_dst", "cross", "rounding", "inverse_dst"):
+        gbs = B * alg[k] / (bph[k] * 1e-3) / 1e9
+        ent = {"ms": round(bph[k], 4), "algorithmic_bytes": B * alg[k], "gbs": round(gbs, 2),
+               "hbm_frac": round(gbs / hbm, 5), "traffic": committed_traffic(k)}
+        if k in cols:
+            fl = B * cols[k] * fft_flops_col
+            ent.update({"fft_flops": fl, "fp32_tflops": round(fl / (bph[k] * 1e-3) / 1e12, 3),
+                        "fp32_frac": round(fl / (bph[k] * 1e-3) / fp32_peak, 4)})
+        phase_roof[k] = ent
     acc = {"single_mixed": mx["rel_err"], "single_fp64": f64["rel_err"],
            "batch_mixed_max": bm["max_rel_err"], "batch_fp64_max": bf["max_rel_err"],
            "tight_fp64": res["tight_fp64"]["rel_err"], "tight_mixed_refined": res["tight_mixed"]["rel_err"]}
@@ -835,6 +882,7 @@ def main():
         "expsum_vs_cross": res["expsum"],
         "tucker3d": res["tucker"],
         "uneven_batch": res["uneven"],
+        "batch_size_sweep": res.get("batch_sweep", []),
         "mixed_batched_over_fp64_single": round(f64["ms"] / value, 2),
         "mixed_batched_over_fp64_batched": round(bf["ms_step"] / bm["ms_step"], 2),
         "batched_effective_gbs": round(alg_total * B / (bm["ms_step"] * 1e-3) / 1e9, 2),
@@ -843,6 +891,7 @@ def main():
                      "traffic": committed_traffic(dom), "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": byts, "launch_ms": round(bph[dom], 4),
                      "problems_per_launch": B},
+        "phase_rooflines": phase_roof,
         "autotune": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                      for k, v in res["autotune"].items()},
         "e2e": {"value": round(eb["ms_step"] / eb["batch"], 5), "unit": "ms", "h2d_bytes_per_step": eb["h2d"],
