@@ -216,6 +216,17 @@ lr_status lr_poisson2d(lr_handle h, const lr_mat* rhs, lr_mat* sol, const lr_opt
 lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol,
                                const lr_options* opt, lr_status* per_problem);
 
+/* Results of an asynchronous lr_poisson2d_batched (LR_FLAG_ASYNC; the paper
+ * has no counterpart): once the caller has synchronised the handle's stream
+ * after that call, writes sol[i].r (the kept rank of problem i) and, if
+ * per_problem is not NULL, its status, as the synchronous call would have.
+ * sol and per_problem are host arrays of the first `batch` problems of that
+ * call; the factors themselves are already in the caller's buffers.  Returns
+ * LR_OK or the first failure of those problems; LR_EINVAL if batch exceeds
+ * the last batched call on this handle.  Reads the handle's status record:
+ * call it before the next batched call on the same handle. */
+lr_status lr_batched_status(lr_handle h, int batch, lr_mat* sol, lr_status* per_problem);
+
 /* Rounding (recompression) of X = U diag(s) V^T in place (Section 3): QR of
  * both factors, SVD of the r x r core, truncation at relative Frobenius
  * tolerance eps, at most min(rmax, X->rmax) columns kept.  float64

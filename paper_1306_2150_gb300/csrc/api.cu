@@ -76,6 +76,7 @@ struct lr_handle_s {
   cudaEvent_t bdesc_ev = nullptr;
   std::map<std::string, char*> graph_desc;
   int cross_rows[2] = {4096, 4096};  // indices per CTA of the batched cross (float64, float32)
+  int last_batch = 0;                // problems of the last lr_poisson2d_batched call (status record)
   int dst_fused[2] = {0, 1};         // batched transforms of M > 4096: one pass per column (1, float32
                                      // only) or the four-step passes through scratch (0); float64
                                      // keeps the four-step passes (FP64-bound either way, and faster)
@@ -867,6 +868,22 @@ lr_status ensure_batch_streams(lr_handle h) {
   return LR_OK;
 }
 
+// Per-problem ranks and statuses of a finished batched call, from the pinned
+// status record its stream wrote last.
+lr_status collect_batch(lr_handle h, int batch, lr_mat* sol, lr_status* per_problem) {
+  lr_status worst = LR_OK;
+  for (int i = 0; i < batch; ++i) {
+    const SolveState& hs = h->h_bstate[i];
+    sol[i].r = hs.rank;
+    const lr_status si = hs.status ? static_cast<lr_status>(hs.status)
+                                   : ((!hs.converged || hs.cut) ? LR_ENOCONV : LR_OK);
+    if (per_problem) per_problem[i] = si;
+    if (si != LR_OK && worst != LR_ENONFINITE) worst = si;
+  }
+  if (worst != LR_OK) fail(h, worst, "some problems did not converge or were cut (see per_problem)");
+  return worst;
+}
+
 template <typename T>
 lr_status solve2d_batched_streams(lr_handle h, int batch, const lr_mat* rhs, lr_mat* sol, const lr_options& o,
                                   const std::vector<Plan*>& plans, lr_status* per_problem) {
@@ -942,17 +959,7 @@ lr_status solve2d_batched_streams(lr_handle h, int batch, const lr_mat* rhs, lr_
   h->info.launches = launches;
   if (o.flags & LR_FLAG_ASYNC) return LR_OK;
   LR_CUDA(h, cudaStreamSynchronize(h->stream), "batched solve");
-  lr_status worst = LR_OK;
-  for (int i = 0; i < batch; ++i) {
-    const SolveState& hs = h->h_bstate[i];
-    sol[i].r = hs.rank;
-    const lr_status si = hs.status ? static_cast<lr_status>(hs.status)
-                                   : ((!hs.converged || hs.cut) ? LR_ENOCONV : LR_OK);
-    if (per_problem) per_problem[i] = si;
-    if (si != LR_OK && worst != LR_ENONFINITE) worst = si;
-  }
-  if (worst != LR_OK) fail(h, worst, "some problems did not converge or were cut (see per_problem)");
-  return worst;
+  return collect_batch(h, batch, sol, per_problem);
 }
 
 // Twiddles exp(-2 pi i q / 4096) of the batched transforms, per precision.
@@ -1314,17 +1321,7 @@ lr_status solve2d_batched_phased(lr_handle h, int batch, const lr_mat* rhs, lr_m
   h->info.launches = launches;
   if (o.flags & LR_FLAG_ASYNC) return LR_OK;
   LR_CUDA(h, cudaStreamSynchronize(h->stream), "batched solve");
-  lr_status worst = LR_OK;
-  for (int i = 0; i < batch; ++i) {
-    const SolveState& hs = h->h_bstate[i];
-    sol[i].r = hs.rank;
-    const lr_status si = hs.status ? static_cast<lr_status>(hs.status)
-                                   : ((!hs.converged || hs.cut) ? LR_ENOCONV : LR_OK);
-    if (per_problem) per_problem[i] = si;
-    if (si != LR_OK && worst != LR_ENONFINITE) worst = si;
-  }
-  if (worst != LR_OK) fail(h, worst, "some problems did not converge or were cut (see per_problem)");
-  return worst;
+  return collect_batch(h, batch, sol, per_problem);
 }
 
 // Batched solves: the phase-batched kernels when every problem fits them
@@ -2617,10 +2614,20 @@ lr_status lr_poisson2d_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat
   }
   h->info = lr_info{};
   h->timed = false;
+  h->last_batch = 0;
   s = o.prec == LR_MIXED ? solve2d_batched<float>(h, batch, rhs, sol, o, plans, per_problem)
                          : solve2d_batched<double>(h, batch, rhs, sol, o, plans, per_problem);
+  if (s == LR_OK || s == LR_ENOCONV || s == LR_ENONFINITE) h->last_batch = batch;
   h->info.status = s;
   return s;
+}
+
+lr_status lr_batched_status(lr_handle h, int batch, lr_mat* sol, lr_status* per_problem) {
+  if (!h) return LR_EINVAL;
+  if (batch < 0 || (batch > 0 && !sol)) return fail(h, LR_EINVAL, "bad batch arguments");
+  if (batch > h->last_batch)
+    return fail(h, LR_EINVAL, "batch exceeds the last batched call on this handle");
+  return collect_batch(h, batch, sol, per_problem);
 }
 
 // Autotuning: time candidate launch shapes on the caller's problem (CUDA

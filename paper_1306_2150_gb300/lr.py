@@ -36,7 +36,8 @@ EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_last_error", "lr_status_string", "lr_dst1", "lr_poisson2d",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
            "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full",
-           "lr_stokes_uzawa", "lr_poisson2d_expsum", "lr_poisson3d_tucker", "lr_set_workspace_limit")
+           "lr_stokes_uzawa", "lr_poisson2d_expsum", "lr_poisson3d_tucker", "lr_set_workspace_limit",
+           "lr_batched_status")
 
 
 class LrMat(ctypes.Structure):
@@ -126,6 +127,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_poisson2d_batched.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(LrMat),
                                          ctypes.POINTER(LrOptions), ctypes.POINTER(c_int)]
     lib.lr_poisson2d_batched.restype = c_int
+    lib.lr_batched_status.argtypes = [c_void_p, c_int, ctypes.POINTER(LrMat), ctypes.POINTER(c_int)]
+    lib.lr_batched_status.restype = c_int
     lib.lr_autotune.argtypes = [c_void_p, ctypes.POINTER(LrMat), ctypes.POINTER(LrOptions), c_int,
                                 ctypes.POINTER(LrTune)]
     lib.lr_autotune.restype = c_int
@@ -400,6 +403,15 @@ class Batch:
         R = self.c_sol[i].r
         Uo, s, Vo = self.out[i]
         return Uo[:, :R], s[:R], Vo[:, :R]
+
+
+def lr_batched_status(h: Handle, batch: Batch, check: bool = True) -> int:
+    """Ranks and statuses of the last asynchronous lr_poisson2d_batched on h
+    (after the caller synchronised its stream) into ``batch``."""
+    st = load().lr_batched_status(h.ptr, len(batch), batch.c_sol, batch.status)
+    if check and st not in (LR_OK, LR_ENOCONV):
+        raise LrError(st, h.last_error())
+    return st
 
 
 def lr_poisson2d_batched(h: Handle, batch: Batch, eps: float = 1e-6, prec="mixed", op="5pt",

@@ -228,3 +228,23 @@ def test_autotune_batched(lr, h, streams):
     for i, (U, V) in enumerate(probs):
         Ub, sb, Vb = (npy(x) for x in batch.result(i))
         assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt") <= 1e-5
+
+
+def test_async_batch_then_status(lr, h):
+    # LR_FLAG_ASYNC: the call returns before the stream finishes; after a
+    # synchronisation lr_batched_status gives the ranks and statuses the
+    # synchronous call reports, and the factors equal the synchronous ones
+    probs = _problems(10, 300, 6000, 12, seed=21)
+    sync_b = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
+    async_b = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
+    assert lr.lr_poisson2d_batched(h, sync_b, eps=1e-6, prec="mixed") == lr.LR_OK
+    assert lr.lr_poisson2d_batched(h, async_b, eps=1e-6, prec="mixed", async_=True) == lr.LR_OK
+    torch.cuda.synchronize()
+    assert lr.lr_batched_status(h, async_b) == lr.LR_OK
+    for i in range(len(probs)):
+        assert async_b.c_sol[i].r == sync_b.c_sol[i].r > 0 and async_b.status[i] == lr.LR_OK
+        for a, b in zip(async_b.result(i), sync_b.result(i)):
+            assert torch.equal(a, b)
+    # a larger batch than the last call is rejected
+    big = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs + probs[:1]])
+    assert lr.lr_batched_status(h, big, check=False) == lr.LR_EINVAL
