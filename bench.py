@@ -709,7 +709,7 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         off += sz
     e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     e2e_h = [lr.Handle(st_) for st_ in e2e_streams]
-    dins, e2e_b, houts = [], [], []
+    dins, e2e_b, houts, obufs, sbufs = [], [], [], [], []
     for k2 in range(2):
         din = torch.empty(sum(sizes), dtype=torch.float64, device="cuda")
         views, off = [], 0
@@ -718,8 +718,20 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
             views.append((din[off: off + n * r].view(r, n).t(), din[off + n * r: off + sz].view(r, n).t()))
             off += sz
         dins.append(din)
-        e2e_b.append(lr.Batch(views))
-        houts.append(torch.empty(B * (2 * n * 64 + 64), dtype=torch.float64).pin_memory())
+        # outputs of all problems in one buffer, [problem][U columns, V columns][n], so
+        # that the kept columns are gathered by one index_select
+        obuf = torch.empty((B, 128, n), dtype=torch.float64, device="cuda")
+        sbuf = torch.empty((B, 64), dtype=torch.float64, device="cuda")
+        bb = lr.Batch(views)
+        for p in range(B):
+            Uo, Vo, so = obuf[p, :64].t(), obuf[p, 64:].t(), sbuf[p]
+            bb.out[p] = (Uo, so, Vo)
+            bb.c_sol[p] = lr.LrMat(n, n, 0, 64, n, Uo.data_ptr(), so.data_ptr(), Vo.data_ptr())
+        obufs.append(obuf)
+        sbufs.append(sbuf)
+        e2e_b.append(bb)
+        houts.append((torch.empty((2 * 64 * B, n), dtype=torch.float64).pin_memory(),
+                      torch.empty(64 * B, dtype=torch.float64).pin_memory()))
     torch.cuda.synchronize()
     for k2 in range(2):
         with torch.cuda.stream(e2e_streams[k2]):
@@ -734,34 +746,42 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         nonlocal d2h
         ev.synchronize()
         lr.lr_batched_status(e2e_h[k2], e2e_b[k2])
+        ranks = np.array([e2e_b[k2].c_sol[p].r for p in range(B)])
+        cols = np.concatenate([np.r_[p * 128 + np.arange(R), p * 128 + 64 + np.arange(R)]
+                               for p, R in enumerate(ranks)]).astype(np.int64)
+        svals = np.concatenate([p * 64 + np.arange(R) for p, R in enumerate(ranks)]).astype(np.int64)
         with torch.cuda.stream(e2e_streams[k2]):
-            parts = []
-            for p in range(B):
-                Uo, so, Vo = e2e_b[k2].result(p)
-                parts += [Uo.t().reshape(-1), Vo.t().reshape(-1), so]
-            dout = torch.cat(parts)
-            houts[k2][: dout.numel()].copy_(dout, non_blocking=True)
-        d2h = dout.numel() * 8
+            ci = torch.from_numpy(cols).cuda(non_blocking=True)
+            si = torch.from_numpy(svals).cuda(non_blocking=True)
+            kept = obufs[k2].view(B * 128, n).index_select(0, ci)
+            sk = sbufs[k2].view(-1).index_select(0, si)
+            houts[k2][0][: kept.shape[0]].copy_(kept, non_blocking=True)
+            houts[k2][1][: sk.shape[0]].copy_(sk, non_blocking=True)
+        d2h = (kept.numel() + sk.numel()) * 8
 
-    nsteps = max(4, args.steps)
+    def run(nsteps):
+        pending = None
+        for i in range(nsteps):
+            k2 = i % 2
+            with torch.cuda.stream(e2e_streams[k2]):
+                dins[k2].copy_(hin, non_blocking=True)
+            lr.lr_poisson2d_batched(e2e_h[k2], e2e_b[k2], eps=EPS, prec="mixed", graph=True, async_=True)
+            ev = torch.cuda.Event()
+            ev.record(e2e_streams[k2])
+            if pending is not None:
+                finish(*pending)
+            pending = (k2, ev)
+        finish(*pending)
+
+    run(4)  # warm-up of the whole pipeline (gather buffers, graph replays)
+    nsteps = max(8, args.steps)
     flush.fill_(3)
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(e2e_streams[0])
     e2e_streams[1].wait_event(t_start)
-    pending = None
-    for i in range(nsteps):
-        k2 = i % 2
-        with torch.cuda.stream(e2e_streams[k2]):
-            dins[k2].copy_(hin, non_blocking=True)
-        lr.lr_poisson2d_batched(e2e_h[k2], e2e_b[k2], eps=EPS, prec="mixed", graph=True, async_=True)
-        ev = torch.cuda.Event()
-        ev.record(e2e_streams[k2])
-        if pending is not None:
-            finish(*pending)
-        pending = (k2, ev)
-    finish(*pending)
+    run(nsteps)
     e2e_streams[0].wait_stream(e2e_streams[1])
     t_end.record(e2e_streams[0])
     t_end.synchronize()
