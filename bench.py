@@ -696,9 +696,10 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     # Every step copies all 64 problems' U and V from one pinned host buffer
     # into one device buffer (the batch's input factors are views of it),
     # solves, gathers every problem's kept factors and singular values on the
-    # device (one kernel) and copies them to pinned host memory.  Two handles
-    # on two streams alternate steps, so one step's copies overlap the other
-    # step's solve; the time is the whole run over both streams.
+    # device (one kernel) and copies them to pinned host memory.  The solves run
+    # back to back on one stream; a step's input copy (on a copy stream) and
+    # its gather and read-back (on a third stream) overlap the neighbouring
+    # steps' solves; the time is the whole run over the three streams.
     sizes = [2 * n * U.shape[1] for U, _ in probs]
     hin = torch.empty(sum(sizes), dtype=torch.float64).pin_memory()
     off = 0
@@ -707,8 +708,11 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         hin[off: off + n * r].copy_(U.t().reshape(-1))
         hin[off + n * r: off + sz].copy_(V.t().reshape(-1))
         off += sz
-    e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    e2e_h = [lr.Handle(st_) for st_ in e2e_streams]
+    # streams: solves (back to back), input copies, gathers and read-backs;
+    # two input, output and gather buffers (one per step parity), one handle
+    # per parity, both on the solve stream
+    cs_, xs_, gs_ = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    e2e_h = [lr.Handle(cs_) for _ in range(2)]
     dins, e2e_b, houts, obufs, sbufs = [], [], [], [], []
     for k2 in range(2):
         din = torch.empty(sum(sizes), dtype=torch.float64, device="cuda")
@@ -734,44 +738,59 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                       torch.empty(64 * B, dtype=torch.float64).pin_memory()))
     torch.cuda.synchronize()
     for k2 in range(2):
-        with torch.cuda.stream(e2e_streams[k2]):
-            dins[k2].copy_(hin)
+        dins[k2].copy_(hin)
         for _ in range(max(2, args.warmup)):
             lr.lr_poisson2d_batched(e2e_h[k2], e2e_b[k2], eps=EPS, prec="mixed", graph=True)
     torch.cuda.synchronize()
     h2d = d2h = 0
+    # gather indices through pinned memory (a pageable copy would block the host
+    # until the gather stream reached it); a parity's buffer is rewritten only
+    # after its previous gather, which the next solve of that parity waits for
+    idx_host = [torch.empty(2 * 64 * B, dtype=torch.int64).pin_memory() for _ in range(2)]
+    sidx_host = [torch.empty(64 * B, dtype=torch.int64).pin_memory() for _ in range(2)]
+    ev_solved = [None, None]    # solve of the step of this parity done (inputs and outputs in use until then)
+    ev_gathered = [None, None]  # its outputs gathered (the next solve of this parity may overwrite them)
 
-    def finish(k2, ev):
-        """Step on stream k2 done: its ranks, then gather and read back."""
+    def finish(k2):
+        """The last solve of parity k2 is done: its ranks, then gather and read back."""
         nonlocal d2h
-        ev.synchronize()
+        ev_solved[k2].synchronize()
         lr.lr_batched_status(e2e_h[k2], e2e_b[k2])
         ranks = np.array([e2e_b[k2].c_sol[p].r for p in range(B)])
         cols = np.concatenate([np.r_[p * 128 + np.arange(R), p * 128 + 64 + np.arange(R)]
                                for p, R in enumerate(ranks)]).astype(np.int64)
         svals = np.concatenate([p * 64 + np.arange(R) for p, R in enumerate(ranks)]).astype(np.int64)
-        with torch.cuda.stream(e2e_streams[k2]):
-            ci = torch.from_numpy(cols).cuda(non_blocking=True)
-            si = torch.from_numpy(svals).cuda(non_blocking=True)
+        idx_host[k2][: len(cols)].numpy()[:] = cols
+        sidx_host[k2][: len(svals)].numpy()[:] = svals
+        with torch.cuda.stream(gs_):
+            ci = idx_host[k2][: len(cols)].cuda(non_blocking=True)
+            si = sidx_host[k2][: len(svals)].cuda(non_blocking=True)
             kept = obufs[k2].view(B * 128, n).index_select(0, ci)
             sk = sbufs[k2].view(-1).index_select(0, si)
+            ev_gathered[k2] = torch.cuda.Event()
+            ev_gathered[k2].record(gs_)
             houts[k2][0][: kept.shape[0]].copy_(kept, non_blocking=True)
             houts[k2][1][: sk.shape[0]].copy_(sk, non_blocking=True)
         d2h = (kept.numel() + sk.numel()) * 8
 
     def run(nsteps):
-        pending = None
         for i in range(nsteps):
             k2 = i % 2
-            with torch.cuda.stream(e2e_streams[k2]):
+            with torch.cuda.stream(xs_):  # inputs of this parity: free once its last solve is done
+                if ev_solved[k2] is not None:
+                    xs_.wait_event(ev_solved[k2])
                 dins[k2].copy_(hin, non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(xs_)
+            cs_.wait_event(ev_in)
+            if ev_gathered[k2] is not None:  # outputs of this parity gathered
+                cs_.wait_event(ev_gathered[k2])
             lr.lr_poisson2d_batched(e2e_h[k2], e2e_b[k2], eps=EPS, prec="mixed", graph=True, async_=True)
-            ev = torch.cuda.Event()
-            ev.record(e2e_streams[k2])
-            if pending is not None:
-                finish(*pending)
-            pending = (k2, ev)
-        finish(*pending)
+            ev_solved[k2] = torch.cuda.Event()
+            ev_solved[k2].record(cs_)
+            if i > 0:
+                finish(1 - k2)
+        finish((nsteps - 1) % 2)
 
     run(4)  # warm-up of the whole pipeline (gather buffers, graph replays)
     nsteps = max(8, args.steps)
@@ -779,11 +798,13 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(e2e_streams[0])
-    e2e_streams[1].wait_event(t_start)
+    t_start.record(cs_)
+    xs_.wait_event(t_start)
+    gs_.wait_event(t_start)
     run(nsteps)
-    e2e_streams[0].wait_stream(e2e_streams[1])
-    t_end.record(e2e_streams[0])
+    cs_.wait_stream(gs_)
+    cs_.wait_stream(xs_)
+    t_end.record(cs_)
     t_end.synchronize()
     h2d = dins[0].numel() * 8
     e2e = [t_start.elapsed_time(t_end) / nsteps]
@@ -954,8 +975,9 @@ def main():
         "e2e": {"value": round(eb["ms_step"] / eb["batch"], 5), "unit": "ms", "h2d_bytes_per_step": eb["h2d"],
                 "d2h_bytes_per_step": eb["d2h"], "steps": eb.get("steps"),
                 "max_rel_err": float(f"{eb.get('max_rel_err', float('nan')):.3e}"),
-                "note": "pinned host factors in, kept factors out, every step; two handles on two streams "
-                        "alternate steps, so one step's copies overlap the other's solve"},
+                "note": "pinned host factors in, kept factors out, every step; solves back to back on one "
+                        "stream, each step's input copy and gather/read-back on two more streams overlap the "
+                        "neighbouring solves"},
         "gpu_launches": bm["launches"] * args.steps,
         "clocks": bm["clocks"],
     }
