@@ -124,14 +124,31 @@ def test_phased_batch_one_pass_transform_long_orders(lr, h):
     eps = 1e-6
     ms = [2500, 4097, 9000, 16385, 20000, 40000, 65536]
     probs = [inputs.separable_random(m, 6, seed=40 + i) for i, m in enumerate(ms)]
+    probs.append((np.zeros((9000, 2), order="F"), np.ones((9000, 2), order="F")))  # rank 0: no live column
     batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
     st = lr.lr_poisson2d_batched(h, batch, eps=eps, prec="mixed")
     torch.cuda.synchronize()
     assert st == lr.LR_OK and all(s == lr.LR_OK for s in batch.status)
-    for i, (U, V) in enumerate(probs):
+    assert batch.c_sol[len(probs) - 1].r == 0
+    for i, (U, V) in enumerate(probs[:-1]):
         Ub, sb, Vb = (npy(t) for t in batch.result(i))
         rows = np.unique(np.linspace(0, U.shape[0] - 1, 128).astype(int))
         assert O.rel_error_freq(Ub, sb, Vb, U, V, "5pt", rows=rows) <= 10 * eps, (i, ms[i])
+
+
+def test_phased_batch_one_pass_transform_semistaggered(lr, h):
+    # the semi-staggered operator (reading G1) through the one-pass transform
+    # and the register-resident cross, mixed, every problem within 10 eps
+    eps = 1e-6
+    probs = [inputs.separable_random(m, 8, seed=60 + i) for i, m in enumerate([5000, 7000, 12000, 16383, 4500])]
+    batch = lr.Batch([(torch.from_numpy(U), torch.from_numpy(V)) for U, V in probs])
+    st = lr.lr_poisson2d_batched(h, batch, eps=eps, prec="mixed", op="semi")
+    torch.cuda.synchronize()
+    assert st == lr.LR_OK
+    for i, (U, V) in enumerate(probs):
+        Ub, sb, Vb = (npy(t) for t in batch.result(i))
+        rows = np.unique(np.linspace(0, U.shape[0] - 1, 128).astype(int))
+        assert O.rel_error_freq(Ub, sb, Vb, U, V, "semi", rows=rows) <= 10 * eps, i
 
 
 def test_phased_batch_headline_shape(lr, h):
