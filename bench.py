@@ -277,24 +277,36 @@ class Clocks:
 
 # ---------------------------------------------------------------- ncu traffic
 # DRAM bytes per launch of each phase's kernel at this workload, from the
-# committed ncu summaries; null once the kernel source has changed since.
+# committed ncu summaries; null once the kernel source has changed since.  The
+# source hash covers the kernel's whole translation unit: the .cu file and the
+# headers it includes, in this order, concatenated.
+BATCH_TU = ["paper_1306_2150_gb300/csrc/" + f for f in
+            ("batch.cu", "fft_common.cuh", "fft_inplace.cuh", "lr_internal.h", "lr_common.cuh")]
 TRAFFIC_FILES = {
-    "cross": ("profiles/batch_cross_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
-    "forward_dst": ("profiles/batch_dst_forward_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
-    "inverse_dst": ("profiles/batch_dst_inverse_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
-    "rounding": ("profiles/batch_rounding_f32_n16384_b64.md", "paper_1306_2150_gb300/csrc/batch.cu"),
+    "cross": ("profiles/batch_cross_f32_n16384_b64.md", BATCH_TU),
+    "forward_dst": ("profiles/batch_dst_forward_f32_n16384_b64.md", BATCH_TU),
+    "inverse_dst": ("profiles/batch_dst_inverse_f32_n16384_b64.md", BATCH_TU),
+    "rounding": ("profiles/batch_rounding_f32_n16384_b64.md", BATCH_TU),
 }
 
 
-def committed_traffic(phase: str):
+def source_hash(files) -> str:
     import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(phase: str):
     import re
     ent = TRAFFIC_FILES.get(phase)
     if not ent:
         return None
     try:
         text = open(os.path.join(ROOT, ent[0])).read()
-        src = hashlib.sha256(open(os.path.join(ROOT, ent[1]), "rb").read()).hexdigest()[:16]
+        src = source_hash(ent[1])
     except OSError:
         return None
     mb = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
