@@ -12,5 +12,6 @@ Everything is plain numpy (float64) written from the paper:
   Section 4.2 (Eq. flr:div), the full-grid solve, a dense LU solve, the cross
   approximation in frequency space (Section 4.2), the rounding of Section 3 and
   the low-rank solve built from them, plus exact error evaluation by Parseval.
+* ``maxvol`` -- the maxvol row selection the cross of Section 4.2 cites.
 """
 from . import poisson_lowrank  # noqa: F401
