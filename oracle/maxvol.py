@@ -11,6 +11,10 @@ rows I are
 
     B = C C[I, :]^{-1}          (m x k, B[I, :] = identity).
 
+B[I, :] is the identity by this definition and is stored as the exact
+identity (a solve would give it only up to rounding, and a rounded 1 + 2^-52
+would look like a coefficient above 1 at delta = 0).
+
 If some |B[i, j]| > 1 + delta, putting row i in place of I[j] multiplies
 |det C[I, :]| by |B[i, j]| (Cramer: row i = sum_l B[i, l] C[I[l], :]), and
 the coefficients of the new basis follow from the old by a rank-1 update
@@ -48,8 +52,9 @@ def maxvol(C: np.ndarray, rows, delta: float, maxswaps: int, trace: bool = False
     Returns (rows, nswaps, bmax): the refined rows (position j holds the row
     whose coefficient vector is e_j), the swaps made and the final largest
     |B| (<= 1 + delta unless maxswaps ran out).  With ``trace`` also a list
-    with one (i, j, largest, second largest) per decision, the last one the
-    decision to stop, so a test can see how far each decision was from a tie.
+    with one (i, j, largest, second largest, largest outside the selected
+    rows) per decision, the last one the decision to stop, so a test can see
+    how far each decision was from a tie.
     """
     C = np.asarray(C, dtype=np.float64)
     m, k = C.shape
@@ -57,13 +62,16 @@ def maxvol(C: np.ndarray, rows, delta: float, maxswaps: int, trace: bool = False
     if len(rows) != k or len(set(rows)) != k or min(rows) < 0 or max(rows) >= m:
         raise ValueError("rows must be k distinct indices in [0, m)")
     B = coefficients(C, rows)
+    B[rows, :] = np.eye(k)
     nswaps = 0
     log = []
     while True:
         i, j, big = _largest(B)
         if trace:
             flat = np.sort(np.abs(B).ravel())
-            log.append((i, j, big, float(flat[-2]) if flat.size > 1 else 0.0))
+            out = np.delete(np.abs(B), rows, axis=0)
+            log.append((i, j, big, float(flat[-2]) if flat.size > 1 else 0.0,
+                        float(out.max()) if out.size else 0.0))
         if not big > 1.0 + delta or nswaps >= maxswaps:
             break
         piv = B[i, j]

@@ -46,7 +46,7 @@ def test_each_swap_multiplies_the_volume_by_the_removed_coefficient():
     rows, nswaps, _, log = M.maxvol(C, rows0, 0.0, 50, trace=True)
     assert len(log) == nswaps + 1
     cur = list(rows0)
-    for i, j, big, _ in log[:-1]:
+    for i, j, big, _, _ in log[:-1]:
         before = abs(np.linalg.det(C[cur, :]))
         cur[j] = i
         after = abs(np.linalg.det(C[cur, :]))
