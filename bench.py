@@ -55,6 +55,8 @@ def parse():
                    help="grid sizes of the full-grid vs low-rank comparison")
     p.add_argument("--expsum", type=int, nargs="*", default=[1024, 16384],
                    help="grid sizes of the exponential-sum vs cross comparison")
+    p.add_argument("--maxvol", type=int, nargs="*", default=[16, 64],
+                   help="ranks k of the maxvol row selection timed at m = n (none: skip)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the untuned launch shapes (for profiler runs, whose per-launch overhead "
                         "would skew the tuner's timings)")
@@ -571,6 +573,33 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
                 row["expsum_terms"] = r0[3]
                 row["expsum_rank"] = int(r0[1].shape[0])
         results["expsum"].append(row)
+    # ---- maxvol row selection (the quasi-optimal pivots that Section 4.2
+    # cites): seeded Gaussian m x k with m = n, rows 0..k-1 to start,
+    # delta = 1e-2; one synchronous call, events around it.  Bytes: C read and
+    # B written by the coefficient kernel, B read and written by each swap.
+    results["maxvol"] = []
+    for kv in args.maxvol:
+        mv_m = args.n
+        Cm = lr.colmajor_empty(mv_m, kv)
+        Cm.copy_(torch.from_numpy(inputs.normal(41 + kv, mv_m * kv).reshape(kv, mv_m).T.copy()))
+        r0 = lr.lr_maxvol(h, Cm, list(range(kv)), 1e-2)
+        per = []
+        for i in range(3):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r0 = lr.lr_maxvol(h, Cm, list(range(kv)), 1e-2)
+            b.record(stream)
+            stream.synchronize()
+            per.append(a.elapsed_time(b))
+        ms = statistics.median(per)
+        byts = mv_m * kv * 8 * (2 + 2 * r0[1])
+        results["maxvol"].append({
+            "m": mv_m, "k": kv, "delta": 1e-2, "ms": round(ms, 4), "swaps": r0[1], "bmax": round(r0[2], 6),
+            "status": r0[3], "algorithmic_bytes": byts, "gbs": round(byts / (ms * 1e-3) / 1e9, 1),
+            "note": "one launch per swap over an L2-resident B, the record read between groups of 16 swaps: "
+                    "bound by launch and host round-trip latency, not by HBM"})
     # ---- the uneven batch: problems with n log-uniform in [512, 16384], r
     # uniform in 1..32 and random separable factors (seed 3), eps = 1e-6; one
     # batched call (one CUDA graph) in each precision against a loop of
@@ -970,6 +999,7 @@ def main():
         "crossover_full_grid_vs_lowrank": res["crossover"],
         "stokes_uzawa_lowrank": res["stokes"],
         "expsum_vs_cross": res["expsum"],
+        "maxvol": res.get("maxvol", []),
         "tucker3d": res["tucker"],
         "uneven_batch": res["uneven"],
         "batch_size_sweep": res.get("batch_sweep", []),

@@ -236,6 +236,35 @@ lr_status lr_batched_status(lr_handle h, int batch, lr_mat* sol, lr_status* per_
  * LR_ENOCONV if more than rmax columns were needed (result cut). */
 lr_status lr_truncate(lr_handle h, lr_mat* X, double eps, int rmax);
 
+/* Maxvol row selection (Section 4.2 names maxvol as the quasi-optimal way to
+ * choose the rows and columns of the cross; the algorithm is the cited one of
+ * Goreinov, Oseledets, Savostyanov, Tyrtyshnikov and Zamarashkin, 2010).
+ * float64 throughout.
+ *
+ * With B = C C[rows, :]^{-1} (the coefficients of every row of C in the basis
+ * of the selected rows; B[rows, :] is the identity), repeatedly take the
+ * largest |B[i, j]| (lowest column-major index j m + i on ties) and, while it
+ * exceeds 1 + delta, put row i in position j -- which multiplies
+ * |det C[rows, :]| by |B[i, j]| -- and update B by the rank-1 formula
+ * B' = B - B[:, j] (B[i, :] - e_j^T) / B[i, j].  On return C[rows, :] is a
+ * (1 + delta)-dominant submatrix unless maxswaps swaps ran out.  To refine
+ * the row pivots of a cross, pass any basis of its column space (the
+ * skeleton columns): B does not depend on the basis.
+ *
+ * C: device, m x k column-major, leading dimension ldc >= m, 1 <= k <= 64,
+ *    k <= m; read only.
+ * rows: host, k distinct indices in [0, m) with C[rows, :] nonsingular; on
+ *    return position j holds the row whose coefficient vector is e_j.
+ * nswaps, bmax (host, may be NULL): the swaps made and the final largest |B|.
+ * Runs on the handle's stream and returns after it has finished; scratch
+ * (m k + 4.2 K doubles) comes from the handle's workspace.
+ * Returns LR_EINVAL for bad arguments or a singular C[rows, :] (rows then
+ * unchanged), LR_ENONFINITE for a non-finite coefficient, LR_ENOCONV if
+ * maxswaps swaps were made and max |B| still exceeds 1 + delta (rows, nswaps
+ * and bmax hold the state reached), LR_ENOMEM, LR_ECUDA. */
+lr_status lr_maxvol(lr_handle h, const double* C, int m, int k, int ldc, double delta, int maxswaps,
+                    int* rows, int* nswaps, double* bmax);
+
 /* Details of the last lr_poisson2d on this handle.  pivots_I / pivots_J (host,
  * may be NULL) receive up to cap cross pivot indices (0-based). */
 lr_status lr_get_info(lr_handle h, lr_info* info, int* pivots_I, int* pivots_J, int cap);

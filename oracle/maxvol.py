@@ -68,9 +68,10 @@ def maxvol(C: np.ndarray, rows, delta: float, maxswaps: int, trace: bool = False
     while True:
         i, j, big = _largest(B)
         if trace:
-            flat = np.sort(np.abs(B).ravel())
-            out = np.delete(np.abs(B), rows, axis=0)
-            log.append((i, j, big, float(flat[-2]) if flat.size > 1 else 0.0,
+            absb = np.abs(B)
+            top2 = np.partition(absb.ravel(), -2)[-2:] if B.size > 1 else np.zeros(2)
+            out = np.delete(absb, rows, axis=0)
+            log.append((i, j, big, float(top2[0]),
                         float(out.max()) if out.size else 0.0))
         if not big > 1.0 + delta or nswaps >= maxswaps:
             break

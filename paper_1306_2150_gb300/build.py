@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrpoisson.so")
 SOURCES = ["dst.cu", "cross.cu", "core.cu", "api.cu", "noalloc.cu", "refine.cu", "stokes.cu", "tucker.cu",
-           "batch.cu"]
+           "batch.cu", "maxvol.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

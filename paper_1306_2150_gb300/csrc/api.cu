@@ -18,6 +18,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "lr_internal.h"
+#include "maxvol.h"
 
 using namespace lrp;
 
@@ -2856,6 +2857,71 @@ lr_status lr_autotune_batched(lr_handle h, int batch, const lr_mat* rhs, lr_mat*
     out->ms_best = best;
     out->ms_default = ms_def;
   }
+  return LR_OK;
+}
+
+lr_status lr_maxvol(lr_handle h, const double* C, int m, int k, int ldc, double delta, int maxswaps,
+                    int* rows, int* nswaps, double* bmax) {
+  NvtxRange nvtx_range("lr_maxvol");
+  if (!h) return LR_EINVAL;
+  if (!C || !rows) return fail(h, LR_EINVAL, "C and rows must be set");
+  if (k < 1 || k > MV_KMAX || m < k || ldc < m) return fail(h, LR_EINVAL, "need 1 <= k <= min(64, m), ldc >= m");
+  if (!(delta >= 0.0) || !(delta < 1e300)) return fail(h, LR_EINVAL, "delta must be finite and >= 0");
+  if (maxswaps < 0) return fail(h, LR_EINVAL, "maxswaps must be >= 0");
+  for (int j = 0; j < k; ++j) {
+    if (rows[j] < 0 || rows[j] >= m) return fail(h, LR_EINVAL, "rows must lie in [0, m)");
+    for (int l = 0; l < j; ++l)
+      if (rows[l] == rows[j]) return fail(h, LR_EINVAL, "rows must be distinct");
+  }
+  const int grid = maxvol_grid(m, h->num_sms);
+  const int ldb = round_up(m, 32);
+  auto layout = [&](Carve& cv, MvArgs& a) {
+    a.B = cv.take<double>(sizeof(double) * (size_t)ldb * k);
+    a.Ainv = cv.take<double>(sizeof(double) * MV_KMAX * MV_KMAX);
+    a.row = cv.take<double>(sizeof(double) * MV_KMAX);
+    a.pabs = cv.take<double>(sizeof(double) * grid);
+    a.pidx = cv.take<long long>(sizeof(long long) * grid);
+    a.rows = cv.take<int>(sizeof(int) * MV_KMAX);
+    a.st = cv.take<MvState>(sizeof(MvState));
+  };
+  MvArgs a{};
+  Carve c;
+  layout(c, a);
+  lr_status s = ensure_ws(h, c.off);
+  if (s != LR_OK) return s;
+  Carve c2;
+  c2.base = static_cast<char*>(h->ws);
+  layout(c2, a);
+  a.C = C;
+  a.ldc = ldc;
+  a.m = m;
+  a.k = k;
+  a.delta = delta;
+  a.maxswaps = maxswaps;
+  a.ldb = ldb;
+  a.grid = grid;
+  cudaStream_t stm = h->stream;
+  MvState hs{};
+  LR_CUDA(h, cudaMemsetAsync(a.st, 0, sizeof(MvState), stm), "maxvol state");
+  LR_CUDA(h, cudaMemcpyAsync(a.rows, rows, sizeof(int) * k, cudaMemcpyHostToDevice, stm), "maxvol rows in");
+  LR_CUDA(h, launch_maxvol_start(a, stm), "maxvol start");
+  // Swaps in groups of 16, the record read between groups; at most maxswaps
+  // swap launches in all (the decision after the last one stops).
+  for (int launched = 0;;) {
+    LR_CUDA(h, cudaMemcpyAsync(&hs, a.st, sizeof(MvState), cudaMemcpyDeviceToHost, stm), "maxvol state out");
+    LR_CUDA(h, cudaStreamSynchronize(stm), "maxvol");
+    if (hs.done || launched >= maxswaps) break;
+    const int g = maxswaps - launched < 16 ? maxswaps - launched : 16;
+    for (int q = 0; q < g; ++q) LR_CUDA(h, launch_maxvol_swap(a, stm), "maxvol swap");
+    launched += g;
+  }
+  LR_CUDA(h, cudaMemcpyAsync(rows, a.rows, sizeof(int) * k, cudaMemcpyDeviceToHost, stm), "maxvol rows out");
+  LR_CUDA(h, cudaStreamSynchronize(stm), "maxvol rows");
+  if (nswaps) *nswaps = hs.nswaps;
+  if (bmax) *bmax = hs.bmax;
+  if (hs.status & 1) return fail(h, LR_EINVAL, "C[rows, :] is singular or not finite");
+  if (hs.status & 2) return fail(h, LR_ENONFINITE, "non-finite coefficient in C C[rows, :]^-1");
+  if (!hs.done || hs.bmax > 1.0 + delta) return fail(h, LR_ENOCONV, "maxswaps swaps made, max |B| > 1 + delta");
   return LR_OK;
 }
 

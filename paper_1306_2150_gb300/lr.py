@@ -37,7 +37,7 @@ EXPORTS = ("lr_options_default", "lr_create", "lr_set_stream", "lr_destroy",
            "lr_truncate", "lr_get_info", "lr_get_phase_times", "lr_truncate_noalloc",
            "lr_poisson2d_batched", "lr_autotune", "lr_autotune_batched", "lr_poisson2d_full",
            "lr_stokes_uzawa", "lr_poisson2d_expsum", "lr_poisson3d_tucker", "lr_set_workspace_limit",
-           "lr_batched_status")
+           "lr_batched_status", "lr_maxvol")
 
 
 class LrMat(ctypes.Structure):
@@ -117,6 +117,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.lr_poisson2d.restype = c_int
     lib.lr_truncate.argtypes = [c_void_p, ctypes.POINTER(LrMat), c_double, c_int]
     lib.lr_truncate.restype = c_int
+    lib.lr_maxvol.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_double, c_int,
+                              ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_double)]
+    lib.lr_maxvol.restype = c_int
     lib.lr_get_info.argtypes = [c_void_p, ctypes.POINTER(LrInfo), ctypes.POINTER(c_int),
                                 ctypes.POINTER(c_int), c_int]
     lib.lr_get_info.restype = c_int
@@ -357,6 +360,24 @@ def lr_truncate(h: Handle, U, s, V, eps: float, rmax: int = 64):
         raise LrError(st, h.last_error())
     R = X.r
     return Uw[:n1, :R], sw[:R], Vw[:n2, :R], st
+
+
+def lr_maxvol(h: Handle, C, rows, delta: float = 1e-2, maxswaps: int | None = None):
+    """Maxvol row selection on C (CUDA float64, m x k, column-major) from the
+    starting rows ``rows``.  Returns (rows, nswaps, bmax, status); status is
+    LR_OK or LR_ENOCONV (swap cap reached), other statuses raise."""
+    C = as_colmajor(C)
+    m, k = C.shape
+    if maxswaps is None:
+        maxswaps = 16 * k
+    arr = (ctypes.c_int * k)(*[int(r) for r in rows])
+    ns = ctypes.c_int(0)
+    bm = ctypes.c_double(0.0)
+    st = load().lr_maxvol(h.ptr, C.data_ptr(), m, k, _ld(C), float(delta), int(maxswaps), arr,
+                          ctypes.byref(ns), ctypes.byref(bm))
+    if st not in (LR_OK, LR_ENOCONV):
+        raise LrError(st, h.last_error())
+    return list(arr), ns.value, bm.value, st
 
 
 def lr_get_phase_times(h: Handle) -> dict:
