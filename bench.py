@@ -598,7 +598,7 @@ def gpu_arm(args, rank: int, world: int) -> dict | None:
         results["maxvol"].append({
             "m": mv_m, "k": kv, "delta": 1e-2, "ms": round(ms, 4), "swaps": r0[1], "bmax": round(r0[2], 6),
             "status": r0[3], "algorithmic_bytes": byts, "gbs": round(byts / (ms * 1e-3) / 1e9, 1),
-            "note": "one launch per swap over an L2-resident B, the record read between groups of 16 swaps: "
+            "note": "one launch per swap over an L2-resident B, the record read between groups of 32 swaps: "
                     "bound by launch and host round-trip latency, not by HBM"})
     # ---- the uneven batch: problems with n log-uniform in [512, 16384], r
     # uniform in 1..32 and random separable factors (seed 3), eps = 1e-6; one

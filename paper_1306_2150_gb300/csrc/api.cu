@@ -2905,13 +2905,13 @@ lr_status lr_maxvol(lr_handle h, const double* C, int m, int k, int ldc, double 
   LR_CUDA(h, cudaMemsetAsync(a.st, 0, sizeof(MvState), stm), "maxvol state");
   LR_CUDA(h, cudaMemcpyAsync(a.rows, rows, sizeof(int) * k, cudaMemcpyHostToDevice, stm), "maxvol rows in");
   LR_CUDA(h, launch_maxvol_start(a, stm), "maxvol start");
-  // Swaps in groups of 16, the record read between groups; at most maxswaps
+  // Swaps in groups of 32, the record read between groups; at most maxswaps
   // swap launches in all (the decision after the last one stops).
   for (int launched = 0;;) {
     LR_CUDA(h, cudaMemcpyAsync(&hs, a.st, sizeof(MvState), cudaMemcpyDeviceToHost, stm), "maxvol state out");
     LR_CUDA(h, cudaStreamSynchronize(stm), "maxvol");
     if (hs.done || launched >= maxswaps) break;
-    const int g = maxswaps - launched < 16 ? maxswaps - launched : 16;
+    const int g = maxswaps - launched < 32 ? maxswaps - launched : 32;
     for (int q = 0; q < g; ++q) LR_CUDA(h, launch_maxvol_swap(a, stm), "maxvol swap");
     launched += g;
   }

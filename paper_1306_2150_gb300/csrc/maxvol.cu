@@ -16,13 +16,14 @@
 //   mv_coeff    grid-stride over rows: B[i, :] = C[i, :] C[I, :]^{-1}, the row of
 //               C in registers, the inverse in shared memory;
 //   mv_swap     grid-stride over rows: the rank-1 update, one thread per row
-//               (it reads B[i, j] before it rewrites the row); row i set to e_j.
+//               (it loads the whole row into registers, B[i, j] included,
+//               before it rewrites it); row i set to e_j.
 // mv_coeff and mv_swap end with the decision: per-CTA argmax of |B| to a
 // partial, then the last CTA to finish (a ticket counter: nobody waits)
 // reduces the partials, records the next swap or the stop, and copies the
 // pivot row B[i, :] for the next update.  The host launches swaps in groups
-// and reads the record between groups; a swap launched after the stop returns
-// at once.
+// of 32 and reads the record between groups; a swap launched after the stop
+// returns at once.
 #include <cfloat>
 #include <climits>
 
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_coeff_kernel(MvArgs a) {
   mv_decide(a, babs, bidx, nonfinite);
 }
 
+template <int KC>
 __global__ void __launch_bounds__(MV_THREADS) mv_swap_kernel(MvArgs a) {
   __shared__ double r[MV_KMAX];
   __shared__ int s_done, s_i, s_j;
@@ -243,12 +245,18 @@ __global__ void __launch_bounds__(MV_THREADS) mv_swap_kernel(MvArgs a) {
         mv_track(v, (long long)l * m + i, babs, bidx, nonfinite);
       }
     } else {
+      double b[KC];
+#pragma unroll
+      for (int l = 0; l < KC; ++l)
+        if (l < k) b[l] = bi[(size_t)l * a.ldb];
       const double f = bi[(size_t)js * a.ldb] / piv;
-      for (int l = 0; l < k; ++l) {
-        const double v = fma(-f, r[l], bi[(size_t)l * a.ldb]);
-        bi[(size_t)l * a.ldb] = v;
-        mv_track(v, (long long)l * m + i, babs, bidx, nonfinite);
-      }
+#pragma unroll
+      for (int l = 0; l < KC; ++l)
+        if (l < k) {
+          const double v = fma(-f, r[l], b[l]);
+          bi[(size_t)l * a.ldb] = v;
+          mv_track(v, (long long)l * m + i, babs, bidx, nonfinite);
+        }
     }
   }
   mv_decide(a, babs, bidx, nonfinite);
@@ -277,7 +285,11 @@ cudaError_t launch_maxvol_start(const MvArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_maxvol_swap(const MvArgs& a, cudaStream_t st) {
-  mv_swap_kernel<<<a.grid, MV_THREADS, 0, st>>>(a);
+  if (a.k < 1 || a.k > MV_KMAX || a.grid < 1) return cudaErrorInvalidValue;
+  if (a.k <= 8) mv_swap_kernel<8><<<a.grid, MV_THREADS, 0, st>>>(a);
+  else if (a.k <= 16) mv_swap_kernel<16><<<a.grid, MV_THREADS, 0, st>>>(a);
+  else if (a.k <= 32) mv_swap_kernel<32><<<a.grid, MV_THREADS, 0, st>>>(a);
+  else mv_swap_kernel<64><<<a.grid, MV_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ struct MvArgs {
 };
 
 constexpr int MV_KMAX = 64;
-constexpr int MV_THREADS = 256;
+constexpr int MV_THREADS = 128;
 
 int maxvol_grid(int m, int num_sms);
 // Inverse of C[rows, :] (Gauss-Jordan with partial pivoting), B = C C[rows, :]^{-1}
