@@ -37,10 +37,14 @@ __device__ __forceinline__ bool mv_better(double a_abs, long long a_idx, double 
   return a_abs > b_abs || (a_abs == b_abs && a_idx < b_idx);
 }
 
-__device__ __forceinline__ void mv_track(double v, long long idx, double& babs, long long& bidx, bool& nonfinite) {
-  const double a = fabs(v);
-  if (!(a <= DBL_MAX)) nonfinite = true;
-  else if (mv_better(a, idx, babs, bidx)) { babs = a; bidx = idx; }
+// Running argmax of |v| on the magnitude bits: for finite doubles the order of
+// |v| is the unsigned order of the bit pattern with the sign cleared, so the
+// per-element work stays off the (slow) float64 pipe.
+__device__ __forceinline__ void mv_track(double v, long long idx, unsigned long long& bbits, long long& bidx,
+                                         bool& nonfinite) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFULL;
+  if (a >= 0x7FF0000000000000ULL) nonfinite = true;
+  else if (a > bbits || (a == bbits && idx < bidx)) { bbits = a; bidx = idx; }
 }
 
 __device__ __forceinline__ void mv_warp_best(double& babs, long long& bidx) {
@@ -69,9 +73,12 @@ __device__ void mv_block_best(double& babs, long long& bidx) {
 }
 
 // The decision after B has been written: CTA partial, then the last CTA
-// reduces all partials and records the next swap or the stop.
-__device__ void mv_decide(const MvArgs& a, double babs, long long bidx, bool nonfinite) {
+// reduces all partials and records the next swap or the stop.  A thread that
+// saw no finite entry holds bbits = 0 with bidx = LLONG_MAX, which any real
+// entry beats.
+__device__ void mv_decide(const MvArgs& a, unsigned long long bbits, long long bidx, bool nonfinite) {
   __shared__ int s_last, s_go, s_i;
+  double babs = bidx == LLONG_MAX ? -1.0 : __longlong_as_double((long long)bbits);
   const bool bad = __syncthreads_or(nonfinite ? 1 : 0) != 0;
   mv_block_best(babs, bidx);
   if (threadIdx.x == 0) {
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_coeff_kernel(MvArgs a) {
   __syncthreads();
   if (s_done) return;
   const int k = a.k, m = a.m;
-  double babs = -1.0;
+  unsigned long long bbits = 0;
   long long bidx = LLONG_MAX;
   bool nonfinite = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_coeff_kernel(MvArgs a) {
       for (int l = 0; l < k; ++l) {
         const double v = l == sel ? 1.0 : 0.0;
         bi[(size_t)l * a.ldb] = v;
-        mv_track(v, (long long)l * m + i, babs, bidx, nonfinite);
+        mv_track(v, (long long)l * m + i, bbits, bidx, nonfinite);
       }
       continue;
     }
@@ -210,10 +217,10 @@ __global__ void __launch_bounds__(MV_THREADS) mv_coeff_kernel(MvArgs a) {
 #pragma unroll
       for (int p = 0; p < KC; ++p) acc = fma(cr[p], Ai[p * KC + l], acc);
       bi[(size_t)l * a.ldb] = acc;
-      mv_track(acc, (long long)l * m + i, babs, bidx, nonfinite);
+      mv_track(acc, (long long)l * m + i, bbits, bidx, nonfinite);
     }
   }
-  mv_decide(a, babs, bidx, nonfinite);
+  mv_decide(a, bbits, bidx, nonfinite);
 }
 
 template <int KC>
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_swap_kernel(MvArgs a) {
   const double piv = s_piv;
   for (int l = threadIdx.x; l < k; l += blockDim.x) r[l] = __ldcg(a.row + l) - (l == js ? 1.0 : 0.0);
   __syncthreads();
-  double babs = -1.0;
+  unsigned long long bbits = 0;
   long long bidx = LLONG_MAX;
   bool nonfinite = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(MV_THREADS) mv_swap_kernel(MvArgs a) {
       for (int l = 0; l < k; ++l) {
         const double v = l == js ? 1.0 : 0.0;
         bi[(size_t)l * a.ldb] = v;
-        mv_track(v, (long long)l * m + i, babs, bidx, nonfinite);
+        mv_track(v, (long long)l * m + i, bbits, bidx, nonfinite);
       }
     } else {
       double b[KC];
@@ -255,11 +262,11 @@ __global__ void __launch_bounds__(MV_THREADS) mv_swap_kernel(MvArgs a) {
         if (l < k) {
           const double v = fma(-f, r[l], b[l]);
           bi[(size_t)l * a.ldb] = v;
-          mv_track(v, (long long)l * m + i, babs, bidx, nonfinite);
+          mv_track(v, (long long)l * m + i, bbits, bidx, nonfinite);
         }
     }
   }
-  mv_decide(a, babs, bidx, nonfinite);
+  mv_decide(a, bbits, bidx, nonfinite);
 }
 
 }  // namespace
