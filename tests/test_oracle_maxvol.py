@@ -103,3 +103,76 @@ def test_swap_cap_and_argument_checks():
         M.maxvol(C, [0, 1, 2, 3, 3], 0.0, 10)
     with pytest.raises(ValueError):
         M.maxvol(C, [0, 1, 2, 3, 100], 0.0, 10)
+
+
+# ---- maxvol-refined pivots of the cross (restricted cross, alternating maxvol)
+from oracle import poisson_lowrank as O  # noqa: E402
+from paper_1306_2150_gb300 import inputs  # noqa: E402
+
+
+def _freq_problem(m, r, seed):
+    U, V = inputs.separable_random(m, r, seed)
+    a, b = O.symbol(m, "5pt")
+    Uh, Vh = O.dst1(U), O.dst1(V)
+    Xh = np.stack([O.freq_row(Uh, Vh, a, b, i) for i in range(m)])
+    return Uh, Vh, a, b, Xh
+
+
+def _skeleton(cr):
+    return (cr.C * cr.d) @ cr.R.T
+
+
+def test_restricted_cross_is_the_cur_interpolant():
+    Uh, Vh, a, b, Xh = _freq_problem(40, 5, 3)
+    rng = np.random.default_rng(4)
+    I = list(rng.choice(40, 6, replace=False))
+    J = list(rng.choice(40, 6, replace=False))
+    cr = M.restricted_cross(Uh, Vh, a, b, I, J)
+    S = _skeleton(cr)
+    cur = Xh[:, J] @ np.linalg.solve(Xh[np.ix_(I, J)], Xh[I, :])
+    assert np.linalg.norm(S - cur) <= 1e-9 * np.linalg.norm(cur)
+    assert np.allclose(S[I, :], Xh[I, :], rtol=0, atol=1e-12 * np.abs(Xh).max())
+    assert np.allclose(S[:, J], Xh[:, J], rtol=0, atol=1e-12 * np.abs(Xh).max())
+    assert sorted(cr.I) == sorted(I) and sorted(cr.J) == sorted(J)
+
+
+def test_restricted_cross_on_the_aca_pivots_gives_the_aca_skeleton():
+    Uh, Vh, a, b, Xh = _freq_problem(64, 6, 5)
+    aca = O.aca_cross(Uh, Vh, a, b, 1e-8, 64)
+    cr = M.restricted_cross(Uh, Vh, a, b, aca.I, aca.J)
+    S0, S1 = _skeleton(aca), _skeleton(cr)
+    assert np.linalg.norm(S1 - S0) <= 1e-9 * np.linalg.norm(S0)
+
+
+def test_restricted_cross_rejects_a_singular_block():
+    Uh, Vh, a, b, _ = _freq_problem(30, 4, 6)
+    Uh = Uh.copy()
+    Uh[7] = 0.0  # row 7 of Xh is zero
+    with pytest.raises(ValueError):
+        M.restricted_cross(Uh, Vh, a, b, [7, 1, 2], [0, 1, 2])
+
+
+def test_refined_pivots_are_dominant_both_ways():
+    Uh, Vh, a, b, Xh = _freq_problem(200, 6, 7)
+    aca = O.aca_cross(Uh, Vh, a, b, 1e-10, 64)
+    I, J, swaps, q = M.refine_pivots(Uh, Vh, a, b, aca.I, aca.J, 1e-2, 400, rounds=8)
+    assert q < 8  # the last round made no swap
+    assert np.abs(M.coefficients(Xh[:, J], I)).max() <= 1.01 + 1e-9
+    assert np.abs(M.coefficients(Xh[I, :].T, J)).max() <= 1.01 + 1e-9
+    v0 = abs(np.linalg.det(Xh[np.ix_(aca.I, aca.J)]))
+    assert abs(np.linalg.det(Xh[np.ix_(I, J)])) >= v0 * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("case", ["config0", "smooth1024"])
+def test_solve_with_refined_pivots(case):
+    if case == "config0":
+        U, V = inputs.separable_random(256, 8, 0)
+        eps = 1e-10
+    else:
+        U, V = inputs.smooth_sum(1024, 1e-6)
+        eps = 1e-6
+    Uo, so, Vo, _ = O.lr_poisson2d(U, V, "5pt", eps)
+    Um, sm, Vm, (cr, cr2, swaps, q) = M.lr_poisson2d_maxvol(U, V, "5pt", eps)
+    assert swaps > 0 and cr2.k == cr.k
+    assert len(sm) <= len(so)
+    assert O.rel_error_freq(Um, sm, Vm, U, V, "5pt") <= 10 * eps
