@@ -63,3 +63,5 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.lr_destroy(None) == lr.LR_EINVAL
     assert lib.lr_poisson2d(None, None, None, None) == lr.LR_EINVAL
     assert lib.lr_last_error(None) == b"null handle"
+    rows = (ctypes.c_int * 2)(0, 1)
+    assert lib.lr_maxvol(None, None, 4, 2, 4, 0.01, 8, rows, None, None) == lr.LR_EINVAL
